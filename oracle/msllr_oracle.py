@@ -1,0 +1,239 @@
+"""Plain FP64 restatement of the multi-scale low rank ADMM (Ong & Lustig).
+
+TEST INFRASTRUCTURE ONLY: imported by tests/, the smoke check and the
+benchmark's CPU baseline; never by the product path.  Every function follows
+one passage of the paper and is written for a reader checking it by eye, not
+for speed: no blocking, fusion or reordering beyond what the passage states.
+
+Notation (paper Sec. 2): Y is M x N, L scales, scale i has block size
+m_i x n_i, R_b extracts block b and R_b^T embeds it back, tau_i = lambda_i/rho.
+
+Readings of passages the paper leaves open (each one is also listed in the
+design notes):
+  * initial state Z_i = U_i = 0 (eq:admm gives none);
+  * Shift_s(X)[r, c] = X[(r + s_r) mod M, (c + s_c) mod N], circular, and one
+    shift s per iteration shared by every scale (Sec. 9);
+  * the shift sequence is drawn with splitmix64 (not given in the paper);
+  * SVT keeps max(sigma - tau, 0), so sigma == tau contributes nothing;
+  * the returned X_i is the X-update of eq:admm applied to the final (Z, U),
+    so that sum_i X_i = Y holds exactly (up to rounding);
+  * masked X-update (Sec. 10.4): the residual term is zero at unobserved
+    entries, and Y there is ignored.
+"""
+
+from __future__ import annotations
+
+import math
+
+import numpy as np
+
+_MASK64 = (1 << 64) - 1
+_GOLDEN_GAMMA = 0x9E3779B97F4A7C15
+
+
+# --------------------------------------------------------------------------
+# Random cycle-spin shifts (Sec. 9, "random cycle spinning").
+# --------------------------------------------------------------------------
+
+def splitmix64(x: int) -> int:
+    """The splitmix64 output function (Steele, Lea & Flood, OOPSLA 2014)
+    applied to the 64-bit state ``x``: two xor-shift-multiply rounds and a
+    final xor-shift."""
+    z = x & _MASK64
+    z = ((z ^ (z >> 30)) * 0xBF58476D1CE4E5B9) & _MASK64
+    z = ((z ^ (z >> 27)) * 0x94D049BB133111EB) & _MASK64
+    return z ^ (z >> 31)
+
+
+def shift_table(seed: int, iters: int, M: int, N: int) -> np.ndarray:
+    """Shift s_k = (s_r, s_c) for iterations k = 0..iters-1 (Sec. 9: "s is
+    randomly chosen from the set S", S = all circular shifts of an M x N
+    matrix).  State for iteration k is seed + (k+1)*golden_gamma, i.e. the
+    k-th splitmix64 draw from ``seed``; the high 32 bits pick the row shift
+    and the low 32 bits the column shift."""
+    out = np.zeros((iters, 2), dtype=np.int64)
+    for k in range(iters):
+        z = splitmix64((seed + (k + 1) * _GOLDEN_GAMMA) & _MASK64)
+        out[k, 0] = (z >> 32) % M
+        out[k, 1] = (z & 0xFFFFFFFF) % N
+    return out
+
+
+# --------------------------------------------------------------------------
+# Regularisation parameters (Sec. 4, eq:lambda).
+# --------------------------------------------------------------------------
+
+def lambda_default(M: int, N: int, m: int, n: int) -> float:
+    """eq:lambda as used in the experiments (Sec. 10):
+    lambda_i = sqrt(m_i) + sqrt(n_i) + sqrt(log(M N / max(m_i, n_i)))."""
+    return math.sqrt(m) + math.sqrt(n) + math.sqrt(math.log(M * N / max(m, n)))
+
+
+def lambda_area(M: int, N: int, m: int, n: int) -> float:
+    """Variant of eq:lambda with the block area inside the log,
+    sqrt(m) + sqrt(n) + sqrt(log(M N / (m n))), as the tiny 64x64 workload
+    specifies it."""
+    return math.sqrt(m) + math.sqrt(n) + math.sqrt(math.log(M * N / (m * n)))
+
+
+# --------------------------------------------------------------------------
+# Shift operators (Sec. 9).
+# --------------------------------------------------------------------------
+
+def shift(X: np.ndarray, s) -> np.ndarray:
+    """Shift_s(X)[r, c] = X[(r + s_r) mod M, (c + s_c) mod N]."""
+    M, N = X.shape
+    rows = (np.arange(M) + int(s[0])) % M
+    cols = (np.arange(N) + int(s[1])) % N
+    return X[np.ix_(rows, cols)]
+
+
+def unshift(X: np.ndarray, s) -> np.ndarray:
+    """Shift_{-s}, the inverse of ``shift``: out[(r+s_r) mod M, (c+s_c) mod N] = X[r, c]."""
+    M, N = X.shape
+    rows = (np.arange(M) + int(s[0])) % M
+    cols = (np.arange(N) + int(s[1])) % N
+    out = np.empty_like(X)
+    out[np.ix_(rows, cols)] = X
+    return out
+
+
+# --------------------------------------------------------------------------
+# Singular value thresholding (Sec. 7, eq:svt and eq:bsvt).
+# --------------------------------------------------------------------------
+
+def svt(B: np.ndarray, tau: float) -> np.ndarray:
+    """eq:svt: SVT_tau(B) = U max(Sigma - tau, 0) V^T from a full SVD."""
+    U, s, Vh = np.linalg.svd(B, full_matrices=False)
+    return (U * np.maximum(s - tau, 0.0)) @ Vh
+
+
+def soft_threshold(a: np.ndarray, tau: float) -> np.ndarray:
+    """The SVD of a 1x1 matrix [a] written out: sigma = |a|, u = sign(a),
+    v = 1, so SVT_tau([a]) = sign(a) max(|a| - tau, 0) -- the element-wise
+    soft threshold that eq:bsvt reduces to for 1x1 blocks (Sec. 7)."""
+    return np.sign(a) * np.maximum(np.abs(a) - tau, 0.0)
+
+
+def _blocks(A: np.ndarray, m: int, n: int) -> np.ndarray:
+    """R_b for every block b of the m x n partition (Sec. 2, Fig. Rop):
+    block (p, q) is A[p*m:(p+1)*m, q*n:(q+1)*n]; returns shape (nb, m, n)."""
+    M, N = A.shape
+    if M % m or N % n:
+        raise ValueError(f"block {m}x{n} does not divide {M}x{N}")
+    return A.reshape(M // m, m, N // n, n).transpose(0, 2, 1, 3).reshape(-1, m, n)
+
+
+def _unblocks(B: np.ndarray, M: int, N: int) -> np.ndarray:
+    """sum_b R_b^T(B_b): the adjoint of ``_blocks`` (blocks do not overlap)."""
+    nb, m, n = B.shape
+    return B.reshape(M // m, N // n, m, n).transpose(0, 2, 1, 3).reshape(M, N)
+
+
+def block_svt(A: np.ndarray, m: int, n: int, tau: float,
+              closed_form_1x1: bool = True) -> np.ndarray:
+    """eq:bsvt: BlockSVT_tau(A) = sum_b R_b^T(SVT_tau(R_b(A))).
+
+    Every block gets a full FP64 SVD (LAPACK gesdd through NumPy, batched over
+    the blocks of the scale).  For 1x1 blocks the 1x1 SVD is written out
+    (``soft_threshold``) unless ``closed_form_1x1`` is False."""
+    M, N = A.shape
+    if m == 1 and n == 1 and closed_form_1x1:
+        return soft_threshold(A, tau)
+    B = _blocks(A, m, n)
+    U, s, Vh = np.linalg.svd(B, full_matrices=False)
+    Zb = (U * np.maximum(s - tau, 0.0)[:, None, :]) @ Vh
+    return _unblocks(Zb, M, N)
+
+
+def block_nuclear_norm(X: np.ndarray, m: int, n: int) -> float:
+    """||X||_(i) = sum_b ||R_b(X)||_* (Sec. 3)."""
+    return float(np.linalg.svd(_blocks(X, m, n), compute_uv=False).sum())
+
+
+def block_dual_norm(X: np.ndarray, m: int, n: int) -> float:
+    """||X||*_(i) = max_b sigma_max(R_b(X)) (Sec. 3)."""
+    return float(np.linalg.svd(_blocks(X, m, n), compute_uv=False).max())
+
+
+# --------------------------------------------------------------------------
+# ADMM (Sec. 7, eq:admm), random cycle spinning (Sec. 9), masked
+# X-update (Sec. 10.4).
+# --------------------------------------------------------------------------
+
+def consensus_residual(Y, Z, U, mask=None):
+    """(1/L)(Y - sum_i (Z_i - U_i)), the data-consistency term of the
+    X-update in eq:admm; zero at unobserved entries (Sec. 10.4)."""
+    L = Z.shape[0]
+    R = (Y - (Z - U).sum(axis=0)) / L
+    if mask is not None:
+        R = np.where(mask, R, 0.0)
+    return R
+
+
+def x_update(Y, Z, U, mask=None):
+    """X_i <- (Z_i - U_i) + (1/L)(Y - sum_j (Z_j - U_j))   (eq:admm, line 1);
+    at unobserved entries X_i <- Z_i - U_i (Sec. 10.4)."""
+    return (Z - U) + consensus_residual(Y, Z, U, mask)[None]
+
+
+def admm_step(Y, Z, U, scales, taus, s, mask=None):
+    """One iteration of eq:admm with the Sec. 9 random-shift Z-update:
+        X_i <- (Z_i - U_i) + (1/L)(Y - sum_j (Z_j - U_j))
+        Z_i <- Shift_{-s}(BlockSVT_{tau_i}(Shift_s(X_i + U_i)))
+        U_i <- U_i - (Z_i - X_i)
+    ``s`` is one (s_r, s_c) pair shared by all scales, or an (L, 2) array
+    with one pair per scale.  Returns (X, Z_new, U_new)."""
+    X = x_update(Y, Z, U, mask)
+    s = np.asarray(s).reshape(-1, 2)
+    Znew = np.empty_like(Z)
+    for i, (m, n) in enumerate(scales):
+        si = s[i] if s.shape[0] > 1 else s[0]
+        Znew[i] = unshift(block_svt(shift(X[i] + U[i], si), m, n, taus[i]), si)
+    Unew = U - (Znew - X)
+    return X, Znew, Unew
+
+
+def admm(Y, scales, lambdas, rho=1.0, iters=100, shifts=None, mask=None,
+         Z0=None, U0=None, history=False):
+    """Solve eq:cvx (or its masked form, Sec. 10.4) by ``iters`` iterations of
+    eq:admm, starting from Z = U = 0 unless (Z0, U0) are given.
+
+    ``shifts``: None (no cycle spinning) or an array with one shift per
+    iteration, shape (iters, 2) or (iters, L, 2).
+    Returns a dict with X (the X-update applied to the final Z, U), Z, U and,
+    if ``history``, per-iteration objective sum_i lambda_i ||Z_i||_(i) and
+    primal residual ||X - Z||_F."""
+    Y = np.asarray(Y, dtype=np.float64)
+    L = len(scales)
+    M, N = Y.shape
+    if mask is not None:
+        mask = np.asarray(mask, dtype=bool)
+        Y = np.where(mask, Y, 0.0)
+    taus = [lam / rho for lam in lambdas]
+    Z = np.zeros((L, M, N)) if Z0 is None else np.array(Z0, dtype=np.float64)
+    U = np.zeros((L, M, N)) if U0 is None else np.array(U0, dtype=np.float64)
+    obj, pres = [], []
+    for k in range(iters):
+        s = (0, 0) if shifts is None else shifts[k]
+        X, Z, U = admm_step(Y, Z, U, scales, taus, s, mask)
+        if history:
+            obj.append(sum(lam * block_nuclear_norm(Z[i], *scales[i])
+                           for i, lam in enumerate(lambdas)))
+            pres.append(float(np.linalg.norm(X - Z)))
+    out = {"X": x_update(Y, Z, U, mask), "Z": Z, "U": U}
+    if history:
+        out["objective"] = np.array(obj)
+        out["primal_residual"] = np.array(pres)
+    return out
+
+
+def relerr(X, Xref, Y) -> np.ndarray:
+    """Per-component relative Frobenius error
+    ||X_i - Xref_i||_F / max(||Xref_i||_F, 1e-6 ||Y||_F)."""
+    X = np.asarray(X, dtype=np.float64)
+    Xref = np.asarray(Xref, dtype=np.float64)
+    floor = 1e-6 * np.linalg.norm(np.asarray(Y, dtype=np.float64))
+    num = np.linalg.norm((X - Xref).reshape(X.shape[0], -1), axis=1)
+    den = np.maximum(np.linalg.norm(Xref.reshape(Xref.shape[0], -1), axis=1), floor)
+    return num / den

@@ -1,0 +1,424 @@
+"""Pins of the FP64 oracle against what the paper and the mathematics fix.
+
+Nothing here compares the oracle with itself: every check uses a closed form,
+a brute-force search, a different LAPACK route (symmetric eigensolvers instead
+of the SVD), a constructed matrix with known factors, or an optimality
+certificate of the convex program (Sec. 5, Thm. opt).  The mutation tests at
+the end plant plausible mistakes in the oracle (on the CPU) and check that one
+of these pins catches each of them.
+"""
+
+import math
+import os
+
+import numpy as np
+import pytest
+
+import oracle as O
+from oracle import msllr_oracle as OM
+from paper_1507_08751_gb300 import synth
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _nuc_eigh(B):
+    """Nuclear norm through the eigenvalues of B^T B (not the SVD routine)."""
+    w = np.linalg.eigvalsh(B.T @ B)
+    return float(np.sqrt(np.maximum(w, 0.0)).sum())
+
+
+def _sv_eigh(B):
+    """Singular values, descending, through eigvalsh of the smaller Gram."""
+    G = B.T @ B if B.shape[0] >= B.shape[1] else B @ B.T
+    return np.sqrt(np.maximum(np.linalg.eigvalsh(G), 0.0))[::-1]
+
+
+# ---------------------------------------------------------------- shifts ----
+
+def test_splitmix64_published_sequence():
+    with open(os.path.join(GOLDEN, "splitmix64_seed0.txt")) as f:
+        want = [int(l, 16) for l in f if l.strip() and not l.startswith("#")]
+    gamma = 0x9E3779B97F4A7C15
+    got = [O.splitmix64(((k + 1) * gamma) & ((1 << 64) - 1)) for k in range(3)]
+    assert got == want
+
+
+def test_shift_table_range_and_uniformity():
+    M, N = 48, 40
+    t = O.shift_table(7, 20000, M, N)
+    assert t.shape == (20000, 2)
+    assert t[:, 0].min() >= 0 and t[:, 0].max() < M
+    assert t[:, 1].min() >= 0 and t[:, 1].max() < N
+    # chi-square of the row shifts against uniform over M cells
+    cnt = np.bincount(t[:, 0], minlength=M)
+    exp = len(t) / M
+    chi2 = ((cnt - exp) ** 2 / exp).sum()
+    assert chi2 < M + 6 * math.sqrt(2 * M)
+    assert not np.array_equal(t, O.shift_table(8, 20000, M, N))
+
+
+def test_shift_matches_definition_by_loops():
+    rng = np.random.default_rng(0)
+    X = rng.standard_normal((5, 7))
+    s = (3, 5)
+    S = O.shift(X, s)
+    for r in range(5):
+        for c in range(7):
+            assert S[r, c] == X[(r + 3) % 5, (c + 5) % 7]
+    assert np.array_equal(O.unshift(S, s), X)
+
+
+# ---------------------------------------------------------------- lambda ----
+
+@pytest.mark.parametrize("m,n", [(1, 1), (4, 4), (16, 16), (8, 32)])
+def test_lambda_tracks_gaussian_complexity(m, n):
+    """eq:gauss: lambda_i ~ E ||G||*_(i) up to a constant; Monte Carlo of the
+    block dual norm of a unit Gaussian matrix must sit within a factor 2."""
+    M, N = 64, 64
+    rng = np.random.default_rng(1)
+    vals = []
+    for _ in range(20):
+        G = rng.standard_normal((M, N))
+        B = G.reshape(M // m, m, N // n, n).transpose(0, 2, 1, 3).reshape(-1, m, n)
+        vals.append(max(_sv_eigh(b)[0] for b in B))
+    ratio = O.lambda_default(M, N, m, n) / np.mean(vals)
+    assert 0.5 < ratio < 2.0
+
+
+def test_lambda_endpoints_paper_text():
+    """Sec. 4: for 1x1 blocks the log term is log(MN); for the full M x N
+    block the first two terms are sqrt(M) + sqrt(N)."""
+    M, N = 1000, 300
+    assert O.lambda_default(M, N, 1, 1) == pytest.approx(2 + math.sqrt(math.log(M * N)))
+    full = O.lambda_default(M, N, M, N)
+    assert full - (math.sqrt(M) + math.sqrt(N)) == pytest.approx(math.sqrt(math.log(N)))
+
+
+# ------------------------------------------------------------------- SVT ----
+
+@pytest.mark.parametrize("shape", [(6, 6), (9, 4), (3, 11), (16, 16)])
+def test_svt_singular_values_closed_form(shape):
+    rng = np.random.default_rng(2)
+    B = rng.standard_normal(shape) * 3
+    sig = _sv_eigh(B)
+    tau = float(np.median(sig))
+    Z = O.svt(B, tau)
+    # compare squared singular values (eigenvalues of Z^T Z): the square root
+    # of a rounding-level eigenvalue would be ~1e-8
+    got2 = np.sort(np.linalg.eigvalsh(Z.T @ Z if Z.shape[0] >= Z.shape[1] else Z @ Z.T))[::-1]
+    np.testing.assert_allclose(got2, np.maximum(sig - tau, 0.0) ** 2, atol=1e-9 * sig[0] ** 2)
+    # Z lives in B's top-k left and right singular subspaces (eigh route)
+    k = int((sig > tau).sum())
+    wl, Ul = np.linalg.eigh(B @ B.T)
+    Pk = Ul[:, -k:] @ Ul[:, -k:].T
+    wr, Vr = np.linalg.eigh(B.T @ B)
+    Qk = Vr[:, -k:] @ Vr[:, -k:].T
+    np.testing.assert_allclose(Pk @ Z @ Qk, Z, atol=1e-9)
+
+
+def _nuc2x2(Z):
+    """sigma_1 + sigma_2 of a 2x2 matrix: sqrt(||Z||_F^2 + 2 |det Z|)."""
+    return math.sqrt((Z * Z).sum() + 2 * abs(np.linalg.det(Z)))
+
+
+@pytest.mark.parametrize("n", [2, 3])
+def test_svt_is_the_prox_brute_force(n):
+    """eq:svt is the prox of tau||.||_*: its objective is never beaten by
+    10^4 random perturbations (2x2 uses the closed-form nuclear norm)."""
+    rng = np.random.default_rng(3 + n)
+    nuc = _nuc2x2 if n == 2 else _nuc_eigh
+    for trial in range(5):
+        A = rng.standard_normal((n, n)) * 2
+        tau = 0.7 + 0.5 * trial
+        Z = O.svt(A, tau)
+        f0 = 0.5 * ((Z - A) ** 2).sum() + tau * nuc(Z)
+        for scale in (1e-1, 1e-3):
+            D = rng.standard_normal((2000, n, n)) * scale
+            f = [0.5 * ((Z + d - A) ** 2).sum() + tau * nuc(Z + d) for d in D]
+            assert min(f) >= f0 - 1e-12
+
+
+@pytest.mark.parametrize("n", [2, 3])
+def test_svt_subgradient_certificate(n):
+    """(A - Z)/tau lies in the subdifferential of ||.||_* at Z (Sec. 5.1):
+    it equals U1 V1^T + W with ||W|| <= 1 and W orthogonal to Z's row and
+    column spaces."""
+    rng = np.random.default_rng(11 + n)
+    for _ in range(10):
+        A = rng.standard_normal((n, n)) * 2
+        tau = 1.0
+        Z = O.svt(A, tau)
+        D = (A - Z) / tau
+        wr, Vr = np.linalg.eigh(Z.T @ Z)
+        k = int((_sv_eigh(A) > tau).sum())
+        if k == 0:
+            assert _sv_eigh(D)[0] <= 1 + 1e-9
+            continue
+        V1 = Vr[:, -k:]
+        # align signs: U1 = Z V1 / sigma
+        U1 = Z @ V1 / np.sqrt(wr[-k:])
+        W = D - U1 @ V1.T
+        assert _sv_eigh(W)[0] <= 1 + 1e-9
+        np.testing.assert_allclose(U1.T @ W, 0, atol=1e-9)
+        np.testing.assert_allclose(W @ V1, 0, atol=1e-9)
+
+
+def test_block_svt_1x1_is_scalar_prox_brute_force():
+    """eq:bsvt with 1x1 blocks is the element-wise soft threshold: compare
+    both oracle routes (written-out 1x1 SVD and batched LAPACK SVD) with a
+    dense grid minimisation of 0.5 (z - a)^2 + tau |z|."""
+    rng = np.random.default_rng(4)
+    A = rng.standard_normal((6, 5)) * 3
+    tau = 1.3
+    grid = np.linspace(-12, 12, 240001)
+    want = np.array([grid[np.argmin(0.5 * (grid - a) ** 2 + tau * np.abs(grid))] for a in A.ravel()])
+    for cf in (True, False):
+        got = O.block_svt(A, 1, 1, tau, closed_form_1x1=cf).ravel()
+        np.testing.assert_allclose(got, want, atol=2e-4)
+
+
+def test_block_svt_1xN_is_group_soft_threshold():
+    """Sec. 7: 1 x n blocks give the joint (group) soft threshold; check
+    against a numerical minimisation of 0.5||z - a||^2 + tau ||z||_2."""
+    from scipy.optimize import minimize
+    rng = np.random.default_rng(5)
+    A = rng.standard_normal((4, 6)) * 2
+    tau = 2.0
+    Z = O.block_svt(A, 1, 6, tau)
+    for r in range(4):
+        a = A[r]
+        res = minimize(lambda z: 0.5 * ((z - a) ** 2).sum() + tau * np.sqrt((z * z).sum() + 1e-30),
+                       np.zeros(6) + 0.01, method="Nelder-Mead",
+                       options={"xatol": 1e-10, "fatol": 1e-14, "maxiter": 40000, "maxfev": 40000})
+        np.testing.assert_allclose(Z[r], res.x, atol=1e-4)
+
+
+def test_block_svt_on_constructed_block_factors():
+    """A = sum_b R_b^T(U_b diag(s_b) V_b^T) with orthonormal U_b, V_b from QR:
+    BlockSVT must return sum_b R_b^T(U_b diag((s_b - tau)_+) V_b^T) -- a
+    closed form that needs no SVD.  Non-square blocks catch transposed
+    reshapes and swapped block indices."""
+    rng = np.random.default_rng(6)
+    M, N, m, n = 12, 20, 4, 5
+    tau = 1.5
+    A = np.zeros((M, N))
+    want = np.zeros((M, N))
+    Sv = []
+    for p in range(M // m):
+        for q in range(N // n):
+            U, _ = np.linalg.qr(rng.standard_normal((m, 3)))
+            V, _ = np.linalg.qr(rng.standard_normal((n, 3)))
+            s = rng.uniform(0, 4, 3)
+            Sv.append(s)
+            A[p * m:(p + 1) * m, q * n:(q + 1) * n] = (U * s) @ V.T
+            want[p * m:(p + 1) * m, q * n:(q + 1) * n] = (U * np.maximum(s - tau, 0)) @ V.T
+    np.testing.assert_allclose(O.block_svt(A, m, n, tau), want, atol=1e-12)
+    # block norms on the same construction (Sec. 3): known singular values
+    assert O.block_nuclear_norm(A, m, n) == pytest.approx(sum(s.sum() for s in Sv), rel=1e-10)
+    assert O.block_dual_norm(A, m, n) == pytest.approx(max(s.max() for s in Sv), rel=1e-10)
+
+
+def test_full_scale_is_plain_svt_and_permutation_equivariant():
+    """The M x N scale reduces to plain SVT (eigh route here), and SVT
+    commutes with row/column permutations -- so cycle-spinning the full scale
+    changes nothing (SVT(P A Q) = P SVT(A) Q)."""
+    rng = np.random.default_rng(7)
+    A = rng.standard_normal((10, 6)) * 2
+    tau = 2.0
+    w, V = np.linalg.eigh(A.T @ A)
+    sig = np.sqrt(np.maximum(w, 0))
+    f = np.where(sig > tau, 1 - tau / np.where(sig > 0, sig, 1), 0)
+    want = A @ (V * f) @ V.T
+    np.testing.assert_allclose(O.block_svt(A, 10, 6, tau), want, atol=1e-10)
+    s = (3, 4)
+    np.testing.assert_allclose(O.unshift(O.block_svt(O.shift(A, s), 10, 6, tau), s), want, atol=1e-10)
+
+
+def test_block_svt_grid_shift_equivariance():
+    """Shifting by whole blocks only permutes blocks."""
+    rng = np.random.default_rng(8)
+    A = rng.standard_normal((16, 24))
+    s = (8, 12)
+    lhs = O.block_svt(O.shift(A, s), 4, 6, 1.0)
+    rhs = O.shift(O.block_svt(A, 4, 6, 1.0), s)
+    np.testing.assert_allclose(lhs, rhs, atol=1e-12)
+
+
+# ------------------------------------------------------------------ ADMM ----
+
+def _hanning_solution(iters=1000, c=1.0):
+    Y, comps, scales = synth.hanning_blobs()
+    M, N = Y.shape
+    lam = [O.lambda_default(M, N, m, n) for m, n in scales]
+    out = O.admm(c * Y, scales, lam, 1.0, iters)
+    return Y * c, comps * c, scales, lam, out
+
+
+@pytest.fixture(scope="module")
+def hanning():
+    return _hanning_solution()
+
+
+def test_admm_kkt_certificate(hanning):
+    """Thm. opt (Sec. 5 appendix): at the optimum, rho U_i tends to one common
+    dual Q with ||Q||*_(i) <= lambda_i, <Q, X_i> = lambda_i ||X_i||_(i), and
+    the duality gap sum_i lambda_i ||X_i||_(i) - <Q, Y> vanishes."""
+    Y, comps, scales, lam, out = hanning
+    X, U = out["X"], out["U"]
+    Q = U.mean(axis=0)
+    assert np.abs(U - Q).max() < 1e-10
+    prim = 0.0
+    for i, (m, n) in enumerate(scales):
+        assert O.block_dual_norm(Q, m, n) <= lam[i] * (1 + 1e-8)
+        nuc = O.block_nuclear_norm(X[i], m, n)
+        assert np.sum(Q * X[i]) == pytest.approx(lam[i] * nuc, rel=1e-8, abs=1e-8)
+        prim += lam[i] * nuc
+    assert (prim - np.sum(Q * Y)) / prim < 1e-10
+
+
+def test_admm_exact_recovery(hanning):
+    """Fig. 1 / Thm. main: incoherent multi-scale Hanning blobs are separated
+    exactly into their scales."""
+    Y, comps, scales, lam, out = hanning
+    for i in range(len(scales)):
+        assert np.linalg.norm(out["X"][i] - comps[i]) <= 1e-8 * np.linalg.norm(comps[i])
+
+
+def test_admm_homogeneity(hanning):
+    """eq:cvx is positively homogeneous: the optimum for 3Y is 3x that for Y."""
+    Y3, comps3, scales, lam, out3 = _hanning_solution(c=3.0)
+    _, _, _, _, out1 = hanning
+    np.testing.assert_allclose(out3["X"], 3 * out1["X"], atol=1e-7)
+
+
+def test_admm_low_rank_plus_sparse_special_case():
+    """Sec. 2: scales {1x1, MxN} are low rank + sparse; the KKT gap closes."""
+    rng = np.random.default_rng(9)
+    M, N = 40, 30
+    Lr = rng.standard_normal((M, 2)) @ rng.standard_normal((N, 2)).T
+    S = (rng.random((M, N)) < 0.05) * rng.standard_normal((M, N)) * 5
+    Y = Lr + S
+    scales = [(1, 1), (M, N)]
+    lam = [O.lambda_default(M, N, m, n) for m, n in scales]
+    out = O.admm(Y, scales, lam, 1.0, 3000)
+    Q = out["U"].mean(axis=0)
+    assert np.abs(out["U"] - Q).max() < 1e-8
+    prim = sum(lam[i] * O.block_nuclear_norm(out["X"][i], *scales[i]) for i in range(2))
+    assert (prim - np.sum(Q * Y)) / prim < 1e-8
+    assert np.abs(Q).max() <= lam[0] * (1 + 1e-8)
+    np.testing.assert_allclose(out["X"][0], S, atol=1e-6)
+    np.testing.assert_allclose(out["X"][1], Lr, atol=1e-6)
+
+
+def test_admm_step_invariants_with_cycle_spinning():
+    """eq:admm with random shifts: after every X-update sum_i X_i = Y, and the
+    dual update satisfies U' = (X + U) - Z'.  Masked (Sec. 10.4): the sum
+    holds on observed entries and X_i = Z_i - U_i elsewhere."""
+    Y, comps, scales = synth.tiny_64()
+    M, N = Y.shape
+    lam = [O.lambda_area(M, N, m, n) for m, n in scales]
+    sh = O.shift_table(5, 30, M, N)
+    L = len(scales)
+    rng = np.random.default_rng(10)
+    mask = rng.random((M, N)) < 0.6
+    for msk in (None, mask):
+        Z = np.zeros((L, M, N))
+        U = np.zeros((L, M, N))
+        Ym = Y if msk is None else np.where(msk, Y, 0)
+        for k in range(30):
+            X, Zn, Un = O.admm_step(Ym, Z, U, scales, lam, sh[k], msk)
+            if msk is None:
+                np.testing.assert_allclose(X.sum(0), Y, atol=1e-10)
+            else:
+                np.testing.assert_allclose(X.sum(0)[msk], Y[msk], atol=1e-10)
+                np.testing.assert_allclose(X[:, ~msk], (Z - U)[:, ~msk], atol=1e-12)
+            np.testing.assert_allclose(Un, X + U - Zn, atol=1e-10)
+            Z, U = Zn, Un
+
+
+def test_admm_full_mask_equals_unmasked():
+    Y, comps, scales = synth.tiny_64()
+    M, N = Y.shape
+    lam = [O.lambda_area(M, N, m, n) for m, n in scales]
+    sh = O.shift_table(3, 20, M, N)
+    a = O.admm(Y, scales, lam, 1.0, 20, shifts=sh)
+    b = O.admm(Y, scales, lam, 1.0, 20, shifts=sh, mask=np.ones((M, N), bool))
+    np.testing.assert_array_equal(a["X"], b["X"])
+
+
+def test_objective_and_primal_residual_trend_down(hanning):
+    """ADMM is not monotone per iteration, and from Z = 0 the objective rises
+    towards the optimum; what must trend down is the distance of the
+    objective sum_i lambda_i ||Z_i||_(i) to the certified optimum and the
+    primal residual ||X - Z||_F: the max over the last 10% of iterations sits
+    well below the value at 10%."""
+    Y, comps, scales, lam, ref = hanning
+    opt = sum(lam[i] * O.block_nuclear_norm(ref["X"][i], *scales[i]) for i in range(len(scales)))
+    out = O.admm(Y, scales, lam, 1.0, 400, history=True)
+    gap = np.abs(out["objective"] - opt)
+    assert gap[-40:].max() < 1e-2 * gap[40]
+    pres = out["primal_residual"]
+    assert pres[-40:].max() < 1e-2 * pres[40]
+
+
+def test_relerr_floor():
+    """relerr uses max(||Xref_i||, 1e-6 ||Y||) so an all-zero component does
+    not divide by zero."""
+    Y = np.ones((4, 4))                      # ||Y||_F = 4
+    Xref = np.zeros((2, 4, 4))
+    Xref[1] = 2.0                            # ||Xref_1||_F = 8
+    X = Xref + 1e-9                          # ||dX_i||_F = 4e-9
+    r = O.relerr(X, Xref, Y)
+    assert r[0] == pytest.approx(4e-9 / 4e-6)
+    assert r[1] == pytest.approx(4e-9 / 8)
+
+
+# ------------------------------------------------------------- mutations ----
+
+def _mut_sign_u_update(Y, Z, U, scales, taus, s, mask=None):
+    X = OM.x_update(Y, Z, U, mask)
+    s = np.asarray(s).reshape(-1, 2)
+    Zn = np.empty_like(Z)
+    for i, (m, n) in enumerate(scales):
+        Zn[i] = OM.unshift(OM.block_svt(OM.shift(X[i] + U[i], s[0]), m, n, taus[i]), s[0])
+    return X, Zn, U + (Zn - X)          # planted: wrong sign
+
+
+def _mut_drop_u_in_prox(Y, Z, U, scales, taus, s, mask=None):
+    X = OM.x_update(Y, Z, U, mask)
+    s = np.asarray(s).reshape(-1, 2)
+    Zn = np.empty_like(Z)
+    for i, (m, n) in enumerate(scales):
+        Zn[i] = OM.unshift(OM.block_svt(OM.shift(X[i], s[0]), m, n, taus[i]), s[0])  # planted: dropped U
+    return X, Zn, U - (Zn - X)
+
+
+def test_planted_admm_mistakes_break_the_certificate(monkeypatch):
+    for bad in (_mut_sign_u_update, _mut_drop_u_in_prox):
+        monkeypatch.setattr(OM, "admm_step", bad)
+        Y, comps, scales = synth.hanning_blobs()
+        M, N = Y.shape
+        lam = [O.lambda_default(M, N, m, n) for m, n in scales]
+        with np.errstate(all="ignore"):
+            out = OM.admm(Y, scales, lam, 1.0, 300)
+        err = max(np.linalg.norm(out["X"][i] - comps[i]) / np.linalg.norm(comps[i]) for i in range(4))
+        assert not (err < 1e-3)
+
+
+def test_planted_transposed_unblock_is_caught(monkeypatch):
+    def bad_unblocks(B, M, N):
+        nb, m, n = B.shape
+        return B.reshape(N // n, M // m, m, n).transpose(1, 2, 0, 3).reshape(M, N)
+    monkeypatch.setattr(OM, "_unblocks", bad_unblocks)
+    with pytest.raises(AssertionError):
+        test_block_svt_on_constructed_block_factors()
+
+
+def test_planted_shift_direction_is_caught(monkeypatch):
+    def bad_shift(X, s):
+        M, N = X.shape
+        return X[np.ix_((np.arange(M) - s[0]) % M, (np.arange(N) - s[1]) % N)]
+    monkeypatch.setattr(OM, "shift", bad_shift)
+    monkeypatch.setattr(O, "shift", bad_shift)
+    with pytest.raises(AssertionError):
+        test_shift_matches_definition_by_loops()
