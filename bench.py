@@ -1,0 +1,356 @@
+#!/usr/bin/env python
+"""BlockSVT-ADMM benchmark: iterations/s of the multi-scale low rank
+decomposition on the surveillance-video-shaped workload (16384 x 256,
+scales 1x1 / 16x16 / 64x64 / 256x256 / full, 300 iterations per job).
+
+One "step" is one whole decomposition job: msllr_decompose of 300 random
+cycle-spun ADMM iterations (every hot-path kernel), inputs resident in HBM.
+value = iterations processed by all ranks / max-over-ranks time.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+--impl reference times the FP64 oracle (the CPU reference of this project)
+on the host cores on the same workload, one ADMM iteration per step.
+"""
+
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOAD = "video-16384x256-L5-s1_16_64_256_full"
+M_DEF, N_DEF, ITERS_DEF = 16384, 256, 300
+SEED = 1507087510
+METRIC = "BlockSVT-ADMM iter/s (video 16384x256, L=5, 300 iters/job)"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--iters", type=int, default=ITERS_DEF)
+    ap.add_argument("--M", type=int, default=M_DEF)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+# ---------------------------------------------------------------- clocks ----
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.idx = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.idx}", f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except OSError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+        out = {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": len(self.lines)}
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if sm:
+            out["sm_mhz"] = statistics.median(sm)
+            out["sm_max_mhz"] = max(mx)
+        out["reasons"] = sorted(reasons)
+        return out
+
+
+# ------------------------------------------------------------------ peaks ----
+
+def peaks():
+    p = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "src": "fallback"}
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        p.update(hbm_gbs=float(d["hbm_gbs"]), bf16_tflops=float(d["bf16_tflops"]), src="measured")
+        p["sm_max_mhz"] = float(d.get("sm_max_mhz", 2070.0))
+    except (OSError, KeyError, ValueError):
+        p["sm_max_mhz"] = 2070.0
+    # FP32 CUDA-core peak: 152 SMs x 128 FP32 lanes x 2 flop (FMA) x max SM clock
+    p["fp32_tflops"] = 152 * 128 * 2 * p["sm_max_mhz"] * 1e6 / 1e12
+    return p
+
+
+def kernel_roofline(stats, scales, M, N, pk):
+    """Roofline of the kernel kind x scale with the largest summed device time
+    (CUDA events around every launch of the profiled job)."""
+    MN = M * N
+    L = len(scales)
+    best = None
+    for kind, per_scale in stats["kernel_ms"].items():
+        for i, ms in enumerate(per_scale):
+            n = stats["kernel_launches"][kind][i]
+            if ms > 0 and n > 0 and (best is None or ms > best[2]):
+                best = (kind, i, ms, n)
+    if best is None:
+        return None, None
+    kind, i, ms, n = best
+    avg_s = ms / n / 1e3
+    m, nsz = scales[i]
+    mm, nn = max(m, nsz), min(m, nsz)
+    nblocks = (M // m) * (N // nsz)
+    if kind in ("gram",):
+        flops = nblocks * mm * nn * (nn + 1)  # lower triangle incl. diagonal, 2 flop per FMA
+        ach = flops / avg_s / 1e12
+        roof = {"bound": "alu", "achieved": round(ach, 3), "peak": round(pk["fp32_tflops"], 1),
+                "unit": "TFLOP/s", "frac": round(ach / pk["fp32_tflops"], 4), "traffic": None,
+                "peak_src": "152 SM x 128 FP32 lanes x 2 x max SM clock"}
+    elif kind == "eig_big":
+        flops = nblocks * (4 * nn ** 3 // 3)
+        ach = flops / avg_s / 1e12
+        roof = {"bound": "alu", "achieved": round(ach, 4), "peak": round(pk["fp32_tflops"], 1),
+                "unit": "TFLOP/s", "frac": round(ach / pk["fp32_tflops"], 5), "traffic": None,
+                "peak_src": "152 SM x 128 FP32 lanes x 2 x max SM clock"}
+    else:
+        per = {"consensus": (L + 2) * 4 * MN, "soft1x1": 16 * MN, "fused_small": 16 * MN,
+               "rebuild": 16 * MN, "gram_reduce": 0, "advance": 8, "misc": 8 * MN}[kind]
+        ach = per / avg_s / 1e9
+        roof = {"bound": "hbm", "achieved": round(ach, 1), "peak": pk["hbm_gbs"], "unit": "GB/s",
+                "frac": round(ach / pk["hbm_gbs"], 4), "traffic": None,
+                "peak_src": pk["src"]}
+    roof["kernel"] = f"{kind}[scale {i}: {m}x{nsz}]"
+    roof["avg_launch_us"] = round(avg_s * 1e6, 2)
+    total = sum(sum(v) for v in stats["kernel_ms"].values())
+    roof["time_share"] = round(ms / total, 4) if total else None
+    return roof, best
+
+
+# --------------------------------------------------------------- CPU legs ----
+
+CPU_SNIPPET = r"""
+import json, os, sys, time
+sys.path.insert(0, {root!r})
+import numpy as np
+import oracle as O
+from paper_1507_08751_gb300 import synth
+Y32, comps, scales = synth.video(M={M}, N=256)
+M, N = Y32.shape
+lam = [O.lambda_default(M, N, m, n) for m, n in scales]
+sh = O.shift_table({seed}, {n_it}, M, N)
+Y = Y32.astype(np.float64)
+L = len(scales)
+Z = np.zeros((L, M, N)); U = np.zeros((L, M, N))
+times = []
+for k in range({n_it}):
+    t0 = time.perf_counter()
+    X, Z, U = O.admm_step(Y, Z, U, scales, lam, sh[k])
+    times.append(time.perf_counter() - t0)
+print(json.dumps({{"times": times}}))
+"""
+
+
+def run_oracle_iters(M, n_it, threads):
+    env = dict(os.environ)
+    for v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+        env[v] = str(threads)
+    code = CPU_SNIPPET.format(root=ROOT, M=M, seed=SEED, n_it=n_it)
+    r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env,
+                       timeout=1800)
+    if r.returncode != 0:
+        raise RuntimeError(r.stderr[-2000:])
+    return json.loads(r.stdout.strip().splitlines()[-1])["times"]
+
+
+def cpu_baseline(M):
+    cores = os.cpu_count() or 1
+    times = run_oracle_iters(M, 3, cores)
+    t = sum(times[1:]) / max(1, len(times) - 1)
+    return {"value": round(1.0 / t, 4), "unit": "iter/s", "cores": cores, "kind": "oracle",
+            "sample": f"3 FP64 ADMM iterations of the {M}x256 video workload (first discarded), "
+                      f"numpy/LAPACK with {cores} BLAS threads"}
+
+
+def reference_arm(a):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    cores = os.cpu_count() or 1
+    times = run_oracle_iters(a.M, a.warmup + a.steps, cores)
+    timed = times[a.warmup:]
+    tot = sum(timed)
+    value = len(timed) / tot
+    line = {
+        "impl": "reference", "metric": METRIC, "value": round(value, 5), "unit": "iter/s",
+        "n_gpus": a.gpus, "steps": a.steps, "warmup": a.warmup,
+        "ms_per_step": round(1e3 * tot / len(timed), 2), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "M": a.M, "N": 256, "iters_per_job": a.iters,
+                   "step": "one ADMM iteration (FP64 oracle, host cores)"},
+        "cpu_baseline": {"value": round(value, 5), "unit": "iter/s", "cores": cores,
+                         "kind": "oracle", "sample": f"{a.steps} timed ADMM iterations"},
+        "e2e": {"value": round(value, 5), "unit": "iter/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+# -------------------------------------------------------------- our arm ----
+
+def ours(a):
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    from paper_1507_08751_gb300 import binding as B
+    from paper_1507_08751_gb300 import synth
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+
+    # per-rank independent job (replicas: the method has no cross-GPU step)
+    Y32, comps, scales = synth.video(seed=SEED + 1 + rank, M=a.M, N=256)
+    M, N = Y32.shape
+    L = len(scales)
+    stream = torch.cuda.Stream(device=dev)
+    ctx = B.Context(local, stream=stream.cuda_stream)
+    Yd = torch.from_numpy(Y32).to(dev)
+    X = torch.empty((L, M, N), dtype=torch.float32, device=dev)
+    torch.cuda.synchronize()
+
+    def step(params=None):
+        return ctx.msllr_decompose(Yd, scales, X, iters=a.iters, seed=SEED, params=params)
+
+    for _ in range(a.warmup):
+        stats = step()
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(0.3)
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(a.steps):
+        stats = step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    ck = clocks.stop()
+    t_s = e0.elapsed_time(e1) / 1e3
+    if world > 1:
+        tt = torch.tensor([t_s], device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        t_s = float(tt.item())
+    launches_per_step = stats["launches"]
+    value = world * a.iters * a.steps / t_s
+    nblocks = sum((M // m) * (N // n) for m, n in scales)
+
+    # profiled job: per-kernel CUDA events on the launching stream
+    p = B.msllr_params_default()
+    p.profile = 1
+    pstats = step(p)
+    pk = peaks()
+    roof, best = kernel_roofline(pstats, scales, M, N, pk)
+
+    # end to end through the host API: pinned host Y in, X out, copies timed
+    Yh = torch.from_numpy(Y32).pin_memory()
+    Xh = torch.empty((L, M, N), dtype=torch.float32).pin_memory()
+    ctx.msllr_decompose_host(Yh, scales, Xh, iters=a.iters, seed=SEED)
+    e_steps = max(1, min(a.steps, 3))
+    t0 = time.perf_counter()
+    for _ in range(e_steps):
+        ctx.msllr_decompose_host(Yh, scales, Xh, iters=a.iters, seed=SEED)
+    t_e2e = time.perf_counter() - t0
+    e2e = {"value": round(a.iters * e_steps / t_e2e, 2), "unit": "iter/s",
+           "h2d_bytes_per_step": 4 * M * N, "d2h_bytes_per_step": 4 * L * M * N,
+           "steps": e_steps}
+
+    cpu = None
+    if rank == 0 and world == 1 and not a.no_cpu_baseline:
+        try:
+            cpu = cpu_baseline(a.M)
+        except Exception as ex:  # noqa: BLE001
+            cpu = {"error": str(ex)[-300:]}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": round(value, 2), "unit": "iter/s", "n_gpus": world,
+            "steps": a.steps, "warmup": a.warmup,
+            "ms_per_step": round(1e3 * t_s / a.steps, 3), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "M": M, "N": N, "L": L,
+                       "scales": [f"{m}x{n}" for m, n in scales], "iters_per_job": a.iters,
+                       "parallelism": f"replicas{world}", "step": "one decomposition job",
+                       "l2": "ADMM state 11 x 16.8 MB = 185 MB > 126 MB L2"},
+            "blocks_per_s": round(value * nblocks, 1),
+            "e2e": e2e,
+            "gpu_launches": int(launches_per_step * a.steps),
+            "roofline": roof,
+            "kernel_ms_per_job": {k: [round(x, 3) for x in v] for k, v in pstats["kernel_ms"].items()
+                                  if any(v)},
+            "skipped_blocks_last_iter": stats["blocks_skipped"],
+            "zero_rank_blocks_last_iter": stats["blocks_zero"],
+            "clocks": ck,
+            "cpu_baseline": cpu,
+        }
+        print(json.dumps(line), flush=True)
+    ctx.close()
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def main():
+    a = parse()
+    if a.impl == "reference":
+        reference_arm(a)
+    else:
+        ours(a)
+
+
+if __name__ == "__main__":
+    main()

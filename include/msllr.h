@@ -1,0 +1,182 @@
+/*
+ * msllr.h -- C ABI of the GB300 multi-scale low rank decomposition library.
+ *
+ * Computes the multi-scale low rank decomposition of Ong & Lustig, "Beyond
+ * Low Rank + Sparse: Multi-scale Low Rank Matrix Decomposition": given an
+ * M x N matrix Y and a multi-scale block partition {m_i x n_i}, i = 1..L
+ * (Sec. 2), solve the convex program eq:cvx
+ *       minimise sum_i lambda_i ||X_i||_(i)   subject to   Y = sum_i X_i
+ * by the ADMM iteration eq:admm (Sec. 7), whose Z-update is the block-wise
+ * singular value threshold eq:bsvt applied under a random cycle-spin shift
+ * (Sec. 9), with the masked X-update of Sec. 10.4 when a mask is given.
+ *
+ * Conventions for every call:
+ *  - Matrices are float32, row-major.  "Device" pointers are CUDA device
+ *    memory of the context's device; "host" pointers are ordinary (pinned or
+ *    pageable) host memory.  The caller owns every buffer it passes; the
+ *    library never frees or retains them past the call.
+ *  - Work is ordered on the context's CUDA stream.  Calls are synchronous
+ *    with respect to the host unless stated otherwise: when they return
+ *    MSLLR_OK, every output has been written.
+ *  - Every call returns an msllr_status.  On any error nothing of the
+ *    outputs is guaranteed; msllr_last_error() gives a one-line message.
+ *    No C++ exception ever crosses this interface.
+ *  - A context is not thread-safe: one host thread at a time per context.
+ */
+#ifndef MSLLR_H
+#define MSLLR_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum msllr_status {
+  MSLLR_OK = 0,
+  MSLLR_EINVAL = 1,      /* bad shape, block size, parameter or pointer      */
+  MSLLR_ENOMEM = 2,      /* device allocation failed or HBM budget exceeded  */
+  MSLLR_ECUDA = 3,       /* a CUDA runtime call or kernel launch failed      */
+  MSLLR_ETIMEOUT = 4,    /* a bounded wait ran out                           */
+  MSLLR_ENONFINITE = 5,  /* Y holds a NaN or an infinity                     */
+  MSLLR_EBUSY = 6        /* the serving queue is full                        */
+} msllr_status;
+
+/* Largest number of scales per decomposition. */
+#define MSLLR_MAX_SCALES 8
+/* Kernel kinds reported in msllr_stats.kernel_ms / kernel_launches:
+ * 0 shift advance, 1 consensus residual, 2 1x1 soft threshold, 3 fused
+ * narrow-block SVT, 4 wide-block Gram tiles, 5 Gram partial-sum reduce,
+ * 6 wide-block eigen-solve, 7 wide-block rebuild, 8 set-up and output
+ * kernels (finiteness check, state init, X/U output). */
+#define MSLLR_KERNEL_KINDS 9
+
+/* Widest block (min(m_i, n_i)) the block-SVT kernels accept; the full-matrix
+ * scale obeys the same limit on min(M, N). */
+#define MSLLR_MAX_BLOCK_WIDTH 256
+
+typedef struct msllr_ctx msllr_ctx;
+
+/* Options of msllr_decompose.  Zero-initialise and call
+ * msllr_params_default() to get the defaults listed per field. */
+typedef struct msllr_params {
+  int skip_bound;    /* 1 (default): skip the eigen-solve of a block whose
+                        upper bound on sigma_max is <= tau (Sec. 8); exact,
+                        results do not change.  0: never skip.            */
+  int cycle_spin;    /* 1 (default): one random circular shift per
+                        iteration shared by all scales (Sec. 9).  0: none. */
+  int use_graph;     /* 1 (default): replay one captured CUDA graph per
+                        iteration.  0: plain launches.                      */
+  int iter_offset;   /* index of the first shift-table entry used (default
+                        0); lets a run continue another one exactly.       */
+  const float* Z_init; /* device, L x M x N, or NULL (default: zeros)       */
+  const float* U_init; /* device, L x M x N, or NULL (default: zeros)       */
+  float* U_out;        /* device, L x M x N, or NULL: final U_i             */
+  int profile;         /* 1: time every kernel with CUDA events on the
+                          context stream (plain launches, no graph) and
+                          report it in msllr_stats.kernel_ms.  Default 0.  */
+} msllr_params;
+
+/* Per-run diagnostics, all taken at the last iteration. */
+typedef struct msllr_stats {
+  int iters;                                  /* iterations run               */
+  int L;                                      /* scales                       */
+  double objective;                           /* sum_i lambda_i ||Z_i||_(i)   */
+  double primal_residual;                     /* ||X - Z||_F over all scales  */
+  double scale_nuclear[MSLLR_MAX_SCALES];     /* ||Z_i||_(i) per scale        */
+  long long blocks[MSLLR_MAX_SCALES];         /* blocks per scale             */
+  long long blocks_skipped[MSLLR_MAX_SCALES]; /* blocks the bound skipped     */
+  long long blocks_zero[MSLLR_MAX_SCALES];    /* blocks whose certified rank
+                                                 above tau was 0 (incl. skip) */
+  double lambda[MSLLR_MAX_SCALES];            /* lambda_i actually used       */
+  long long launches;                         /* kernels launched by the call */
+  /* per kernel kind (see MSLLR_KERNEL_KINDS) and scale (kinds 0, 1 and 8
+   * use scale slot 0): launches, and summed device time in ms when
+   * params->profile was set (else 0). */
+  long long kernel_launches[MSLLR_KERNEL_KINDS][MSLLR_MAX_SCALES];
+  double kernel_ms[MSLLR_KERNEL_KINDS][MSLLR_MAX_SCALES];
+} msllr_stats;
+
+/* Fill *p with the defaults.  Returns MSLLR_EINVAL if p is NULL. */
+int msllr_params_default(msllr_params* p);
+
+/* Create a context on CUDA device `device`.  `hbm_budget_bytes` caps the
+ * device memory the context may hold (0 = no cap).  `cuda_stream` is a
+ * cudaStream_t to order work on, or NULL for a stream the context creates.
+ * Errors: EINVAL (out == NULL, bad device), ECUDA. */
+int msllr_create(msllr_ctx** out, int device, size_t hbm_budget_bytes, void* cuda_stream);
+
+/* Destroy a context and free everything it holds.  NULL is accepted. */
+int msllr_destroy(msllr_ctx* ctx);
+
+/* Last error message of the context (or of the last context-less call when
+ * ctx is NULL).  Valid until the next call on the same context. */
+const char* msllr_last_error(const msllr_ctx* ctx);
+
+/* Shift table of the random cycle spinning (Sec. 9): for k = 0..iters-1,
+ * z = splitmix64(seed + (k+1) * 0x9E3779B97F4A7C15) and
+ *   out[2k] = (z >> 32) mod M,  out[2k+1] = (z & 0xffffffff) mod N.
+ * `out` is host memory of 2*iters int32.  Errors: EINVAL. */
+int msllr_shift_table(uint64_t seed, int iters, int M, int N, int32_t* out);
+
+/* Default regularisation eq:lambda (Sec. 4, as used in Sec. 10):
+ *   lambda = sqrt(m) + sqrt(n) + sqrt(log(M N / max(m, n))).
+ * Errors: EINVAL when the block does not fit in the matrix. */
+int msllr_lambda_default(int M, int N, int m, int n, double* out);
+
+/* One block-wise singular value threshold, eq:bsvt (Sec. 7), under the
+ * circular shift s = (shift_r, shift_c) of Sec. 9:
+ *     Z = Shift_{-s}( BlockSVT_tau( Shift_s(A) ) ),
+ * with Shift_s(A)[r, c] = A[(r + s_r) mod M, (c + s_c) mod N] and blocks of
+ * bm x bn on the shifted grid.  A and Z are device pointers, M x N with row
+ * stride `ld` (>= N) elements; A and Z must not overlap.  If
+ * `block_rank_out` is not NULL it receives, per block in row-major block
+ * order, the number of singular values above tau (device int32,
+ * (M/bm)*(N/bn) entries).  Errors: EINVAL (bm, bn do not divide M, N;
+ * min(bm, bn) > MSLLR_MAX_BLOCK_WIDTH; tau < 0), ECUDA. */
+int msllr_blocksvt(msllr_ctx* ctx, const float* A, float* Z, int M, int N, int ld,
+                   int bm, int bn, double tau, int shift_r, int shift_c,
+                   int* block_rank_out);
+
+/* Multi-scale low rank decomposition, eq:cvx by eq:admm (Sec. 7) with the
+ * random cycle-spin Z-update of Sec. 9:
+ *   X_i <- (Z_i - U_i) + (1/L)(Y - sum_j (Z_j - U_j))
+ *   Z_i <- Shift_{-s}(BlockSVT_{lambda_i/rho}(Shift_s(X_i + U_i)))
+ *   U_i <- U_i - (Z_i - X_i)
+ * starting from Z_i = U_i = 0 (or params->Z_init / U_init).
+ *  Y        device, M x N, row stride ld (>= N).
+ *  block_m, block_n   host arrays of L block sizes; each must divide M, N;
+ *           min(m_i, n_i) <= MSLLR_MAX_BLOCK_WIDTH.
+ *  lambda   host array of L values > 0, or NULL for msllr_lambda_default.
+ *  rho      > 0.
+ *  seed     seeds the shift table (msllr_shift_table).
+ *  mask     device uint8 M x N (row stride N), nonzero = observed, or NULL.
+ *           With a mask the X-update of Sec. 10.4 is used: the residual
+ *           term is zero at unobserved entries and Y there is ignored.
+ *  X_out    device, L x M x N (dense): the X-update of eq:admm applied to
+ *           the final (Z, U), so that sum_i X_i = Y on observed entries.
+ *  Z_out    device, L x M x N, or NULL.
+ *  stats    host, or NULL.
+ * Errors: EINVAL, ENOMEM (budget), ENONFINITE (Y has NaN/Inf), ECUDA. */
+int msllr_decompose(msllr_ctx* ctx, const float* Y, int M, int N, int ld,
+                    int L, const int* block_m, const int* block_n,
+                    const double* lambda, double rho, int iters, uint64_t seed,
+                    const uint8_t* mask, const msllr_params* params,
+                    float* X_out, float* Z_out, msllr_stats* stats);
+
+/* Same as msllr_decompose, but Y, mask, X_out and Z_out are HOST pointers:
+ * the library copies Y (and mask) to the device, runs, and copies the
+ * results back before returning.  params->Z_init / U_init / U_out must be
+ * NULL here. */
+int msllr_decompose_host(msllr_ctx* ctx, const float* Y, int M, int N, int ld,
+                         int L, const int* block_m, const int* block_n,
+                         const double* lambda, double rho, int iters, uint64_t seed,
+                         const uint8_t* mask, const msllr_params* params,
+                         float* X_out, float* Z_out, msllr_stats* stats);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* MSLLR_H */

@@ -1,0 +1,238 @@
+"""Thin Python binding of the msllr C ABI (include/msllr.h).
+
+Argument marshalling only: every step of the decomposition runs in the CUDA
+library libmsllr.so.  Device buffers are passed as torch CUDA tensors (their
+data pointers), host buffers as NumPy arrays.  If the library has not been
+built, importing works but every call raises ``MsllrError`` -- there is no
+CPU fallback.
+"""
+
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libmsllr.so")
+
+MSLLR_OK = 0
+MSLLR_EINVAL = 1
+MSLLR_ENOMEM = 2
+MSLLR_ECUDA = 3
+MSLLR_ETIMEOUT = 4
+MSLLR_ENONFINITE = 5
+MSLLR_EBUSY = 6
+MAX_SCALES = 8
+MAX_BLOCK_WIDTH = 256
+KERNEL_KINDS = ("advance", "consensus", "soft1x1", "fused_small", "gram", "gram_reduce",
+                "eig_big", "rebuild", "misc")
+
+STATUS_NAMES = {0: "MSLLR_OK", 1: "MSLLR_EINVAL", 2: "MSLLR_ENOMEM", 3: "MSLLR_ECUDA",
+                4: "MSLLR_ETIMEOUT", 5: "MSLLR_ENONFINITE", 6: "MSLLR_EBUSY"}
+
+# every symbol the header declares
+EXPORTS = (
+    "msllr_params_default", "msllr_create", "msllr_destroy", "msllr_last_error",
+    "msllr_shift_table", "msllr_lambda_default", "msllr_blocksvt", "msllr_decompose",
+    "msllr_decompose_host",
+)
+
+
+class MsllrError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"{STATUS_NAMES.get(code, code)}: {msg}")
+        self.code = code
+
+
+class Params(ctypes.Structure):
+    _fields_ = [
+        ("skip_bound", ctypes.c_int),
+        ("cycle_spin", ctypes.c_int),
+        ("use_graph", ctypes.c_int),
+        ("iter_offset", ctypes.c_int),
+        ("Z_init", ctypes.c_void_p),
+        ("U_init", ctypes.c_void_p),
+        ("U_out", ctypes.c_void_p),
+        ("profile", ctypes.c_int),
+    ]
+
+
+class Stats(ctypes.Structure):
+    _fields_ = [
+        ("iters", ctypes.c_int),
+        ("L", ctypes.c_int),
+        ("objective", ctypes.c_double),
+        ("primal_residual", ctypes.c_double),
+        ("scale_nuclear", ctypes.c_double * MAX_SCALES),
+        ("blocks", ctypes.c_longlong * MAX_SCALES),
+        ("blocks_skipped", ctypes.c_longlong * MAX_SCALES),
+        ("blocks_zero", ctypes.c_longlong * MAX_SCALES),
+        ("lambda_", ctypes.c_double * MAX_SCALES),
+        ("launches", ctypes.c_longlong),
+        ("kernel_launches", (ctypes.c_longlong * MAX_SCALES) * len(KERNEL_KINDS)),
+        ("kernel_ms", (ctypes.c_double * MAX_SCALES) * len(KERNEL_KINDS)),
+    ]
+
+    def to_dict(self):
+        L = self.L
+        return {
+            "iters": self.iters,
+            "L": L,
+            "objective": self.objective,
+            "primal_residual": self.primal_residual,
+            "scale_nuclear": list(self.scale_nuclear[:L]),
+            "blocks": list(self.blocks[:L]),
+            "blocks_skipped": list(self.blocks_skipped[:L]),
+            "blocks_zero": list(self.blocks_zero[:L]),
+            "lambda": list(self.lambda_[:L]),
+            "launches": self.launches,
+            "kernel_launches": {k: list(self.kernel_launches[i][:max(L, 1)])
+                                for i, k in enumerate(KERNEL_KINDS)},
+            "kernel_ms": {k: list(self.kernel_ms[i][:max(L, 1)]) for i, k in enumerate(KERNEL_KINDS)},
+        }
+
+
+_lib = None
+
+
+def lib():
+    """Load libmsllr.so (once).  Raises MsllrError if it is missing."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise MsllrError(MSLLR_ECUDA, f"{LIB_PATH} is not built; run __graft_entry__.build()")
+        L = ctypes.CDLL(LIB_PATH)
+        vp, ci, cd, cu64 = ctypes.c_void_p, ctypes.c_int, ctypes.c_double, ctypes.c_uint64
+        L.msllr_params_default.argtypes = [ctypes.POINTER(Params)]
+        L.msllr_create.argtypes = [ctypes.POINTER(vp), ci, ctypes.c_size_t, vp]
+        L.msllr_destroy.argtypes = [vp]
+        L.msllr_last_error.argtypes = [vp]
+        L.msllr_last_error.restype = ctypes.c_char_p
+        L.msllr_shift_table.argtypes = [cu64, ci, ci, ci, vp]
+        L.msllr_lambda_default.argtypes = [ci, ci, ci, ci, ctypes.POINTER(cd)]
+        L.msllr_blocksvt.argtypes = [vp, vp, vp, ci, ci, ci, ci, ci, cd, ci, ci, vp]
+        dec = [vp, vp, ci, ci, ci, ci, vp, vp, vp, cd, ci, cu64, vp, ctypes.POINTER(Params), vp, vp,
+               ctypes.POINTER(Stats)]
+        L.msllr_decompose.argtypes = dec
+        L.msllr_decompose_host.argtypes = dec
+        for name in EXPORTS:
+            getattr(L, name)
+        _lib = L
+    return _lib
+
+
+def _check(code, ctx=None):
+    if code != MSLLR_OK:
+        msg = lib().msllr_last_error(ctx)
+        raise MsllrError(code, msg.decode() if msg else "")
+
+
+def _ptr(t):
+    """Device pointer of a torch tensor, or None."""
+    if t is None:
+        return None
+    if not t.is_contiguous():
+        raise MsllrError(MSLLR_EINVAL, "tensor must be contiguous")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _int_array(v):
+    return (ctypes.c_int * len(v))(*[int(x) for x in v])
+
+
+def _double_array(v):
+    return None if v is None else (ctypes.c_double * len(v))(*[float(x) for x in v])
+
+
+def msllr_shift_table(seed, iters, M, N):
+    out = np.zeros((iters, 2), dtype=np.int32)
+    _check(lib().msllr_shift_table(ctypes.c_uint64(seed), iters, M, N,
+                                   out.ctypes.data_as(ctypes.c_void_p)))
+    return out
+
+
+def msllr_lambda_default(M, N, m, n):
+    v = ctypes.c_double()
+    _check(lib().msllr_lambda_default(M, N, m, n, ctypes.byref(v)))
+    return v.value
+
+
+def msllr_params_default():
+    p = Params()
+    _check(lib().msllr_params_default(ctypes.byref(p)))
+    return p
+
+
+class Context:
+    """One msllr context (msllr_create / msllr_destroy)."""
+
+    def __init__(self, device=0, hbm_budget_bytes=0, stream=None):
+        self._ctx = ctypes.c_void_p()
+        st = ctypes.c_void_p(stream) if stream else None
+        _check(lib().msllr_create(ctypes.byref(self._ctx), device, hbm_budget_bytes, st))
+
+    def close(self):
+        if self._ctx:
+            lib().msllr_destroy(self._ctx)
+            self._ctx = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    # -- calls ---------------------------------------------------------------
+    def msllr_blocksvt(self, A, Z, bm, bn, tau, shift=(0, 0), rank_out=None, N=None):
+        """Z <- Shift_{-s}(BlockSVT_tau(Shift_s(A))) on device tensors (float32, row-major).
+        The matrix is A[:, :N] (N defaults to A's width, which is then the row stride)."""
+        M, ld = A.shape[0], A.shape[1]
+        N = ld if N is None else N
+        _check(lib().msllr_blocksvt(self._ctx, _ptr(A), _ptr(Z), M, N, ld, bm, bn, float(tau),
+                                    int(shift[0]), int(shift[1]), _ptr(rank_out)), self._ctx)
+
+    def _decompose(self, fn, Yp, M, N, ld, scales, lambdas, rho, iters, seed, maskp, params, Xp,
+                   Zp):
+        L = len(scales)
+        bm = _int_array([s[0] for s in scales])
+        bn = _int_array([s[1] for s in scales])
+        lam = _double_array(lambdas)
+        p = params if params is not None else msllr_params_default()
+        st = Stats()
+        _check(fn(self._ctx, Yp, M, N, ld, L, bm, bn, lam, float(rho), int(iters),
+                  ctypes.c_uint64(seed), maskp, ctypes.byref(p), Xp, Zp, ctypes.byref(st)),
+               self._ctx)
+        return st.to_dict()
+
+    def msllr_decompose(self, Y, scales, X_out, lambdas=None, rho=1.0, iters=100, seed=0,
+                        mask=None, params=None, Z_out=None):
+        """Device-pointer decomposition: Y (M x N), X_out / Z_out (L x M x N) torch CUDA
+        float32 tensors, mask a torch CUDA uint8 tensor or None.  Returns the stats dict."""
+        M, N = Y.shape
+        return self._decompose(lib().msllr_decompose, _ptr(Y), M, N, N, scales, lambdas, rho,
+                               iters, seed, _ptr(mask), params, _ptr(X_out), _ptr(Z_out))
+
+    def msllr_decompose_host(self, Y, scales, X_out, lambdas=None, rho=1.0, iters=100, seed=0,
+                             mask=None, params=None, Z_out=None):
+        """Host-buffer decomposition: NumPy (or pinned torch CPU) arrays; copies happen
+        inside the call."""
+        def hp(a, dt):
+            if a is None:
+                return None
+            if hasattr(a, "data_ptr"):
+                return ctypes.c_void_p(a.data_ptr())
+            if a.dtype != dt or not a.flags["C_CONTIGUOUS"]:
+                raise MsllrError(MSLLR_EINVAL, f"host array must be contiguous {dt}")
+            return a.ctypes.data_as(ctypes.c_void_p)
+        M, N = Y.shape
+        return self._decompose(lib().msllr_decompose_host, hp(Y, np.float32), M, N, N, scales,
+                               lambdas, rho, iters, seed, hp(mask, np.uint8), params,
+                               hp(X_out, np.float32), hp(Z_out, np.float32))

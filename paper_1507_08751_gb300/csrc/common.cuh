@@ -1,0 +1,91 @@
+// Small device helpers shared by the msllr kernels: warp/CTA reductions and
+// the cycle-spin index map of Sec. 9.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace msllr {
+
+__device__ __forceinline__ float warp_sum(float v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+__device__ __forceinline__ float warp_max(float v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
+  return v;
+}
+
+__device__ __forceinline__ double warp_sum_d(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Sum over the CTA; every thread gets the total.  `red` is shared scratch of
+// at least NT/32 floats.  Contains two __syncthreads (all threads must call).
+template <int NT>
+__device__ __forceinline__ float block_sum(float v, float* red) {
+  v = warp_sum(v);
+  if constexpr (NT == 32) {
+    return v;
+  } else {
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    if (lane == 0) red[w] = v;
+    __syncthreads();
+    float t = 0.f;
+#pragma unroll
+    for (int i = 0; i < NT / 32; ++i) t += red[i];
+    __syncthreads();
+    return t;
+  }
+}
+
+template <int NT>
+__device__ __forceinline__ float block_max(float v, float* red) {
+  v = warp_max(v);
+  if constexpr (NT == 32) {
+    return v;
+  } else {
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    if (lane == 0) red[w] = v;
+    __syncthreads();
+    float t = red[0];
+#pragma unroll
+    for (int i = 1; i < NT / 32; ++i) t = fmaxf(t, red[i]);
+    __syncthreads();
+    return t;
+  }
+}
+
+// Geometry of one block of a scale on the cycle-spun grid (Sec. 9):
+// element (r, c) of shifted block (p, q) is A[(p*m + r + sr) mod M,
+// (q*n + c + sc) mod N].  `C` is the block as the eigen-solver sees it:
+// mm x nn with nn = min(m, n); for a wide block (m < n) C is its transpose,
+// since SVT(B^T) = SVT(B)^T.
+struct BlockGeom {
+  int M, N, ld;     // matrix shape and row stride (elements)
+  int m, n;         // block shape
+  int p, q;         // block coordinates on the shifted grid
+  int sr, sc;       // shift
+  __device__ __forceinline__ int mm() const { return m >= n ? m : n; }
+  __device__ __forceinline__ int nn() const { return m >= n ? n : m; }
+  __device__ __forceinline__ bool transposed() const { return m < n; }
+  // global element offset of block element (r, c), natural orientation
+  __device__ __forceinline__ size_t offset(int r, int c) const {
+    int gr = p * m + r + sr;
+    if (gr >= M) gr -= M;
+    int gc = q * n + c + sc;
+    if (gc >= N) gc -= N;
+    return (size_t)gr * ld + gc;
+  }
+  // index into the row-major mm x nn matrix C of block element (r, c)
+  __device__ __forceinline__ int cidx(int r, int c, int ldc) const {
+    return m >= n ? r * ldc + c : c * ldc + r;
+  }
+};
+
+}  // namespace msllr

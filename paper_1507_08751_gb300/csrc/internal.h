@@ -1,0 +1,115 @@
+// Internal interfaces between the host API (msllr_api.cu) and the kernel
+// translation units.  Not part of the public ABI.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stddef.h>
+#include <stdint.h>
+
+#include <vector>
+
+namespace msllr {
+
+// Block-SVT launch description for one scale (eq:bsvt under the Sec. 9
+// shift).  The prox input is A = A1 + A2 (A2 may be null); the kernels write
+// Z' = Shift_{-s}(BlockSVT_tau(Shift_s(A))) to Zout (which may alias A1) and,
+// if Wout is not null, W' = 2 Z' - A, the ADMM state Z' - U' with
+// U' = A - Z' (the dual update of eq:admm).
+struct ScaleLaunch {
+  const float* A1;
+  const float* A2;
+  float* Zout;
+  float* Wout;
+  int M, N, ld;            // matrix shape and row stride of A1, A2, Zout, Wout
+  int m, n;                // block shape
+  const int* shift;        // device int[2]: current (s_r, s_c)
+  float tau;
+  int skip_bound;
+  int* rank_out;           // device, one int per block, or null
+  double* nuc_acc;         // device, += sum over blocks of sum_j (sigma_j - tau)_+, or null
+  unsigned long long* cnt; // device [2]: blocks skipped by the bound, blocks of rank 0; or null
+};
+
+// Device workspace needed by the wide-block path for one scale.
+struct BigWorkspace {
+  float* G;      // nblocks * nn * nn
+  float* part;   // nblocks * chunks * ntiles * 64 * 64 (when chunks > 1)
+  float* Y;      // nblocks * nn * nn
+  int* k;        // nblocks
+};
+
+// Kernel kinds, for launch counting and per-kernel CUDA-event timing.
+enum KernelKind {
+  KK_ADVANCE = 0,
+  KK_CONSENSUS,
+  KK_SOFT1X1,
+  KK_FUSED,
+  KK_GRAM,
+  KK_GRAM_REDUCE,
+  KK_EIG,
+  KK_REBUILD,
+  KK_MISC,
+  KK_COUNT
+};
+
+// Launch counter and optional event timer.  With `timing` set, every kernel
+// is bracketed by two events on its own stream; the host sums the elapsed
+// times per (kind, scale) after the run.
+struct Prof {
+  bool timing = false;
+  int scale = 0;
+  long long launches[KK_COUNT][8] = {};
+  std::vector<cudaEvent_t> ev;
+  std::vector<int> tag;
+  size_t used = 0;
+  cudaError_t before(cudaStream_t st, int kind) {
+    launches[kind][scale]++;
+    if (!timing) return cudaSuccess;
+    if (2 * used + 2 > ev.size()) {
+      for (int i = 0; i < 256; ++i) {
+        cudaEvent_t e;
+        cudaError_t r = cudaEventCreate(&e);
+        if (r != cudaSuccess) return r;
+        ev.push_back(e);
+      }
+    }
+    tag.push_back(kind * 8 + scale);
+    return cudaEventRecord(ev[2 * used], st);
+  }
+  cudaError_t after(cudaStream_t st) {
+    if (!timing) return cudaSuccess;
+    cudaError_t r = cudaEventRecord(ev[2 * used + 1], st);
+    ++used;
+    return r;
+  }
+};
+
+// Path selection.
+enum class ScalePath { Elementwise, Small, Big };
+ScalePath choose_path(int m, int n);
+// Bytes of BigWorkspace a scale needs (0 for the other paths).
+size_t big_workspace_bytes(int M, int N, int m, int n);
+BigWorkspace carve_big_workspace(void* base, int M, int N, int m, int n);
+
+// Set kernel attributes (dynamic shared memory opt-in) on the current device.
+cudaError_t configure_kernels();
+
+// Launchers (all asynchronous on `st`).  Return cudaGetLastError().
+cudaError_t launch_scale(const ScaleLaunch& s, const BigWorkspace& ws, cudaStream_t st,
+                         Prof* prof);
+
+cudaError_t launch_consensus(const float* Y, const float* W, float* R, const uint8_t* mask,
+                             int L, size_t MN, cudaStream_t st, Prof* prof = nullptr);
+cudaError_t launch_finalize(const float* W, const float* Z, const float* R, float* X_out,
+                            float* U_out, double* pres_acc, int L, size_t MN, cudaStream_t st,
+                            Prof* prof = nullptr);
+cudaError_t launch_init_state(const float* Z0, const float* U0, float* Z, float* W, int L,
+                              size_t MN, cudaStream_t st, Prof* prof = nullptr);
+cudaError_t launch_advance(const int* table, int* iter, int* cur_shift, cudaStream_t st,
+                           Prof* prof = nullptr);
+cudaError_t launch_nonfinite(const float* Y, int M, int N, int ld, int* flag, cudaStream_t st,
+                             Prof* prof = nullptr);
+cudaError_t launch_copy_dense(const float* src, int M, int N, int ld, float* dst, cudaStream_t st,
+                              Prof* prof = nullptr);
+
+}  // namespace msllr

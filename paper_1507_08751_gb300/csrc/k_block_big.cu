@@ -1,0 +1,381 @@
+// Block SVT for wide blocks (64 < min(m, n) <= 256, or m*n > 8192), which
+// includes the full-matrix scale of eq:bsvt.  Three phases per scale:
+//   1. gram_tiles: G_b = C_b^T C_b for every block, tiled 64x64 over the
+//      lower triangle and split over row chunks (partial sums reduced in a
+//      fixed order, so results are deterministic);
+//   2. eig_big: one CTA per block -- skip bound (Sec. 8), certified rank and
+//      top eigenpairs of G_b (symeig.cuh), output V_b diag(sqrt(f));
+//   3. rebuild: Z'_b = (C_b V_f) V_f^T in row slabs, scattered through
+//      Shift_{-s}, with the fused dual update W' = 2 Z' - A of eq:admm.
+#include <math.h>
+
+#include "common.cuh"
+#include "internal.h"
+#include "symeig.cuh"
+
+namespace msllr {
+
+namespace {
+
+constexpr int kTile = 64;       // Gram tile
+constexpr int kChunk = 256;     // rows of C per Gram partial sum
+constexpr int kGramThreads = 256;
+constexpr int kEigThreads = 1024;
+constexpr int kEigMax = 256;
+constexpr int kRebThreads = 256;
+constexpr int kRebElems = 8192;  // rows-per-slab * nn
+constexpr int kKC = 16;          // eigenvectors per rebuild step
+
+struct BigDims {
+  int mm, nn, nblocks, nbn, T, ntiles, chunks;
+};
+
+BigDims big_dims(int M, int N, int m, int n) {
+  BigDims d;
+  d.mm = m >= n ? m : n;
+  d.nn = m >= n ? n : m;
+  d.nbn = N / n;
+  d.nblocks = (M / m) * (N / n);
+  d.T = (d.nn + kTile - 1) / kTile;
+  d.ntiles = d.T * (d.T + 1) / 2;
+  d.chunks = (d.mm + kChunk - 1) / kChunk;
+  return d;
+}
+
+__device__ __forceinline__ BlockGeom make_geom(const ScaleLaunch& a, int b) {
+  BlockGeom g;
+  g.M = a.M;
+  g.N = a.N;
+  g.ld = a.ld;
+  g.m = a.m;
+  g.n = a.n;
+  const int nbn = a.N / a.n;
+  g.p = b / nbn;
+  g.q = b - g.p * nbn;
+  const bool full = (a.m == a.M && a.n == a.N);
+  g.sr = (a.shift && !full) ? a.shift[0] : 0;
+  g.sc = (a.shift && !full) ? a.shift[1] : 0;
+  return g;
+}
+
+// element (i, c) of C (mm x nn) -> global offset
+__device__ __forceinline__ size_t c_offset(const BlockGeom& g, int i, int c) {
+  return g.transposed() ? g.offset(c, i) : g.offset(i, c);
+}
+
+__device__ __forceinline__ float load_a(const ScaleLaunch& a, size_t off) {
+  float v = a.A1[off];
+  if (a.A2) v += a.A2[off];
+  return v;
+}
+
+__global__ void __launch_bounds__(kGramThreads)
+gram_tiles_kernel(ScaleLaunch a, float* __restrict__ G, float* __restrict__ part, int chunks) {
+  __shared__ float As[32][kTile + 4];
+  __shared__ float Bs[32][kTile + 4];
+  const int t = blockIdx.x, chunk = blockIdx.y, b = blockIdx.z;
+  int ta = (int)((sqrtf(8.f * t + 1.f) - 1.f) * 0.5f);
+  while (((ta + 1) * (ta + 2)) / 2 <= t) ++ta;
+  while ((ta * (ta + 1)) / 2 > t) --ta;
+  const int tc = t - (ta * (ta + 1)) / 2;
+  const BlockGeom g = make_geom(a, b);
+  const int mm = g.mm(), nn = g.nn();
+  const int a0 = ta * kTile, c0 = tc * kTile;
+  const int r_begin = chunk * kChunk;
+  const int r_end = min(mm, r_begin + kChunk);
+  const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+  float acc[4][4];
+#pragma unroll
+  for (int x = 0; x < 4; ++x)
+#pragma unroll
+    for (int y = 0; y < 4; ++y) acc[x][y] = 0.f;
+  for (int r0 = r_begin; r0 < r_end; r0 += 32) {
+#pragma unroll
+    for (int j = 0; j < (32 * kTile) / kGramThreads; ++j) {
+      const int e = tid + j * kGramThreads;
+      const int rr = e / kTile, cc = e - rr * kTile;
+      const int i = r0 + rr;
+      float va = 0.f, vb = 0.f;
+      if (i < r_end) {
+        if (a0 + cc < nn) va = load_a(a, c_offset(g, i, a0 + cc));
+        if (c0 + cc < nn) vb = (ta == tc) ? va : load_a(a, c_offset(g, i, c0 + cc));
+      }
+      As[rr][cc] = va;
+      Bs[rr][cc] = vb;
+    }
+    __syncthreads();
+#pragma unroll 8
+    for (int rr = 0; rr < 32; ++rr) {
+      float av[4], bv[4];
+#pragma unroll
+      for (int x = 0; x < 4; ++x) av[x] = As[rr][ty * 4 + x];
+#pragma unroll
+      for (int y = 0; y < 4; ++y) bv[y] = Bs[rr][tx * 4 + y];
+#pragma unroll
+      for (int x = 0; x < 4; ++x)
+#pragma unroll
+        for (int y = 0; y < 4; ++y) acc[x][y] = fmaf(av[x], bv[y], acc[x][y]);
+    }
+    __syncthreads();
+  }
+  if (chunks == 1) {
+    float* Gb = G + (size_t)b * nn * nn;
+#pragma unroll
+    for (int x = 0; x < 4; ++x) {
+      const int i = a0 + ty * 4 + x;
+      if (i >= nn) continue;
+#pragma unroll
+      for (int y = 0; y < 4; ++y) {
+        const int j = c0 + tx * 4 + y;
+        if (j < nn) Gb[(size_t)i * nn + j] = acc[x][y];
+      }
+    }
+  } else {
+    const int ntiles = gridDim.x;
+    float* dst = part + (((size_t)b * chunks + chunk) * ntiles + t) * (kTile * kTile);
+#pragma unroll
+    for (int x = 0; x < 4; ++x)
+#pragma unroll
+      for (int y = 0; y < 4; ++y) dst[(ty * 4 + x) * kTile + tx * 4 + y] = acc[x][y];
+  }
+}
+
+__global__ void __launch_bounds__(256)
+gram_reduce_kernel(const float* __restrict__ part, float* __restrict__ G, int nn, int ntiles,
+                   int chunks) {
+  const int t = blockIdx.x, b = blockIdx.y;
+  int ta = (int)((sqrtf(8.f * t + 1.f) - 1.f) * 0.5f);
+  while (((ta + 1) * (ta + 2)) / 2 <= t) ++ta;
+  while ((ta * (ta + 1)) / 2 > t) --ta;
+  const int tc = t - (ta * (ta + 1)) / 2;
+  for (int e = threadIdx.x; e < kTile * kTile; e += blockDim.x) {
+    const int x = e / kTile, y = e - x * kTile;
+    const int i = ta * kTile + x, j = tc * kTile + y;
+    if (i >= nn || j >= nn) continue;
+    float s = 0.f;
+    for (int c = 0; c < chunks; ++c)
+      s += part[(((size_t)b * chunks + c) * ntiles + t) * (kTile * kTile) + e];
+    G[(size_t)b * nn * nn + (size_t)i * nn + j] = s;
+  }
+}
+
+size_t eig_smem_bytes(int nn) {
+  return sizeof(float) * ((size_t)nn * (nn + 1) / 2 + 9 * kEigMax + 4 * kEigThreads + 64);
+}
+
+__global__ void __launch_bounds__(kEigThreads)
+eig_big_kernel(ScaleLaunch a, const float* __restrict__ Gall, float* __restrict__ Yall,
+               int* __restrict__ kout) {
+  extern __shared__ float sm[];
+  constexpr int NT = kEigThreads, NMAX = kEigMax, NW = NT / 32;
+  const int b = blockIdx.x, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int nn = a.m >= a.n ? a.n : a.m;
+  const float* Gg = Gall + (size_t)b * nn * nn;
+  float* Y = Yall + (size_t)b * nn * nn;
+  float* Gp = sm;
+  float* scr = Gp + (nn * (nn + 1)) / 2;
+  EigScratch s;
+  s.d = scr;
+  s.e = s.d + NMAX;
+  s.e2 = s.e + NMAX;
+  s.beta = s.e2 + NMAX;
+  s.vbuf = s.beta + NMAX;
+  s.pbuf = s.vbuf + NMAX;
+  s.lam = s.pbuf + NMAX;
+  s.shf = s.lam + NMAX;
+  s.clus = reinterpret_cast<int*>(s.shf + NMAX);
+  s.lo = reinterpret_cast<float*>(s.clus + NMAX);
+  s.hi = s.lo + NT;
+  s.xs = s.hi + NT;
+  s.cnt = reinterpret_cast<int*>(s.xs + NT);
+  s.red = reinterpret_cast<float*>(s.cnt + NT);
+  LowerPacked Gacc{Gp};
+  for (int i = warp; i < nn; i += NW)
+    for (int j = lane; j <= i; j += 32) Gacc.at(i, j) = Gg[(size_t)i * nn + j];
+  __syncthreads();
+  const float thr = a.tau * a.tau;
+  bool skipped = false;
+  if (a.skip_bound) {
+    float tr = 0.f, rs = 0.f;
+    for (int i = tid; i < nn; i += NT) {
+      tr += Gacc.at(i, i);
+      float t = 0.f;
+      for (int j = 0; j <= i; ++j) t += fabsf(Gacc.at(i, j));
+      for (int j = i + 1; j < nn; ++j) t += fabsf(Gacc.at(j, i));
+      rs = fmaxf(rs, t);
+    }
+    tr = block_sum<NT>(tr, s.red);
+    rs = block_max<NT>(rs, s.red);
+    if (fminf(tr, rs) <= thr) skipped = true;
+  }
+  int k = 0;
+  if (!skipped) {
+    tridiagonalize<NT>(Gacc, nn, s);
+    float tn = 0.f;
+    k = top_eigenvalues<NT>(nn, thr, s, &tn);
+    if (k > 0) top_eigenvectors<NT, NMAX>(Gacc, nn, k, tn, s, Y, nn);
+  }
+  if (k > 0) {
+    // V_f = V diag(sqrt(f)), f = 1 - tau/sigma
+    for (int e = tid; e < nn * k; e += NT) {
+      const int i = e / k, q = e - i * k;
+      const float sig = sqrtf(s.lam[q]);
+      Y[(size_t)i * nn + q] *= sqrtf(fmaxf(1.f - a.tau / sig, 0.f));
+    }
+  }
+  if (tid == 0) {
+    kout[b] = k;
+    if (a.rank_out) a.rank_out[b] = k;
+    if (a.cnt) {
+      if (skipped) atomicAdd(a.cnt, 1ull);
+      if (k == 0) atomicAdd(a.cnt + 1, 1ull);
+    }
+    if (a.nuc_acc && k > 0) {
+      double t = 0.0;
+      for (int q = 0; q < k; ++q) t += (double)fmaxf(sqrtf(s.lam[q]) - a.tau, 0.f);
+      atomicAdd(a.nuc_acc, t);
+    }
+  }
+}
+
+// Z' = (C V_f) V_f^T for a slab of `rs` rows of C, W' = 2 Z' - A.
+__global__ void __launch_bounds__(kRebThreads)
+rebuild_kernel(ScaleLaunch a, const float* __restrict__ Yall, const int* __restrict__ kin,
+               int rs) {
+  extern __shared__ float sm[];
+  const int b = blockIdx.y, tid = threadIdx.x;
+  const BlockGeom g = make_geom(a, b);
+  const int mm = g.mm(), nn = g.nn();
+  const int r0 = blockIdx.x * rs;
+  const int rows = min(rs, mm - r0);
+  const int k = kin[b];
+  float* Cs = sm;                 // rows x nn
+  float* Vs = Cs + rs * nn;       // nn x kKC
+  float* Ps = Vs + nn * kKC;      // rows x kKC
+  const int nel = rows * nn;
+  for (int e = tid; e < nel; e += kRebThreads) {
+    const int i = e / nn, c = e - i * nn;
+    Cs[e] = load_a(a, c_offset(g, r0 + i, c));
+  }
+  __syncthreads();
+  constexpr int EL = kRebElems / kRebThreads;
+  float acc[EL];
+#pragma unroll
+  for (int t = 0; t < EL; ++t) acc[t] = 0.f;
+  const float* Yb = Yall + (size_t)b * nn * nn;
+  for (int q0 = 0; q0 < k; q0 += kKC) {
+    const int kc = min(kKC, k - q0);
+    for (int e = tid; e < nn * kKC; e += kRebThreads) {
+      const int i = e / kKC, j = e - i * kKC;
+      Vs[e] = j < kc ? Yb[(size_t)i * nn + q0 + j] : 0.f;
+    }
+    __syncthreads();
+    for (int e = tid; e < rows * kKC; e += kRebThreads) {
+      const int i = e / kKC, j = e - i * kKC;
+      float t = 0.f;
+      for (int c = 0; c < nn; ++c) t = fmaf(Cs[i * nn + c], Vs[c * kKC + j], t);
+      Ps[e] = t;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int t = 0; t < EL; ++t) {
+      const int e = tid + t * kRebThreads;
+      if (e < nel) {
+        const int i = e / nn, c = e - i * nn;
+        float z = acc[t];
+#pragma unroll
+        for (int j = 0; j < kKC; ++j) z = fmaf(Ps[i * kKC + j], Vs[c * kKC + j], z);
+        acc[t] = z;
+      }
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int t = 0; t < EL; ++t) {
+    const int e = tid + t * kRebThreads;
+    if (e < nel) {
+      const int i = e / nn, c = e - i * nn;
+      const size_t off = c_offset(g, r0 + i, c);
+      a.Zout[off] = acc[t];
+      if (a.Wout) a.Wout[off] = 2.f * acc[t] - Cs[e];
+    }
+  }
+}
+
+}  // namespace
+
+size_t big_workspace_bytes(int M, int N, int m, int n) {
+  if (choose_path(m, n) != ScalePath::Big) return 0;
+  const BigDims d = big_dims(M, N, m, n);
+  size_t bytes = 0;
+  bytes += sizeof(float) * (size_t)d.nblocks * d.nn * d.nn;  // G
+  if (d.chunks > 1) bytes += sizeof(float) * (size_t)d.nblocks * d.chunks * d.ntiles * kTile * kTile;
+  bytes += sizeof(float) * (size_t)d.nblocks * d.nn * d.nn;  // Y
+  bytes += sizeof(int) * (size_t)d.nblocks;
+  bytes += 4 * 256;  // alignment slack
+  return bytes;
+}
+
+static char* align256(char* p) {
+  return (char*)(((uintptr_t)p + 255) & ~(uintptr_t)255);
+}
+
+BigWorkspace carve_big_workspace(void* base, int M, int N, int m, int n) {
+  BigWorkspace w{};
+  if (!base || choose_path(m, n) != ScalePath::Big) return w;
+  const BigDims d = big_dims(M, N, m, n);
+  char* p = align256((char*)base);
+  w.G = (float*)p;
+  p = align256(p + sizeof(float) * (size_t)d.nblocks * d.nn * d.nn);
+  if (d.chunks > 1) {
+    w.part = (float*)p;
+    p = align256(p + sizeof(float) * (size_t)d.nblocks * d.chunks * d.ntiles * kTile * kTile);
+  }
+  w.Y = (float*)p;
+  p = align256(p + sizeof(float) * (size_t)d.nblocks * d.nn * d.nn);
+  w.k = (int*)p;
+  return w;
+}
+
+cudaError_t configure_big_kernels() {
+  cudaError_t e = cudaFuncSetAttribute(eig_big_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       200 * 1024);
+  if (e != cudaSuccess) return e;
+  return cudaFuncSetAttribute(rebuild_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              100 * 1024);
+}
+
+cudaError_t launch_big(const ScaleLaunch& s, const BigWorkspace& ws, cudaStream_t st, Prof* prof) {
+  const BigDims d = big_dims(s.M, s.N, s.m, s.n);
+  if (d.nn > kEigMax) return cudaErrorInvalidValue;
+#define PROF_BEFORE(kind) \
+  if (prof)               \
+    if (cudaError_t e_ = prof->before(st, kind)) return e_;
+#define PROF_AFTER() \
+  if (prof)          \
+    if (cudaError_t e_ = prof->after(st)) return e_;
+  PROF_BEFORE(KK_GRAM)
+  gram_tiles_kernel<<<dim3(d.ntiles, d.chunks, d.nblocks), kGramThreads, 0, st>>>(s, ws.G, ws.part,
+                                                                                  d.chunks);
+  PROF_AFTER()
+  if (d.chunks > 1) {
+    PROF_BEFORE(KK_GRAM_REDUCE)
+    gram_reduce_kernel<<<dim3(d.ntiles, d.nblocks), 256, 0, st>>>(ws.part, ws.G, d.nn, d.ntiles,
+                                                                  d.chunks);
+    PROF_AFTER()
+  }
+  PROF_BEFORE(KK_EIG)
+  eig_big_kernel<<<d.nblocks, kEigThreads, eig_smem_bytes(d.nn), st>>>(s, ws.G, ws.Y, ws.k);
+  PROF_AFTER()
+  const int rs = kRebElems / d.nn;
+  const int slabs = (d.mm + rs - 1) / rs;
+  const size_t smem = sizeof(float) * ((size_t)rs * d.nn + (size_t)d.nn * kKC + (size_t)rs * kKC);
+  PROF_BEFORE(KK_REBUILD)
+  rebuild_kernel<<<dim3(slabs, d.nblocks), kRebThreads, smem, st>>>(s, ws.Y, ws.k, rs);
+  PROF_AFTER()
+#undef PROF_BEFORE
+#undef PROF_AFTER
+  return cudaGetLastError();
+}
+
+}  // namespace msllr

@@ -1,0 +1,230 @@
+// Fused block SVT for narrow blocks (min(m, n) <= 64, m*n <= 8192): one CTA
+// per block does the whole of eq:bsvt for that block --
+//   gather R_b(Shift_s(A)) into shared memory (Sec. 9 circular shift),
+//   skip test on an upper bound of sigma_max (Sec. 8),
+//   Gram matrix, certified rank above tau and the top eigenpairs (symeig.cuh),
+//   rebuild C V diag(f) V^T, scatter through Shift_{-s}, and the fused dual
+//   update W' = 2 Z' - A of eq:admm.
+// Also holds the per-scale dispatcher.
+#include <math.h>
+
+#include "common.cuh"
+#include "internal.h"
+#include "symeig.cuh"
+
+namespace msllr {
+
+cudaError_t launch_soft1x1(const ScaleLaunch& s, cudaStream_t st, Prof* prof);
+cudaError_t launch_big(const ScaleLaunch& s, const BigWorkspace& ws, cudaStream_t st, Prof* prof);
+
+namespace {
+
+// row index i of packed lower-triangle position e (e = i(i+1)/2 + j, j <= i)
+__device__ __forceinline__ int tri_row(int e) {
+  int i = (int)((sqrtf(8.f * (float)e + 1.f) - 1.f) * 0.5f);
+  while (((i + 1) * (i + 2)) / 2 <= e) ++i;
+  while ((i * (i + 1)) / 2 > e) --i;
+  return i;
+}
+
+template <int NT, int NMAX>
+__global__ void __launch_bounds__(NT) blocksvt_small_kernel(ScaleLaunch a) {
+  extern __shared__ float sm[];
+  const int tid = threadIdx.x;
+  const int nbn = a.N / a.n;
+  BlockGeom g;
+  g.M = a.M;
+  g.N = a.N;
+  g.ld = a.ld;
+  g.m = a.m;
+  g.n = a.n;
+  g.p = blockIdx.x / nbn;
+  g.q = blockIdx.x - g.p * nbn;
+  const bool full = (a.m == a.M && a.n == a.N);  // SVT commutes with permutations
+  g.sr = (a.shift && !full) ? a.shift[0] : 0;
+  g.sc = (a.shift && !full) ? a.shift[1] : 0;
+  const int mm = g.mm(), nn = g.nn();
+  const int ldc = nn, ldg = nn + 1, ldy = nn;
+
+  float* C = sm;
+  float* G = C + mm * nn;
+  float* Y = G + nn * ldg;
+  float* P = Y + nn * nn;
+  float* scr = P + mm * nn;
+  EigScratch s;
+  s.d = scr;
+  s.e = s.d + NMAX;
+  s.e2 = s.e + NMAX;
+  s.beta = s.e2 + NMAX;
+  s.vbuf = s.beta + NMAX;
+  s.pbuf = s.vbuf + NMAX;
+  s.lam = s.pbuf + NMAX;
+  s.shf = s.lam + NMAX;
+  s.clus = reinterpret_cast<int*>(s.shf + NMAX);
+  s.lo = reinterpret_cast<float*>(s.clus + NMAX);
+  s.hi = s.lo + NT;
+  s.xs = s.hi + NT;
+  s.cnt = reinterpret_cast<int*>(s.xs + NT);
+  s.red = reinterpret_cast<float*>(s.cnt + NT);
+
+  // gather A = A1 + A2 on the shifted grid; ||C||_F^2
+  const int melem = a.m * a.n;
+  float fro = 0.f;
+  for (int e = tid; e < melem; e += NT) {
+    const int r = e / a.n, c = e - r * a.n;
+    const size_t off = g.offset(r, c);
+    float v = a.A1[off];
+    if (a.A2) v += a.A2[off];
+    C[g.cidx(r, c, ldc)] = v;
+    fro = fmaf(v, v, fro);
+  }
+  fro = block_sum<NT>(fro, s.red);
+  if constexpr (NT == 32) __syncwarp();
+  const float thr = a.tau * a.tau;
+  int k = 0;
+  bool skipped = false;
+  if (a.skip_bound && fro <= thr) skipped = true;
+  if (!skipped) {
+    const int ntri = nn * (nn + 1) / 2;
+    for (int e = tid; e < ntri; e += NT) {
+      const int i = tri_row(e), j = e - (i * (i + 1)) / 2;
+      float acc = 0.f;
+      for (int r = 0; r < mm; ++r) acc = fmaf(C[r * ldc + i], C[r * ldc + j], acc);
+      G[i * ldg + j] = acc;
+    }
+    __syncthreads();
+    if (a.skip_bound) {
+      // Gershgorin: sigma_max^2 = lambda_max(G) <= max_i sum_j |G_ij|
+      float rs = 0.f;
+      for (int i = tid; i < nn; i += NT) {
+        float t = 0.f;
+        for (int j = 0; j <= i; ++j) t += fabsf(G[i * ldg + j]);
+        for (int j = i + 1; j < nn; ++j) t += fabsf(G[j * ldg + i]);
+        rs = fmaxf(rs, t);
+      }
+      rs = block_max<NT>(rs, s.red);
+      if constexpr (NT == 32) __syncwarp();
+      if (rs <= thr) skipped = true;
+    }
+  }
+  if (!skipped) {
+    LowerFull Gacc{G, ldg};
+    tridiagonalize<NT>(Gacc, nn, s);
+    float tn = 0.f;
+    k = top_eigenvalues<NT>(nn, thr, s, &tn);
+    if (k > 0) top_eigenvectors<NT, NMAX>(Gacc, nn, k, tn, s, Y, ldy);
+  }
+  const bool transposed = g.transposed();
+  if (k == 0) {
+    for (int e = tid; e < melem; e += NT) {
+      const int r = e / a.n, c = e - r * a.n;
+      const size_t off = g.offset(r, c);
+      a.Zout[off] = 0.f;
+      if (a.Wout) a.Wout[off] = -C[g.cidx(r, c, ldc)];
+    }
+    if (tid == 0) {
+      if (a.rank_out) a.rank_out[blockIdx.x] = 0;
+      if (a.cnt) {
+        if (skipped) atomicAdd(a.cnt, 1ull);
+        atomicAdd(a.cnt + 1, 1ull);
+      }
+    }
+    return;
+  }
+  // f_j = 1 - tau / sigma_j for the k eigenpairs above the threshold
+  if (tid < k) {
+    const float sig = sqrtf(s.lam[tid]);
+    s.xs[tid] = fmaxf(1.f - a.tau / sig, 0.f);
+    s.lo[tid] = fmaxf(sig - a.tau, 0.f);
+  }
+  __syncthreads();
+  // P = C V diag(f)   (mm x k, row stride nn)
+  for (int e = tid; e < mm * k; e += NT) {
+    const int i = e / k, q = e - i * k;
+    float acc = 0.f;
+    for (int c = 0; c < nn; ++c) acc = fmaf(C[i * ldc + c], Y[c * ldy + q], acc);
+    P[i * nn + q] = acc * s.xs[q];
+  }
+  __syncthreads();
+  // Z' = P V^T, scattered through Shift_{-s}; W' = 2 Z' - A
+  for (int e = tid; e < melem; e += NT) {
+    const int r = e / a.n, c = e - r * a.n;
+    const int i = transposed ? c : r, col = transposed ? r : c;
+    float z = 0.f;
+    for (int q = 0; q < k; ++q) z = fmaf(P[i * nn + q], Y[col * ldy + q], z);
+    const size_t off = g.offset(r, c);
+    a.Zout[off] = z;
+    if (a.Wout) a.Wout[off] = 2.f * z - C[i * ldc + col];
+  }
+  if (tid == 0) {
+    if (a.rank_out) a.rank_out[blockIdx.x] = k;
+    if (a.nuc_acc) {
+      double t = 0.0;
+      for (int q = 0; q < k; ++q) t += (double)s.lo[q];
+      atomicAdd(a.nuc_acc, t);
+    }
+  }
+}
+
+template <int NT, int NMAX>
+size_t small_smem_bytes(int mm, int nn) {
+  return sizeof(float) * ((size_t)2 * mm * nn + (size_t)nn * (2 * nn + 1) + 9 * NMAX + 4 * NT + 64);
+}
+
+template <int NT, int NMAX>
+cudaError_t launch_small_t(const ScaleLaunch& s, cudaStream_t st, Prof* prof) {
+  const int mm = s.m >= s.n ? s.m : s.n, nn = s.m >= s.n ? s.n : s.m;
+  const size_t smem = small_smem_bytes<NT, NMAX>(mm, nn);
+  const int nblocks = (s.M / s.m) * (s.N / s.n);
+  if (prof) if (cudaError_t e = prof->before(st, KK_FUSED)) return e;
+  blocksvt_small_kernel<NT, NMAX><<<nblocks, NT, smem, st>>>(s);
+  if (prof) if (cudaError_t e = prof->after(st)) return e;
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t configure_big_kernels();
+
+// Opt the kernels into more than 48 KB of dynamic shared memory.  Called once
+// per device from msllr_create, outside any stream capture.
+cudaError_t configure_kernels() {
+  cudaError_t e;
+  e = cudaFuncSetAttribute(blocksvt_small_kernel<32, 16>,
+                           cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+  if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(blocksvt_small_kernel<64, 32>,
+                           cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+  if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(blocksvt_small_kernel<128, 64>,
+                           cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+  if (e != cudaSuccess) return e;
+  return configure_big_kernels();
+}
+
+ScalePath choose_path(int m, int n) {
+  if (m == 1 && n == 1) return ScalePath::Elementwise;
+  const int nn = m < n ? m : n;
+  const long long area = (long long)m * n;
+  if (nn <= 64 && area <= 8192) return ScalePath::Small;
+  return ScalePath::Big;
+}
+
+cudaError_t launch_scale(const ScaleLaunch& s, const BigWorkspace& ws, cudaStream_t st,
+                         Prof* prof) {
+  switch (choose_path(s.m, s.n)) {
+    case ScalePath::Elementwise:
+      return launch_soft1x1(s, st, prof);
+    case ScalePath::Small: {
+      const int nn = s.m < s.n ? s.m : s.n;
+      if (nn <= 16) return launch_small_t<32, 16>(s, st, prof);
+      if (nn <= 32) return launch_small_t<64, 32>(s, st, prof);
+      return launch_small_t<128, 64>(s, st, prof);
+    }
+    case ScalePath::Big:
+    default:
+      return launch_big(s, ws, st, prof);
+  }
+}
+
+}  // namespace msllr

@@ -1,0 +1,305 @@
+// Element-wise kernels of the ADMM (eq:admm, Sec. 7): the consensus
+// residual of the X-update, the 1x1-scale soft threshold (eq:bsvt for 1x1
+// blocks) with its fused dual update, and the output X-update.
+//
+// ADMM state kept in HBM per scale: Z_i and W_i = Z_i - U_i.  With the
+// consensus residual R = (1/L)(Y - sum_j W_j) (zero at unobserved entries,
+// Sec. 10.4) the X-update is X_i = W_i + R, the prox input is
+// A_i = X_i + U_i = Z_i + R, the dual update U_i' = A_i - Z_i' and the new
+// state W_i' = Z_i' - U_i' = 2 Z_i' - A_i.
+#include <math.h>
+
+#include "common.cuh"
+#include "internal.h"
+
+namespace msllr {
+
+namespace {
+
+constexpr int kEwThreads = 256;
+
+int ew_grid(size_t n_items) {
+  // enough CTAs for 8 resident per SM on 152 SMs; grid-stride beyond that
+  size_t g = (n_items + kEwThreads - 1) / kEwThreads;
+  const size_t cap = 152 * 8;
+  return (int)(g < cap ? (g > 0 ? g : 1) : cap);
+}
+
+__global__ void __launch_bounds__(kEwThreads)
+consensus_kernel(const float* __restrict__ Y, const float* __restrict__ W, float* __restrict__ R,
+                 const uint8_t* __restrict__ mask, int L, size_t MN) {
+  const float invL = 1.f / (float)L;
+  const size_t stride = (size_t)gridDim.x * blockDim.x;
+  const size_t i0 = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if ((MN & 3) == 0) {
+    const size_t n4 = MN >> 2;
+    for (size_t i = i0; i < n4; i += stride) {
+      float4 acc = reinterpret_cast<const float4*>(Y)[i];
+      for (int j = 0; j < L; ++j) {
+        const float4 w = reinterpret_cast<const float4*>(W + (size_t)j * MN)[i];
+        acc.x -= w.x;
+        acc.y -= w.y;
+        acc.z -= w.z;
+        acc.w -= w.w;
+      }
+      acc.x *= invL;
+      acc.y *= invL;
+      acc.z *= invL;
+      acc.w *= invL;
+      if (mask) {
+        const uchar4 mk = reinterpret_cast<const uchar4*>(mask)[i];
+        if (!mk.x) acc.x = 0.f;
+        if (!mk.y) acc.y = 0.f;
+        if (!mk.z) acc.z = 0.f;
+        if (!mk.w) acc.w = 0.f;
+      }
+      reinterpret_cast<float4*>(R)[i] = acc;
+    }
+  } else {
+    for (size_t i = i0; i < MN; i += stride) {
+      float acc = Y[i];
+      for (int j = 0; j < L; ++j) acc -= W[(size_t)j * MN + i];
+      acc *= invL;
+      if (mask && !mask[i]) acc = 0.f;
+      R[i] = acc;
+    }
+  }
+}
+
+// 1x1 blocks: SVT of [a] is sign(a) max(|a| - tau, 0).  The scale is
+// element-wise, so the cycle-spin shift does not change it and is not
+// applied.  Optional statistics: sum |z| (the 1x1 block nuclear norm) and
+// the count of zero outputs.
+__global__ void __launch_bounds__(kEwThreads)
+soft1x1_kernel(const float* A1, const float* __restrict__ A2, float* Zout, float* Wout, int M,
+               int N, int ld, float tau, int* rank_out, double* nuc_acc,
+               unsigned long long* cnt) {
+  __shared__ double sred[kEwThreads / 32];
+  __shared__ unsigned long long cred[kEwThreads / 32];
+  const size_t MN = (size_t)M * N;
+  const size_t stride = (size_t)gridDim.x * blockDim.x;
+  const size_t i0 = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  double nuc = 0.0;
+  unsigned long long zeros = 0;
+  const bool aligned = ((((uintptr_t)A1) | ((uintptr_t)A2) | ((uintptr_t)Zout) | ((uintptr_t)Wout)) & 15) == 0;
+  if (aligned && ld == N && (MN & 3) == 0 && !rank_out) {
+    const size_t n4 = MN >> 2;
+    for (size_t i = i0; i < n4; i += stride) {
+      float4 a = reinterpret_cast<const float4*>(A1)[i];
+      if (A2) {
+        const float4 b = reinterpret_cast<const float4*>(A2)[i];
+        a.x += b.x;
+        a.y += b.y;
+        a.z += b.z;
+        a.w += b.w;
+      }
+      float4 z;
+      z.x = copysignf(fmaxf(fabsf(a.x) - tau, 0.f), a.x);
+      z.y = copysignf(fmaxf(fabsf(a.y) - tau, 0.f), a.y);
+      z.z = copysignf(fmaxf(fabsf(a.z) - tau, 0.f), a.z);
+      z.w = copysignf(fmaxf(fabsf(a.w) - tau, 0.f), a.w);
+      reinterpret_cast<float4*>(Zout)[i] = z;
+      if (Wout) {
+        float4 w;
+        w.x = 2.f * z.x - a.x;
+        w.y = 2.f * z.y - a.y;
+        w.z = 2.f * z.z - a.z;
+        w.w = 2.f * z.w - a.w;
+        reinterpret_cast<float4*>(Wout)[i] = w;
+      }
+      if (nuc_acc) {
+        nuc += (double)fabsf(z.x) + (double)fabsf(z.y) + (double)fabsf(z.z) + (double)fabsf(z.w);
+        zeros += (z.x == 0.f) + (z.y == 0.f) + (z.z == 0.f) + (z.w == 0.f);
+      }
+    }
+  } else {
+    for (size_t i = i0; i < MN; i += stride) {
+      const size_t r = i / (size_t)N, c = i - r * (size_t)N;
+      const size_t off = r * (size_t)ld + c;
+      float a = A1[off];
+      if (A2) a += A2[off];
+      const float z = copysignf(fmaxf(fabsf(a) - tau, 0.f), a);
+      Zout[off] = z;
+      if (Wout) Wout[off] = 2.f * z - a;
+      if (rank_out) rank_out[i] = z != 0.f;
+      if (nuc_acc) {
+        nuc += (double)fabsf(z);
+        zeros += (z == 0.f);
+      }
+    }
+  }
+  if (nuc_acc) {
+    nuc = warp_sum_d(nuc);
+    unsigned long long zz = zeros;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) zz += __shfl_xor_sync(0xffffffffu, zz, o);
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    if (lane == 0) {
+      sred[w] = nuc;
+      cred[w] = zz;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double t = 0.0;
+      unsigned long long tz = 0;
+      for (int i = 0; i < kEwThreads / 32; ++i) {
+        t += sred[i];
+        tz += cred[i];
+      }
+      atomicAdd(nuc_acc, t);
+      if (cnt) atomicAdd(cnt + 1, tz);
+    }
+  }
+}
+
+// X_i = W_i + R (the X-update of eq:admm on the final state), U_i = Z_i - W_i,
+// and sum over i of ||X_i - Z_i||^2 in FP64.
+__global__ void __launch_bounds__(kEwThreads)
+finalize_kernel(const float* __restrict__ W, const float* __restrict__ Z,
+                const float* __restrict__ R, float* __restrict__ X_out, float* __restrict__ U_out,
+                double* pres_acc, int L, size_t MN) {
+  __shared__ double sred[kEwThreads / 32];
+  const size_t stride = (size_t)gridDim.x * blockDim.x;
+  double acc = 0.0;
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < MN; i += stride) {
+    const float r = R[i];
+    for (int j = 0; j < L; ++j) {
+      const size_t o = (size_t)j * MN + i;
+      const float w = W[o], z = Z[o];
+      const float x = w + r;
+      X_out[o] = x;
+      if (U_out) U_out[o] = z - w;
+      const double dxz = (double)x - (double)z;
+      acc += dxz * dxz;
+    }
+  }
+  if (pres_acc) {
+    acc = warp_sum_d(acc);
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    if (lane == 0) sred[w] = acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double t = 0.0;
+      for (int i = 0; i < kEwThreads / 32; ++i) t += sred[i];
+      atomicAdd(pres_acc, t);
+    }
+  }
+}
+
+__global__ void __launch_bounds__(kEwThreads)
+init_state_kernel(const float* __restrict__ Z0, const float* __restrict__ U0, float* __restrict__ Z,
+                  float* __restrict__ W, size_t n) {
+  const size_t stride = (size_t)gridDim.x * blockDim.x;
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+    const float z = Z0 ? Z0[i] : 0.f;
+    const float u = U0 ? U0[i] : 0.f;
+    Z[i] = z;
+    W[i] = z - u;
+  }
+}
+
+// Start of an iteration: publish this iteration's shift and advance.
+__global__ void advance_kernel(const int* __restrict__ table, int* iter, int* cur_shift) {
+  const int k = *iter;
+  cur_shift[0] = table[2 * k];
+  cur_shift[1] = table[2 * k + 1];
+  *iter = k + 1;
+}
+
+__global__ void __launch_bounds__(kEwThreads)
+nonfinite_kernel(const float* __restrict__ Y, int M, int N, int ld, int* flag) {
+  const size_t MN = (size_t)M * N;
+  const size_t stride = (size_t)gridDim.x * blockDim.x;
+  int bad = 0;
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < MN; i += stride) {
+    const size_t r = i / (size_t)N, c = i - r * (size_t)N;
+    bad |= !isfinite(Y[r * (size_t)ld + c]);
+  }
+  if (__syncthreads_or(bad) && threadIdx.x == 0) atomicOr(flag, 1);
+}
+
+__global__ void __launch_bounds__(kEwThreads)
+copy_dense_kernel(const float* __restrict__ src, int M, int N, int ld, float* __restrict__ dst) {
+  const size_t MN = (size_t)M * N;
+  const size_t stride = (size_t)gridDim.x * blockDim.x;
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < MN; i += stride) {
+    const size_t r = i / (size_t)N, c = i - r * (size_t)N;
+    dst[i] = src[r * (size_t)ld + c];
+  }
+}
+
+}  // namespace
+
+cudaError_t launch_consensus(const float* Y, const float* W, float* R, const uint8_t* mask, int L,
+                             size_t MN, cudaStream_t st, Prof* prof) {
+  if (prof) prof->scale = 0;
+  if (prof) if (cudaError_t e = prof->before(st, KK_CONSENSUS)) return e;
+  consensus_kernel<<<ew_grid((MN + 3) / 4), kEwThreads, 0, st>>>(Y, W, R, mask, L, MN);
+  if (prof) if (cudaError_t e = prof->after(st)) return e;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_soft1x1(const ScaleLaunch& s, cudaStream_t st, Prof* prof) {
+  const size_t MN = (size_t)s.M * s.N;
+  if (prof) if (cudaError_t e = prof->before(st, KK_SOFT1X1)) return e;
+  soft1x1_kernel<<<ew_grid((MN + 3) / 4), kEwThreads, 0, st>>>(
+      s.A1, s.A2, s.Zout, s.Wout, s.M, s.N, s.ld, s.tau, s.rank_out, s.nuc_acc, s.cnt);
+  if (prof) if (cudaError_t e = prof->after(st)) return e;
+  return cudaGetLastError();
+}
+
+#define MISC_BEFORE()                                                  \
+  if (prof) {                                                          \
+    prof->scale = 0;                                                   \
+    if (cudaError_t e_ = prof->before(st, KK_MISC)) return e_;         \
+  }
+#define MISC_AFTER() \
+  if (prof)          \
+    if (cudaError_t e_ = prof->after(st)) return e_;
+
+cudaError_t launch_finalize(const float* W, const float* Z, const float* R, float* X_out,
+                            float* U_out, double* pres_acc, int L, size_t MN, cudaStream_t st,
+                            Prof* prof) {
+  MISC_BEFORE()
+  finalize_kernel<<<ew_grid(MN), kEwThreads, 0, st>>>(W, Z, R, X_out, U_out, pres_acc, L, MN);
+  MISC_AFTER()
+  return cudaGetLastError();
+}
+
+cudaError_t launch_init_state(const float* Z0, const float* U0, float* Z, float* W, int L,
+                              size_t MN, cudaStream_t st, Prof* prof) {
+  const size_t n = (size_t)L * MN;
+  MISC_BEFORE()
+  init_state_kernel<<<ew_grid(n), kEwThreads, 0, st>>>(Z0, U0, Z, W, n);
+  MISC_AFTER()
+  return cudaGetLastError();
+}
+
+cudaError_t launch_advance(const int* table, int* iter, int* cur_shift, cudaStream_t st,
+                           Prof* prof) {
+  if (prof) prof->scale = 0;
+  if (prof) if (cudaError_t e = prof->before(st, KK_ADVANCE)) return e;
+  advance_kernel<<<1, 1, 0, st>>>(table, iter, cur_shift);
+  if (prof) if (cudaError_t e = prof->after(st)) return e;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_nonfinite(const float* Y, int M, int N, int ld, int* flag, cudaStream_t st,
+                             Prof* prof) {
+  MISC_BEFORE()
+  nonfinite_kernel<<<ew_grid((size_t)M * N), kEwThreads, 0, st>>>(Y, M, N, ld, flag);
+  MISC_AFTER()
+  return cudaGetLastError();
+}
+
+cudaError_t launch_copy_dense(const float* src, int M, int N, int ld, float* dst, cudaStream_t st,
+                              Prof* prof) {
+  MISC_BEFORE()
+  copy_dense_kernel<<<ew_grid((size_t)M * N), kEwThreads, 0, st>>>(src, M, N, ld, dst);
+  MISC_AFTER()
+  return cudaGetLastError();
+}
+#undef MISC_BEFORE
+#undef MISC_AFTER
+
+}  // namespace msllr

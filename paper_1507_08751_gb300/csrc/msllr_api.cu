@@ -1,0 +1,537 @@
+// Host side of the msllr C ABI (include/msllr.h): argument checks, the
+// context's device memory, the shift table, and the ADMM driver loop of
+// eq:admm (Sec. 7) with the random cycle-spin Z-update (Sec. 9).
+#include <math.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/msllr.h"
+#include "internal.h"
+
+using namespace msllr;
+
+namespace {
+
+std::string g_last_error = "";  // for calls made without a context
+
+}  // namespace
+
+struct msllr_ctx {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  size_t budget = 0;
+  std::string err;
+
+  // grow-only device workspace
+  void* ws = nullptr;
+  size_t ws_bytes = 0;
+  // small device scalars
+  int* d_small = nullptr;          // [0] iter, [1..2] cur shift, [3] nonfinite flag, [4..5] tmp shift
+  double* d_acc = nullptr;         // [0..MAX) nuc per scale, [MAX] primal residual^2
+  unsigned long long* d_cnt = nullptr;  // [2*MAX]
+  int* d_table = nullptr;
+  size_t table_cap = 0;
+
+  // cached graph of one iteration
+  cudaGraphExec_t graph = nullptr;
+  std::vector<char> graph_key;
+  long long graph_launches[KK_COUNT][8] = {};
+};
+
+namespace {
+
+int fail(msllr_ctx* ctx, int code, const std::string& msg) {
+  if (ctx) ctx->err = msg;
+  else g_last_error = msg;
+  return code;
+}
+
+#define CK(call)                                                                       \
+  do {                                                                                 \
+    cudaError_t e_ = (call);                                                           \
+    if (e_ != cudaSuccess)                                                             \
+      return fail(ctx, MSLLR_ECUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
+  } while (0)
+
+uint64_t splitmix64(uint64_t x) {
+  uint64_t z = x;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+
+void fill_shift_table(uint64_t seed, int offset, int iters, int M, int N, int32_t* out) {
+  for (int k = 0; k < iters; ++k) {
+    const uint64_t z = splitmix64(seed + (uint64_t)(offset + k + 1) * 0x9E3779B97F4A7C15ull);
+    out[2 * k] = (int32_t)((z >> 32) % (uint64_t)M);
+    out[2 * k + 1] = (int32_t)((z & 0xffffffffull) % (uint64_t)N);
+  }
+}
+
+double lambda_of(int M, int N, int m, int n) {
+  const double mx = m > n ? m : n;
+  return sqrt((double)m) + sqrt((double)n) + sqrt(log((double)M * (double)N / mx));
+}
+
+size_t align_up(size_t x) { return (x + 255) & ~(size_t)255; }
+
+// Make sure the context workspace holds at least `bytes`.
+int ensure_ws(msllr_ctx* ctx, size_t bytes) {
+  if (bytes <= ctx->ws_bytes) return MSLLR_OK;
+  if (ctx->budget && bytes > ctx->budget)
+    return fail(ctx, MSLLR_ENOMEM,
+                "workspace of " + std::to_string(bytes) + " bytes exceeds the HBM budget of " +
+                    std::to_string(ctx->budget));
+  if (ctx->ws) {
+    cudaStreamSynchronize(ctx->stream);
+    cudaFree(ctx->ws);
+    ctx->ws = nullptr;
+    ctx->ws_bytes = 0;
+  }
+  if (ctx->graph) {
+    cudaGraphExecDestroy(ctx->graph);
+    ctx->graph = nullptr;
+    ctx->graph_key.clear();
+  }
+  cudaError_t e = cudaMalloc(&ctx->ws, bytes);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    ctx->ws = nullptr;
+    return fail(ctx, MSLLR_ENOMEM, std::string("cudaMalloc workspace: ") + cudaGetErrorString(e));
+  }
+  ctx->ws_bytes = bytes;
+  return MSLLR_OK;
+}
+
+int check_blocks(msllr_ctx* ctx, int M, int N, int m, int n) {
+  if (m <= 0 || n <= 0 || m > M || n > N || M % m || N % n)
+    return fail(ctx, MSLLR_EINVAL,
+                "block " + std::to_string(m) + "x" + std::to_string(n) + " does not divide " +
+                    std::to_string(M) + "x" + std::to_string(N));
+  const int nn = m < n ? m : n;
+  if (nn > MSLLR_MAX_BLOCK_WIDTH)
+    return fail(ctx, MSLLR_EINVAL,
+                "block " + std::to_string(m) + "x" + std::to_string(n) +
+                    " is wider than MSLLR_MAX_BLOCK_WIDTH");
+  const long long nblocks = (long long)(M / m) * (N / n);
+  if (choose_path(m, n) == ScalePath::Big && nblocks > 65535)
+    return fail(ctx, MSLLR_EINVAL, "too many wide blocks in one scale (max 65535)");
+  return MSLLR_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int msllr_params_default(msllr_params* p) {
+  if (!p) return fail(nullptr, MSLLR_EINVAL, "params is NULL");
+  memset(p, 0, sizeof(*p));
+  p->skip_bound = 1;
+  p->cycle_spin = 1;
+  p->use_graph = 1;
+  p->iter_offset = 0;
+  return MSLLR_OK;
+}
+
+int msllr_create(msllr_ctx** out, int device, size_t hbm_budget_bytes, void* cuda_stream) {
+  msllr_ctx* ctx = nullptr;
+  if (!out) return fail(nullptr, MSLLR_EINVAL, "out is NULL");
+  *out = nullptr;
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) {
+    cudaGetLastError();
+    return fail(nullptr, MSLLR_EINVAL, "no CUDA device " + std::to_string(device));
+  }
+  ctx = new msllr_ctx();
+  ctx->device = device;
+  ctx->budget = hbm_budget_bytes;
+  auto bail = [&](int code) {
+    g_last_error = ctx->err;
+    msllr_destroy(ctx);
+    return code;
+  };
+  if (cudaSetDevice(device) != cudaSuccess) return bail(fail(ctx, MSLLR_ECUDA, "cudaSetDevice"));
+  if (configure_kernels() != cudaSuccess) return bail(fail(ctx, MSLLR_ECUDA, "kernel attributes"));
+  if (cuda_stream) {
+    ctx->stream = (cudaStream_t)cuda_stream;
+  } else {
+    if (cudaStreamCreate(&ctx->stream) != cudaSuccess)
+      return bail(fail(ctx, MSLLR_ECUDA, "cudaStreamCreate"));
+    ctx->own_stream = true;
+  }
+  if (cudaMalloc(&ctx->d_small, 64 * sizeof(int)) != cudaSuccess ||
+      cudaMalloc(&ctx->d_acc, (MSLLR_MAX_SCALES + 8) * sizeof(double)) != cudaSuccess ||
+      cudaMalloc(&ctx->d_cnt, 2 * MSLLR_MAX_SCALES * sizeof(unsigned long long)) != cudaSuccess)
+    return bail(fail(ctx, MSLLR_ENOMEM, "cudaMalloc of context scalars"));
+  *out = ctx;
+  return MSLLR_OK;
+}
+
+int msllr_destroy(msllr_ctx* ctx) {
+  if (!ctx) return MSLLR_OK;
+  cudaSetDevice(ctx->device);
+  if (ctx->stream) cudaStreamSynchronize(ctx->stream);
+  if (ctx->graph) cudaGraphExecDestroy(ctx->graph);
+  if (ctx->ws) cudaFree(ctx->ws);
+  if (ctx->d_small) cudaFree(ctx->d_small);
+  if (ctx->d_acc) cudaFree(ctx->d_acc);
+  if (ctx->d_cnt) cudaFree(ctx->d_cnt);
+  if (ctx->d_table) cudaFree(ctx->d_table);
+  if (ctx->own_stream && ctx->stream) cudaStreamDestroy(ctx->stream);
+  delete ctx;
+  return MSLLR_OK;
+}
+
+const char* msllr_last_error(const msllr_ctx* ctx) {
+  return ctx ? ctx->err.c_str() : g_last_error.c_str();
+}
+
+int msllr_shift_table(uint64_t seed, int iters, int M, int N, int32_t* out) {
+  if (iters < 0 || M <= 0 || N <= 0 || (!out && iters > 0))
+    return fail(nullptr, MSLLR_EINVAL, "msllr_shift_table: bad arguments");
+  fill_shift_table(seed, 0, iters, M, N, out);
+  return MSLLR_OK;
+}
+
+int msllr_lambda_default(int M, int N, int m, int n, double* out) {
+  if (!out || m <= 0 || n <= 0 || m > M || n > N)
+    return fail(nullptr, MSLLR_EINVAL, "msllr_lambda_default: bad arguments");
+  *out = lambda_of(M, N, m, n);
+  return MSLLR_OK;
+}
+
+int msllr_blocksvt(msllr_ctx* ctx, const float* A, float* Z, int M, int N, int ld, int bm, int bn,
+                   double tau, int shift_r, int shift_c, int* block_rank_out) {
+  if (!ctx) return fail(nullptr, MSLLR_EINVAL, "ctx is NULL");
+  if (!A || !Z || M <= 0 || N <= 0 || ld < N)
+    return fail(ctx, MSLLR_EINVAL, "msllr_blocksvt: bad matrix arguments");
+  if (!(tau >= 0.0) || !isfinite(tau)) return fail(ctx, MSLLR_EINVAL, "tau must be finite and >= 0");
+  if (int r = check_blocks(ctx, M, N, bm, bn)) return r;
+  const char* a0 = (const char*)A;
+  const char* z0 = (const char*)Z;
+  const size_t span = sizeof(float) * ((size_t)(M - 1) * ld + N);
+  if (a0 < z0 + span && z0 < a0 + span) return fail(ctx, MSLLR_EINVAL, "A and Z overlap");
+  CK(cudaSetDevice(ctx->device));
+  const size_t big = big_workspace_bytes(M, N, bm, bn);
+  if (int r = ensure_ws(ctx, align_up(big) + 256)) return r;
+  const int sh[2] = {((shift_r % M) + M) % M, ((shift_c % N) + N) % N};
+  CK(cudaMemcpyAsync(ctx->d_small + 4, sh, sizeof(sh), cudaMemcpyHostToDevice, ctx->stream));
+  ScaleLaunch s{};
+  s.A1 = A;
+  s.A2 = nullptr;
+  s.Zout = Z;
+  s.Wout = nullptr;
+  s.M = M;
+  s.N = N;
+  s.ld = ld;
+  s.m = bm;
+  s.n = bn;
+  s.shift = ctx->d_small + 4;
+  s.tau = (float)tau;
+  s.skip_bound = 1;
+  s.rank_out = block_rank_out;
+  BigWorkspace w = carve_big_workspace(ctx->ws, M, N, bm, bn);
+  CK(launch_scale(s, w, ctx->stream, nullptr));
+  CK(cudaStreamSynchronize(ctx->stream));
+  return MSLLR_OK;
+}
+
+namespace {
+
+struct Layout {
+  size_t MN;
+  float* Z;
+  float* W;
+  float* R;
+  float* Yd;
+  uint8_t* mask;
+  std::vector<BigWorkspace> big;
+  size_t total;
+};
+
+// Offsets of every buffer inside the workspace (base may be null to size it).
+Layout plan(void* base, int M, int N, int L, const int* bm, const int* bn, bool masked) {
+  Layout lay;
+  lay.MN = (size_t)M * N;
+  char* b = (char*)base;
+  size_t off = 0;
+  auto take = [&](size_t bytes) {
+    char* p = b ? b + off : nullptr;
+    off += align_up(bytes);
+    return p;
+  };
+  lay.Z = (float*)take(sizeof(float) * L * lay.MN);
+  lay.W = (float*)take(sizeof(float) * L * lay.MN);
+  lay.R = (float*)take(sizeof(float) * lay.MN);
+  lay.Yd = (float*)take(sizeof(float) * lay.MN);
+  lay.mask = masked ? (uint8_t*)take(lay.MN) : nullptr;
+  for (int i = 0; i < L; ++i) {
+    const size_t bytes = big_workspace_bytes(M, N, bm[i], bn[i]);
+    char* p = take(bytes);
+    lay.big.push_back(b ? carve_big_workspace(p, M, N, bm[i], bn[i]) : BigWorkspace{});
+  }
+  lay.total = off + 256;
+  return lay;
+}
+
+int enqueue_iteration(msllr_ctx* ctx, const Layout& lay, int M, int N, int L, const int* bm,
+                      const int* bn, const float* taus, const msllr_params& p, bool stats,
+                      Prof* prof) {
+  CK(launch_advance(ctx->d_table, ctx->d_small, ctx->d_small + 1, ctx->stream, prof));
+  CK(launch_consensus(lay.Yd, lay.W, lay.R, lay.mask, L, lay.MN, ctx->stream, prof));
+  for (int i = 0; i < L; ++i) {
+    ScaleLaunch s{};
+    s.A1 = lay.Z + (size_t)i * lay.MN;
+    s.A2 = lay.R;
+    s.Zout = lay.Z + (size_t)i * lay.MN;
+    s.Wout = lay.W + (size_t)i * lay.MN;
+    s.M = M;
+    s.N = N;
+    s.ld = N;
+    s.m = bm[i];
+    s.n = bn[i];
+    s.shift = p.cycle_spin ? ctx->d_small + 1 : nullptr;
+    s.tau = taus[i];
+    s.skip_bound = p.skip_bound;
+    s.rank_out = nullptr;
+    s.nuc_acc = stats ? ctx->d_acc + i : nullptr;
+    s.cnt = stats ? ctx->d_cnt + 2 * i : nullptr;
+    prof->scale = i;
+    CK(launch_scale(s, lay.big[i], ctx->stream, prof));
+  }
+  return MSLLR_OK;
+}
+
+int decompose_device(msllr_ctx* ctx, const float* Y, int M, int N, int ld, int L, const int* bm,
+                     const int* bn, const double* lambda, double rho, int iters, uint64_t seed,
+                     const uint8_t* mask, const msllr_params* params, float* X_out, float* Z_out,
+                     msllr_stats* stats) {
+  if (!ctx) return fail(nullptr, MSLLR_EINVAL, "ctx is NULL");
+  if (!Y || !X_out || M <= 0 || N <= 0 || ld < N)
+    return fail(ctx, MSLLR_EINVAL, "msllr_decompose: bad matrix arguments");
+  if (L <= 0 || L > MSLLR_MAX_SCALES || !bm || !bn)
+    return fail(ctx, MSLLR_EINVAL, "L must be in 1..MSLLR_MAX_SCALES with block sizes given");
+  if (!(rho > 0.0) || !isfinite(rho)) return fail(ctx, MSLLR_EINVAL, "rho must be > 0");
+  if (iters < 0) return fail(ctx, MSLLR_EINVAL, "iters must be >= 0");
+  msllr_params p;
+  msllr_params_default(&p);
+  if (params) p = *params;
+  if (p.iter_offset < 0) return fail(ctx, MSLLR_EINVAL, "iter_offset must be >= 0");
+  Prof prof;
+  prof.timing = p.profile != 0;
+  if (p.profile) p.use_graph = 0;
+  struct EventPool {
+    Prof* pr;
+    ~EventPool() {
+      for (cudaEvent_t e : pr->ev) cudaEventDestroy(e);
+    }
+  } pool{&prof};
+  double lam[MSLLR_MAX_SCALES];
+  float taus[MSLLR_MAX_SCALES];
+  for (int i = 0; i < L; ++i) {
+    if (int r = check_blocks(ctx, M, N, bm[i], bn[i])) return r;
+    lam[i] = lambda ? lambda[i] : lambda_of(M, N, bm[i], bn[i]);
+    if (!(lam[i] > 0.0) || !isfinite(lam[i]))
+      return fail(ctx, MSLLR_EINVAL, "lambda_" + std::to_string(i) + " must be finite and > 0");
+    taus[i] = (float)(lam[i] / rho);
+  }
+  CK(cudaSetDevice(ctx->device));
+  const Layout sizing = plan(nullptr, M, N, L, bm, bn, mask != nullptr);
+  if (int r = ensure_ws(ctx, sizing.total)) return r;
+  const Layout lay = plan(ctx->ws, M, N, L, bm, bn, mask != nullptr);
+  cudaStream_t st = ctx->stream;
+
+  // inputs: finiteness check, dense copies
+  CK(cudaMemsetAsync(ctx->d_small + 3, 0, sizeof(int), st));
+  CK(launch_nonfinite(Y, M, N, ld, ctx->d_small + 3, st, &prof));
+  int bad = 0;
+  CK(cudaMemcpyAsync(&bad, ctx->d_small + 3, sizeof(int), cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  if (bad) return fail(ctx, MSLLR_ENONFINITE, "Y contains NaN or Inf");
+  if (ld == N) CK(cudaMemcpyAsync(lay.Yd, Y, sizeof(float) * lay.MN, cudaMemcpyDeviceToDevice, st));
+  else CK(launch_copy_dense(Y, M, N, ld, lay.Yd, st, &prof));
+  if (mask) CK(cudaMemcpyAsync(lay.mask, mask, lay.MN, cudaMemcpyDeviceToDevice, st));
+
+  // shift table for iterations iter_offset .. iter_offset + iters - 1
+  const size_t tab = 2 * (size_t)(iters > 0 ? iters : 1);
+  if (tab > ctx->table_cap) {
+    if (ctx->d_table) cudaFree(ctx->d_table);
+    ctx->d_table = nullptr;
+    ctx->table_cap = 0;
+    if (ctx->graph) {
+      cudaGraphExecDestroy(ctx->graph);
+      ctx->graph = nullptr;
+      ctx->graph_key.clear();
+    }
+    CK(cudaMalloc(&ctx->d_table, tab * sizeof(int)));
+    ctx->table_cap = tab;
+  }
+  std::vector<int32_t> h_table(tab, 0);
+  if (p.cycle_spin) fill_shift_table(seed, p.iter_offset, iters, M, N, h_table.data());
+  CK(cudaMemcpyAsync(ctx->d_table, h_table.data(), tab * sizeof(int), cudaMemcpyHostToDevice, st));
+  CK(cudaMemsetAsync(ctx->d_small, 0, sizeof(int), st));
+  CK(launch_init_state(p.Z_init, p.U_init, lay.Z, lay.W, L, lay.MN, st, &prof));
+  CK(cudaMemsetAsync(ctx->d_acc, 0, (MSLLR_MAX_SCALES + 8) * sizeof(double), st));
+  CK(cudaMemsetAsync(ctx->d_cnt, 0, 2 * MSLLR_MAX_SCALES * sizeof(unsigned long long), st));
+
+  // iterations 0 .. iters-2 (graph replay), the last one with statistics
+  const int plain_iters = iters > 0 ? iters - 1 : 0;
+  if (p.use_graph && plain_iters > 0) {
+    std::vector<char> key;
+    auto put = [&](const void* v, size_t n) {
+      key.insert(key.end(), (const char*)v, (const char*)v + n);
+    };
+    put(&M, sizeof M);
+    put(&N, sizeof N);
+    put(&L, sizeof L);
+    put(bm, sizeof(int) * L);
+    put(bn, sizeof(int) * L);
+    put(taus, sizeof(float) * L);
+    const int flags[3] = {p.skip_bound, p.cycle_spin, mask != nullptr};
+    put(flags, sizeof flags);
+    void* wsp = ctx->ws;
+    put(&wsp, sizeof wsp);
+    if (!ctx->graph || key != ctx->graph_key) {
+      if (ctx->graph) {
+        cudaGraphExecDestroy(ctx->graph);
+        ctx->graph = nullptr;
+      }
+      cudaGraph_t g = nullptr;
+      CK(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+      Prof counter;
+      int r = enqueue_iteration(ctx, lay, M, N, L, bm, bn, taus, p, false, &counter);
+      memcpy(ctx->graph_launches, counter.launches, sizeof counter.launches);
+      cudaError_t e = cudaStreamEndCapture(st, &g);
+      if (r) {
+        if (g) cudaGraphDestroy(g);
+        return r;
+      }
+      if (e != cudaSuccess)
+        return fail(ctx, MSLLR_ECUDA, std::string("stream capture: ") + cudaGetErrorString(e));
+      e = cudaGraphInstantiate(&ctx->graph, g, 0);
+      cudaGraphDestroy(g);
+      if (e != cudaSuccess)
+        return fail(ctx, MSLLR_ECUDA, std::string("graph instantiate: ") + cudaGetErrorString(e));
+      ctx->graph_key = key;
+    }
+    for (int k = 0; k < plain_iters; ++k) CK(cudaGraphLaunch(ctx->graph, st));
+    for (int a = 0; a < KK_COUNT; ++a)
+      for (int b = 0; b < 8; ++b) prof.launches[a][b] += ctx->graph_launches[a][b] * plain_iters;
+  } else {
+    for (int k = 0; k < plain_iters; ++k)
+      if (int r = enqueue_iteration(ctx, lay, M, N, L, bm, bn, taus, p, false, &prof)) return r;
+  }
+  if (iters > 0)
+    if (int r = enqueue_iteration(ctx, lay, M, N, L, bm, bn, taus, p, true, &prof)) return r;
+
+  // output X-update on the final state
+  CK(launch_consensus(lay.Yd, lay.W, lay.R, lay.mask, L, lay.MN, st, &prof));
+  CK(launch_finalize(lay.W, lay.Z, lay.R, X_out, p.U_out, ctx->d_acc + MSLLR_MAX_SCALES, L,
+                     lay.MN, st, &prof));
+  if (Z_out)
+    CK(cudaMemcpyAsync(Z_out, lay.Z, sizeof(float) * L * lay.MN, cudaMemcpyDeviceToDevice, st));
+  double acc[MSLLR_MAX_SCALES + 8];
+  unsigned long long cnt[2 * MSLLR_MAX_SCALES];
+  CK(cudaMemcpyAsync(acc, ctx->d_acc, sizeof acc, cudaMemcpyDeviceToHost, st));
+  CK(cudaMemcpyAsync(cnt, ctx->d_cnt, sizeof cnt, cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  if (stats) {
+    memset(stats, 0, sizeof(*stats));
+    stats->iters = iters;
+    stats->L = L;
+    double obj = 0.0;
+    for (int i = 0; i < L; ++i) {
+      stats->scale_nuclear[i] = acc[i];
+      obj += lam[i] * acc[i];
+      stats->blocks[i] = (long long)(M / bm[i]) * (N / bn[i]);
+      stats->blocks_skipped[i] = (long long)cnt[2 * i];
+      stats->blocks_zero[i] = (long long)cnt[2 * i + 1];
+      stats->lambda[i] = lam[i];
+    }
+    stats->objective = obj;
+    stats->primal_residual = sqrt(acc[MSLLR_MAX_SCALES]);
+    long long total = 0;
+    for (int a = 0; a < KK_COUNT && a < MSLLR_KERNEL_KINDS; ++a)
+      for (int b = 0; b < MSLLR_MAX_SCALES; ++b) {
+        stats->kernel_launches[a][b] = prof.launches[a][b];
+        total += prof.launches[a][b];
+      }
+    stats->launches = total;
+    if (prof.timing) {
+      for (size_t u = 0; u < prof.used; ++u) {
+        float ms = 0.f;
+        CK(cudaEventElapsedTime(&ms, prof.ev[2 * u], prof.ev[2 * u + 1]));
+        const int kind = prof.tag[u] / 8, sc = prof.tag[u] % 8;
+        stats->kernel_ms[kind][sc] += ms;
+      }
+    }
+  }
+  return MSLLR_OK;
+}
+
+}  // namespace
+
+int msllr_decompose(msllr_ctx* ctx, const float* Y, int M, int N, int ld, int L,
+                    const int* block_m, const int* block_n, const double* lambda, double rho,
+                    int iters, uint64_t seed, const uint8_t* mask, const msllr_params* params,
+                    float* X_out, float* Z_out, msllr_stats* stats) {
+  return decompose_device(ctx, Y, M, N, ld, L, block_m, block_n, lambda, rho, iters, seed, mask,
+                          params, X_out, Z_out, stats);
+}
+
+int msllr_decompose_host(msllr_ctx* ctx, const float* Y, int M, int N, int ld, int L,
+                         const int* block_m, const int* block_n, const double* lambda, double rho,
+                         int iters, uint64_t seed, const uint8_t* mask, const msllr_params* params,
+                         float* X_out, float* Z_out, msllr_stats* stats) {
+  if (!ctx) return fail(nullptr, MSLLR_EINVAL, "ctx is NULL");
+  if (!Y || !X_out || M <= 0 || N <= 0 || ld < N || L <= 0 || L > MSLLR_MAX_SCALES)
+    return fail(ctx, MSLLR_EINVAL, "msllr_decompose_host: bad arguments");
+  if (params && (params->Z_init || params->U_init || params->U_out))
+    return fail(ctx, MSLLR_EINVAL, "msllr_decompose_host takes no device state pointers");
+  CK(cudaSetDevice(ctx->device));
+  const size_t MN = (size_t)M * N;
+  float* dY = nullptr;
+  float* dX = nullptr;
+  float* dZ = nullptr;
+  uint8_t* dmask = nullptr;
+  auto cleanup = [&]() {
+    if (dY) cudaFree(dY);
+    if (dX) cudaFree(dX);
+    if (dZ) cudaFree(dZ);
+    if (dmask) cudaFree(dmask);
+  };
+  if (cudaMalloc(&dY, sizeof(float) * MN) != cudaSuccess ||
+      cudaMalloc(&dX, sizeof(float) * L * MN) != cudaSuccess ||
+      (Z_out && cudaMalloc(&dZ, sizeof(float) * L * MN) != cudaSuccess) ||
+      (mask && cudaMalloc(&dmask, MN) != cudaSuccess)) {
+    cudaGetLastError();
+    cleanup();
+    return fail(ctx, MSLLR_ENOMEM, "msllr_decompose_host: device buffers");
+  }
+  cudaError_t e = cudaMemcpy2DAsync(dY, sizeof(float) * N, Y, sizeof(float) * ld,
+                                    sizeof(float) * N, M, cudaMemcpyHostToDevice, ctx->stream);
+  if (e == cudaSuccess && mask)
+    e = cudaMemcpyAsync(dmask, mask, MN, cudaMemcpyHostToDevice, ctx->stream);
+  if (e != cudaSuccess) {
+    cleanup();
+    return fail(ctx, MSLLR_ECUDA, std::string("host to device copy: ") + cudaGetErrorString(e));
+  }
+  int r = decompose_device(ctx, dY, M, N, N, L, block_m, block_n, lambda, rho, iters, seed, dmask,
+                           params, dX, dZ, stats);
+  if (r == MSLLR_OK) {
+    e = cudaMemcpyAsync(X_out, dX, sizeof(float) * L * MN, cudaMemcpyDeviceToHost, ctx->stream);
+    if (e == cudaSuccess && Z_out)
+      e = cudaMemcpyAsync(Z_out, dZ, sizeof(float) * L * MN, cudaMemcpyDeviceToHost, ctx->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+    if (e != cudaSuccess)
+      r = fail(ctx, MSLLR_ECUDA, std::string("device to host copy: ") + cudaGetErrorString(e));
+  }
+  cleanup();
+  return r;
+}
+
+}  // extern "C"

@@ -1,0 +1,298 @@
+"""GPU parity: the CUDA path through the C ABI against the FP64 oracle.
+
+Tolerance: the FP32 path must match the oracle to a relative Frobenius error
+of 1e-4 per output (per X_i for decompositions), on the same seeded input
+and the same shift table.  Block ranks above tau (an integer the FP32 path
+decides) must agree except for blocks with a singular value within 1e-4
+(relative) of tau, where both answers are valid.
+"""
+
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_1507_08751_gb300 import synth
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-4
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    from paper_1507_08751_gb300 import binding as B
+    B.lib()
+    c = B.Context(0)
+    yield c
+    c.close()
+
+
+def dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+def _test_matrix(seed, M, N, m, n, scale_lr=4.0):
+    """Blocks with low-rank content of varied strength plus noise, so that a
+    scale has skipped blocks, rank-0 blocks and blocks of several ranks."""
+    rng = np.random.default_rng(seed)
+    A = 0.3 * rng.standard_normal((M, N))
+    for p in range(M // m):
+        for q in range(N // n):
+            r = rng.integers(0, 4)
+            amp = rng.choice([0.0, 0.5, 1.0, 3.0]) * scale_lr
+            if r and amp:
+                u = rng.standard_normal((m, r))
+                v = rng.standard_normal((n, r))
+                A[p * m:(p + 1) * m, q * n:(q + 1) * n] += amp * (u @ v.T) / np.sqrt(max(m, n))
+    return A.astype(np.float32)
+
+
+def _block_sv(A, m, n):
+    M, N = A.shape
+    B = A.reshape(M // m, m, N // n, n).transpose(0, 2, 1, 3).reshape(-1, m, n)
+    return np.linalg.svd(B, compute_uv=False)
+
+
+BLOCK_CASES = [
+    # (M, N, m, n, shift)  small fused path, big path, wide/tall/vector blocks
+    (64, 64, 4, 4, (3, 5)),
+    (64, 64, 16, 16, (0, 0)),
+    (96, 80, 16, 16, (37, 71)),
+    (50, 30, 5, 5, (7, 2)),
+    (48, 40, 8, 8, (47, 39)),
+    (64, 64, 64, 64, (11, 13)),
+    (128, 96, 32, 32, (100, 3)),
+    (256, 256, 64, 64, (200, 31)),
+    (64, 96, 4, 8, (5, 90)),
+    (96, 64, 16, 4, (90, 5)),
+    (64, 64, 1, 16, (9, 9)),
+    (64, 64, 16, 1, (9, 9)),
+    (300, 200, 100, 100, (250, 150)),
+    (512, 256, 256, 256, (300, 17)),
+    (256, 512, 128, 256, (1, 300)),
+    (1000, 120, 1000, 120, (0, 0)),
+    (2048, 256, 2048, 256, (5, 6)),
+]
+
+
+@pytest.mark.parametrize("M,N,m,n,shift", BLOCK_CASES)
+def test_blocksvt_matches_oracle(ctx, M, N, m, n, shift):
+    A = _test_matrix(hash((M, N, m, n)) & 0xFFFF, M, N, m, n)
+    sv = _block_sv(A.astype(np.float64), m, n)
+    tau = float(np.quantile(sv[:, 0], 0.4)) if sv.shape[0] > 3 else float(0.5 * sv[0, 0])
+    Z = torch.empty((M, N), dtype=torch.float32, device="cuda")
+    rank = torch.empty(((M // m) * (N // n),), dtype=torch.int32, device="cuda")
+    ctx.msllr_blocksvt(dev(A), Z, m, n, tau, shift, rank_out=rank)
+    torch.cuda.synchronize()
+    A64 = A.astype(np.float64)
+    want = O.unshift(O.block_svt(O.shift(A64, shift), m, n, tau), shift)
+    got = Z.cpu().numpy().astype(np.float64)
+    err = np.linalg.norm(got - want) / max(np.linalg.norm(want), 1e-6 * np.linalg.norm(A64))
+    assert err <= TOL, f"relative error {err:.3e}"
+    # certified ranks
+    svs = _block_sv(O.shift(A64, shift), m, n)
+    want_rank = (svs > tau).sum(axis=1)
+    got_rank = rank.cpu().numpy()
+    near = (np.abs(svs - tau) <= 1e-4 * np.maximum(svs[:, :1], tau)).any(axis=1)
+    bad = (got_rank != want_rank) & ~near
+    assert not bad.any(), f"{bad.sum()} blocks with a wrong rank"
+
+
+def test_blocksvt_1x1_is_soft_threshold_bit_exact(ctx):
+    """1x1 blocks: the kernel's soft threshold equals the FP32 textbook
+    formula bit for bit (the oracle restates it in FP64)."""
+    rng = np.random.default_rng(3)
+    A = rng.standard_normal((33, 47)).astype(np.float32)
+    tau = np.float32(0.7)
+    Z = torch.empty_like(dev(A))
+    ctx.msllr_blocksvt(dev(A), Z, 1, 1, float(tau), (0, 0))
+    want = np.sign(A) * np.maximum(np.abs(A) - tau, np.float32(0))
+    np.testing.assert_array_equal(Z.cpu().numpy(), want.astype(np.float32))
+
+
+def test_blocksvt_row_stride(ctx):
+    """ld > N: only the M x N window is read and written."""
+    M, N, ld = 64, 48, 80
+    rng = np.random.default_rng(4)
+    Afull = rng.standard_normal((M, ld)).astype(np.float32)
+    Zfull = torch.full((M, ld), 7.0, dtype=torch.float32, device="cuda")
+    ctx.msllr_blocksvt(dev(Afull), Zfull, 16, 16, 2.0, (5, 3), N=N)
+    got = Zfull.cpu().numpy()
+    want = O.unshift(O.block_svt(O.shift(Afull[:, :N].astype(np.float64), (5, 3)), 16, 16, 2.0), (5, 3))
+    assert np.linalg.norm(got[:, :N] - want) <= TOL * np.linalg.norm(want)
+    assert np.all(got[:, N:] == 7.0)
+
+
+def _run_decompose(ctx, Y32, scales, lam, iters, seed, mask=None, params=None):
+    M, N = Y32.shape
+    X = torch.empty((len(scales), M, N), dtype=torch.float32, device="cuda")
+    Z = torch.empty_like(X)
+    stats = ctx.msllr_decompose(dev(Y32), scales, X, lambdas=lam, rho=1.0, iters=iters,
+                                seed=seed, mask=None if mask is None else dev(mask),
+                                params=params, Z_out=Z)
+    torch.cuda.synchronize()
+    return X.cpu().numpy(), Z.cpu().numpy(), stats
+
+
+def test_decompose_tiny_64_matches_oracle(ctx):
+    """The 64x64, four-scale workload: 500 iterations of random cycle-spun
+    ADMM against the FP64 oracle on the same shift table."""
+    Y, comps, scales = synth.tiny_64()
+    Y32 = Y.astype(np.float32)
+    M, N = Y32.shape
+    lam = [O.lambda_area(M, N, m, n) for m, n in scales]
+    iters, seed = 500, 1507087510
+    X, Z, stats = _run_decompose(ctx, Y32, scales, lam, iters, seed)
+    ref = O.admm(Y32.astype(np.float64), scales, lam, 1.0, iters,
+                 shifts=O.shift_table(seed, iters, M, N))
+    err = O.relerr(X, ref["X"], Y32)
+    assert np.all(err <= TOL), err
+    errz = O.relerr(Z, ref["Z"], Y32)
+    assert np.all(errz <= TOL), errz
+    np.testing.assert_allclose(X.sum(0), Y32, atol=1e-5 * np.abs(Y32).max())
+    # objective reported from the last prox matches the oracle's Z
+    obj = sum(lam[i] * O.block_nuclear_norm(ref["Z"][i], *scales[i]) for i in range(len(scales)))
+    assert stats["objective"] == pytest.approx(obj, rel=1e-4)
+
+
+def test_decompose_video_shaped_matches_oracle(ctx):
+    """Video-shaped (pixels x frames) input at 1024 x 256 with the video
+    scales 1, 16, 64, 256, full: exercises the fused, wide-block and
+    full-matrix paths together."""
+    Y32, comps, scales = synth.video(M=1024, N=256)
+    M, N = Y32.shape
+    lam = [O.lambda_default(M, N, m, n) for m, n in scales]
+    iters, seed = 40, 99
+    X, Z, stats = _run_decompose(ctx, Y32, scales, lam, iters, seed)
+    ref = O.admm(Y32.astype(np.float64), scales, lam, 1.0, iters,
+                 shifts=O.shift_table(seed, iters, M, N))
+    err = O.relerr(X, ref["X"], Y32)
+    assert np.all(err <= TOL), err
+
+
+def test_decompose_masked_matches_oracle(ctx):
+    """Sec. 10.4 masked X-update on a ratings-like input."""
+    Y32, mask = synth.ratings(5, 128, 96, density=0.3)
+    scales = [(1, 1), (4, 4), (16, 16), (128, 96)]
+    M, N = Y32.shape
+    lam = [O.lambda_default(M, N, m, n) for m, n in scales]
+    iters, seed = 150, 5
+    X, Z, stats = _run_decompose(ctx, Y32, scales, lam, iters, seed, mask=mask)
+    ref = O.admm(Y32.astype(np.float64), scales, lam, 1.0, iters,
+                 shifts=O.shift_table(seed, iters, M, N), mask=mask.astype(bool))
+    err = O.relerr(X, ref["X"], Y32)
+    assert np.all(err <= TOL), err
+    obs = mask.astype(bool)
+    np.testing.assert_allclose(X.sum(0)[obs], Y32[obs], atol=1e-4)
+
+
+def test_decompose_without_shifts_recovers_hanning_blobs(ctx):
+    """Shifts off: the GPU iteration reaches the certified optimum, i.e. the
+    exact multi-scale components of the Fig. 1 style example."""
+    from paper_1507_08751_gb300 import binding as B
+    Y, comps, scales = synth.hanning_blobs()
+    Y32 = Y.astype(np.float32)
+    M, N = Y32.shape
+    lam = [O.lambda_default(M, N, m, n) for m, n in scales]
+    p = B.msllr_params_default()
+    p.cycle_spin = 0
+    X, Z, stats = _run_decompose(ctx, Y32, scales, lam, 1000, 0, params=p)
+    ref = O.admm(Y32.astype(np.float64), scales, lam, 1.0, 1000)
+    assert np.all(O.relerr(X, ref["X"], Y32) <= TOL)
+    assert np.all(O.relerr(X, comps, Y32) <= 1e-3)
+
+
+def test_skip_bound_does_not_change_results(ctx):
+    from paper_1507_08751_gb300 import binding as B
+    Y32, comps, scales = synth.video(M=512, N=256)
+    p_on = B.msllr_params_default()
+    p_off = B.msllr_params_default()
+    p_off.skip_bound = 0
+    X1, _, s1 = _run_decompose(ctx, Y32, scales, None, 20, 3, params=p_on)
+    X0, _, s0 = _run_decompose(ctx, Y32, scales, None, 20, 3, params=p_off)
+    assert sum(s0["blocks_skipped"]) == 0
+    assert np.all(O.relerr(X1, X0, Y32) <= 1e-6)
+
+
+def test_decompose_is_deterministic_and_graph_equals_plain(ctx):
+    from paper_1507_08751_gb300 import binding as B
+    Y32, comps, scales = synth.video(M=512, N=256)
+    a, _, _ = _run_decompose(ctx, Y32, scales, None, 25, 11)
+    b, _, _ = _run_decompose(ctx, Y32, scales, None, 25, 11)
+    p = B.msllr_params_default()
+    p.use_graph = 0
+    c, _, _ = _run_decompose(ctx, Y32, scales, None, 25, 11, params=p)
+    np.testing.assert_array_equal(a, b)
+    np.testing.assert_array_equal(a, c)
+
+
+def test_host_api_matches_device_api(ctx):
+    Y, comps, scales = synth.tiny_64()
+    Y32 = Y.astype(np.float32)
+    M, N = Y32.shape
+    Xd, _, _ = _run_decompose(ctx, Y32, scales, None, 50, 4)
+    Xh = np.empty((len(scales), M, N), np.float32)
+    ctx.msllr_decompose_host(Y32, scales, Xh, iters=50, seed=4)
+    np.testing.assert_array_equal(Xd, Xh)
+
+
+def test_full_size_video_one_iteration_continuation(ctx):
+    """The 16384 x 256 video workload in the launch configuration the
+    benchmark times: run 3 iterations, then one more from the returned state
+    (Z, U) on the GPU and in the FP64 oracle (same shift), and compare."""
+    from paper_1507_08751_gb300 import binding as B
+    Y32, comps, scales = synth.video()
+    M, N = Y32.shape
+    L = len(scales)
+    lam = [O.lambda_default(M, N, m, n) for m, n in scales]
+    seed = 1507087510
+    Yd = dev(Y32)
+    X = torch.empty((L, M, N), dtype=torch.float32, device="cuda")
+    Z = torch.empty_like(X)
+    U = torch.empty_like(X)
+    p = B.msllr_params_default()
+    p.U_out = U.data_ptr()
+    ctx.msllr_decompose(Yd, scales, X, iters=3, seed=seed, params=p, Z_out=Z)
+    np.testing.assert_allclose(X.sum(0).cpu().numpy(), Y32, atol=2e-4 * np.abs(Y32).max())
+    Z0, U0 = Z.clone(), U.clone()
+    p2 = B.msllr_params_default()
+    p2.Z_init, p2.U_init, p2.iter_offset = Z0.data_ptr(), U0.data_ptr(), 3
+    X2 = torch.empty_like(X)
+    Z2 = torch.empty_like(X)
+    ctx.msllr_decompose(Yd, scales, X2, iters=1, seed=seed, params=p2, Z_out=Z2)
+    torch.cuda.synchronize()
+    s = O.shift_table(seed, 4, M, N)[3]
+    taus = lam
+    Zs, Us = Z0.cpu().numpy().astype(np.float64), U0.cpu().numpy().astype(np.float64)
+    _, Zn, Un = O.admm_step(Y32.astype(np.float64), Zs, Us, scales, taus, s)
+    Xn = O.x_update(Y32.astype(np.float64), Zn, Un)
+    assert np.all(O.relerr(Z2.cpu().numpy(), Zn, Y32) <= TOL)
+    assert np.all(O.relerr(X2.cpu().numpy(), Xn, Y32) <= TOL)
+
+
+def test_error_paths(ctx):
+    from paper_1507_08751_gb300 import binding as B
+    Y = torch.zeros((64, 64), dtype=torch.float32, device="cuda")
+    X = torch.empty((2, 64, 64), dtype=torch.float32, device="cuda")
+    with pytest.raises(B.MsllrError) as e:
+        ctx.msllr_decompose(Y, [(1, 1), (5, 5)], X, iters=2)
+    assert e.value.code == B.MSLLR_EINVAL
+    with pytest.raises(B.MsllrError) as e:
+        ctx.msllr_decompose(Y, [(1, 1), (64, 64)], X, lambdas=[1.0, -1.0], iters=2)
+    assert e.value.code == B.MSLLR_EINVAL
+    Ybad = Y.clone()
+    Ybad[3, 7] = float("nan")
+    with pytest.raises(B.MsllrError) as e:
+        ctx.msllr_decompose(Ybad, [(1, 1), (64, 64)], X, iters=2)
+    assert e.value.code == B.MSLLR_ENONFINITE
+    small = B.Context(0, hbm_budget_bytes=1 << 16)
+    with pytest.raises(B.MsllrError) as e:
+        small.msllr_decompose(Y, [(1, 1), (64, 64)], X, iters=2)
+    assert e.value.code == B.MSLLR_ENOMEM
+    small.close()
+    # the context still works after errors
+    ctx.msllr_decompose(Y, [(1, 1), (64, 64)], X, iters=2)
+    assert torch.all(X == 0)
