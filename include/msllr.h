@@ -82,7 +82,9 @@ typedef struct msllr_params {
 typedef struct msllr_stats {
   int iters;                                  /* iterations run               */
   int L;                                      /* scales                       */
-  double objective;                           /* sum_i lambda_i ||Z_i||_(i)   */
+  double objective;                           /* sum_i lambda_i ||Z_i||_(i),
+                                                 blocks taken on the grid of
+                                                 the last iteration's shift   */
   double primal_residual;                     /* ||X - Z||_F over all scales  */
   double scale_nuclear[MSLLR_MAX_SCALES];     /* ||Z_i||_(i) per scale        */
   long long blocks[MSLLR_MAX_SCALES];         /* blocks per scale             */

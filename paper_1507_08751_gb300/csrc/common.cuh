@@ -88,4 +88,20 @@ struct BlockGeom {
   }
 };
 
+// Optional per-phase timing (debug aid, enabled by the MSLLR_PHASE_TIMING
+// environment variable): thread 0 of every CTA adds clock64() deltas between
+// phase marks to acc[(slot * 16 + phase) * 2] and counts to the next entry.
+// Each translation unit holds its own pointer, set by set_phase_buffer_*().
+static __device__ unsigned long long* g_phase_acc = nullptr;
+#define PHASE_INIT() long long ph_t_ = (g_phase_acc && threadIdx.x == 0) ? clock64() : 0
+#define PHASE(slot, p)                                                         \
+  do {                                                                         \
+    if (g_phase_acc && threadIdx.x == 0) {                                     \
+      const long long t_ = clock64();                                          \
+      atomicAdd(&g_phase_acc[((slot) * 16 + (p)) * 2], (unsigned long long)(t_ - ph_t_)); \
+      atomicAdd(&g_phase_acc[((slot) * 16 + (p)) * 2 + 1], 1ull);              \
+      ph_t_ = t_;                                                              \
+    }                                                                          \
+  } while (0)
+
 }  // namespace msllr

@@ -15,6 +15,10 @@
 
 namespace msllr {
 
+cudaError_t set_phase_buffer_big(unsigned long long* p) {
+  return cudaMemcpyToSymbol(g_phase_acc, &p, sizeof(p));
+}
+
 namespace {
 
 constexpr int kTile = 64;       // Gram tile
@@ -148,7 +152,9 @@ gram_reduce_kernel(const float* __restrict__ part, float* __restrict__ G, int nn
   while (((ta + 1) * (ta + 2)) / 2 <= t) ++ta;
   while ((ta * (ta + 1)) / 2 > t) --ta;
   const int tc = t - (ta * (ta + 1)) / 2;
-  for (int e = threadIdx.x; e < kTile * kTile; e += blockDim.x) {
+  const int per = (kTile * kTile) / gridDim.z;
+  const int e0 = blockIdx.z * per;
+  for (int e = e0 + threadIdx.x; e < e0 + per; e += blockDim.x) {
     const int x = e / kTile, y = e - x * kTile;
     const int i = ta * kTile + x, j = tc * kTile + y;
     if (i >= nn || j >= nn) continue;
@@ -160,7 +166,8 @@ gram_reduce_kernel(const float* __restrict__ part, float* __restrict__ G, int nn
 }
 
 size_t eig_smem_bytes(int nn) {
-  return sizeof(float) * ((size_t)nn * (nn + 1) / 2 + 9 * kEigMax + 4 * kEigThreads + 64);
+  return sizeof(float) * ((((size_t)nn * (nn + 1) / 2 + 3) & ~(size_t)3) + 8 * kEigMax +
+                          9 * kEigMax + 4 * kEigThreads + 64);
 }
 
 __global__ void __launch_bounds__(kEigThreads)
@@ -173,7 +180,8 @@ eig_big_kernel(ScaleLaunch a, const float* __restrict__ Gall, float* __restrict_
   const float* Gg = Gall + (size_t)b * nn * nn;
   float* Y = Yall + (size_t)b * nn * nn;
   float* Gp = sm;
-  float* scr = Gp + (nn * (nn + 1)) / 2;
+  float* panel = Gp + (((nn * (nn + 1)) / 2 + 3) & ~3);  // NMAX x 8, 16-byte aligned
+  float* scr = panel + NMAX * 8;
   EigScratch s;
   s.d = scr;
   s.e = s.d + NMAX;
@@ -189,10 +197,12 @@ eig_big_kernel(ScaleLaunch a, const float* __restrict__ Gall, float* __restrict_
   s.xs = s.hi + NT;
   s.cnt = reinterpret_cast<int*>(s.xs + NT);
   s.red = reinterpret_cast<float*>(s.cnt + NT);
+  PHASE_INIT();
   LowerPacked Gacc{Gp};
   for (int i = warp; i < nn; i += NW)
     for (int j = lane; j <= i; j += 32) Gacc.at(i, j) = Gg[(size_t)i * nn + j];
   __syncthreads();
+  PHASE(3, 0);
   const float thr = a.tau * a.tau;
   bool skipped = false;
   if (a.skip_bound) {
@@ -206,14 +216,33 @@ eig_big_kernel(ScaleLaunch a, const float* __restrict__ Gall, float* __restrict_
     }
     tr = block_sum<NT>(tr, s.red);
     rs = block_max<NT>(rs, s.red);
-    if (fminf(tr, rs) <= thr) skipped = true;
+    const float bound = fminf(tr, rs);
+    if (bound <= thr) {
+      skipped = true;
+    } else {
+      // certified lambda_max(G) < tau^2 by Cholesky of (tau^2 - margin) I - G
+      const float margin = (float)nn * (float)nn * FLT_EPSILON * (thr + bound);
+      const float c = thr - margin;
+      if (c > 0.f && shifted_cholesky_pd<NT>(Gacc, nn, c, panel, s.cnt)) {
+        skipped = true;
+      } else {
+        __syncthreads();
+        for (int i = warp; i < nn; i += NW)
+          for (int j = lane; j <= i; j += 32) Gacc.at(i, j) = Gg[(size_t)i * nn + j];
+      }
+      __syncthreads();
+    }
   }
+  PHASE(3, 1);
   int k = 0;
   if (!skipped) {
     tridiagonalize<NT>(Gacc, nn, s);
+    PHASE(3, 2);
     float tn = 0.f;
     k = top_eigenvalues<NT>(nn, thr, s, &tn);
-    if (k > 0) top_eigenvectors<NT, NMAX>(Gacc, nn, k, tn, s, Y, nn);
+    PHASE(3, 3);
+    if (k > 0) top_eigenvectors<NT, NMAX>(Gacc, nn, k, tn, s, Y, nn, 3);
+    PHASE(3, 4);
   }
   if (k > 0) {
     // V_f = V diag(sqrt(f)), f = 1 - tau/sigma
@@ -312,7 +341,7 @@ size_t big_workspace_bytes(int M, int N, int m, int n) {
   if (d.chunks > 1) bytes += sizeof(float) * (size_t)d.nblocks * d.chunks * d.ntiles * kTile * kTile;
   bytes += sizeof(float) * (size_t)d.nblocks * d.nn * d.nn;  // Y
   bytes += sizeof(int) * (size_t)d.nblocks;
-  bytes += 4 * 256;  // alignment slack
+  bytes += 8 * 256;  // alignment slack for the carve below
   return bytes;
 }
 
@@ -360,8 +389,8 @@ cudaError_t launch_big(const ScaleLaunch& s, const BigWorkspace& ws, cudaStream_
   PROF_AFTER()
   if (d.chunks > 1) {
     PROF_BEFORE(KK_GRAM_REDUCE)
-    gram_reduce_kernel<<<dim3(d.ntiles, d.nblocks), 256, 0, st>>>(ws.part, ws.G, d.nn, d.ntiles,
-                                                                  d.chunks);
+    gram_reduce_kernel<<<dim3(d.ntiles, d.nblocks, 16), 256, 0, st>>>(ws.part, ws.G, d.nn,
+                                                                      d.ntiles, d.chunks);
     PROF_AFTER()
   }
   PROF_BEFORE(KK_EIG)

@@ -17,6 +17,10 @@ namespace msllr {
 cudaError_t launch_soft1x1(const ScaleLaunch& s, cudaStream_t st, Prof* prof);
 cudaError_t launch_big(const ScaleLaunch& s, const BigWorkspace& ws, cudaStream_t st, Prof* prof);
 
+cudaError_t set_phase_buffer_small(unsigned long long* p) {
+  return cudaMemcpyToSymbol(g_phase_acc, &p, sizeof(p));
+}
+
 namespace {
 
 // row index i of packed lower-triangle position e (e = i(i+1)/2 + j, j <= i)
@@ -31,6 +35,8 @@ template <int NT, int NMAX>
 __global__ void __launch_bounds__(NT) blocksvt_small_kernel(ScaleLaunch a) {
   extern __shared__ float sm[];
   const int tid = threadIdx.x;
+  constexpr int SLOT = NT == 32 ? 0 : (NT == 64 ? 1 : 2);
+  PHASE_INIT();
   const int nbn = a.N / a.n;
   BlockGeom g;
   g.M = a.M;
@@ -50,7 +56,9 @@ __global__ void __launch_bounds__(NT) blocksvt_small_kernel(ScaleLaunch a) {
   float* G = C + mm * nn;
   float* Y = G + nn * ldg;
   float* P = Y + nn * nn;
-  float* scr = P + mm * nn;
+  const int panel_off = (int)(P - sm) + mm * nn;
+  float* panel = sm + ((panel_off + 3) & ~3);  // NMAX x 8, 16-byte aligned (absolute offset)
+  float* scr = panel + NMAX * 8;
   EigScratch s;
   s.d = scr;
   s.e = s.d + NMAX;
@@ -80,6 +88,7 @@ __global__ void __launch_bounds__(NT) blocksvt_small_kernel(ScaleLaunch a) {
   }
   fro = block_sum<NT>(fro, s.red);
   if constexpr (NT == 32) __syncwarp();
+  PHASE(SLOT, 0);
   const float thr = a.tau * a.tau;
   int k = 0;
   bool skipped = false;
@@ -93,6 +102,7 @@ __global__ void __launch_bounds__(NT) blocksvt_small_kernel(ScaleLaunch a) {
       G[i * ldg + j] = acc;
     }
     __syncthreads();
+    PHASE(SLOT, 1);
     if (a.skip_bound) {
       // Gershgorin: sigma_max^2 = lambda_max(G) <= max_i sum_j |G_ij|
       float rs = 0.f;
@@ -104,15 +114,33 @@ __global__ void __launch_bounds__(NT) blocksvt_small_kernel(ScaleLaunch a) {
       }
       rs = block_max<NT>(rs, s.red);
       if constexpr (NT == 32) __syncwarp();
-      if (rs <= thr) skipped = true;
+      if (rs <= thr) {
+        skipped = true;
+      } else {
+        // certified lambda_max(G) < tau^2 by Cholesky of (tau^2 - margin) I - G
+        // on a copy of G (the Y region is free until the eigenvectors)
+        for (int e = tid; e < nn * nn; e += NT) {
+          const int i = e / nn, j = e - i * nn;
+          if (j <= i) Y[i * nn + j] = G[i * ldg + j];
+        }
+        __syncthreads();
+        const float margin = (float)(nn * nn) * FLT_EPSILON * (thr + rs);
+        const float c = thr - margin;
+        if (c > 0.f && shifted_cholesky_pd<NT>(LowerFull{Y, nn}, nn, c, panel, s.cnt)) skipped = true;
+        __syncthreads();
+      }
     }
   }
+  PHASE(SLOT, 2);
   if (!skipped) {
     LowerFull Gacc{G, ldg};
     tridiagonalize<NT>(Gacc, nn, s);
+    PHASE(SLOT, 3);
     float tn = 0.f;
     k = top_eigenvalues<NT>(nn, thr, s, &tn);
-    if (k > 0) top_eigenvectors<NT, NMAX>(Gacc, nn, k, tn, s, Y, ldy);
+    PHASE(SLOT, 4);
+    if (k > 0) top_eigenvectors<NT, NMAX>(Gacc, nn, k, tn, s, Y, ldy, SLOT);
+    PHASE(SLOT, 5);
   }
   const bool transposed = g.transposed();
   if (k == 0) {
@@ -156,6 +184,7 @@ __global__ void __launch_bounds__(NT) blocksvt_small_kernel(ScaleLaunch a) {
     a.Zout[off] = z;
     if (a.Wout) a.Wout[off] = 2.f * z - C[i * ldc + col];
   }
+  PHASE(SLOT, 6);
   if (tid == 0) {
     if (a.rank_out) a.rank_out[blockIdx.x] = k;
     if (a.nuc_acc) {
@@ -168,7 +197,8 @@ __global__ void __launch_bounds__(NT) blocksvt_small_kernel(ScaleLaunch a) {
 
 template <int NT, int NMAX>
 size_t small_smem_bytes(int mm, int nn) {
-  return sizeof(float) * ((size_t)2 * mm * nn + (size_t)nn * (2 * nn + 1) + 9 * NMAX + 4 * NT + 64);
+  return sizeof(float) * ((size_t)2 * mm * nn + (size_t)nn * (2 * nn + 1) + 8 * NMAX + 4 +
+                          9 * NMAX + 4 * NT + 64);
 }
 
 template <int NT, int NMAX>

@@ -3,6 +3,7 @@
 // eq:admm (Sec. 7) with the random cycle-spin Z-update (Sec. 9).
 #include <math.h>
 #include <stdio.h>
+#include <stdlib.h>
 #include <string.h>
 
 #include <string>
@@ -36,10 +37,16 @@ struct msllr_ctx {
   int* d_table = nullptr;
   size_t table_cap = 0;
 
+  // one stream per scale: the scales of an iteration are independent given R
+  cudaStream_t side[MSLLR_MAX_SCALES] = {};
+  cudaEvent_t ev_fork = nullptr;
+  cudaEvent_t ev_join[MSLLR_MAX_SCALES] = {};
+
   // cached graph of one iteration
   cudaGraphExec_t graph = nullptr;
   std::vector<char> graph_key;
   long long graph_launches[KK_COUNT][8] = {};
+  unsigned long long* d_phase = nullptr;  // MSLLR_PHASE_TIMING debug accumulators
 };
 
 namespace {
@@ -163,6 +170,19 @@ int msllr_create(msllr_ctx** out, int device, size_t hbm_budget_bytes, void* cud
       return bail(fail(ctx, MSLLR_ECUDA, "cudaStreamCreate"));
     ctx->own_stream = true;
   }
+  for (int i = 0; i < MSLLR_MAX_SCALES; ++i)
+    if (cudaStreamCreateWithFlags(&ctx->side[i], cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&ctx->ev_join[i], cudaEventDisableTiming) != cudaSuccess)
+      return bail(fail(ctx, MSLLR_ECUDA, "cudaStreamCreate (scale streams)"));
+  if (cudaEventCreateWithFlags(&ctx->ev_fork, cudaEventDisableTiming) != cudaSuccess)
+    return bail(fail(ctx, MSLLR_ECUDA, "cudaEventCreate"));
+  if (getenv("MSLLR_PHASE_TIMING")) {
+    if (cudaMalloc(&ctx->d_phase, 4 * 16 * 2 * sizeof(unsigned long long)) != cudaSuccess ||
+        cudaMemset(ctx->d_phase, 0, 4 * 16 * 2 * sizeof(unsigned long long)) != cudaSuccess ||
+        set_phase_buffer_small(ctx->d_phase) != cudaSuccess ||
+        set_phase_buffer_big(ctx->d_phase) != cudaSuccess)
+      return bail(fail(ctx, MSLLR_ECUDA, "phase timing buffer"));
+  }
   if (cudaMalloc(&ctx->d_small, 64 * sizeof(int)) != cudaSuccess ||
       cudaMalloc(&ctx->d_acc, (MSLLR_MAX_SCALES + 8) * sizeof(double)) != cudaSuccess ||
       cudaMalloc(&ctx->d_cnt, 2 * MSLLR_MAX_SCALES * sizeof(unsigned long long)) != cudaSuccess)
@@ -177,10 +197,33 @@ int msllr_destroy(msllr_ctx* ctx) {
   if (ctx->stream) cudaStreamSynchronize(ctx->stream);
   if (ctx->graph) cudaGraphExecDestroy(ctx->graph);
   if (ctx->ws) cudaFree(ctx->ws);
+  if (ctx->d_phase) {
+    unsigned long long h[4 * 16 * 2];
+    if (cudaMemcpy(h, ctx->d_phase, sizeof h, cudaMemcpyDeviceToHost) == cudaSuccess) {
+      static const char* names[4] = {"small32", "small64", "small128", "eig_big"};
+      for (int k = 0; k < 4; ++k) {
+        fprintf(stderr, "[msllr phase] %s:", names[k]);
+        for (int p = 0; p < 16; ++p)
+          if (h[(k * 16 + p) * 2 + 1])
+            fprintf(stderr, " p%d=%.0f(x%llu)", p,
+                    (double)h[(k * 16 + p) * 2] / (double)h[(k * 16 + p) * 2 + 1],
+                    h[(k * 16 + p) * 2 + 1]);
+        fprintf(stderr, "\n");
+      }
+    }
+    set_phase_buffer_small(nullptr);
+    set_phase_buffer_big(nullptr);
+    cudaFree(ctx->d_phase);
+  }
   if (ctx->d_small) cudaFree(ctx->d_small);
   if (ctx->d_acc) cudaFree(ctx->d_acc);
   if (ctx->d_cnt) cudaFree(ctx->d_cnt);
   if (ctx->d_table) cudaFree(ctx->d_table);
+  for (int i = 0; i < MSLLR_MAX_SCALES; ++i) {
+    if (ctx->side[i]) cudaStreamDestroy(ctx->side[i]);
+    if (ctx->ev_join[i]) cudaEventDestroy(ctx->ev_join[i]);
+  }
+  if (ctx->ev_fork) cudaEventDestroy(ctx->ev_fork);
   if (ctx->own_stream && ctx->stream) cudaStreamDestroy(ctx->stream);
   delete ctx;
   return MSLLR_OK;
@@ -283,7 +326,14 @@ int enqueue_iteration(msllr_ctx* ctx, const Layout& lay, int M, int N, int L, co
                       Prof* prof) {
   CK(launch_advance(ctx->d_table, ctx->d_small, ctx->d_small + 1, ctx->stream, prof));
   CK(launch_consensus(lay.Yd, lay.W, lay.R, lay.mask, L, lay.MN, ctx->stream, prof));
+  // fork: scale i > 0 runs on its own stream, scale 0 on the context stream.
+  // When kernels are timed one by one (profile), everything stays on the
+  // context stream so that each event pair brackets one kernel running alone.
+  const bool fork = !(prof && prof->timing);
+  if (fork) CK(cudaEventRecord(ctx->ev_fork, ctx->stream));
   for (int i = 0; i < L; ++i) {
+    cudaStream_t st = (i == 0 || !fork) ? ctx->stream : ctx->side[i];
+    if (i > 0 && fork) CK(cudaStreamWaitEvent(st, ctx->ev_fork, 0));
     ScaleLaunch s{};
     s.A1 = lay.Z + (size_t)i * lay.MN;
     s.A2 = lay.R;
@@ -301,8 +351,12 @@ int enqueue_iteration(msllr_ctx* ctx, const Layout& lay, int M, int N, int L, co
     s.nuc_acc = stats ? ctx->d_acc + i : nullptr;
     s.cnt = stats ? ctx->d_cnt + 2 * i : nullptr;
     prof->scale = i;
-    CK(launch_scale(s, lay.big[i], ctx->stream, prof));
+    CK(launch_scale(s, lay.big[i], st, prof));
+    if (i > 0 && fork) CK(cudaEventRecord(ctx->ev_join[i], st));
   }
+  // join
+  if (fork)
+    for (int i = 1; i < L; ++i) CK(cudaStreamWaitEvent(ctx->stream, ctx->ev_join[i], 0));
   return MSLLR_OK;
 }
 

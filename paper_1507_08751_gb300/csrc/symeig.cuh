@@ -64,19 +64,39 @@ template <int NT, class S>
 __device__ void tridiagonalize(S G, int n, EigScratch& s) {
   constexpr int NW = NT / 32;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  // Entries of a column below max(FLT_MIN, 2^-40 max_i |G_ii|) are treated as
+  // already zero: dropping them perturbs G far below FP32 rounding, and their
+  // reciprocal would overflow (denormal residues).
+  float gdiag = 0.f;
+  for (int i = tid; i < n; i += NT) gdiag = fmaxf(gdiag, fabsf(G.at(i, i)));
+  gdiag = block_max<NT>(gdiag, s.red);
+  if constexpr (NT == 32) __syncwarp();
+  const float negligible = fmaxf(FLT_MIN, gdiag * 9.094947e-13f);
   for (int j = 0; j < n - 2; ++j) {
     const int len = n - j - 1;
-    float part = 0.f;
+    // The reflector is scale invariant, so the column is scaled by its
+    // largest magnitude first: this keeps |x|^2 away from underflow (denormal
+    // residues) and overflow.
+    float amax = 0.f;
     for (int i = tid; i < len; i += NT) {
       const float x = G.at(j + 1 + i, j);
       s.vbuf[i] = x;
-      if (i > 0) part += x * x;
+      amax = fmaxf(amax, fabsf(x));
+    }
+    amax = block_max<NT>(amax, s.red);
+    if constexpr (NT == 32) __syncwarp();
+    const float inv = amax > negligible ? 1.f / amax : 0.f;
+    float part = 0.f;
+    for (int i = tid + 1; i < len; i += NT) {
+      const float x = s.vbuf[i] * inv;
+      part = fmaf(x, x, part);
     }
     const float sigma = block_sum<NT>(part, s.red);
     if constexpr (NT == 32) __syncwarp();
     const float x0 = s.vbuf[0];
     const float dj = G.at(j, j);
     if (sigma == 0.f) {
+      // the column is already a multiple of e_1 (to working precision)
       __syncthreads();
       if (tid == 0) {
         s.d[j] = dj;
@@ -86,16 +106,23 @@ __device__ void tridiagonalize(S G, int n, EigScratch& s) {
       __syncthreads();
       continue;
     }
-    const float xnorm = sqrtf(x0 * x0 + sigma);
-    const float alpha = (x0 >= 0.f) ? -xnorm : xnorm;
-    const float v0 = x0 - alpha;
+    const float x0s = x0 * inv;
+    const float xnorm = sqrtf(x0s * x0s + sigma);
+    const float alpha = (x0s >= 0.f) ? -xnorm : xnorm;
+    const float v0 = x0s - alpha;
     const float b = 2.f / (v0 * v0 + sigma);
     __syncthreads();
+    // scaled reflector v = (x / amax) - alpha e_1, H = I - b v v^T
+    for (int i = tid + 1; i < len; i += NT) {
+      const float x = s.vbuf[i] * inv;
+      s.vbuf[i] = x;
+      G.at(j + 1 + i, j) = x;
+    }
     if (tid == 0) {
       s.vbuf[0] = v0;
       G.at(j + 1, j) = v0;
       s.d[j] = dj;
-      s.e[j] = alpha;
+      s.e[j] = alpha * amax;
       s.beta[j] = b;
     }
     __syncthreads();
@@ -139,6 +166,101 @@ __device__ void tridiagonalize(S G, int n, EigScratch& s) {
     }
   }
   __syncthreads();
+}
+
+// ---------------------------------------------------------------------------
+// Certified test "lambda_max(A) < c": c I - A is positive definite iff its
+// Cholesky factorisation exists.  A is symmetric in the lower triangle of H
+// (n x n) and is overwritten.  Right-looking blocked Cholesky with panels of
+// 8 columns: the 8x8 diagonal block is factored by one thread, every row
+// below solves for its 8 panel entries independently, then a rank-8 update
+// of the trailing triangle.  `panel` is shared scratch of n * 8 floats and
+// `flag` one shared int.  Returns true iff every pivot was positive.
+// Rounding: a successful factorisation is exact for c I - A + E with
+// ||E||_2 <= n^2 eps ||c I - A||_2 (Cholesky backward error), so callers
+// subtract that margin from c.
+// ---------------------------------------------------------------------------
+template <int NT, class S>
+__device__ bool shifted_cholesky_pd(S H, int n, float c, float* panel, int* flag) {
+  constexpr int NW = NT / 32;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  for (int r = warp; r < n; r += NW)
+    for (int cc = lane; cc <= r; cc += 32) {
+      float& h = H.at(r, cc);
+      h = (r == cc ? c : 0.f) - h;
+    }
+  __syncthreads();
+  for (int j0 = 0; j0 < n; j0 += 8) {
+    const int jb = min(8, n - j0);
+    if (tid == 0) {
+      int ok = 1;
+      for (int j = 0; j < jb && ok; ++j) {
+        float d = H.at(j0 + j, j0 + j);
+        for (int t = 0; t < j; ++t) {
+          const float l = panel[(j0 + j) * 8 + t];
+          d -= l * l;
+        }
+        if (!(d > 0.f)) {
+          ok = 0;
+          break;
+        }
+        const float l = sqrtf(d);
+        panel[(j0 + j) * 8 + j] = l;
+        H.at(j0 + j, j0 + j) = l;
+        for (int i = j + 1; i < jb; ++i) {
+          float v = H.at(j0 + i, j0 + j);
+          for (int t = 0; t < j; ++t) v -= panel[(j0 + i) * 8 + t] * panel[(j0 + j) * 8 + t];
+          v /= l;
+          panel[(j0 + i) * 8 + j] = v;
+          H.at(j0 + i, j0 + j) = v;
+        }
+      }
+      *flag = ok;
+    }
+    __syncthreads();
+    if (!*flag) return false;
+    // rows below the diagonal block: forward substitution against it
+    for (int i = j0 + jb + tid; i < n; i += NT) {
+      float li[8];
+#pragma unroll
+      for (int j = 0; j < 8; ++j) {
+        if (j < jb) {
+          float v = H.at(i, j0 + j);
+          for (int t = 0; t < j; ++t) v -= li[t] * panel[(j0 + j) * 8 + t];
+          v /= panel[(j0 + j) * 8 + j];
+          li[j] = v;
+          H.at(i, j0 + j) = v;
+          panel[i * 8 + j] = v;
+        } else {
+          li[j] = 0.f;
+          panel[i * 8 + j] = 0.f;
+        }
+      }
+    }
+    __syncthreads();
+    // trailing update H(r, cc) -= sum_t L(r, t) L(cc, t), j0+jb <= cc <= r
+    const int t0 = j0 + jb;
+    for (int r = t0 + warp; r < n; r += NW) {
+      const float4 ra = *reinterpret_cast<const float4*>(panel + r * 8);
+      const float4 rb = *reinterpret_cast<const float4*>(panel + r * 8 + 4);
+      for (int cc = t0 + lane; cc <= r; cc += 32) {
+        const float4 ca = *reinterpret_cast<const float4*>(panel + cc * 8);
+        const float4 cb = *reinterpret_cast<const float4*>(panel + cc * 8 + 4);
+        float acc = ra.x * ca.x;
+        acc = fmaf(ra.y, ca.y, acc);
+        acc = fmaf(ra.z, ca.z, acc);
+        acc = fmaf(ra.w, ca.w, acc);
+        acc = fmaf(rb.x, cb.x, acc);
+        acc = fmaf(rb.y, cb.y, acc);
+        acc = fmaf(rb.z, cb.z, acc);
+        acc = fmaf(rb.w, cb.w, acc);
+        float& h = H.at(r, cc);
+        h -= acc;
+      }
+    }
+    __syncthreads();
+  }
+  return true;
 }
 
 // Number of eigenvalues of T (d, e2 = e^2) strictly below x (Sturm count via
@@ -326,8 +448,9 @@ __device__ void cluster_mgs(float* Y, int ldy, int n, int k, const int* clus, fl
 // ---------------------------------------------------------------------------
 template <int NT, int NMAX, class S>
 __device__ void top_eigenvectors(S G, int n, int k, float tnorm, EigScratch& s, float* Y,
-                                 int ldy) {
+                                 int ldy, int slot = 0) {
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  PHASE_INIT();
   constexpr int NW = NT / 32;
   TriLU<NMAX> lu;
   const float tiny = FLT_EPSILON * tnorm;
@@ -345,16 +468,20 @@ __device__ void top_eigenvectors(S G, int n, int k, float tnorm, EigScratch& s, 
     normalize_column(Y + tid, ldy, n);
   }
   __syncthreads();
+  PHASE(slot, 8);
   cluster_mgs<NT>(Y, ldy, n, k, s.clus, s.red);
   __syncthreads();
+  PHASE(slot, 9);
   if (tid < k) {
     for (int i = 0; i < n; ++i) Y[i * ldy + tid] *= tiny;
     lu.solve(Y + tid, ldy, n);
     normalize_column(Y + tid, ldy, n);
   }
   __syncthreads();
+  PHASE(slot, 10);
   cluster_mgs<NT>(Y, ldy, n, k, s.clus, s.red);
   __syncthreads();
+  PHASE(slot, 11);
   // back-transform v = H_0 (H_1 (... H_{n-3} y)), one warp per vector
   for (int q = warp; q < k; q += NW) {
     for (int j = n - 3; j >= 0; --j) {
@@ -368,6 +495,7 @@ __device__ void top_eigenvectors(S G, int n, int k, float tnorm, EigScratch& s, 
     }
   }
   __syncthreads();
+  PHASE(slot, 12);
 }
 
 }  // namespace msllr
