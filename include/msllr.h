@@ -177,6 +177,37 @@ int msllr_decompose_host(msllr_ctx* ctx, const float* Y, int M, int N, int ld,
                          const uint8_t* mask, const msllr_params* params,
                          float* X_out, float* Z_out, msllr_stats* stats);
 
+/* Bytes of the fixed device scratch used by msllr_blocksvt_noalloc. */
+#define MSLLR_NOALLOC_SCRATCH_BYTES (32 * 1024 * 1024)
+
+/* msllr_blocksvt without any device allocation.  The paper has no
+ * counterpart: this entry point exists for callers that cannot call
+ * cudaMalloc -- code running while a CUDA graph is being captured (where
+ * allocation is not allowed), processes whose device memory is handed out
+ * by their own pool and must not be touched by libraries, and loops that
+ * cannot afford the device-wide synchronisation cudaMalloc/cudaFree imply.
+ * It needs no msllr_ctx.
+ *
+ * Computes exactly what msllr_blocksvt computes, with the same argument
+ * meaning, on the stream `cuda_stream` (a cudaStream_t, or NULL for the
+ * legacy default stream) of the current CUDA device, and returns after
+ * that stream has finished the work.  Its workspace is one fixed array of
+ * MSLLR_NOALLOC_SCRATCH_BYTES in device memory that every GPU loading the
+ * library holds until the process exits; a call whose workspace would not
+ * fit (many or wide blocks; the 1x1 and narrow-block paths need almost
+ * none) fails with MSLLR_EINVAL and a message giving the size.
+ *
+ * The first call on a device does a one-time set-up on that device (it
+ * looks up the scratch's device address and sets kernel attributes); make
+ * that first call before any stream capture.  Every call shares the one
+ * scratch array and leaves its contents behind: calls that overlap on the
+ * GPU (other host threads, other streams) race and must be serialised by
+ * the caller.  Errors: EINVAL, ECUDA; the message is available from
+ * msllr_last_error(NULL). */
+int msllr_blocksvt_noalloc(const float* A, float* Z, int M, int N, int ld, int bm, int bn,
+                           double tau, int shift_r, int shift_c, int* block_rank_out,
+                           void* cuda_stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -36,8 +36,9 @@ STATUS_NAMES = {0: "MSLLR_OK", 1: "MSLLR_EINVAL", 2: "MSLLR_ENOMEM", 3: "MSLLR_E
 EXPORTS = (
     "msllr_params_default", "msllr_create", "msllr_destroy", "msllr_last_error",
     "msllr_shift_table", "msllr_lambda_default", "msllr_blocksvt", "msllr_decompose",
-    "msllr_decompose_host",
+    "msllr_decompose_host", "msllr_blocksvt_noalloc",
 )
+NOALLOC_SCRATCH_BYTES = 32 * 1024 * 1024
 
 
 class MsllrError(RuntimeError):
@@ -117,6 +118,7 @@ def lib():
                ctypes.POINTER(Stats)]
         L.msllr_decompose.argtypes = dec
         L.msllr_decompose_host.argtypes = dec
+        L.msllr_blocksvt_noalloc.argtypes = [vp, vp, ci, ci, ci, ci, ci, cd, ci, ci, vp, vp]
         for name in EXPORTS:
             getattr(L, name)
         _lib = L
@@ -157,6 +159,17 @@ def msllr_lambda_default(M, N, m, n):
     v = ctypes.c_double()
     _check(lib().msllr_lambda_default(M, N, m, n, ctypes.byref(v)))
     return v.value
+
+
+def msllr_blocksvt_noalloc(A, Z, bm, bn, tau, shift=(0, 0), rank_out=None, N=None, stream=None):
+    """Block SVT without any device allocation (no context needed): same result as
+    Context.msllr_blocksvt, using the library's fixed device scratch.  Runs on `stream`
+    (a cudaStream_t handle, or None for the default stream) of the current device."""
+    M, ld = A.shape[0], A.shape[1]
+    N = ld if N is None else N
+    st = ctypes.c_void_p(stream) if stream else None
+    _check(lib().msllr_blocksvt_noalloc(_ptr(A), _ptr(Z), M, N, ld, bm, bn, float(tau),
+                                        int(shift[0]), int(shift[1]), _ptr(rank_out), st))
 
 
 def msllr_params_default():

@@ -91,6 +91,9 @@ ScalePath choose_path(int m, int n);
 size_t big_workspace_bytes(int M, int N, int m, int n);
 BigWorkspace carve_big_workspace(void* base, int M, int N, int m, int n);
 
+// Message returned by msllr_last_error(NULL).
+void set_contextless_error(const char* msg);
+
 // Debug phase timing buffers (see PHASE in common.cuh).
 cudaError_t set_phase_buffer_small(unsigned long long* p);
 cudaError_t set_phase_buffer_big(unsigned long long* p);

@@ -20,6 +20,11 @@ std::string g_last_error = "";  // for calls made without a context
 
 }  // namespace
 
+namespace msllr {
+// Error message of calls made without a context (msllr_last_error(NULL)).
+void set_contextless_error(const char* msg) { g_last_error = msg; }
+}  // namespace msllr
+
 struct msllr_ctx {
   int device = 0;
   cudaStream_t stream = nullptr;
