@@ -335,6 +335,8 @@ def ours(a):
                                   if any(v)},
             "skipped_blocks_last_iter": stats["blocks_skipped"],
             "zero_rank_blocks_last_iter": stats["blocks_zero"],
+            "lanczos_blocks_last_iter": stats["blocks_lanczos"],
+            "householder_blocks_last_iter": stats["blocks_householder"],
             "clocks": ck,
             "cpu_baseline": cpu,
         }

@@ -61,9 +61,13 @@ typedef struct msllr_ctx msllr_ctx;
 /* Options of msllr_decompose.  Zero-initialise and call
  * msllr_params_default() to get the defaults listed per field. */
 typedef struct msllr_params {
-  int skip_bound;    /* 1 (default): skip the eigen-solve of a block whose
-                        upper bound on sigma_max is <= tau (Sec. 8); exact,
-                        results do not change.  0: never skip.            */
+  int skip_bound;    /* 1 (default): certified shortcuts -- skip a block whose
+                        upper bound on sigma_max is <= tau (Sec. 8: trace,
+                        Gershgorin, or a Cholesky of tau^2 I - G), and for
+                        wide blocks find the pairs above tau by certified
+                        Lanczos before falling back to Householder.
+                        0: every block takes the full Householder
+                        eigen-solve (reference path).                       */
   int cycle_spin;    /* 1 (default): one random circular shift per
                         iteration shared by all scales (Sec. 9).  0: none. */
   int use_graph;     /* 1 (default): replay one captured CUDA graph per
@@ -92,6 +96,8 @@ typedef struct msllr_stats {
   long long blocks_zero[MSLLR_MAX_SCALES];    /* blocks whose certified rank
                                                  above tau was 0 (incl. skip) */
   double lambda[MSLLR_MAX_SCALES];            /* lambda_i actually used       */
+  long long blocks_lanczos[MSLLR_MAX_SCALES]; /* eigenpairs by certified Lanczos */
+  long long blocks_householder[MSLLR_MAX_SCALES]; /* by the Householder path   */
   long long launches;                         /* kernels launched by the call */
   /* per kernel kind (see MSLLR_KERNEL_KINDS) and scale (kinds 0, 1 and 8
    * use scale slot 0): launches, and summed device time in ms when

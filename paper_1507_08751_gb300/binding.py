@@ -71,6 +71,8 @@ class Stats(ctypes.Structure):
         ("blocks_skipped", ctypes.c_longlong * MAX_SCALES),
         ("blocks_zero", ctypes.c_longlong * MAX_SCALES),
         ("lambda_", ctypes.c_double * MAX_SCALES),
+        ("blocks_lanczos", ctypes.c_longlong * MAX_SCALES),
+        ("blocks_householder", ctypes.c_longlong * MAX_SCALES),
         ("launches", ctypes.c_longlong),
         ("kernel_launches", (ctypes.c_longlong * MAX_SCALES) * len(KERNEL_KINDS)),
         ("kernel_ms", (ctypes.c_double * MAX_SCALES) * len(KERNEL_KINDS)),
@@ -88,6 +90,8 @@ class Stats(ctypes.Structure):
             "blocks_skipped": list(self.blocks_skipped[:L]),
             "blocks_zero": list(self.blocks_zero[:L]),
             "lambda": list(self.lambda_[:L]),
+            "blocks_lanczos": list(self.blocks_lanczos[:L]),
+            "blocks_householder": list(self.blocks_householder[:L]),
             "launches": self.launches,
             "kernel_launches": {k: list(self.kernel_launches[i][:max(L, 1)])
                                 for i, k in enumerate(KERNEL_KINDS)},

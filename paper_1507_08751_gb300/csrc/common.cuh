@@ -96,7 +96,7 @@ static __device__ unsigned long long* g_phase_acc = nullptr;
 #define PHASE_INIT() long long ph_t_ = (g_phase_acc && threadIdx.x == 0) ? clock64() : 0
 #define PHASE(slot, p)                                                         \
   do {                                                                         \
-    if (g_phase_acc && threadIdx.x == 0) {                                     \
+    if (g_phase_acc && threadIdx.x == 0 && (slot) >= 0) {                      \
       const long long t_ = clock64();                                          \
       atomicAdd(&g_phase_acc[((slot) * 16 + (p)) * 2], (unsigned long long)(t_ - ph_t_)); \
       atomicAdd(&g_phase_acc[((slot) * 16 + (p)) * 2 + 1], 1ull);              \

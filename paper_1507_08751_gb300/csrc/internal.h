@@ -25,17 +25,23 @@ struct ScaleLaunch {
   const int* shift;        // device int[2]: current (s_r, s_c)
   float tau;
   int skip_bound;
+  int warm_start;          // wide blocks: start Lanczos from the previous call's Ritz
+                           // vectors (only where the block grid does not move)
   int* rank_out;           // device, one int per block, or null
   double* nuc_acc;         // device, += sum over blocks of sum_j (sigma_j - tau)_+, or null
-  unsigned long long* cnt; // device [2]: blocks skipped by the bound, blocks of rank 0; or null
+  unsigned long long* cnt; // device [4]: blocks skipped by a bound, blocks of rank 0,
+                           // blocks solved by certified Lanczos, by Householder; or null
 };
 
 // Device workspace needed by the wide-block path for one scale.
 struct BigWorkspace {
   float* G;      // nblocks * nn * nn
   float* part;   // nblocks * chunks * ntiles * 64 * 64 (when chunks > 1)
-  float* Y;      // nblocks * nn * nn
+  float* Y;      // nblocks * ystride: eigenvectors / Lanczos scratch per block
   int* k;        // nblocks
+  float* warm;   // nblocks * 8 * nn: previous Ritz vectors (warm start)
+  int* kwarm;    // nblocks: how many of them (0 = none)
+  size_t ystride;
 };
 
 // Kernel kinds, for launch counting and per-kernel CUDA-event timing.
@@ -90,6 +96,8 @@ ScalePath choose_path(int m, int n);
 // Bytes of BigWorkspace a scale needs (0 for the other paths).
 size_t big_workspace_bytes(int M, int N, int m, int n);
 BigWorkspace carve_big_workspace(void* base, int M, int N, int m, int n);
+// Zero the warm-start counts of a scale's workspace (start of a decomposition).
+cudaError_t reset_warm_start(const BigWorkspace& w, int M, int N, int m, int n, cudaStream_t st);
 
 // Message returned by msllr_last_error(NULL).
 void set_contextless_error(const char* msg);

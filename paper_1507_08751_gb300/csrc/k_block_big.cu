@@ -11,6 +11,7 @@
 
 #include "common.cuh"
 #include "internal.h"
+#include "lanczos.cuh"
 #include "symeig.cuh"
 
 namespace msllr {
@@ -24,10 +25,10 @@ namespace {
 constexpr int kTile = 64;       // Gram tile
 constexpr int kChunk = 256;     // rows of C per Gram partial sum
 constexpr int kGramThreads = 256;
-constexpr int kEigThreads = 1024;
+constexpr int kEigThreads = 512;
 constexpr int kEigMax = 256;
 constexpr int kRebThreads = 256;
-constexpr int kRebElems = 8192;  // rows-per-slab * nn
+constexpr int kRebElems = 4096;  // rows-per-slab * nn
 constexpr int kKC = 16;          // eigenvectors per rebuild step
 
 struct BigDims {
@@ -165,23 +166,64 @@ gram_reduce_kernel(const float* __restrict__ part, float* __restrict__ G, int nn
   }
 }
 
+constexpr int kEigCT = kEigMax / 32;                   // symv column slots per lane
+constexpr int kEigRT = kEigMax / (kEigThreads / 32);   // symv rows per warp
+constexpr int kEigPart = (kEigThreads / 32) * 32 * kEigCT;
+// panel region: Cholesky panel, or Lanczos Q (kLzMaxJ x n) followed by the symv scratch
+constexpr int kEigPanelFloats =
+    (kPanelStride * kEigMax + 32 * 33 > kLzMaxJ * kEigMax + kEigPart)
+        ? kPanelStride * kEigMax + 32 * 33
+        : kLzMaxJ * kEigMax + kEigPart;
+
 size_t eig_smem_bytes(int nn) {
-  return sizeof(float) * ((((size_t)nn * (nn + 1) / 2 + 3) & ~(size_t)3) + 8 * kEigMax +
-                          9 * kEigMax + 4 * kEigThreads + 64);
+  return sizeof(float) * ((((size_t)nn * (nn + 1) / 2 + 3) & ~(size_t)3) + kEigPanelFloats +
+                          9 * kEigMax + 4 * kEigThreads + 64 + lz_scratch_floats(kEigMax, kLzMaxJ));
+}
+
+// Three power steps from a pseudo-random vector: true when the Rayleigh
+// quotient (a lower bound of lambda_max(G)) already exceeds thr, i.e. the
+// block certainly has a singular value above tau.
+template <class S>
+__device__ bool power_above(S G, int n, float thr, EigScratch& s, LzScratch& z) {
+  constexpr int NT = kEigThreads;
+  const int tid = threadIdx.x;
+  float part = 0.f;
+  for (int e = tid; e < n; e += NT) {
+    const float v = lz_hash(0xC0FFEEu, e) + 1.5f;
+    z.x[e] = v;
+    part = fmaf(v, v, part);
+  }
+  float nrm = sqrtf(block_sum<NT>(part, s.red));
+  float rq = 0.f;
+  for (int it = 0; it < 3; ++it) {
+    for (int e = tid; e < n; e += NT) z.x[e] /= nrm;
+    __syncthreads();
+    symv_lower<NT, kEigCT, kEigRT>(G, n, z.x, z.w, z.part);
+    float p1 = 0.f, p2 = 0.f;
+    for (int e = tid; e < n; e += NT) {
+      p1 = fmaf(z.x[e], z.w[e], p1);
+      p2 = fmaf(z.w[e], z.w[e], p2);
+    }
+    rq = block_sum<NT>(p1, s.red);
+    nrm = sqrtf(block_sum<NT>(p2, s.red));
+    if (rq > thr || !(nrm > 0.f)) break;
+    for (int e = tid; e < n; e += NT) z.x[e] = z.w[e];
+    __syncthreads();
+  }
+  return rq > thr;
 }
 
 __global__ void __launch_bounds__(kEigThreads)
-eig_big_kernel(ScaleLaunch a, const float* __restrict__ Gall, float* __restrict__ Yall,
-               int* __restrict__ kout) {
+eig_big_kernel(ScaleLaunch a, const float* __restrict__ Gall, BigWorkspace ws) {
   extern __shared__ float sm[];
   constexpr int NT = kEigThreads, NMAX = kEigMax, NW = NT / 32;
   const int b = blockIdx.x, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int nn = a.m >= a.n ? a.n : a.m;
   const float* Gg = Gall + (size_t)b * nn * nn;
-  float* Y = Yall + (size_t)b * nn * nn;
+  float* Y = ws.Y + (size_t)b * ws.ystride;
   float* Gp = sm;
-  float* panel = Gp + (((nn * (nn + 1)) / 2 + 3) & ~3);  // NMAX x 8, 16-byte aligned
-  float* scr = panel + NMAX * 8;
+  float* panel = Gp + (((nn * (nn + 1)) / 2 + 3) & ~3);  // NMAX x kPanelStride, 16-byte aligned
+  float* scr = panel + kEigPanelFloats;
   EigScratch s;
   s.d = scr;
   s.e = s.d + NMAX;
@@ -197,45 +239,87 @@ eig_big_kernel(ScaleLaunch a, const float* __restrict__ Gall, float* __restrict_
   s.xs = s.hi + NT;
   s.cnt = reinterpret_cast<int*>(s.xs + NT);
   s.red = reinterpret_cast<float*>(s.cnt + NT);
+  LzScratch z;
+  // Lanczos Q and the symv scratch share the panel region with the Cholesky
+  // panel; they are never live together
+  float* Qs = panel;
+  lz_bind<NT>(z, s.red + 64, NMAX, kLzMaxJ, panel + kLzMaxJ * NMAX);
   PHASE_INIT();
   LowerPacked Gacc{Gp};
-  for (int i = warp; i < nn; i += NW)
-    for (int j = lane; j <= i; j += 32) Gacc.at(i, j) = Gg[(size_t)i * nn + j];
-  __syncthreads();
+  auto load_g = [&]() {
+    for (int i = warp; i < nn; i += NW)
+      for (int j = lane; j <= i; j += 32) Gacc.at(i, j) = Gg[(size_t)i * nn + j];
+    __syncthreads();
+  };
+  load_g();
   PHASE(3, 0);
   const float thr = a.tau * a.tau;
+  // trace and Gershgorin bounds of lambda_max(G)
+  float tr = 0.f, rs = 0.f;
+  for (int i = tid; i < nn; i += NT) {
+    tr += Gacc.at(i, i);
+    float t = 0.f;
+    for (int j = 0; j <= i; ++j) t += fabsf(Gacc.at(i, j));
+    for (int j = i + 1; j < nn; ++j) t += fabsf(Gacc.at(j, i));
+    rs = fmaxf(rs, t);
+  }
+  tr = block_sum<NT>(tr, s.red);
+  rs = block_max<NT>(rs, s.red);
+  const float gbound = fminf(tr, rs);
+  const bool full = (a.m == a.M && a.n == a.N);
+  const int kwarm = (a.warm_start && (full || !a.shift)) ? min(ws.kwarm[b], kLzMaxK) : 0;
   bool skipped = false;
+  int k = -1;
   if (a.skip_bound) {
-    float tr = 0.f, rs = 0.f;
-    for (int i = tid; i < nn; i += NT) {
-      tr += Gacc.at(i, i);
-      float t = 0.f;
-      for (int j = 0; j <= i; ++j) t += fabsf(Gacc.at(i, j));
-      for (int j = i + 1; j < nn; ++j) t += fabsf(Gacc.at(j, i));
-      rs = fmaxf(rs, t);
-    }
-    tr = block_sum<NT>(tr, s.red);
-    rs = block_max<NT>(rs, s.red);
-    const float bound = fminf(tr, rs);
-    if (bound <= thr) {
+    if (gbound <= thr) {
       skipped = true;
-    } else {
+      k = 0;
+    } else if (kwarm == 0 && !power_above(Gacc, nn, thr, s, z)) {
       // certified lambda_max(G) < tau^2 by Cholesky of (tau^2 - margin) I - G
-      const float margin = (float)nn * (float)nn * FLT_EPSILON * (thr + bound);
+      const float margin = (float)nn * (float)nn * FLT_EPSILON * (thr + gbound);
       const float c = thr - margin;
-      if (c > 0.f && shifted_cholesky_pd<NT>(Gacc, nn, c, panel, s.cnt)) {
+      if (c > 0.f && shifted_cholesky_pd_nb<NT, 8>(Gacc, nn, c, panel, s.cnt, 3)) {
         skipped = true;
+        k = 0;
       } else {
-        __syncthreads();
-        for (int i = warp; i < nn; i += NW)
-          for (int j = lane; j <= i; j += 32) Gacc.at(i, j) = Gg[(size_t)i * nn + j];
+        load_g();
       }
-      __syncthreads();
     }
   }
   PHASE(3, 1);
-  int k = 0;
-  if (!skipped) {
+  bool lanczos_ok = false;
+  int ku = 0;
+  if (k < 0 && a.skip_bound) {
+    // Lanczos + residual + deflated-Cholesky certificate
+    const float* warm = ws.warm + (size_t)b * kLzMaxK * nn;
+    float* U = Y;
+    float* Wm = Y + (size_t)kLzMaxK * nn;
+    k = lanczos_certified<NT, kEigCT, kEigRT>(Gacc, LowerFull{const_cast<float*>(Gg), nn}, Gacc, nn,
+                                              thr, gbound, Qs, min(nn, kLzMaxJ), U, Wm, warm,
+                                              kwarm, 0x1234567u + 977u * b, s, z, panel, s.cnt,
+                                              &ku, 3);
+    lanczos_ok = k >= 0;
+    PHASE(3, 5);
+    if (lanczos_ok) {
+      // keep the Ritz vectors for the next call's warm start
+      float* wdst = ws.warm + (size_t)b * kLzMaxK * nn;
+      for (int e = tid; e < nn * ku; e += NT) wdst[e] = U[e];
+      if (tid == 0) ws.kwarm[b] = ku;
+      // V_f (row-major, ld nn) for the rebuild, staged through shared memory
+      for (int e = tid; e < nn * k; e += NT) panel[e] = U[e];
+      __syncthreads();
+      for (int e = tid; e < nn * k; e += NT) {
+        const int i = e / k, q = e - i * k;
+        const float sig = sqrtf(s.lam[q]);
+        Y[(size_t)i * nn + q] = panel[(size_t)q * nn + i] * sqrtf(fmaxf(1.f - a.tau / sig, 0.f));
+      }
+    } else {
+      load_g();
+    }
+  }
+  if (k < 0) {
+    // Householder fallback
+    if (tid == 0 && ws.kwarm) ws.kwarm[b] = 0;
     tridiagonalize<NT>(Gacc, nn, s);
     PHASE(3, 2);
     float tn = 0.f;
@@ -243,21 +327,23 @@ eig_big_kernel(ScaleLaunch a, const float* __restrict__ Gall, float* __restrict_
     PHASE(3, 3);
     if (k > 0) top_eigenvectors<NT, NMAX>(Gacc, nn, k, tn, s, Y, nn, 3);
     PHASE(3, 4);
-  }
-  if (k > 0) {
-    // V_f = V diag(sqrt(f)), f = 1 - tau/sigma
-    for (int e = tid; e < nn * k; e += NT) {
-      const int i = e / k, q = e - i * k;
-      const float sig = sqrtf(s.lam[q]);
-      Y[(size_t)i * nn + q] *= sqrtf(fmaxf(1.f - a.tau / sig, 0.f));
+    if (k > 0) {
+      // V_f = V diag(sqrt(f)), f = 1 - tau/sigma
+      for (int e = tid; e < nn * k; e += NT) {
+        const int i = e / k, q = e - i * k;
+        const float sig = sqrtf(s.lam[q]);
+        Y[(size_t)i * nn + q] *= sqrtf(fmaxf(1.f - a.tau / sig, 0.f));
+      }
     }
   }
   if (tid == 0) {
-    kout[b] = k;
+    ws.k[b] = k;
     if (a.rank_out) a.rank_out[b] = k;
     if (a.cnt) {
       if (skipped) atomicAdd(a.cnt, 1ull);
       if (k == 0) atomicAdd(a.cnt + 1, 1ull);
+      if (lanczos_ok) atomicAdd(a.cnt + 2, 1ull);
+      else if (!skipped) atomicAdd(a.cnt + 3, 1ull);
     }
     if (a.nuc_acc && k > 0) {
       double t = 0.0;
@@ -269,8 +355,8 @@ eig_big_kernel(ScaleLaunch a, const float* __restrict__ Gall, float* __restrict_
 
 // Z' = (C V_f) V_f^T for a slab of `rs` rows of C, W' = 2 Z' - A.
 __global__ void __launch_bounds__(kRebThreads)
-rebuild_kernel(ScaleLaunch a, const float* __restrict__ Yall, const int* __restrict__ kin,
-               int rs) {
+rebuild_kernel(ScaleLaunch a, const float* __restrict__ Yall, size_t ystride,
+               const int* __restrict__ kin, int rs) {
   extern __shared__ float sm[];
   const int b = blockIdx.y, tid = threadIdx.x;
   const BlockGeom g = make_geom(a, b);
@@ -278,10 +364,12 @@ rebuild_kernel(ScaleLaunch a, const float* __restrict__ Yall, const int* __restr
   const int r0 = blockIdx.x * rs;
   const int rows = min(rs, mm - r0);
   const int k = kin[b];
-  float* Cs = sm;                 // rows x nn
-  float* Vs = Cs + rs * nn;       // nn x kKC
-  float* Ps = Vs + nn * kKC;      // rows x kKC
+  float* Cs = sm;                          // rows x nn
+  float* Vs = Cs + rs * nn;                // kKC x (nn + 1): V_f chunk, transposed
+  float* Ps = Vs + kKC * (nn + 1);         // rows x kKC
+  const int ldv = nn + 1;
   const int nel = rows * nn;
+#pragma unroll 4
   for (int e = tid; e < nel; e += kRebThreads) {
     const int i = e / nn, c = e - i * nn;
     Cs[e] = load_a(a, c_offset(g, r0 + i, c));
@@ -291,19 +379,28 @@ rebuild_kernel(ScaleLaunch a, const float* __restrict__ Yall, const int* __restr
   float acc[EL];
 #pragma unroll
   for (int t = 0; t < EL; ++t) acc[t] = 0.f;
-  const float* Yb = Yall + (size_t)b * nn * nn;
+  const float* Yb = Yall + (size_t)b * ystride;
   for (int q0 = 0; q0 < k; q0 += kKC) {
     const int kc = min(kKC, k - q0);
     for (int e = tid; e < nn * kKC; e += kRebThreads) {
       const int i = e / kKC, j = e - i * kKC;
-      Vs[e] = j < kc ? Yb[(size_t)i * nn + q0 + j] : 0.f;
+      Vs[j * ldv + i] = j < kc ? Yb[(size_t)i * nn + q0 + j] : 0.f;
     }
     __syncthreads();
     for (int e = tid; e < rows * kKC; e += kRebThreads) {
       const int i = e / kKC, j = e - i * kKC;
-      float t = 0.f;
-      for (int c = 0; c < nn; ++c) t = fmaf(Cs[i * nn + c], Vs[c * kKC + j], t);
-      Ps[e] = t;
+      const float* crow = Cs + i * nn;
+      const float* vrow = Vs + j * ldv;
+      float t0 = 0.f, t1 = 0.f, t2 = 0.f, t3 = 0.f;
+      int c = 0;
+      for (; c + 3 < nn; c += 4) {
+        t0 = fmaf(crow[c], vrow[c], t0);
+        t1 = fmaf(crow[c + 1], vrow[c + 1], t1);
+        t2 = fmaf(crow[c + 2], vrow[c + 2], t2);
+        t3 = fmaf(crow[c + 3], vrow[c + 3], t3);
+      }
+      for (; c < nn; ++c) t0 = fmaf(crow[c], vrow[c], t0);
+      Ps[e] = (t0 + t1) + (t2 + t3);
     }
     __syncthreads();
 #pragma unroll
@@ -313,7 +410,7 @@ rebuild_kernel(ScaleLaunch a, const float* __restrict__ Yall, const int* __restr
         const int i = e / nn, c = e - i * nn;
         float z = acc[t];
 #pragma unroll
-        for (int j = 0; j < kKC; ++j) z = fmaf(Ps[i * kKC + j], Vs[c * kKC + j], z);
+        for (int j = 0; j < kKC; ++j) z = fmaf(Ps[i * kKC + j], Vs[j * ldv + c], z);
         acc[t] = z;
       }
     }
@@ -333,14 +430,21 @@ rebuild_kernel(ScaleLaunch a, const float* __restrict__ Yall, const int* __restr
 
 }  // namespace
 
+static size_t y_stride(int nn) {
+  const size_t a = (size_t)nn * nn, b = (size_t)(kLzMaxJ + 2 * kLzMaxK) * nn;
+  return ((a > b ? a : b) + 63) & ~(size_t)63;
+}
+
 size_t big_workspace_bytes(int M, int N, int m, int n) {
   if (choose_path(m, n) != ScalePath::Big) return 0;
   const BigDims d = big_dims(M, N, m, n);
   size_t bytes = 0;
   bytes += sizeof(float) * (size_t)d.nblocks * d.nn * d.nn;  // G
   if (d.chunks > 1) bytes += sizeof(float) * (size_t)d.nblocks * d.chunks * d.ntiles * kTile * kTile;
-  bytes += sizeof(float) * (size_t)d.nblocks * d.nn * d.nn;  // Y
-  bytes += sizeof(int) * (size_t)d.nblocks;
+  bytes += sizeof(float) * (size_t)d.nblocks * y_stride(d.nn);  // Y
+  bytes += sizeof(int) * (size_t)d.nblocks;                      // k
+  bytes += sizeof(float) * (size_t)d.nblocks * kLzMaxK * d.nn;   // warm
+  bytes += sizeof(int) * (size_t)d.nblocks;                      // kwarm
   bytes += 8 * 256;  // alignment slack for the carve below
   return bytes;
 }
@@ -360,15 +464,26 @@ BigWorkspace carve_big_workspace(void* base, int M, int N, int m, int n) {
     w.part = (float*)p;
     p = align256(p + sizeof(float) * (size_t)d.nblocks * d.chunks * d.ntiles * kTile * kTile);
   }
+  w.ystride = y_stride(d.nn);
   w.Y = (float*)p;
-  p = align256(p + sizeof(float) * (size_t)d.nblocks * d.nn * d.nn);
+  p = align256(p + sizeof(float) * (size_t)d.nblocks * w.ystride);
   w.k = (int*)p;
+  p = align256(p + sizeof(int) * (size_t)d.nblocks);
+  w.warm = (float*)p;
+  p = align256(p + sizeof(float) * (size_t)d.nblocks * kLzMaxK * d.nn);
+  w.kwarm = (int*)p;
   return w;
+}
+
+cudaError_t reset_warm_start(const BigWorkspace& w, int M, int N, int m, int n, cudaStream_t st) {
+  if (!w.kwarm) return cudaSuccess;
+  const BigDims d = big_dims(M, N, m, n);
+  return cudaMemsetAsync(w.kwarm, 0, sizeof(int) * (size_t)d.nblocks, st);
 }
 
 cudaError_t configure_big_kernels() {
   cudaError_t e = cudaFuncSetAttribute(eig_big_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       200 * 1024);
+                                       (int)eig_smem_bytes(kEigMax));
   if (e != cudaSuccess) return e;
   return cudaFuncSetAttribute(rebuild_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                               100 * 1024);
@@ -394,13 +509,13 @@ cudaError_t launch_big(const ScaleLaunch& s, const BigWorkspace& ws, cudaStream_
     PROF_AFTER()
   }
   PROF_BEFORE(KK_EIG)
-  eig_big_kernel<<<d.nblocks, kEigThreads, eig_smem_bytes(d.nn), st>>>(s, ws.G, ws.Y, ws.k);
+  eig_big_kernel<<<d.nblocks, kEigThreads, eig_smem_bytes(d.nn), st>>>(s, ws.G, ws);
   PROF_AFTER()
   const int rs = kRebElems / d.nn;
   const int slabs = (d.mm + rs - 1) / rs;
-  const size_t smem = sizeof(float) * ((size_t)rs * d.nn + (size_t)d.nn * kKC + (size_t)rs * kKC);
+  const size_t smem = sizeof(float) * ((size_t)rs * d.nn + (size_t)(d.nn + 1) * kKC + (size_t)rs * kKC);
   PROF_BEFORE(KK_REBUILD)
-  rebuild_kernel<<<dim3(slabs, d.nblocks), kRebThreads, smem, st>>>(s, ws.Y, ws.k, rs);
+  rebuild_kernel<<<dim3(slabs, d.nblocks), kRebThreads, smem, st>>>(s, ws.Y, ws.ystride, ws.k, rs);
   PROF_AFTER()
 #undef PROF_BEFORE
 #undef PROF_AFTER

@@ -10,6 +10,7 @@
 
 #include "common.cuh"
 #include "internal.h"
+#include "lanczos.cuh"
 #include "symeig.cuh"
 
 namespace msllr {
@@ -55,10 +56,10 @@ __global__ void __launch_bounds__(NT) blocksvt_small_kernel(ScaleLaunch a) {
   float* C = sm;
   float* G = C + mm * nn;
   float* Y = G + nn * ldg;
-  float* P = Y + nn * nn;
+  float* P = Y + nn * (nn + 1);  // Y region holds nn x (nn + 1)
   const int panel_off = (int)(P - sm) + mm * nn;
   float* panel = sm + ((panel_off + 3) & ~3);  // NMAX x 8, 16-byte aligned (absolute offset)
-  float* scr = panel + NMAX * 8;
+  float* scr = panel + NMAX * kPanelStride + 32 * 33;
   EigScratch s;
   s.d = scr;
   s.e = s.d + NMAX;
@@ -74,6 +75,15 @@ __global__ void __launch_bounds__(NT) blocksvt_small_kernel(ScaleLaunch a) {
   s.xs = s.hi + NT;
   s.cnt = reinterpret_cast<int*>(s.xs + NT);
   s.red = reinterpret_cast<float*>(s.cnt + NT);
+  // Lanczos region: Q (NMAX x JCAP), U and W (NMAX x kLzMaxK each), symv scratch
+  constexpr int JCAP = NMAX < kLzMaxJ ? NMAX : kLzMaxJ;
+  constexpr int CT = (NMAX + 31) / 32, RT = NMAX / (NT / 32);
+  float* Qs = s.red + 64;
+  float* Us = Qs + NMAX * JCAP;
+  float* Ws = Us + NMAX * kLzMaxK;
+  float* part = Ws + NMAX * kLzMaxK;
+  LzScratch z;
+  lz_bind<NT>(z, part + (NT / 32) * 32 * CT, NMAX, JCAP, part);
 
   // gather A = A1 + A2 on the shifted grid; ||C||_F^2
   const int melem = a.m * a.n;
@@ -92,6 +102,7 @@ __global__ void __launch_bounds__(NT) blocksvt_small_kernel(ScaleLaunch a) {
   const float thr = a.tau * a.tau;
   int k = 0;
   bool skipped = false;
+  float gbound = fro;  // trace(G) >= lambda_max(G)
   if (a.skip_bound && fro <= thr) skipped = true;
   if (!skipped) {
     const int ntri = nn * (nn + 1) / 2;
@@ -114,6 +125,7 @@ __global__ void __launch_bounds__(NT) blocksvt_small_kernel(ScaleLaunch a) {
       }
       rs = block_max<NT>(rs, s.red);
       if constexpr (NT == 32) __syncwarp();
+      gbound = fminf(gbound, rs);
       if (rs <= thr) {
         skipped = true;
       } else {
@@ -121,18 +133,38 @@ __global__ void __launch_bounds__(NT) blocksvt_small_kernel(ScaleLaunch a) {
         // on a copy of G (the Y region is free until the eigenvectors)
         for (int e = tid; e < nn * nn; e += NT) {
           const int i = e / nn, j = e - i * nn;
-          if (j <= i) Y[i * nn + j] = G[i * ldg + j];
+          if (j <= i) Y[i * (nn + 1) + j] = G[i * ldg + j];
         }
         __syncthreads();
         const float margin = (float)(nn * nn) * FLT_EPSILON * (thr + rs);
         const float c = thr - margin;
-        if (c > 0.f && shifted_cholesky_pd<NT>(LowerFull{Y, nn}, nn, c, panel, s.cnt)) skipped = true;
+        if (c > 0.f && shifted_cholesky_pd_nb<NT, 8>(LowerFull{Y, nn + 1}, nn, c, panel, s.cnt))
+          skipped = true;
         __syncthreads();
       }
     }
   }
   PHASE(SLOT, 2);
-  if (!skipped) {
+  bool lanczos_ok = false;
+  if (!skipped && a.skip_bound) {
+    // certified Lanczos; P G P and its Cholesky go to the Y region, G stays
+    int ku = 0;
+    k = lanczos_certified<NT, CT, RT>(LowerFull{G, ldg}, LowerFull{G, ldg}, LowerFull{Y, nn + 1}, nn,
+                                      thr, gbound, Qs, nn < JCAP ? nn : JCAP, Us, Ws, nullptr, 0,
+                                      0x51ED27u + 131u * blockIdx.x, s, z, panel, s.cnt, &ku);
+    lanczos_ok = k >= 0;
+    if (lanczos_ok) {
+      for (int e = tid; e < nn * k; e += NT) {
+        const int i = e / k, q = e - i * k;
+        Y[i * ldy + q] = Us[q * nn + i];
+      }
+      __syncthreads();
+    } else {
+      k = 0;
+    }
+  }
+  PHASE(SLOT, 7);
+  if (!skipped && !lanczos_ok) {
     LowerFull Gacc{G, ldg};
     tridiagonalize<NT>(Gacc, nn, s);
     PHASE(SLOT, 3);
@@ -155,6 +187,8 @@ __global__ void __launch_bounds__(NT) blocksvt_small_kernel(ScaleLaunch a) {
       if (a.cnt) {
         if (skipped) atomicAdd(a.cnt, 1ull);
         atomicAdd(a.cnt + 1, 1ull);
+        if (lanczos_ok) atomicAdd(a.cnt + 2, 1ull);
+        else if (!skipped) atomicAdd(a.cnt + 3, 1ull);
       }
     }
     return;
@@ -187,6 +221,10 @@ __global__ void __launch_bounds__(NT) blocksvt_small_kernel(ScaleLaunch a) {
   PHASE(SLOT, 6);
   if (tid == 0) {
     if (a.rank_out) a.rank_out[blockIdx.x] = k;
+    if (a.cnt) {
+      if (lanczos_ok) atomicAdd(a.cnt + 2, 1ull);
+      else atomicAdd(a.cnt + 3, 1ull);
+    }
     if (a.nuc_acc) {
       double t = 0.0;
       for (int q = 0; q < k; ++q) t += (double)s.lo[q];
@@ -197,8 +235,12 @@ __global__ void __launch_bounds__(NT) blocksvt_small_kernel(ScaleLaunch a) {
 
 template <int NT, int NMAX>
 size_t small_smem_bytes(int mm, int nn) {
-  return sizeof(float) * ((size_t)2 * mm * nn + (size_t)nn * (2 * nn + 1) + 8 * NMAX + 4 +
-                          9 * NMAX + 4 * NT + 64);
+  constexpr int JCAP = NMAX < kLzMaxJ ? NMAX : kLzMaxJ;
+  constexpr int CT = (NMAX + 31) / 32;
+  return sizeof(float) * ((size_t)2 * mm * nn + (size_t)nn * (2 * nn + 2) + kPanelStride * NMAX +
+                          32 * 33 +
+                          4 + 9 * NMAX + 4 * NT + 64 + NMAX * JCAP + 2 * NMAX * kLzMaxK +
+                          (NT / 32) * 32 * CT + lz_scratch_floats(NMAX, JCAP));
 }
 
 template <int NT, int NMAX>

@@ -1,0 +1,395 @@
+// Certified top eigenpairs of a block's Gram matrix G = C^T C without a full
+// tridiagonalisation, for the block SVT (eq:svt): SVT needs only the
+// eigenpairs with lambda > tau^2.
+//
+//  1. Lanczos with full reorthogonalisation (Golub & Van Loan, Sec. 10.1)
+//     builds an orthonormal Q_J and the tridiagonal T_J = Q_J^T G Q_J.  The
+//     start vector is either pseudo-random or the sum of the previous
+//     iteration's Ritz vectors (warm start).  On breakdown the process is
+//     continued from a random vector orthogonal to Q_J.
+//  2. Ritz pairs of T_J above 0.95 tau^2: Sturm-count multisection and
+//     inverse iteration on T_J (symeig.cuh), U = Q_J Y.
+//  3. Explicit residuals: W = G U, B = U^T W, rho = ||W - U diag(B)||_F.
+//  4. Certificate: with P = I - U U^T, every eigenvalue of G lies within
+//     2 rho of an eigenvalue of diag(B) (+) (P G P restricted to range P)
+//     (Weyl, block form in the basis [U, U_perp]).  If the Cholesky of
+//     (tau^2 - 2 rho - margins) I - P G P succeeds, no eigenvalue of G
+//     outside span(U) exceeds tau^2, so the eigenpairs above tau^2 are the
+//     Ritz pairs above tau^2 (up to pairs within 2 rho of tau^2, whose
+//     thresholded contribution is below rho / tau).
+// If any step fails (too many pairs, no convergence, certificate refused),
+// the caller falls back to the Householder path.
+#pragma once
+
+#include <float.h>
+
+#include "common.cuh"
+#include "symeig.cuh"
+
+namespace msllr {
+
+constexpr int kLzMaxJ = 32;  // Lanczos steps
+constexpr int kLzMaxK = 8;   // Ritz pairs kept (above 0.95 tau^2)
+
+// Shared-memory scratch of the Lanczos path.
+struct LzScratch {
+  float* x;      // [n] current Lanczos vector q_j
+  float* w;      // [n] G q_j, then the next residual
+  float* qprev;  // [n] q_{j-1}
+  float* alpha;  // [kLzMaxJ]
+  float* beta;   // [kLzMaxJ]
+  float* h;      // [kLzMaxJ + 8] reorthogonalisation coefficients
+  float* ty;     // [jcap * kLzMaxK] eigenvectors of T_J (row i, column q)
+  float* lu;     // [4 * jcap * kLzMaxK] inverse-iteration LU factors
+  unsigned* piv; // [2 * kLzMaxK] pivot bits
+  float* Bm;     // [kLzMaxK * kLzMaxK] U^T G U
+  float* part;   // symv scratch (NW * 32 * CT floats)
+  int jcap;      // row capacity of ty / lu (>= Lanczos steps)
+};
+
+// floats of LzScratch for a given n capacity and J capacity
+__host__ __device__ constexpr int lz_scratch_floats(int nmax, int jcap) {
+  return 3 * nmax + 2 * kLzMaxJ + (kLzMaxJ + 8) + jcap * kLzMaxK + 4 * jcap * kLzMaxK +
+         2 * kLzMaxK + kLzMaxK * kLzMaxK;
+}
+
+template <int NT>
+__device__ void lz_bind(LzScratch& z, float* base, int nmax, int jcap, float* part) {
+  z.x = base;
+  z.w = z.x + nmax;
+  z.qprev = z.w + nmax;
+  z.alpha = z.qprev + nmax;
+  z.beta = z.alpha + kLzMaxJ;
+  z.h = z.beta + kLzMaxJ;
+  z.ty = z.h + kLzMaxJ + 8;
+  z.lu = z.ty + jcap * kLzMaxK;
+  z.piv = reinterpret_cast<unsigned*>(z.lu + 4 * jcap * kLzMaxK);
+  z.Bm = reinterpret_cast<float*>(z.piv + 2 * kLzMaxK);
+  z.part = part;
+  z.jcap = jcap;
+}
+
+__device__ __forceinline__ float lz_hash(uint32_t seed, int i) {
+  uint32_t h = seed * 0x9E3779B9u + (uint32_t)i * 0x85EBCA6Bu + 0x27D4EB2Fu;
+  h ^= h >> 15;
+  h *= 0x2C1B3C6Du;
+  h ^= h >> 12;
+  h *= 0x297A2D39u;
+  h ^= h >> 15;
+  return (float)(h >> 8) * (2.f / 16777216.f) - 1.f;
+}
+
+// Orthogonalise the shared vector w (n) against Q's columns 0..nq-1 (column
+// j at Q + j*n, shared) twice, classical Gram-Schmidt per pass.
+template <int NT>
+__device__ void lz_reorth(float* w, const float* Q, int n, int nq, float* h) {
+  constexpr int NW = NT / 32;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  for (int pass = 0; pass < 2; ++pass) {
+    for (int i = warp; i < nq; i += NW) {
+      float d = 0.f;
+      for (int e = lane; e < n; e += 32) d = fmaf(Q[i * n + e], w[e], d);
+      d = warp_sum(d);
+      if (lane == 0) h[i] = d;
+    }
+    __syncthreads();
+    for (int e = tid; e < n; e += NT) {
+      float v = w[e];
+      for (int i = 0; i < nq; ++i) v = fmaf(-h[i], Q[i * n + e], v);
+      w[e] = v;
+    }
+    __syncthreads();
+  }
+}
+
+// Inverse iteration on T (s.d, s.e, size J) for the k shifts s.shf[0..k),
+// one thread per target, LU factors in shared memory; eigenvectors into ty
+// (row i, column q, stride kLzMaxK), orthonormalised inside clusters.
+template <int NT>
+__device__ void lz_tri_vectors(int J, int k, float tnorm, EigScratch& s, LzScratch& z) {
+  const int tid = threadIdx.x;
+  const float tiny = FLT_EPSILON * tnorm;
+  constexpr int ST = kLzMaxK;
+  float* dd = z.lu;
+  float* du = dd + z.jcap * ST;
+  float* du2 = du + z.jcap * ST;
+  float* dl = du2 + z.jcap * ST;
+  for (int pass = 0; pass < 2; ++pass) {
+    if (tid < k) {
+      const int q = tid;
+      if (pass == 0) {
+        const float shift = s.shf[q];
+        for (int i = 0; i < J; ++i) dd[i * ST + q] = s.d[i] - shift;
+        for (int i = 0; i < J - 1; ++i) {
+          du[i * ST + q] = s.e[i];
+          dl[i * ST + q] = s.e[i];
+          du2[i * ST + q] = 0.f;
+        }
+        unsigned bits[2] = {0u, 0u};
+        for (int i = 0; i < J - 1; ++i) {
+          const float di = dd[i * ST + q], li = dl[i * ST + q];
+          if (fabsf(di) >= fabsf(li)) {
+            const float dv = (di == 0.f) ? tiny : di;
+            dd[i * ST + q] = dv;
+            const float f = li / dv;
+            dl[i * ST + q] = f;
+            dd[(i + 1) * ST + q] -= f * du[i * ST + q];
+          } else {
+            const float f = di / li;
+            dd[i * ST + q] = li;
+            dl[i * ST + q] = f;
+            const float t = du[i * ST + q];
+            du[i * ST + q] = dd[(i + 1) * ST + q];
+            dd[(i + 1) * ST + q] = t - f * dd[(i + 1) * ST + q];
+            if (i < J - 2) {
+              du2[i * ST + q] = du[(i + 1) * ST + q];
+              du[(i + 1) * ST + q] = -f * du[(i + 1) * ST + q];
+            }
+            bits[i >> 5] |= 1u << (i & 31);
+          }
+        }
+        for (int i = 0; i < J; ++i) {
+          const float v = dd[i * ST + q];
+          if (fabsf(v) < tiny) dd[i * ST + q] = v < 0.f ? -tiny : tiny;
+        }
+        z.piv[2 * q] = bits[0];
+        z.piv[2 * q + 1] = bits[1];
+        for (int i = 0; i < J; ++i) z.ty[i * ST + q] = tiny * lz_hash(977u + q, i);
+      } else {
+        for (int i = 0; i < J; ++i) z.ty[i * ST + q] *= tiny;
+      }
+      // solve (T - shift I) y = y
+      const unsigned b0 = z.piv[2 * q], b1 = z.piv[2 * q + 1];
+      float* y = z.ty + q;
+      for (int i = 0; i < J - 1; ++i) {
+        const float a = y[i * ST], b = y[(i + 1) * ST];
+        const bool pv = (i < 32) ? ((b0 >> i) & 1u) : ((b1 >> (i - 32)) & 1u);
+        if (pv) {
+          y[i * ST] = b;
+          y[(i + 1) * ST] = a - dl[i * ST + q] * b;
+        } else {
+          y[(i + 1) * ST] = b - dl[i * ST + q] * a;
+        }
+      }
+      y[(J - 1) * ST] /= dd[(J - 1) * ST + q];
+      if (J > 1)
+        y[(J - 2) * ST] = (y[(J - 2) * ST] - du[(J - 2) * ST + q] * y[(J - 1) * ST]) / dd[(J - 2) * ST + q];
+      for (int i = J - 3; i >= 0; --i)
+        y[i * ST] = (y[i * ST] - du[i * ST + q] * y[(i + 1) * ST] - du2[i * ST + q] * y[(i + 2) * ST]) /
+                    dd[i * ST + q];
+      normalize_column(y, ST, J);
+    }
+    __syncthreads();
+    cluster_mgs<NT>(z.ty, ST, J, k, s.clus, s.red);
+    __syncthreads();
+  }
+}
+
+// Ritz values of T_J above thr (descending) into s.lam and their vectors
+// into z.ty.  Returns the count (a count above kLzMaxK means "too many").
+template <int NT>
+__device__ int lz_ritz(int J, float thr, EigScratch& s, LzScratch& z, float* tnorm_out) {
+  const int tid = threadIdx.x;
+  for (int i = tid; i < J; i += NT) {
+    s.d[i] = z.alpha[i];
+    s.e[i] = (i < J - 1) ? z.beta[i] : 0.f;
+  }
+  __syncthreads();
+  float tn = 0.f;
+  const int k = top_eigenvalues<NT>(J, thr, s, &tn);
+  *tnorm_out = tn;
+  if (k == 0 || k > kLzMaxK) return k;
+  lz_tri_vectors<NT>(J, k, tn, s, z);
+  return k;
+}
+
+// Gershgorin bound max_i sum_j |A_ij| of a symmetric matrix in lower storage.
+template <int NT, class S>
+__device__ float gershgorin_lower(S A, int n, float* red) {
+  float rs = 0.f;
+  for (int i = threadIdx.x; i < n; i += NT) {
+    float t = 0.f;
+    for (int j = 0; j <= i; ++j) t += fabsf(A.at(i, j));
+    for (int j = i + 1; j < n; ++j) t += fabsf(A.at(j, i));
+    rs = fmaxf(rs, t);
+  }
+  return block_max<NT>(rs, red);
+}
+
+// The whole Lanczos + certificate path.
+//  Gs  G in lower storage, read only (the Lanczos operator);
+//  Gr  G in lower storage, read only (source for P G P; may equal Gs);
+//  Gd  lower storage receiving P G P and then its Cholesky factor (may
+//      equal Gs only if Gs is not needed afterwards).
+//  Q   shared scratch of jmax * n floats (column j at Q + j*n), jmax <= n.
+//  U, Wm  scratch of kLzMaxK * n floats each (column-major, any memory).
+//  warm / kwarm: previous Ritz vectors (column-major n x kwarm) or kwarm = 0.
+//  gbound: an upper bound of ||G||_2.
+// On success returns k >= 0 (pairs above thr) with s.lam[0..k) and the
+// vectors in U's columns 0..k-1 (U holds ku >= k kept pairs, *ku_out = ku).
+// Returns -1 when the caller must fall back.
+template <int NT, int CT, int RT, class SG, class SR, class SD>
+__device__ int lanczos_certified(SG Gs, SR Gr, SD Gd, int n, float thr, float gbound, float* Q,
+                                 int jmax, float* U, float* Wm, const float* warm, int kwarm,
+                                 uint32_t seed, EigScratch& s, LzScratch& z, float* panel,
+                                 int* flag, int* ku_out, int slot = -1) {
+  constexpr int NW = NT / 32;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  PHASE_INIT();
+  const float thr_keep = 0.95f * thr;  // pairs kept in U (deflated)
+
+  // start vector
+  float part = 0.f;
+  for (int e = tid; e < n; e += NT) {
+    float v = 0.f;
+    for (int i = 0; i < kwarm; ++i) v += warm[(size_t)i * n + e] * (1.f + 0.25f * i);
+    v += 1e-3f * lz_hash(seed, e);
+    z.x[e] = v;
+    part = fmaf(v, v, part);
+  }
+  const float nrm = sqrtf(block_sum<NT>(part, s.red));
+  for (int e = tid; e < n; e += NT) {
+    z.x[e] /= nrm;
+    Q[e] = z.x[e];
+    z.qprev[e] = 0.f;
+  }
+  __syncthreads();
+  const int jmin = min(jmax, kwarm > 0 ? kwarm + 3 : 8);
+  int J = 0, k = -1;
+  float tn = 0.f;
+  float beta_prev = 0.f;
+  uint32_t restart = 1;
+  PHASE(slot, 6);
+  for (int j = 0; j < jmax; ++j) {
+    symv_lower<NT, CT, RT>(Gs, n, z.x, z.w, z.part);
+    PHASE(slot, 7);
+    part = 0.f;
+    for (int e = tid; e < n; e += NT) part = fmaf(z.x[e], z.w[e], part);
+    const float a = block_sum<NT>(part, s.red);
+    for (int e = tid; e < n; e += NT) z.w[e] = z.w[e] - a * z.x[e] - beta_prev * z.qprev[e];
+    __syncthreads();
+    PHASE(slot, 8);
+    lz_reorth<NT>(z.w, Q, n, j + 1, z.h);
+    PHASE(slot, 9);
+    part = 0.f;
+    for (int e = tid; e < n; e += NT) part = fmaf(z.w[e], z.w[e], part);
+    float b = sqrtf(block_sum<NT>(part, s.red));
+    if (tid == 0) {
+      z.alpha[j] = a;
+      z.beta[j] = b;
+    }
+    J = j + 1;
+    if (J == n) break;  // Q spans everything: T_J is similar to G
+    if (J < jmax) {
+      if (!(b > 1e-5f * gbound)) {
+        // breakdown: an invariant subspace was found; continue from a random
+        // direction orthogonal to it
+        for (int e = tid; e < n; e += NT) z.w[e] = lz_hash(seed + 7919u * restart, e);
+        ++restart;
+        __syncthreads();
+        lz_reorth<NT>(z.w, Q, n, j + 1, z.h);
+        part = 0.f;
+        for (int e = tid; e < n; e += NT) part = fmaf(z.w[e], z.w[e], part);
+        const float bn = sqrtf(block_sum<NT>(part, s.red));
+        if (!(bn > 0.f)) break;
+        if (tid == 0) z.beta[j] = 0.f;
+        b = bn;
+        beta_prev = 0.f;
+      } else {
+        beta_prev = b;
+      }
+      for (int e = tid; e < n; e += NT) {
+        z.qprev[e] = z.x[e];
+        const float q = z.w[e] / b;
+        z.x[e] = q;
+        Q[(j + 1) * n + e] = q;
+      }
+      __syncthreads();
+    }
+    PHASE(slot, 10);
+    if (J >= jmin && ((J - jmin) % 4 == 0 || J == jmax)) {
+      // converged when every kept Ritz pair has |beta_J * y_{J-1}| small
+      k = lz_ritz<NT>(J, thr_keep, s, z, &tn);
+      PHASE(slot, 11);
+      if (k > kLzMaxK) return -1;
+      bool conv = true;
+      const float bJ = z.beta[J - 1];
+      for (int q = 0; q < k; ++q)
+        if (fabsf(bJ * z.ty[(J - 1) * kLzMaxK + q]) > 1e-5f * fmaxf(s.lam[0], thr)) conv = false;
+      if (conv) break;
+      k = -1;
+    }
+  }
+  if (k < 0) {
+    k = lz_ritz<NT>(J, thr_keep, s, z, &tn);
+    if (k > kLzMaxK) return -1;
+  }
+  const int ku = k;
+  // U = Q_J Y (n x ku)
+  for (int e = tid; e < n * ku; e += NT) {
+    const int q = e / n, r = e - q * n;
+    float v = 0.f;
+    for (int jj = 0; jj < J; ++jj) v = fmaf(Q[jj * n + r], z.ty[jj * kLzMaxK + q], v);
+    U[(size_t)q * n + r] = v;
+  }
+  __syncthreads();
+  // W = G U, B = U^T W, rho
+  for (int q = 0; q < ku; ++q) {
+    for (int e = tid; e < n; e += NT) z.x[e] = U[(size_t)q * n + e];
+    __syncthreads();
+    symv_lower<NT, CT, RT>(Gs, n, z.x, z.w, z.part);
+    for (int e = tid; e < n; e += NT) Wm[(size_t)q * n + e] = z.w[e];
+    __syncthreads();
+  }
+  for (int pq = warp; pq < ku * ku; pq += NW) {
+    const int p = pq / ku, q = pq - p * ku;
+    float d = 0.f;
+    for (int e = lane; e < n; e += 32) d = fmaf(U[(size_t)p * n + e], Wm[(size_t)q * n + e], d);
+    d = warp_sum(d);
+    if (lane == 0) z.Bm[p * kLzMaxK + q] = d;
+  }
+  __syncthreads();
+  part = 0.f;
+  for (int e = tid; e < n * ku; e += NT) {
+    const int q = e / n, r = e - q * n;
+    const float rr = Wm[(size_t)q * n + r] - z.Bm[q * kLzMaxK + q] * U[(size_t)q * n + r];
+    part = fmaf(rr, rr, part);
+  }
+  const float rho = sqrtf(block_sum<NT>(part, s.red));
+  // kept pairs: Rayleigh quotients, count above thr; pairs above thr first
+  int kk = 0;
+  for (int q = 0; q < ku; ++q) {
+    const float th = z.Bm[q * kLzMaxK + q];
+    kk += th > thr;
+    if (q > 0 && th > thr && !(z.Bm[(q - 1) * kLzMaxK + (q - 1)] > thr)) return -1;
+  }
+  const float c0 = thr - 2.f * rho - 8.f * (float)(ku + 1) * FLT_EPSILON * gbound;
+  if (!(c0 > 0.f)) return -1;
+  __syncthreads();
+  if (tid < ku) s.lam[tid] = z.Bm[tid * kLzMaxK + tid];
+  // P G P = G - U W^T - W U^T + U B U^T (lower triangle) into Gd
+  for (int r = warp; r < n; r += NW) {
+    for (int cc = lane; cc <= r; cc += 32) {
+      float v = Gr.at(r, cc);
+      for (int p = 0; p < ku; ++p) {
+        const float ur = U[(size_t)p * n + r], uc = U[(size_t)p * n + cc];
+        v -= ur * Wm[(size_t)p * n + cc] + Wm[(size_t)p * n + r] * uc;
+        float ub = 0.f;
+        for (int q = 0; q < ku; ++q) ub = fmaf(z.Bm[p * kLzMaxK + q], U[(size_t)q * n + cc], ub);
+        v = fmaf(ur, ub, v);
+      }
+      Gd.at(r, cc) = v;
+    }
+  }
+  __syncthreads();
+  // Cholesky backward error is bounded by n^2 eps ||c I - PGP||
+  const float gd = gershgorin_lower<NT>(Gd, n, s.red);
+  const float c = c0 - (float)n * (float)n * FLT_EPSILON * (c0 + gd);
+  if (!(c > 0.f)) return -1;
+  PHASE(slot, 11);
+  if (!shifted_cholesky_pd_nb<NT, 8>(Gd, n, c, panel, flag, slot)) return -1;
+  *ku_out = ku;
+  return kk;
+}
+
+}  // namespace msllr

@@ -190,7 +190,7 @@ int msllr_create(msllr_ctx** out, int device, size_t hbm_budget_bytes, void* cud
   }
   if (cudaMalloc(&ctx->d_small, 64 * sizeof(int)) != cudaSuccess ||
       cudaMalloc(&ctx->d_acc, (MSLLR_MAX_SCALES + 8) * sizeof(double)) != cudaSuccess ||
-      cudaMalloc(&ctx->d_cnt, 2 * MSLLR_MAX_SCALES * sizeof(unsigned long long)) != cudaSuccess)
+      cudaMalloc(&ctx->d_cnt, 4 * MSLLR_MAX_SCALES * sizeof(unsigned long long)) != cudaSuccess)
     return bail(fail(ctx, MSLLR_ENOMEM, "cudaMalloc of context scalars"));
   *out = ctx;
   return MSLLR_OK;
@@ -352,9 +352,10 @@ int enqueue_iteration(msllr_ctx* ctx, const Layout& lay, int M, int N, int L, co
     s.shift = p.cycle_spin ? ctx->d_small + 1 : nullptr;
     s.tau = taus[i];
     s.skip_bound = p.skip_bound;
+    s.warm_start = 1;
     s.rank_out = nullptr;
     s.nuc_acc = stats ? ctx->d_acc + i : nullptr;
-    s.cnt = stats ? ctx->d_cnt + 2 * i : nullptr;
+    s.cnt = stats ? ctx->d_cnt + 4 * i : nullptr;
     prof->scale = i;
     CK(launch_scale(s, lay.big[i], st, prof));
     if (i > 0 && fork) CK(cudaEventRecord(ctx->ev_join[i], st));
@@ -434,8 +435,9 @@ int decompose_device(msllr_ctx* ctx, const float* Y, int M, int N, int ld, int L
   CK(cudaMemcpyAsync(ctx->d_table, h_table.data(), tab * sizeof(int), cudaMemcpyHostToDevice, st));
   CK(cudaMemsetAsync(ctx->d_small, 0, sizeof(int), st));
   CK(launch_init_state(p.Z_init, p.U_init, lay.Z, lay.W, L, lay.MN, st, &prof));
+  for (int i = 0; i < L; ++i) CK(reset_warm_start(lay.big[i], M, N, bm[i], bn[i], st));
   CK(cudaMemsetAsync(ctx->d_acc, 0, (MSLLR_MAX_SCALES + 8) * sizeof(double), st));
-  CK(cudaMemsetAsync(ctx->d_cnt, 0, 2 * MSLLR_MAX_SCALES * sizeof(unsigned long long), st));
+  CK(cudaMemsetAsync(ctx->d_cnt, 0, 4 * MSLLR_MAX_SCALES * sizeof(unsigned long long), st));
 
   // iterations 0 .. iters-2 (graph replay), the last one with statistics
   const int plain_iters = iters > 0 ? iters - 1 : 0;
@@ -494,7 +496,7 @@ int decompose_device(msllr_ctx* ctx, const float* Y, int M, int N, int ld, int L
   if (Z_out)
     CK(cudaMemcpyAsync(Z_out, lay.Z, sizeof(float) * L * lay.MN, cudaMemcpyDeviceToDevice, st));
   double acc[MSLLR_MAX_SCALES + 8];
-  unsigned long long cnt[2 * MSLLR_MAX_SCALES];
+  unsigned long long cnt[4 * MSLLR_MAX_SCALES];
   CK(cudaMemcpyAsync(acc, ctx->d_acc, sizeof acc, cudaMemcpyDeviceToHost, st));
   CK(cudaMemcpyAsync(cnt, ctx->d_cnt, sizeof cnt, cudaMemcpyDeviceToHost, st));
   CK(cudaStreamSynchronize(st));
@@ -507,8 +509,10 @@ int decompose_device(msllr_ctx* ctx, const float* Y, int M, int N, int ld, int L
       stats->scale_nuclear[i] = acc[i];
       obj += lam[i] * acc[i];
       stats->blocks[i] = (long long)(M / bm[i]) * (N / bn[i]);
-      stats->blocks_skipped[i] = (long long)cnt[2 * i];
-      stats->blocks_zero[i] = (long long)cnt[2 * i + 1];
+      stats->blocks_skipped[i] = (long long)cnt[4 * i];
+      stats->blocks_zero[i] = (long long)cnt[4 * i + 1];
+      stats->blocks_lanczos[i] = (long long)cnt[4 * i + 2];
+      stats->blocks_householder[i] = (long long)cnt[4 * i + 3];
       stats->lambda[i] = lam[i];
     }
     stats->objective = obj;

@@ -172,95 +172,333 @@ __device__ void tridiagonalize(S G, int n, EigScratch& s) {
 // Certified test "lambda_max(A) < c": c I - A is positive definite iff its
 // Cholesky factorisation exists.  A is symmetric in the lower triangle of H
 // (n x n) and is overwritten.  Right-looking blocked Cholesky with panels of
-// 8 columns: the 8x8 diagonal block is factored by one thread, every row
-// below solves for its 8 panel entries independently, then a rank-8 update
-// of the trailing triangle.  `panel` is shared scratch of n * 8 floats and
-// `flag` one shared int.  Returns true iff every pivot was positive.
+// 32 columns: warp 0 factors the 32x32 diagonal block in registers (lane i
+// owns row i), every row below solves for its 32 panel entries on its own,
+// then a rank-32 update of the trailing triangle.  `panel` is shared scratch
+// of n * kPanelStride + 32 * 33 floats (16-byte aligned) and `flag` one
+// shared int.
+// Returns true iff every pivot was positive.
 // Rounding: a successful factorisation is exact for c I - A + E with
 // ||E||_2 <= n^2 eps ||c I - A||_2 (Cholesky backward error), so callers
 // subtract that margin from c.
 // ---------------------------------------------------------------------------
+constexpr int kPanel = 32;
+constexpr int kPanelStride = 36;  // floats; 4-bank skew keeps 128-bit loads conflict-free
+
 template <int NT, class S>
-__device__ bool shifted_cholesky_pd(S H, int n, float c, float* panel, int* flag) {
+__device__ bool shifted_cholesky_pd(S H, int n, float c, float* panel, int* flag, int slot = -1) {
   constexpr int NW = NT / 32;
+  constexpr int LD = kPanelStride;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  float* linv = panel + n * LD;  // 32 x 33: inverse of the diagonal block
+  PHASE_INIT();
   for (int r = warp; r < n; r += NW)
     for (int cc = lane; cc <= r; cc += 32) {
       float& h = H.at(r, cc);
       h = (r == cc ? c : 0.f) - h;
     }
   __syncthreads();
-  for (int j0 = 0; j0 < n; j0 += 8) {
-    const int jb = min(8, n - j0);
-    if (tid == 0) {
+  PHASE(slot, 12);
+  for (int j0 = 0; j0 < n; j0 += kPanel) {
+    const int jb = min(kPanel, n - j0);
+    if (warp == 0) {
+      // factor the diagonal block in panel rows j0..j0+jb-1 (lane = row)
+      float* D = panel + j0 * LD;
+      if (lane < jb)
+        for (int t = 0; t < kPanel; ++t) D[lane * LD + t] = (t <= lane) ? H.at(j0 + lane, j0 + t) : 0.f;
+      __syncwarp();
       int ok = 1;
-      for (int j = 0; j < jb && ok; ++j) {
-        float d = H.at(j0 + j, j0 + j);
-        for (int t = 0; t < j; ++t) {
-          const float l = panel[(j0 + j) * 8 + t];
-          d -= l * l;
+      for (int j = 0; j < jb; ++j) {
+        const float dj = D[j * LD + j];
+        ok &= (dj > 0.f);
+        const float l = sqrtf(dj > 0.f ? dj : 1.f);
+        __syncwarp();
+        if (lane == j) D[j * LD + j] = l;
+        else if (lane > j && lane < jb) D[lane * LD + j] *= 1.f / l;
+        __syncwarp();
+        if (lane > j && lane < jb) {
+          const float lij = D[lane * LD + j];
+          for (int t = j + 1; t <= lane; ++t) D[lane * LD + t] = fmaf(-lij, D[t * LD + j], D[lane * LD + t]);
         }
-        if (!(d > 0.f)) {
-          ok = 0;
-          break;
-        }
-        const float l = sqrtf(d);
-        panel[(j0 + j) * 8 + j] = l;
-        H.at(j0 + j, j0 + j) = l;
-        for (int i = j + 1; i < jb; ++i) {
-          float v = H.at(j0 + i, j0 + j);
-          for (int t = 0; t < j; ++t) v -= panel[(j0 + i) * 8 + t] * panel[(j0 + j) * 8 + t];
-          v /= l;
-          panel[(j0 + i) * 8 + j] = v;
-          H.at(j0 + i, j0 + j) = v;
-        }
+        __syncwarp();
       }
-      *flag = ok;
+      // inverse of the diagonal block, one column per lane
+      if (lane < jb) {
+        for (int i = 0; i < lane; ++i) linv[i * 33 + lane] = 0.f;
+        linv[lane * 33 + lane] = 1.f / D[lane * LD + lane];
+        for (int i = lane + 1; i < jb; ++i) {
+          float acc = 0.f;
+          for (int u = lane; u < i; ++u) acc = fmaf(D[i * LD + u], linv[u * 33 + lane], acc);
+          linv[i * 33 + lane] = -acc / D[i * LD + i];
+        }
+        for (int t = 0; t <= lane; ++t) H.at(j0 + lane, j0 + t) = D[lane * LD + t];
+      }
+      if (lane == 0) *flag = ok;
     }
     __syncthreads();
+    PHASE(slot, 13);
     if (!*flag) return false;
-    // rows below the diagonal block: forward substitution against it
+    // rows below: L(i, :) = H(i, :) L11^{-T}, in place in the panel row,
+    // columns in decreasing order (column t needs H(i, 0..t) only)
     for (int i = j0 + jb + tid; i < n; i += NT) {
-      float li[8];
+      float* row = panel + i * LD;
+      for (int u = 0; u < kPanel; ++u) row[u] = (u < jb) ? H.at(i, j0 + u) : 0.f;
+      for (int t = jb - 1; t >= 0; --t) {
+        float acc = 0.f;
+        for (int u = 0; u <= t; ++u) acc = fmaf(row[u], linv[t * 33 + u], acc);
+        row[t] = acc;
+        H.at(i, j0 + t) = acc;
+      }
+    }
+    __syncthreads();
+    PHASE(slot, 14);
+    // trailing update H(r, cc) -= sum_t L(r, t) L(cc, t), j0+jb <= cc <= r.
+    // Work items are (32-row group, 32-column chunk) pairs of the trailing
+    // triangle; lanes own rows (their panel row in registers) and read the
+    // column's panel row as a broadcast.
+    const int t0 = j0 + jb;
+    const int ngroups = (n - t0 + 31) >> 5;
+    const int nitems = ngroups * (ngroups + 1) / 2;
+    for (int it = warp; it < nitems; it += NW) {
+      int g = (int)((sqrtf(8.f * it + 1.f) - 1.f) * 0.5f);
+      while (((g + 1) * (g + 2)) / 2 <= it) ++g;
+      while ((g * (g + 1)) / 2 > it) --g;
+      const int q = it - (g * (g + 1)) / 2;
+      const int r = t0 + 32 * g + lane;
+      const bool rvalid = r < n;
+      float4 pr[kPanel / 4];
 #pragma unroll
-      for (int j = 0; j < 8; ++j) {
-        if (j < jb) {
-          float v = H.at(i, j0 + j);
-          for (int t = 0; t < j; ++t) v -= li[t] * panel[(j0 + j) * 8 + t];
-          v /= panel[(j0 + j) * 8 + j];
-          li[j] = v;
-          H.at(i, j0 + j) = v;
-          panel[i * 8 + j] = v;
-        } else {
-          li[j] = 0.f;
-          panel[i * 8 + j] = 0.f;
+      for (int u = 0; u < kPanel / 4; ++u)
+        pr[u] = rvalid ? *reinterpret_cast<const float4*>(panel + r * LD + 4 * u)
+                       : make_float4(0.f, 0.f, 0.f, 0.f);
+      const int c_begin = t0 + 32 * q;
+      const int c_end = min(c_begin + 32, n);
+      for (int cc = c_begin; cc < c_end; ++cc) {
+        float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f;
+#pragma unroll
+        for (int u = 0; u < kPanel / 4; ++u) {
+          const float4 pc = *reinterpret_cast<const float4*>(panel + cc * LD + 4 * u);
+          a0 = fmaf(pr[u].x, pc.x, a0);
+          a1 = fmaf(pr[u].y, pc.y, a1);
+          a2 = fmaf(pr[u].z, pc.z, a2);
+          a3 = fmaf(pr[u].w, pc.w, a3);
+        }
+        if (rvalid && cc <= r) {
+          float& h = H.at(r, cc);
+          h -= (a0 + a1) + (a2 + a3);
         }
       }
     }
     __syncthreads();
-    // trailing update H(r, cc) -= sum_t L(r, t) L(cc, t), j0+jb <= cc <= r
-    const int t0 = j0 + jb;
-    for (int r = t0 + warp; r < n; r += NW) {
-      const float4 ra = *reinterpret_cast<const float4*>(panel + r * 8);
-      const float4 rb = *reinterpret_cast<const float4*>(panel + r * 8 + 4);
-      for (int cc = t0 + lane; cc <= r; cc += 32) {
-        const float4 ca = *reinterpret_cast<const float4*>(panel + cc * 8);
-        const float4 cb = *reinterpret_cast<const float4*>(panel + cc * 8 + 4);
-        float acc = ra.x * ca.x;
-        acc = fmaf(ra.y, ca.y, acc);
-        acc = fmaf(ra.z, ca.z, acc);
-        acc = fmaf(ra.w, ca.w, acc);
-        acc = fmaf(rb.x, cb.x, acc);
-        acc = fmaf(rb.y, cb.y, acc);
-        acc = fmaf(rb.z, cb.z, acc);
-        acc = fmaf(rb.w, cb.w, acc);
-        float& h = H.at(r, cc);
-        h -= acc;
-      }
-    }
-    __syncthreads();
+    PHASE(slot, 15);
   }
   return true;
+}
+
+// ---------------------------------------------------------------------------
+// Same test with narrow panels of PB (8 or 16) columns: the PB x PB diagonal
+// block is factored in registers by lanes 0..PB-1 of warp 0 (one row each,
+// fully unrolled -- little code), its inverse is formed one column per
+// lane, rows below multiply by it, and the rank-PB trailing update has lanes
+// owning rows and reading each column's panel row as a broadcast.
+// `panel` needs n * (PB + 4) + PB * (PB + 1) floats (16-byte aligned).
+// ---------------------------------------------------------------------------
+template <int NT, int PB, class S>
+__device__ bool shifted_cholesky_pd_nb(S H, int n, float c, float* panel, int* flag, int slot = -1) {
+  constexpr int NW = NT / 32;
+  constexpr int LD = PB + 4;
+  static_assert(PB == 8 || PB == 16, "panel width");
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  float* linv = panel + n * LD;  // PB x (PB + 1)
+  PHASE_INIT();
+  for (int r = warp; r < n; r += NW)
+    for (int cc = lane; cc <= r; cc += 32) {
+      float& h = H.at(r, cc);
+      h = (r == cc ? c : 0.f) - h;
+    }
+  __syncthreads();
+  PHASE(slot, 12);
+  for (int j0 = 0; j0 < n; j0 += PB) {
+    const int jb = min(PB, n - j0);
+    if (warp == 0) {
+      float row[PB];
+#pragma unroll
+      for (int t = 0; t < PB; ++t)
+        row[t] = (lane < jb) ? ((t <= lane) ? H.at(j0 + lane, j0 + t) : 0.f)
+                             : (t == lane ? 1.f : 0.f);
+      int ok = 1;
+#pragma unroll
+      for (int j = 0; j < PB; ++j) {
+        const float dj = __shfl_sync(0xffffffffu, row[j], j);
+        ok &= (dj > 0.f);
+        const float l = sqrtf(dj > 0.f ? dj : 1.f);
+        const float inv = 1.f / l;
+        row[j] = (lane == j) ? l : ((lane > j) ? row[j] * inv : row[j]);
+#pragma unroll
+        for (int t = j + 1; t < PB; ++t) {
+          const float ltj = __shfl_sync(0xffffffffu, row[j], t);
+          if (lane >= t) row[t] = fmaf(-row[j], ltj, row[t]);
+        }
+      }
+      // L11 to the panel and H; inverse column `lane` of L11 by forward substitution
+      if (lane < jb) {
+#pragma unroll
+        for (int t = 0; t < PB; ++t) {
+          panel[(j0 + lane) * LD + t] = (t <= lane) ? row[t] : 0.f;
+          if (t <= lane) H.at(j0 + lane, j0 + t) = row[t];
+        }
+      }
+      __syncwarp();
+      if (lane < jb) {
+        const float* D = panel + j0 * LD;
+        float x[PB];
+#pragma unroll
+        for (int i = 0; i < PB; ++i) {
+          float v = 0.f;
+          if (i == lane) v = 1.f / D[i * LD + i];
+          else if (i > lane && i < jb) {
+            float acc = 0.f;
+#pragma unroll
+            for (int u = 0; u < i; ++u)
+              if (u >= lane) acc = fmaf(D[i * LD + u], x[u], acc);
+            v = -acc / D[i * LD + i];
+          }
+          x[i] = v;
+          linv[i * (PB + 1) + lane] = v;
+        }
+      }
+      if (lane == 0) *flag = ok;
+    }
+    __syncthreads();
+    PHASE(slot, 13);
+    if (!*flag) return false;
+    // rows below: L(i, :) = H(i, :) L11^{-T}
+    for (int i = j0 + jb + tid; i < n; i += NT) {
+      float h[PB];
+#pragma unroll
+      for (int u = 0; u < PB; ++u) h[u] = (u < jb) ? H.at(i, j0 + u) : 0.f;
+      float v[PB];
+#pragma unroll
+      for (int t = 0; t < PB; ++t) {
+        float acc = 0.f;
+#pragma unroll
+        for (int u = 0; u <= t; ++u) acc = fmaf(h[u], linv[t * (PB + 1) + u], acc);
+        v[t] = (t < jb) ? acc : 0.f;
+        if (t < jb) H.at(i, j0 + t) = v[t];
+      }
+#pragma unroll
+      for (int t = 0; t < PB; t += 4)
+        *reinterpret_cast<float4*>(panel + i * LD + t) = make_float4(v[t], v[t + 1], v[t + 2], v[t + 3]);
+    }
+    __syncthreads();
+    PHASE(slot, 14);
+    // trailing rank-PB update
+    const int t0 = j0 + jb;
+    const int ngroups = (n - t0 + 31) >> 5;
+    const int nitems = ngroups * (ngroups + 1) / 2;
+    for (int it = warp; it < nitems; it += NW) {
+      int g = (int)((sqrtf(8.f * it + 1.f) - 1.f) * 0.5f);
+      while (((g + 1) * (g + 2)) / 2 <= it) ++g;
+      while ((g * (g + 1)) / 2 > it) --g;
+      const int q = it - (g * (g + 1)) / 2;
+      const int r = t0 + 32 * g + lane;
+      const bool rvalid = r < n;
+      float4 pr[PB / 4];
+#pragma unroll
+      for (int u = 0; u < PB / 4; ++u)
+        pr[u] = rvalid ? *reinterpret_cast<const float4*>(panel + r * LD + 4 * u)
+                       : make_float4(0.f, 0.f, 0.f, 0.f);
+      const int c_begin = t0 + 32 * q;
+      const int c_end = min(c_begin + 32, n);
+      // two columns per step for independent dependency chains
+      for (int cc = c_begin; cc < c_end; cc += 2) {
+        const int cd = min(cc + 1, c_end - 1);
+        float a0 = 0.f, a1 = 0.f, b0 = 0.f, b1 = 0.f;
+#pragma unroll
+        for (int u = 0; u < PB / 4; ++u) {
+          const float4 pc = *reinterpret_cast<const float4*>(panel + cc * LD + 4 * u);
+          const float4 pd = *reinterpret_cast<const float4*>(panel + cd * LD + 4 * u);
+          a0 = fmaf(pr[u].x, pc.x, a0);
+          a1 = fmaf(pr[u].y, pc.y, a1);
+          b0 = fmaf(pr[u].x, pd.x, b0);
+          b1 = fmaf(pr[u].y, pd.y, b1);
+          a0 = fmaf(pr[u].z, pc.z, a0);
+          a1 = fmaf(pr[u].w, pc.w, a1);
+          b0 = fmaf(pr[u].z, pd.z, b0);
+          b1 = fmaf(pr[u].w, pd.w, b1);
+        }
+        if (rvalid && cc <= r) {
+          float& hh = H.at(r, cc);
+          hh -= a0 + a1;
+        }
+        if (rvalid && cd != cc && cd <= r) {
+          float& hh = H.at(r, cd);
+          hh -= b0 + b1;
+        }
+      }
+    }
+    __syncthreads();
+    PHASE(slot, 15);
+  }
+  return true;
+}
+
+// ---------------------------------------------------------------------------
+// y = G x for G symmetric in the lower triangle (n <= 32 * RMAX * NT/32...):
+// warp w takes rows r = w, w + NW, ...; for row r lane l reads G(r, c),
+// c = l + 32 t <= r (contiguous), adds G(r, c) x_c to the row sum and
+// G(r, c) x_r to its private partial of column c (the transposed half).
+// Row sums are reduced across lanes in one interleaved butterfly, column
+// partials across warps through `part` (NW * 32 * CT floats of shared
+// scratch, CT = ceil(n / 32)).  x and y are shared; y must not alias x.
+// ---------------------------------------------------------------------------
+template <int NT, int CT, int RT, class S>
+__device__ void symv_lower(S G, int n, const float* x, float* y, float* part) {
+  constexpr int NW = NT / 32;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  float colp[CT];
+  float rs[RT];
+#pragma unroll
+  for (int t = 0; t < CT; ++t) colp[t] = 0.f;
+#pragma unroll
+  for (int q = 0; q < RT; ++q) {
+    rs[q] = 0.f;
+    const int r = warp + q * NW;
+    if (r < n) {
+      const float xr = x[r];
+#pragma unroll
+      for (int t = 0; t < CT; ++t) {
+        const int cc = lane + 32 * t;
+        if (cc <= r) {
+          const float g = G.at(r, cc);
+          rs[q] = fmaf(g, x[cc], rs[q]);
+          if (cc < r) colp[t] = fmaf(g, xr, colp[t]);
+        }
+      }
+    }
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+    for (int q = 0; q < RT; ++q) rs[q] += __shfl_xor_sync(0xffffffffu, rs[q], o);
+#pragma unroll
+  for (int t = 0; t < CT; ++t) part[(warp * CT + t) * 32 + lane] = colp[t];
+  __syncthreads();
+  for (int cc = tid; cc < n; cc += NT) {
+    float acc = 0.f;
+    const int t = cc >> 5, l = cc & 31;
+    for (int w = 0; w < NW; ++w) acc += part[(w * CT + t) * 32 + l];
+    y[cc] = acc;
+  }
+  __syncthreads();
+  if (lane == 0) {
+#pragma unroll
+    for (int q = 0; q < RT; ++q) {
+      const int r = warp + q * NW;
+      if (r < n) y[r] += rs[q];
+    }
+  }
+  __syncthreads();
 }
 
 // Number of eigenvalues of T (d, e2 = e^2) strictly below x (Sturm count via
@@ -271,7 +509,9 @@ __device__ __forceinline__ int sturm_below(const float* d, const float* e2, int 
   if (fabsf(q) < pivmin) q = -pivmin;
   int c = q < 0.f;
   for (int i = 1; i < n; ++i) {
-    q = (d[i] - x) - e2[i - 1] / q;
+    // approximate division: a few-ulp error per pivot only perturbs T by a
+    // few ulps, within the backward error the Sturm count tolerates
+    q = (d[i] - x) - __fdividef(e2[i - 1], q);
     if (fabsf(q) < pivmin) q = -pivmin;
     c += q < 0.f;
   }

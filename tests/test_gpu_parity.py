@@ -208,16 +208,25 @@ def test_decompose_without_shifts_recovers_hanning_blobs(ctx):
     assert np.all(O.relerr(X, comps, Y32) <= 1e-3)
 
 
-def test_skip_bound_does_not_change_results(ctx):
+def test_certified_paths_match_the_householder_reference(ctx):
+    """skip_bound=0 runs every block through the Householder eigen-solve;
+    the default path (bounds, Cholesky certificate, certified Lanczos) must
+    agree with it and with the oracle within the FP32 tolerance."""
     from paper_1507_08751_gb300 import binding as B
     Y32, comps, scales = synth.video(M=512, N=256)
+    M, N = Y32.shape
     p_on = B.msllr_params_default()
     p_off = B.msllr_params_default()
     p_off.skip_bound = 0
     X1, _, s1 = _run_decompose(ctx, Y32, scales, None, 20, 3, params=p_on)
     X0, _, s0 = _run_decompose(ctx, Y32, scales, None, 20, 3, params=p_off)
     assert sum(s0["blocks_skipped"]) == 0
-    assert np.all(O.relerr(X1, X0, Y32) <= 1e-6)
+    assert sum(s1["blocks_skipped"]) > 0
+    assert np.all(O.relerr(X1, X0, Y32) <= TOL)
+    lam = [O.lambda_default(M, N, m, n) for m, n in scales]
+    ref = O.admm(Y32.astype(np.float64), scales, lam, 1.0, 20, shifts=O.shift_table(3, 20, M, N))
+    assert np.all(O.relerr(X1, ref["X"], Y32) <= TOL)
+    assert np.all(O.relerr(X0, ref["X"], Y32) <= TOL)
 
 
 def test_decompose_is_deterministic_and_graph_equals_plain(ctx):
