@@ -111,7 +111,7 @@ cudaError_t configure_kernels();
 
 // Launchers (all asynchronous on `st`).  Return cudaGetLastError().
 cudaError_t launch_scale(const ScaleLaunch& s, const BigWorkspace& ws, cudaStream_t st,
-                         Prof* prof);
+                         Prof* prof, cudaEvent_t after_gram = nullptr);
 
 cudaError_t launch_consensus(const float* Y, const float* W, float* R, const uint8_t* mask,
                              int L, size_t MN, cudaStream_t st, Prof* prof = nullptr);

@@ -255,16 +255,10 @@ eig_big_kernel(ScaleLaunch a, const float* __restrict__ Gall, BigWorkspace ws) {
   PHASE(3, 0);
   const float thr = a.tau * a.tau;
   // trace and Gershgorin bounds of lambda_max(G)
-  float tr = 0.f, rs = 0.f;
-  for (int i = tid; i < nn; i += NT) {
-    tr += Gacc.at(i, i);
-    float t = 0.f;
-    for (int j = 0; j <= i; ++j) t += fabsf(Gacc.at(i, j));
-    for (int j = i + 1; j < nn; ++j) t += fabsf(Gacc.at(j, i));
-    rs = fmaxf(rs, t);
-  }
+  float tr = 0.f;
+  for (int i = tid; i < nn; i += NT) tr += Gacc.at(i, i);
   tr = block_sum<NT>(tr, s.red);
-  rs = block_max<NT>(rs, s.red);
+  const float rs = gershgorin_lower<NT, kEigCT, kEigRT>(Gacc, nn, z.x, z.w, z.part, s.red);
   const float gbound = fminf(tr, rs);
   const bool full = (a.m == a.M && a.n == a.N);
   const int kwarm = (a.warm_start && (full || !a.shift)) ? min(ws.kwarm[b], kLzMaxK) : 0;
@@ -489,7 +483,10 @@ cudaError_t configure_big_kernels() {
                               100 * 1024);
 }
 
-cudaError_t launch_big(const ScaleLaunch& s, const BigWorkspace& ws, cudaStream_t st, Prof* prof) {
+// `after_gram` (optional) is recorded on `st` once the Gram kernels are
+// enqueued, so that other streams can wait for the Gram phase to finish.
+cudaError_t launch_big(const ScaleLaunch& s, const BigWorkspace& ws, cudaStream_t st, Prof* prof,
+                       cudaEvent_t after_gram) {
   const BigDims d = big_dims(s.M, s.N, s.m, s.n);
   if (d.nn > kEigMax) return cudaErrorInvalidValue;
 #define PROF_BEFORE(kind) \
@@ -508,6 +505,8 @@ cudaError_t launch_big(const ScaleLaunch& s, const BigWorkspace& ws, cudaStream_
                                                                       d.ntiles, d.chunks);
     PROF_AFTER()
   }
+  if (after_gram)
+    if (cudaError_t e_ = cudaEventRecord(after_gram, st)) return e_;
   PROF_BEFORE(KK_EIG)
   eig_big_kernel<<<d.nblocks, kEigThreads, eig_smem_bytes(d.nn), st>>>(s, ws.G, ws);
   PROF_AFTER()

@@ -16,7 +16,8 @@
 namespace msllr {
 
 cudaError_t launch_soft1x1(const ScaleLaunch& s, cudaStream_t st, Prof* prof);
-cudaError_t launch_big(const ScaleLaunch& s, const BigWorkspace& ws, cudaStream_t st, Prof* prof);
+cudaError_t launch_big(const ScaleLaunch& s, const BigWorkspace& ws, cudaStream_t st, Prof* prof,
+                       cudaEvent_t after_gram);
 
 cudaError_t set_phase_buffer_small(unsigned long long* p) {
   return cudaMemcpyToSymbol(g_phase_acc, &p, sizeof(p));
@@ -88,6 +89,7 @@ __global__ void __launch_bounds__(NT) blocksvt_small_kernel(ScaleLaunch a) {
   // gather A = A1 + A2 on the shifted grid; ||C||_F^2
   const int melem = a.m * a.n;
   float fro = 0.f;
+#pragma unroll 8
   for (int e = tid; e < melem; e += NT) {
     const int r = e / a.n, c = e - r * a.n;
     const size_t off = g.offset(r, c);
@@ -108,9 +110,16 @@ __global__ void __launch_bounds__(NT) blocksvt_small_kernel(ScaleLaunch a) {
     const int ntri = nn * (nn + 1) / 2;
     for (int e = tid; e < ntri; e += NT) {
       const int i = tri_row(e), j = e - (i * (i + 1)) / 2;
-      float acc = 0.f;
-      for (int r = 0; r < mm; ++r) acc = fmaf(C[r * ldc + i], C[r * ldc + j], acc);
-      G[i * ldg + j] = acc;
+      float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f;
+      int r = 0;
+      for (; r + 3 < mm; r += 4) {
+        a0 = fmaf(C[r * ldc + i], C[r * ldc + j], a0);
+        a1 = fmaf(C[(r + 1) * ldc + i], C[(r + 1) * ldc + j], a1);
+        a2 = fmaf(C[(r + 2) * ldc + i], C[(r + 2) * ldc + j], a2);
+        a3 = fmaf(C[(r + 3) * ldc + i], C[(r + 3) * ldc + j], a3);
+      }
+      for (; r < mm; ++r) a0 = fmaf(C[r * ldc + i], C[r * ldc + j], a0);
+      G[i * ldg + j] = (a0 + a1) + (a2 + a3);
     }
     __syncthreads();
     PHASE(SLOT, 1);
@@ -283,7 +292,7 @@ ScalePath choose_path(int m, int n) {
 }
 
 cudaError_t launch_scale(const ScaleLaunch& s, const BigWorkspace& ws, cudaStream_t st,
-                         Prof* prof) {
+                         Prof* prof, cudaEvent_t after_gram) {
   switch (choose_path(s.m, s.n)) {
     case ScalePath::Elementwise:
       return launch_soft1x1(s, st, prof);
@@ -295,7 +304,7 @@ cudaError_t launch_scale(const ScaleLaunch& s, const BigWorkspace& ws, cudaStrea
     }
     case ScalePath::Big:
     default:
-      return launch_big(s, ws, st, prof);
+      return launch_big(s, ws, st, prof, after_gram);
   }
 }
 

@@ -203,17 +203,16 @@ __device__ int lz_ritz(int J, float thr, EigScratch& s, LzScratch& z, float* tno
   return k;
 }
 
-// Gershgorin bound max_i sum_j |A_ij| of a symmetric matrix in lower storage.
-template <int NT, class S>
-__device__ float gershgorin_lower(S A, int n, float* red) {
-  float rs = 0.f;
-  for (int i = threadIdx.x; i < n; i += NT) {
-    float t = 0.f;
-    for (int j = 0; j <= i; ++j) t += fabsf(A.at(i, j));
-    for (int j = i + 1; j < n; ++j) t += fabsf(A.at(j, i));
-    rs = fmaxf(rs, t);
-  }
-  return block_max<NT>(rs, red);
+// Gershgorin bound max_i sum_j |A_ij| of a symmetric matrix in lower storage:
+// the row sums are |A| times a vector of ones (conflict-free symv pattern).
+template <int NT, int CT, int RT, class S>
+__device__ float gershgorin_lower(S A, int n, float* ones, float* sums, float* part, float* red) {
+  for (int e = threadIdx.x; e < n; e += NT) ones[e] = 1.f;
+  __syncthreads();
+  symv_lower<NT, CT, RT, S, true>(A, n, ones, sums, part);
+  float m = 0.f;
+  for (int e = threadIdx.x; e < n; e += NT) m = fmaxf(m, sums[e]);
+  return block_max<NT>(m, red);
 }
 
 // The whole Lanczos + certificate path.
@@ -383,7 +382,7 @@ __device__ int lanczos_certified(SG Gs, SR Gr, SD Gd, int n, float thr, float gb
   }
   __syncthreads();
   // Cholesky backward error is bounded by n^2 eps ||c I - PGP||
-  const float gd = gershgorin_lower<NT>(Gd, n, s.red);
+  const float gd = gershgorin_lower<NT, CT, RT>(Gd, n, z.x, z.w, z.part, s.red);
   const float c = c0 - (float)n * (float)n * FLT_EPSILON * (c0 + gd);
   if (!(c > 0.f)) return -1;
   PHASE(slot, 11);

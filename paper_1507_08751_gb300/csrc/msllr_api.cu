@@ -42,10 +42,14 @@ struct msllr_ctx {
   int* d_table = nullptr;
   size_t table_cap = 0;
 
-  // one stream per scale: the scales of an iteration are independent given R
+  // one stream per scale: the scales of an iteration are independent given R.
+  // Wide-block scales (the longest dependency chain) get high-priority
+  // streams, the others low-priority ones.
   cudaStream_t side[MSLLR_MAX_SCALES] = {};
+  cudaStream_t side_hi[MSLLR_MAX_SCALES] = {};
   cudaEvent_t ev_fork = nullptr;
   cudaEvent_t ev_join[MSLLR_MAX_SCALES] = {};
+  cudaEvent_t ev_gate[MSLLR_MAX_SCALES] = {};
 
   // cached graph of one iteration
   cudaGraphExec_t graph = nullptr;
@@ -175,9 +179,14 @@ int msllr_create(msllr_ctx** out, int device, size_t hbm_budget_bytes, void* cud
       return bail(fail(ctx, MSLLR_ECUDA, "cudaStreamCreate"));
     ctx->own_stream = true;
   }
+  int prio_lo = 0, prio_hi = 0;
+  if (cudaDeviceGetStreamPriorityRange(&prio_lo, &prio_hi) != cudaSuccess)
+    return bail(fail(ctx, MSLLR_ECUDA, "cudaDeviceGetStreamPriorityRange"));
   for (int i = 0; i < MSLLR_MAX_SCALES; ++i)
-    if (cudaStreamCreateWithFlags(&ctx->side[i], cudaStreamNonBlocking) != cudaSuccess ||
-        cudaEventCreateWithFlags(&ctx->ev_join[i], cudaEventDisableTiming) != cudaSuccess)
+    if (cudaStreamCreateWithPriority(&ctx->side[i], cudaStreamNonBlocking, prio_lo) != cudaSuccess ||
+        cudaStreamCreateWithPriority(&ctx->side_hi[i], cudaStreamNonBlocking, prio_hi) != cudaSuccess ||
+        cudaEventCreateWithFlags(&ctx->ev_join[i], cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&ctx->ev_gate[i], cudaEventDisableTiming) != cudaSuccess)
       return bail(fail(ctx, MSLLR_ECUDA, "cudaStreamCreate (scale streams)"));
   if (cudaEventCreateWithFlags(&ctx->ev_fork, cudaEventDisableTiming) != cudaSuccess)
     return bail(fail(ctx, MSLLR_ECUDA, "cudaEventCreate"));
@@ -226,7 +235,9 @@ int msllr_destroy(msllr_ctx* ctx) {
   if (ctx->d_table) cudaFree(ctx->d_table);
   for (int i = 0; i < MSLLR_MAX_SCALES; ++i) {
     if (ctx->side[i]) cudaStreamDestroy(ctx->side[i]);
+    if (ctx->side_hi[i]) cudaStreamDestroy(ctx->side_hi[i]);
     if (ctx->ev_join[i]) cudaEventDestroy(ctx->ev_join[i]);
+    if (ctx->ev_gate[i]) cudaEventDestroy(ctx->ev_gate[i]);
   }
   if (ctx->ev_fork) cudaEventDestroy(ctx->ev_fork);
   if (ctx->own_stream && ctx->stream) cudaStreamDestroy(ctx->stream);
@@ -336,29 +347,43 @@ int enqueue_iteration(msllr_ctx* ctx, const Layout& lay, int M, int N, int L, co
   // context stream so that each event pair brackets one kernel running alone.
   const bool fork = !(prof && prof->timing);
   if (fork) CK(cudaEventRecord(ctx->ev_fork, ctx->stream));
-  for (int i = 0; i < L; ++i) {
-    cudaStream_t st = (i == 0 || !fork) ? ctx->stream : ctx->side[i];
-    if (i > 0 && fork) CK(cudaStreamWaitEvent(st, ctx->ev_fork, 0));
-    ScaleLaunch s{};
-    s.A1 = lay.Z + (size_t)i * lay.MN;
-    s.A2 = lay.R;
-    s.Zout = lay.Z + (size_t)i * lay.MN;
-    s.Wout = lay.W + (size_t)i * lay.MN;
-    s.M = M;
-    s.N = N;
-    s.ld = N;
-    s.m = bm[i];
-    s.n = bn[i];
-    s.shift = p.cycle_spin ? ctx->d_small + 1 : nullptr;
-    s.tau = taus[i];
-    s.skip_bound = p.skip_bound;
-    s.warm_start = 1;
-    s.rank_out = nullptr;
-    s.nuc_acc = stats ? ctx->d_acc + i : nullptr;
-    s.cnt = stats ? ctx->d_cnt + 4 * i : nullptr;
-    prof->scale = i;
-    CK(launch_scale(s, lay.big[i], st, prof));
-    if (i > 0 && fork) CK(cudaEventRecord(ctx->ev_join[i], st));
+  // Wide-block scales are enqueued first on high-priority streams.  Their
+  // eigen kernel needs whole SMs, so the other scales wait until the wide
+  // scales' Gram phase is over; the eigen CTAs then claim SMs first and the
+  // narrow-block kernels fill the rest.
+  bool gated[MSLLR_MAX_SCALES] = {};
+  for (int pass = 0; pass < 2; ++pass) {
+    for (int i = 0; i < L; ++i) {
+      const bool wide = choose_path(bm[i], bn[i]) == ScalePath::Big;
+      if ((pass == 0) != wide) continue;
+      cudaStream_t st = (i == 0 || !fork) ? ctx->stream : (wide ? ctx->side_hi[i] : ctx->side[i]);
+      if (i > 0 && fork) CK(cudaStreamWaitEvent(st, ctx->ev_fork, 0));
+      if (pass == 1 && fork)
+        for (int j = 0; j < L; ++j)
+          if (gated[j]) CK(cudaStreamWaitEvent(st, ctx->ev_gate[j], 0));
+      ScaleLaunch s{};
+      s.A1 = lay.Z + (size_t)i * lay.MN;
+      s.A2 = lay.R;
+      s.Zout = lay.Z + (size_t)i * lay.MN;
+      s.Wout = lay.W + (size_t)i * lay.MN;
+      s.M = M;
+      s.N = N;
+      s.ld = N;
+      s.m = bm[i];
+      s.n = bn[i];
+      s.shift = p.cycle_spin ? ctx->d_small + 1 : nullptr;
+      s.tau = taus[i];
+      s.skip_bound = p.skip_bound;
+      s.warm_start = 1;
+      s.rank_out = nullptr;
+      s.nuc_acc = stats ? ctx->d_acc + i : nullptr;
+      s.cnt = stats ? ctx->d_cnt + 4 * i : nullptr;
+      prof->scale = i;
+      const bool gate = fork && wide && i > 0;
+      CK(launch_scale(s, lay.big[i], st, prof, gate ? ctx->ev_gate[i] : nullptr));
+      gated[i] = gate;
+      if (i > 0 && fork) CK(cudaEventRecord(ctx->ev_join[i], st));
+    }
   }
   // join
   if (fork)

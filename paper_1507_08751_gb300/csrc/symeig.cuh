@@ -296,20 +296,88 @@ __device__ bool shifted_cholesky_pd(S H, int n, float c, float* panel, int* flag
 }
 
 // ---------------------------------------------------------------------------
-// Same test with narrow panels of PB (8 or 16) columns: the PB x PB diagonal
-// block is factored in registers by lanes 0..PB-1 of warp 0 (one row each,
-// fully unrolled -- little code), its inverse is formed one column per
-// lane, rows below multiply by it, and the rank-PB trailing update has lanes
-// owning rows and reading each column's panel row as a broadcast.
-// `panel` needs n * (PB + 4) + PB * (PB + 1) floats (16-byte aligned).
+// Same test with narrow panels of PB (8 or 16) columns and one panel of
+// lookahead.  Per panel: every row below the diagonal block forms its PB
+// factor entries by multiplying with the inverse of the (already factored)
+// diagonal block; then warps 1.. apply the rank-PB update to the trailing
+// triangle in register-tiled 4x4 tiles while warp 0 updates and factors the
+// NEXT diagonal block (registers, lanes = rows) and inverts it, so the serial
+// part overlaps the update.  Only the "all pivots positive" answer is kept.
+// `panel` needs n * (PB + 4) + 2 * PB * (PB + 1) + PB * (PB + 4) floats
+// (16-byte aligned); `flag` is one shared int.
 // ---------------------------------------------------------------------------
+template <int PB, class S>
+__device__ int chol_diag_block(S H, int t0, int jb, const float* panel, float* D, float* linv,
+                               bool update) {
+  constexpr int LD = PB + 4;
+  const int lane = threadIdx.x & 31;
+  float row[PB];
+#pragma unroll
+  for (int t = 0; t < PB; ++t) {
+    float v = (lane < jb) ? ((t <= lane) ? H.at(t0 + lane, t0 + t) : 0.f) : (t == lane ? 1.f : 0.f);
+    if (update && lane < jb && t <= lane) {
+      // rank-PB update of the block from the previous panel's factor rows
+      float acc = 0.f;
+#pragma unroll
+      for (int u = 0; u < PB; ++u) acc = fmaf(panel[(t0 + lane) * LD + u], panel[(t0 + t) * LD + u], acc);
+      v -= acc;
+    }
+    row[t] = v;
+  }
+  int ok = 1;
+#pragma unroll
+  for (int j = 0; j < PB; ++j) {
+    const float dj = __shfl_sync(0xffffffffu, row[j], j);
+    ok &= (dj > 0.f);
+    const float l = sqrtf(dj > 0.f ? dj : 1.f);
+    const float inv = 1.f / l;
+    row[j] = (lane == j) ? l : ((lane > j) ? row[j] * inv : row[j]);
+#pragma unroll
+    for (int t = j + 1; t < PB; ++t) {
+      const float ltj = __shfl_sync(0xffffffffu, row[j], t);
+      if (lane >= t) row[t] = fmaf(-row[j], ltj, row[t]);
+    }
+  }
+  if (lane < PB) {
+#pragma unroll
+    for (int t = 0; t < PB; ++t) D[lane * LD + t] = (t <= lane) ? row[t] : 0.f;
+  }
+  __syncwarp();
+  // inverse of the block, column `lane`, by forward substitution
+  if (lane < PB) {
+    float x[PB];
+#pragma unroll
+    for (int i = 0; i < PB; ++i) {
+      float v = 0.f;
+      if (i == lane) {
+        v = 1.f / D[i * LD + i];
+      } else if (i > lane) {
+        float acc = 0.f;
+#pragma unroll
+        for (int u = 0; u < i; ++u)
+          if (u >= lane) acc = fmaf(D[i * LD + u], x[u], acc);
+        v = -acc / D[i * LD + i];
+      }
+      x[i] = v;
+      linv[i * (PB + 1) + lane] = v;
+    }
+  }
+  return __all_sync(0xffffffffu, ok);
+}
+
 template <int NT, int PB, class S>
 __device__ bool shifted_cholesky_pd_nb(S H, int n, float c, float* panel, int* flag, int slot = -1) {
   constexpr int NW = NT / 32;
   constexpr int LD = PB + 4;
+  constexpr int TB = PB / 4;                  // 4x4 tile rows covered by the next diagonal block
+  constexpr int SKIP = TB * (TB + 1) / 2;     // its tiles, done by warp 0
   static_assert(PB == 8 || PB == 16, "panel width");
+  // with a single warp the lookahead block and the trailing update run one
+  // after the other (they touch disjoint entries)
+  constexpr int TW = NT == 32 ? 0 : 32;       // first thread of the trailing update
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  float* linv = panel + n * LD;  // PB x (PB + 1)
+  float* linv = panel + n * LD;               // 2 x PB x (PB + 1), double buffered
+  float* D = linv + 2 * PB * (PB + 1);        // PB x LD scratch of the diagonal factor
   PHASE_INIT();
   for (int r = warp; r < n; r += NW)
     for (int cc = lane; cc <= r; cc += 32) {
@@ -317,61 +385,17 @@ __device__ bool shifted_cholesky_pd_nb(S H, int n, float c, float* panel, int* f
       h = (r == cc ? c : 0.f) - h;
     }
   __syncthreads();
+  if (warp == 0) {
+    const int ok = chol_diag_block<PB>(H, 0, min(PB, n), panel, D, linv, false);
+    if (lane == 0) *flag = ok;
+  }
+  __syncthreads();
   PHASE(slot, 12);
+  int buf = 0;
   for (int j0 = 0; j0 < n; j0 += PB) {
-    const int jb = min(PB, n - j0);
-    if (warp == 0) {
-      float row[PB];
-#pragma unroll
-      for (int t = 0; t < PB; ++t)
-        row[t] = (lane < jb) ? ((t <= lane) ? H.at(j0 + lane, j0 + t) : 0.f)
-                             : (t == lane ? 1.f : 0.f);
-      int ok = 1;
-#pragma unroll
-      for (int j = 0; j < PB; ++j) {
-        const float dj = __shfl_sync(0xffffffffu, row[j], j);
-        ok &= (dj > 0.f);
-        const float l = sqrtf(dj > 0.f ? dj : 1.f);
-        const float inv = 1.f / l;
-        row[j] = (lane == j) ? l : ((lane > j) ? row[j] * inv : row[j]);
-#pragma unroll
-        for (int t = j + 1; t < PB; ++t) {
-          const float ltj = __shfl_sync(0xffffffffu, row[j], t);
-          if (lane >= t) row[t] = fmaf(-row[j], ltj, row[t]);
-        }
-      }
-      // L11 to the panel and H; inverse column `lane` of L11 by forward substitution
-      if (lane < jb) {
-#pragma unroll
-        for (int t = 0; t < PB; ++t) {
-          panel[(j0 + lane) * LD + t] = (t <= lane) ? row[t] : 0.f;
-          if (t <= lane) H.at(j0 + lane, j0 + t) = row[t];
-        }
-      }
-      __syncwarp();
-      if (lane < jb) {
-        const float* D = panel + j0 * LD;
-        float x[PB];
-#pragma unroll
-        for (int i = 0; i < PB; ++i) {
-          float v = 0.f;
-          if (i == lane) v = 1.f / D[i * LD + i];
-          else if (i > lane && i < jb) {
-            float acc = 0.f;
-#pragma unroll
-            for (int u = 0; u < i; ++u)
-              if (u >= lane) acc = fmaf(D[i * LD + u], x[u], acc);
-            v = -acc / D[i * LD + i];
-          }
-          x[i] = v;
-          linv[i * (PB + 1) + lane] = v;
-        }
-      }
-      if (lane == 0) *flag = ok;
-    }
-    __syncthreads();
-    PHASE(slot, 13);
     if (!*flag) return false;
+    const int jb = min(PB, n - j0);
+    const float* li = linv + buf * PB * (PB + 1);
     // rows below: L(i, :) = H(i, :) L11^{-T}
     for (int i = j0 + jb + tid; i < n; i += NT) {
       float h[PB];
@@ -382,9 +406,8 @@ __device__ bool shifted_cholesky_pd_nb(S H, int n, float c, float* panel, int* f
       for (int t = 0; t < PB; ++t) {
         float acc = 0.f;
 #pragma unroll
-        for (int u = 0; u <= t; ++u) acc = fmaf(h[u], linv[t * (PB + 1) + u], acc);
+        for (int u = 0; u <= t; ++u) acc = fmaf(h[u], li[t * (PB + 1) + u], acc);
         v[t] = (t < jb) ? acc : 0.f;
-        if (t < jb) H.at(i, j0 + t) = v[t];
       }
 #pragma unroll
       for (int t = 0; t < PB; t += 4)
@@ -392,53 +415,69 @@ __device__ bool shifted_cholesky_pd_nb(S H, int n, float c, float* panel, int* f
     }
     __syncthreads();
     PHASE(slot, 14);
-    // trailing rank-PB update
     const int t0 = j0 + jb;
-    const int ngroups = (n - t0 + 31) >> 5;
-    const int nitems = ngroups * (ngroups + 1) / 2;
-    for (int it = warp; it < nitems; it += NW) {
-      int g = (int)((sqrtf(8.f * it + 1.f) - 1.f) * 0.5f);
-      while (((g + 1) * (g + 2)) / 2 <= it) ++g;
-      while ((g * (g + 1)) / 2 > it) --g;
-      const int q = it - (g * (g + 1)) / 2;
-      const int r = t0 + 32 * g + lane;
-      const bool rvalid = r < n;
-      float4 pr[PB / 4];
+    if (t0 >= n) break;
+    if (warp == 0) {
+      // lookahead: update and factor the next diagonal block
+      const int ok = chol_diag_block<PB>(H, t0, min(PB, n - t0), panel, D,
+                                         linv + (buf ^ 1) * PB * (PB + 1), true);
+      if (lane == 0) *flag = ok;
+    }
+    if (NT == 32) __syncwarp();
+    if (NT == 32 || warp > 0) {
+      // trailing rank-PB update of everything else, 4x4 register tiles
+      const int tr = (n - t0 + 3) >> 2;
+      const int ntiles = tr * (tr + 1) / 2;
+      for (int tt = SKIP + (tid - TW); tt < ntiles; tt += NT - TW) {
+        int a = (int)((sqrtf(8.f * tt + 1.f) - 1.f) * 0.5f);
+        while (((a + 1) * (a + 2)) / 2 <= tt) ++a;
+        while ((a * (a + 1)) / 2 > tt) --a;
+        const int b = tt - (a * (a + 1)) / 2;
+        const int r0 = t0 + 4 * a, c0 = t0 + 4 * b;
+        float acc[4][4];
 #pragma unroll
-      for (int u = 0; u < PB / 4; ++u)
-        pr[u] = rvalid ? *reinterpret_cast<const float4*>(panel + r * LD + 4 * u)
-                       : make_float4(0.f, 0.f, 0.f, 0.f);
-      const int c_begin = t0 + 32 * q;
-      const int c_end = min(c_begin + 32, n);
-      // two columns per step for independent dependency chains
-      for (int cc = c_begin; cc < c_end; cc += 2) {
-        const int cd = min(cc + 1, c_end - 1);
-        float a0 = 0.f, a1 = 0.f, b0 = 0.f, b1 = 0.f;
+        for (int i = 0; i < 4; ++i)
 #pragma unroll
-        for (int u = 0; u < PB / 4; ++u) {
-          const float4 pc = *reinterpret_cast<const float4*>(panel + cc * LD + 4 * u);
-          const float4 pd = *reinterpret_cast<const float4*>(panel + cd * LD + 4 * u);
-          a0 = fmaf(pr[u].x, pc.x, a0);
-          a1 = fmaf(pr[u].y, pc.y, a1);
-          b0 = fmaf(pr[u].x, pd.x, b0);
-          b1 = fmaf(pr[u].y, pd.y, b1);
-          a0 = fmaf(pr[u].z, pc.z, a0);
-          a1 = fmaf(pr[u].w, pc.w, a1);
-          b0 = fmaf(pr[u].z, pd.z, b0);
-          b1 = fmaf(pr[u].w, pd.w, b1);
+          for (int j = 0; j < 4; ++j) acc[i][j] = 0.f;
+#pragma unroll
+        for (int u = 0; u < PB; u += 4) {
+          float4 pr[4], pc[4];
+#pragma unroll
+          for (int i = 0; i < 4; ++i) {
+            const int r = min(r0 + i, n - 1), cc = min(c0 + i, n - 1);
+            pr[i] = *reinterpret_cast<const float4*>(panel + r * LD + u);
+            pc[i] = *reinterpret_cast<const float4*>(panel + cc * LD + u);
+          }
+#pragma unroll
+          for (int i = 0; i < 4; ++i)
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+              float v = acc[i][j];
+              v = fmaf(pr[i].x, pc[j].x, v);
+              v = fmaf(pr[i].y, pc[j].y, v);
+              v = fmaf(pr[i].z, pc[j].z, v);
+              v = fmaf(pr[i].w, pc[j].w, v);
+              acc[i][j] = v;
+            }
         }
-        if (rvalid && cc <= r) {
-          float& hh = H.at(r, cc);
-          hh -= a0 + a1;
-        }
-        if (rvalid && cd != cc && cd <= r) {
-          float& hh = H.at(r, cd);
-          hh -= b0 + b1;
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+          const int r = r0 + i;
+          if (r >= n) break;
+#pragma unroll
+          for (int j = 0; j < 4; ++j) {
+            const int cc = c0 + j;
+            if (cc <= r && cc < n) {
+              float& hh = H.at(r, cc);
+              hh -= acc[i][j];
+            }
+          }
         }
       }
     }
     __syncthreads();
     PHASE(slot, 15);
+    buf ^= 1;
   }
   return true;
 }
@@ -452,7 +491,7 @@ __device__ bool shifted_cholesky_pd_nb(S H, int n, float c, float* panel, int* f
 // partials across warps through `part` (NW * 32 * CT floats of shared
 // scratch, CT = ceil(n / 32)).  x and y are shared; y must not alias x.
 // ---------------------------------------------------------------------------
-template <int NT, int CT, int RT, class S>
+template <int NT, int CT, int RT, class S, bool ABS = false>
 __device__ void symv_lower(S G, int n, const float* x, float* y, float* part) {
   constexpr int NW = NT / 32;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -470,7 +509,7 @@ __device__ void symv_lower(S G, int n, const float* x, float* y, float* part) {
       for (int t = 0; t < CT; ++t) {
         const int cc = lane + 32 * t;
         if (cc <= r) {
-          const float g = G.at(r, cc);
+          const float g = ABS ? fabsf(G.at(r, cc)) : G.at(r, cc);
           rs[q] = fmaf(g, x[cc], rs[q]);
           if (cc < r) colp[t] = fmaf(g, xr, colp[t]);
         }
@@ -549,28 +588,57 @@ __device__ int top_eigenvalues(int n, float thr, EigScratch& s, float* tnorm) {
     s.hi[tid] = top;
   }
   __syncthreads();
-  const int g = NT / k;
+  // one warp (32 points per round) per target when there are enough warps,
+  // otherwise NT / k threads per target with a serial scan by the leader
+  const int g = (NT / k >= 32) ? 32 : NT / k;
   const int q = tid / g, mb = tid - q * g;
   const int target = n - 1 - q;  // ascending index of the eigenvalue sought
   const float tol = 2.f * FLT_EPSILON * tn;
   for (int round = 0; round < 64; ++round) {
     bool active = false;
+    float x = 0.f;
+    int cntx = 0;
     if (q < k) {
       const float lo = s.lo[q], hi = s.hi[q];
       if (hi - lo > fmaxf(tol, 2.f * FLT_EPSILON * fmaxf(fabsf(lo), fabsf(hi)))) {
         active = true;
-        const float x = lo + (hi - lo) * ((float)(mb + 1) / (float)(g + 1));
-        s.xs[tid] = x;
-        s.cnt[tid] = sturm_below(s.d, s.e2, n, x, pivmin);
+        x = lo + (hi - lo) * ((float)(mb + 1) / (float)(g + 1));
+        cntx = sturm_below(s.d, s.e2, n, x, pivmin);
+        if (g < 32) {
+          s.xs[tid] = x;
+          s.cnt[tid] = cntx;
+        }
       }
     }
     if (!__syncthreads_or(active)) break;
-    if (active && mb == 0) {
+    if (g == 32) {
+      if (q < k) {
+        // counts grow with x: the first point above the target brackets it
+        const unsigned above = __ballot_sync(0xffffffffu, active && cntx > target);
+        const float lo = s.lo[q], hi = s.hi[q];
+        if (active) {
+          float nlo = lo, nhi = hi;
+          if (above == 0u) {
+            nlo = __shfl_sync(0xffffffffu, x, 31);
+          } else {
+            const int f = __ffs(above) - 1;
+            nhi = __shfl_sync(0xffffffffu, x, f);
+            if (f > 0) nlo = __shfl_sync(0xffffffffu, x, f - 1);
+          }
+          if (nlo > nhi) nlo = nhi;
+          __syncwarp();
+          if (mb == 0) {
+            s.lo[q] = nlo;
+            s.hi[q] = nhi;
+          }
+        }
+      }
+    } else if (active && mb == 0) {
       float lo = s.lo[q], hi = s.hi[q];
       for (int j = 0; j < g; ++j) {
-        const float x = s.xs[tid + j];
-        if (s.cnt[tid + j] <= target) lo = fmaxf(lo, x);
-        else hi = fminf(hi, x);
+        const float xj = s.xs[tid + j];
+        if (s.cnt[tid + j] <= target) lo = fmaxf(lo, xj);
+        else hi = fminf(hi, xj);
       }
       if (lo > hi) lo = hi;
       s.lo[q] = lo;
