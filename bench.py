@@ -297,6 +297,13 @@ def ours(a):
     pk = peaks()
     roof, best = kernel_roofline(pstats, scales, M, N, pk)
 
+    # concurrent per-scale segment times (profile mode 2)
+    p2 = B.msllr_params_default()
+    p2.profile = 2
+    cstats = step(p2)
+    seg = {f"{m}x{n}": round(max(cstats["kernel_ms"]["eig_big"][i], cstats["kernel_ms"]["fused_small"][i])
+                             / a.iters * 1e3, 1) for i, (m, n) in enumerate(scales)}
+
     # end to end through the host API: pinned host Y in, X out, copies timed
     Yh = torch.from_numpy(Y32).pin_memory()
     Xh = torch.empty((L, M, N), dtype=torch.float32).pin_memory()
@@ -333,6 +340,7 @@ def ours(a):
             "roofline": roof,
             "kernel_ms_per_job": {k: [round(x, 3) for x in v] for k, v in pstats["kernel_ms"].items()
                                   if any(v)},
+            "scale_segment_us_concurrent": seg,
             "skipped_blocks_last_iter": stats["blocks_skipped"],
             "zero_rank_blocks_last_iter": stats["blocks_zero"],
             "lanczos_blocks_last_iter": stats["blocks_lanczos"],

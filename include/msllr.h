@@ -78,8 +78,11 @@ typedef struct msllr_params {
   const float* U_init; /* device, L x M x N, or NULL (default: zeros)       */
   float* U_out;        /* device, L x M x N, or NULL: final U_i             */
   int profile;         /* 1: time every kernel with CUDA events on the
-                          context stream (plain launches, no graph) and
-                          report it in msllr_stats.kernel_ms.  Default 0.  */
+                          context stream, scales one after the other (plain
+                          launches, no graph), into msllr_stats.kernel_ms.
+                          2: scales run concurrently as usual and each
+                          scale's whole segment is timed (kind 6 for wide
+                          scales, 3 for the others).  Default 0.            */
 } msllr_params;
 
 /* Per-run diagnostics, all taken at the last iteration. */

@@ -63,6 +63,7 @@ enum KernelKind {
 // times per (kind, scale) after the run.
 struct Prof {
   bool timing = false;
+  bool per_scale = false;  // time whole per-scale segments in the forked iteration
   int scale = 0;
   long long launches[KK_COUNT][8] = {};
   std::vector<cudaEvent_t> ev;

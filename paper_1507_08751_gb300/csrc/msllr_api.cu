@@ -345,7 +345,7 @@ int enqueue_iteration(msllr_ctx* ctx, const Layout& lay, int M, int N, int L, co
   // fork: scale i > 0 runs on its own stream, scale 0 on the context stream.
   // When kernels are timed one by one (profile), everything stays on the
   // context stream so that each event pair brackets one kernel running alone.
-  const bool fork = !(prof && prof->timing);
+  const bool fork = !(prof && prof->timing && !prof->per_scale);
   if (fork) CK(cudaEventRecord(ctx->ev_fork, ctx->stream));
   // Wide-block scales are enqueued first on high-priority streams.  Their
   // eigen kernel needs whole SMs, so the other scales wait until the wide
@@ -380,7 +380,16 @@ int enqueue_iteration(msllr_ctx* ctx, const Layout& lay, int M, int N, int L, co
       s.cnt = stats ? ctx->d_cnt + 4 * i : nullptr;
       prof->scale = i;
       const bool gate = fork && wide && i > 0;
-      CK(launch_scale(s, lay.big[i], st, prof, gate ? ctx->ev_gate[i] : nullptr));
+      if (prof->per_scale) {
+        // concurrent profile: one event pair around the scale's whole segment
+        CK(prof->before(st, wide ? KK_EIG : KK_FUSED));
+        prof->timing = false;
+        CK(launch_scale(s, lay.big[i], st, prof, gate ? ctx->ev_gate[i] : nullptr));
+        prof->timing = true;
+        CK(prof->after(st));
+      } else {
+        CK(launch_scale(s, lay.big[i], st, prof, gate ? ctx->ev_gate[i] : nullptr));
+      }
       gated[i] = gate;
       if (i > 0 && fork) CK(cudaEventRecord(ctx->ev_join[i], st));
     }
@@ -408,6 +417,7 @@ int decompose_device(msllr_ctx* ctx, const float* Y, int M, int N, int ld, int L
   if (p.iter_offset < 0) return fail(ctx, MSLLR_EINVAL, "iter_offset must be >= 0");
   Prof prof;
   prof.timing = p.profile != 0;
+  prof.per_scale = p.profile == 2;
   if (p.profile) p.use_graph = 0;
   struct EventPool {
     Prof* pr;
