@@ -171,8 +171,8 @@ constexpr int kEigRT = kEigMax / (kEigThreads / 32);   // symv rows per warp
 constexpr int kEigPart = (kEigThreads / 32) * 32 * kEigCT;
 // panel region: Cholesky panel, or Lanczos Q (kLzMaxJ x n) followed by the symv scratch
 constexpr int kEigPanelFloats =
-    (kPanelStride * kEigMax + 32 * 33 > kLzMaxJ * kEigMax + kEigPart)
-        ? kPanelStride * kEigMax + 32 * 33
+    (lz_cert_floats(kEigMax, kEigThreads) > kLzMaxJ * kEigMax + kEigPart)
+        ? lz_cert_floats(kEigMax, kEigThreads)
         : kLzMaxJ * kEigMax + kEigPart;
 
 size_t eig_smem_bytes(int nn) {
@@ -222,7 +222,7 @@ eig_big_kernel(ScaleLaunch a, const float* __restrict__ Gall, BigWorkspace ws) {
   const float* Gg = Gall + (size_t)b * nn * nn;
   float* Y = ws.Y + (size_t)b * ws.ystride;
   float* Gp = sm;
-  float* panel = Gp + (((nn * (nn + 1)) / 2 + 3) & ~3);  // NMAX x kPanelStride, 16-byte aligned
+  float* panel = Gp + (((nn * (nn + 1)) / 2 + 3) & ~3);  // kEigPanelFloats, 16-byte aligned
   float* scr = panel + kEigPanelFloats;
   EigScratch s;
   s.d = scr;
@@ -270,13 +270,13 @@ eig_big_kernel(ScaleLaunch a, const float* __restrict__ Gall, BigWorkspace ws) {
       k = 0;
     } else if (kwarm == 0 && !power_above(Gacc, nn, thr, s, z)) {
       // certified lambda_max(G) < tau^2 by Cholesky of (tau^2 - margin) I - G
-      const float margin = (float)nn * (float)nn * FLT_EPSILON * (thr + gbound);
+      const float n8 = (float)((nn + 7) & ~7);
+      const float margin = n8 * n8 * FLT_EPSILON * (thr + gbound);
       const float c = thr - margin;
-      if (c > 0.f && shifted_cholesky_pd_nb<NT, 8>(Gacc, nn, c, panel, s.cnt, 3)) {
+      if (c > 0.f &&
+          regchol_pd<NT, NMAX>(Gacc, nn, c, false, nullptr, nullptr, 0, panel, s.red)) {
         skipped = true;
         k = 0;
-      } else {
-        load_g();
       }
     }
   }
@@ -288,10 +288,9 @@ eig_big_kernel(ScaleLaunch a, const float* __restrict__ Gall, BigWorkspace ws) {
     const float* warm = ws.warm + (size_t)b * kLzMaxK * nn;
     float* U = Y;
     float* Wm = Y + (size_t)kLzMaxK * nn;
-    k = lanczos_certified<NT, kEigCT, kEigRT>(Gacc, LowerFull{const_cast<float*>(Gg), nn}, Gacc, nn,
-                                              thr, gbound, Qs, min(nn, kLzMaxJ), U, Wm, warm,
-                                              kwarm, 0x1234567u + 977u * b, s, z, panel, s.cnt,
-                                              &ku, 3);
+    k = lanczos_certified<NT, NMAX, kEigCT, kEigRT>(Gacc, Gacc, nn, thr, gbound, Qs,
+                                                    min(nn, kLzMaxJ), U, Wm, warm, kwarm,
+                                                    0x1234567u + 977u * b, s, z, panel, &ku, 3);
     lanczos_ok = k >= 0;
     PHASE(3, 5);
     if (lanczos_ok) {
@@ -307,8 +306,6 @@ eig_big_kernel(ScaleLaunch a, const float* __restrict__ Gall, BigWorkspace ws) {
         const float sig = sqrtf(s.lam[q]);
         Y[(size_t)i * nn + q] = panel[(size_t)q * nn + i] * sqrtf(fmaxf(1.f - a.tau / sig, 0.f));
       }
-    } else {
-      load_g();
     }
   }
   if (k < 0) {

@@ -59,8 +59,8 @@ __global__ void __launch_bounds__(NT) blocksvt_small_kernel(ScaleLaunch a) {
   float* Y = G + nn * ldg;
   float* P = Y + nn * (nn + 1);  // Y region holds nn x (nn + 1)
   const int panel_off = (int)(P - sm) + mm * nn;
-  float* panel = sm + ((panel_off + 3) & ~3);  // NMAX x 8, 16-byte aligned (absolute offset)
-  float* scr = panel + NMAX * kPanelStride + 32 * 33;
+  float* panel = sm + ((panel_off + 3) & ~3);  // certificate scratch, 16-byte aligned (absolute offset)
+  float* scr = panel + lz_cert_floats(NMAX, NT);
   EigScratch s;
   s.d = scr;
   s.e = s.d + NMAX;
@@ -139,15 +139,11 @@ __global__ void __launch_bounds__(NT) blocksvt_small_kernel(ScaleLaunch a) {
         skipped = true;
       } else {
         // certified lambda_max(G) < tau^2 by Cholesky of (tau^2 - margin) I - G
-        // on a copy of G (the Y region is free until the eigenvectors)
-        for (int e = tid; e < nn * nn; e += NT) {
-          const int i = e / nn, j = e - i * nn;
-          if (j <= i) Y[i * (nn + 1) + j] = G[i * ldg + j];
-        }
-        __syncthreads();
-        const float margin = (float)(nn * nn) * FLT_EPSILON * (thr + rs);
+        const int n8 = (nn + 7) & ~7;
+        const float margin = (float)(n8 * n8) * FLT_EPSILON * (thr + rs);
         const float c = thr - margin;
-        if (c > 0.f && shifted_cholesky_pd_nb<NT, 8>(LowerFull{Y, nn + 1}, nn, c, panel, s.cnt))
+        if (c > 0.f &&
+            regchol_pd<NT, NMAX>(LowerFull{G, ldg}, nn, c, false, nullptr, nullptr, 0, panel, s.red))
           skipped = true;
         __syncthreads();
       }
@@ -156,11 +152,11 @@ __global__ void __launch_bounds__(NT) blocksvt_small_kernel(ScaleLaunch a) {
   PHASE(SLOT, 2);
   bool lanczos_ok = false;
   if (!skipped && a.skip_bound) {
-    // certified Lanczos; P G P and its Cholesky go to the Y region, G stays
+    // certified Lanczos (G stays intact for the fallback)
     int ku = 0;
-    k = lanczos_certified<NT, CT, RT>(LowerFull{G, ldg}, LowerFull{G, ldg}, LowerFull{Y, nn + 1}, nn,
-                                      thr, gbound, Qs, nn < JCAP ? nn : JCAP, Us, Ws, nullptr, 0,
-                                      0x51ED27u + 131u * blockIdx.x, s, z, panel, s.cnt, &ku);
+    k = lanczos_certified<NT, NMAX, CT, RT>(LowerFull{G, ldg}, LowerFull{G, ldg}, nn, thr, gbound,
+                                            Qs, nn < JCAP ? nn : JCAP, Us, Ws, nullptr, 0,
+                                            0x51ED27u + 131u * blockIdx.x, s, z, panel, &ku);
     lanczos_ok = k >= 0;
     if (lanczos_ok) {
       for (int e = tid; e < nn * k; e += NT) {
@@ -246,8 +242,7 @@ template <int NT, int NMAX>
 size_t small_smem_bytes(int mm, int nn) {
   constexpr int JCAP = NMAX < kLzMaxJ ? NMAX : kLzMaxJ;
   constexpr int CT = (NMAX + 31) / 32;
-  return sizeof(float) * ((size_t)2 * mm * nn + (size_t)nn * (2 * nn + 2) + kPanelStride * NMAX +
-                          32 * 33 +
+  return sizeof(float) * ((size_t)2 * mm * nn + (size_t)nn * (2 * nn + 2) + lz_cert_floats(NMAX, NT) +
                           4 + 9 * NMAX + 4 * NT + 64 + NMAX * JCAP + 2 * NMAX * kLzMaxK +
                           (NT / 32) * 32 * CT + lz_scratch_floats(NMAX, JCAP));
 }

@@ -24,12 +24,18 @@
 #include <float.h>
 
 #include "common.cuh"
+#include "regchol.cuh"
 #include "symeig.cuh"
 
 namespace msllr {
 
 constexpr int kLzMaxJ = 32;  // Lanczos steps
 constexpr int kLzMaxK = 8;   // Ritz pairs kept (above 0.95 tau^2)
+
+// shared scratch (floats) of the certificate step of lanczos_certified
+__host__ __device__ constexpr int lz_cert_floats(int nmax, int nt) {
+  return 16 * nmax + regchol_scratch_floats(nmax, nt);
+}
 
 // Shared-memory scratch of the Lanczos path.
 struct LzScratch {
@@ -217,21 +223,21 @@ __device__ float gershgorin_lower(S A, int n, float* ones, float* sums, float* p
 
 // The whole Lanczos + certificate path.
 //  Gs  G in lower storage, read only (the Lanczos operator);
-//  Gr  G in lower storage, read only (source for P G P; may equal Gs);
-//  Gd  lower storage receiving P G P and then its Cholesky factor (may
-//      equal Gs only if Gs is not needed afterwards).
+//  Gr  G in lower storage, read only (source for P G P; may equal Gs).
 //  Q   shared scratch of jmax * n floats (column j at Q + j*n), jmax <= n.
 //  U, Wm  scratch of kLzMaxK * n floats each (column-major, any memory).
 //  warm / kwarm: previous Ritz vectors (column-major n x kwarm) or kwarm = 0.
 //  gbound: an upper bound of ||G||_2.
+//  panel: lz_cert_floats(NMAX, NT) floats of 16-byte aligned shared
+//      scratch for the certificate (may alias Q and the symv scratch).
 // On success returns k >= 0 (pairs above thr) with s.lam[0..k) and the
 // vectors in U's columns 0..k-1 (U holds ku >= k kept pairs, *ku_out = ku).
-// Returns -1 when the caller must fall back.
-template <int NT, int CT, int RT, class SG, class SR, class SD>
-__device__ int lanczos_certified(SG Gs, SR Gr, SD Gd, int n, float thr, float gbound, float* Q,
+// Returns -1 when the caller must fall back.  G is never modified.
+template <int NT, int NMAX, int CT, int RT, class SG, class SR>
+__device__ int lanczos_certified(SG Gs, SR Gr, int n, float thr, float gbound, float* Q,
                                  int jmax, float* U, float* Wm, const float* warm, int kwarm,
                                  uint32_t seed, EigScratch& s, LzScratch& z, float* panel,
-                                 int* flag, int* ku_out, int slot = -1) {
+                                 int* ku_out, int slot = -1) {
   constexpr int NW = NT / 32;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   PHASE_INIT();
@@ -366,27 +372,26 @@ __device__ int lanczos_certified(SG Gs, SR Gr, SD Gd, int n, float thr, float gb
   if (!(c0 > 0.f)) return -1;
   __syncthreads();
   if (tid < ku) s.lam[tid] = z.Bm[tid * kLzMaxK + tid];
-  // P G P = G - U W^T - W U^T + U B U^T (lower triangle) into Gd
-  for (int r = warp; r < n; r += NW) {
-    for (int cc = lane; cc <= r; cc += 32) {
-      float v = Gr.at(r, cc);
-      for (int p = 0; p < ku; ++p) {
-        const float ur = U[(size_t)p * n + r], uc = U[(size_t)p * n + cc];
-        v -= ur * Wm[(size_t)p * n + cc] + Wm[(size_t)p * n + r] * uc;
-        float ub = 0.f;
-        for (int q = 0; q < ku; ++q) ub = fmaf(z.Bm[p * kLzMaxK + q], U[(size_t)q * n + cc], ub);
-        v = fmaf(ur, ub, v);
-      }
-      Gd.at(r, cc) = v;
+  // P G P = G - U What^T - What U^T with What = W - U sym(B) / 2, staged in
+  // shared memory for the register Cholesky of (c I - P G P)
+  const int n8 = (n + 7) & ~7;
+  float* U8 = panel;
+  float* W8 = panel + 8 * n8;
+  for (int e = tid; e < ku * n8; e += NT) {
+    const int q = e / n8, r = e - q * n8;
+    float u = 0.f, w = 0.f;
+    if (r < n) {
+      u = U[(size_t)q * n + r];
+      w = Wm[(size_t)q * n + r];
+      for (int p = 0; p < ku; ++p)
+        w = fmaf(-0.25f * (z.Bm[p * kLzMaxK + q] + z.Bm[q * kLzMaxK + p]), U[(size_t)p * n + r], w);
     }
+    U8[e] = u;
+    W8[e] = w;
   }
   __syncthreads();
-  // Cholesky backward error is bounded by n^2 eps ||c I - PGP||
-  const float gd = gershgorin_lower<NT, CT, RT>(Gd, n, z.x, z.w, z.part, s.red);
-  const float c = c0 - (float)n * (float)n * FLT_EPSILON * (c0 + gd);
-  if (!(c > 0.f)) return -1;
   PHASE(slot, 11);
-  if (!shifted_cholesky_pd_nb<NT, 8>(Gd, n, c, panel, flag, slot)) return -1;
+  if (!regchol_pd<NT, NMAX>(Gr, n, c0, true, U8, W8, ku, panel + 16 * n8, s.red)) return -1;
   *ku_out = ku;
   return kk;
 }

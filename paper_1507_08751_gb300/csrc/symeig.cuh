@@ -169,320 +169,6 @@ __device__ void tridiagonalize(S G, int n, EigScratch& s) {
 }
 
 // ---------------------------------------------------------------------------
-// Certified test "lambda_max(A) < c": c I - A is positive definite iff its
-// Cholesky factorisation exists.  A is symmetric in the lower triangle of H
-// (n x n) and is overwritten.  Right-looking blocked Cholesky with panels of
-// 32 columns: warp 0 factors the 32x32 diagonal block in registers (lane i
-// owns row i), every row below solves for its 32 panel entries on its own,
-// then a rank-32 update of the trailing triangle.  `panel` is shared scratch
-// of n * kPanelStride + 32 * 33 floats (16-byte aligned) and `flag` one
-// shared int.
-// Returns true iff every pivot was positive.
-// Rounding: a successful factorisation is exact for c I - A + E with
-// ||E||_2 <= n^2 eps ||c I - A||_2 (Cholesky backward error), so callers
-// subtract that margin from c.
-// ---------------------------------------------------------------------------
-constexpr int kPanel = 32;
-constexpr int kPanelStride = 36;  // floats; 4-bank skew keeps 128-bit loads conflict-free
-
-template <int NT, class S>
-__device__ bool shifted_cholesky_pd(S H, int n, float c, float* panel, int* flag, int slot = -1) {
-  constexpr int NW = NT / 32;
-  constexpr int LD = kPanelStride;
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  float* linv = panel + n * LD;  // 32 x 33: inverse of the diagonal block
-  PHASE_INIT();
-  for (int r = warp; r < n; r += NW)
-    for (int cc = lane; cc <= r; cc += 32) {
-      float& h = H.at(r, cc);
-      h = (r == cc ? c : 0.f) - h;
-    }
-  __syncthreads();
-  PHASE(slot, 12);
-  for (int j0 = 0; j0 < n; j0 += kPanel) {
-    const int jb = min(kPanel, n - j0);
-    if (warp == 0) {
-      // factor the diagonal block in panel rows j0..j0+jb-1 (lane = row)
-      float* D = panel + j0 * LD;
-      if (lane < jb)
-        for (int t = 0; t < kPanel; ++t) D[lane * LD + t] = (t <= lane) ? H.at(j0 + lane, j0 + t) : 0.f;
-      __syncwarp();
-      int ok = 1;
-      for (int j = 0; j < jb; ++j) {
-        const float dj = D[j * LD + j];
-        ok &= (dj > 0.f);
-        const float l = sqrtf(dj > 0.f ? dj : 1.f);
-        __syncwarp();
-        if (lane == j) D[j * LD + j] = l;
-        else if (lane > j && lane < jb) D[lane * LD + j] *= 1.f / l;
-        __syncwarp();
-        if (lane > j && lane < jb) {
-          const float lij = D[lane * LD + j];
-          for (int t = j + 1; t <= lane; ++t) D[lane * LD + t] = fmaf(-lij, D[t * LD + j], D[lane * LD + t]);
-        }
-        __syncwarp();
-      }
-      // inverse of the diagonal block, one column per lane
-      if (lane < jb) {
-        for (int i = 0; i < lane; ++i) linv[i * 33 + lane] = 0.f;
-        linv[lane * 33 + lane] = 1.f / D[lane * LD + lane];
-        for (int i = lane + 1; i < jb; ++i) {
-          float acc = 0.f;
-          for (int u = lane; u < i; ++u) acc = fmaf(D[i * LD + u], linv[u * 33 + lane], acc);
-          linv[i * 33 + lane] = -acc / D[i * LD + i];
-        }
-        for (int t = 0; t <= lane; ++t) H.at(j0 + lane, j0 + t) = D[lane * LD + t];
-      }
-      if (lane == 0) *flag = ok;
-    }
-    __syncthreads();
-    PHASE(slot, 13);
-    if (!*flag) return false;
-    // rows below: L(i, :) = H(i, :) L11^{-T}, in place in the panel row,
-    // columns in decreasing order (column t needs H(i, 0..t) only)
-    for (int i = j0 + jb + tid; i < n; i += NT) {
-      float* row = panel + i * LD;
-      for (int u = 0; u < kPanel; ++u) row[u] = (u < jb) ? H.at(i, j0 + u) : 0.f;
-      for (int t = jb - 1; t >= 0; --t) {
-        float acc = 0.f;
-        for (int u = 0; u <= t; ++u) acc = fmaf(row[u], linv[t * 33 + u], acc);
-        row[t] = acc;
-        H.at(i, j0 + t) = acc;
-      }
-    }
-    __syncthreads();
-    PHASE(slot, 14);
-    // trailing update H(r, cc) -= sum_t L(r, t) L(cc, t), j0+jb <= cc <= r.
-    // Work items are (32-row group, 32-column chunk) pairs of the trailing
-    // triangle; lanes own rows (their panel row in registers) and read the
-    // column's panel row as a broadcast.
-    const int t0 = j0 + jb;
-    const int ngroups = (n - t0 + 31) >> 5;
-    const int nitems = ngroups * (ngroups + 1) / 2;
-    for (int it = warp; it < nitems; it += NW) {
-      int g = (int)((sqrtf(8.f * it + 1.f) - 1.f) * 0.5f);
-      while (((g + 1) * (g + 2)) / 2 <= it) ++g;
-      while ((g * (g + 1)) / 2 > it) --g;
-      const int q = it - (g * (g + 1)) / 2;
-      const int r = t0 + 32 * g + lane;
-      const bool rvalid = r < n;
-      float4 pr[kPanel / 4];
-#pragma unroll
-      for (int u = 0; u < kPanel / 4; ++u)
-        pr[u] = rvalid ? *reinterpret_cast<const float4*>(panel + r * LD + 4 * u)
-                       : make_float4(0.f, 0.f, 0.f, 0.f);
-      const int c_begin = t0 + 32 * q;
-      const int c_end = min(c_begin + 32, n);
-      for (int cc = c_begin; cc < c_end; ++cc) {
-        float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f;
-#pragma unroll
-        for (int u = 0; u < kPanel / 4; ++u) {
-          const float4 pc = *reinterpret_cast<const float4*>(panel + cc * LD + 4 * u);
-          a0 = fmaf(pr[u].x, pc.x, a0);
-          a1 = fmaf(pr[u].y, pc.y, a1);
-          a2 = fmaf(pr[u].z, pc.z, a2);
-          a3 = fmaf(pr[u].w, pc.w, a3);
-        }
-        if (rvalid && cc <= r) {
-          float& h = H.at(r, cc);
-          h -= (a0 + a1) + (a2 + a3);
-        }
-      }
-    }
-    __syncthreads();
-    PHASE(slot, 15);
-  }
-  return true;
-}
-
-// ---------------------------------------------------------------------------
-// Same test with narrow panels of PB (8 or 16) columns and one panel of
-// lookahead.  Per panel: every row below the diagonal block forms its PB
-// factor entries by multiplying with the inverse of the (already factored)
-// diagonal block; then warps 1.. apply the rank-PB update to the trailing
-// triangle in register-tiled 4x4 tiles while warp 0 updates and factors the
-// NEXT diagonal block (registers, lanes = rows) and inverts it, so the serial
-// part overlaps the update.  Only the "all pivots positive" answer is kept.
-// `panel` needs n * (PB + 4) + 2 * PB * (PB + 1) + PB * (PB + 4) floats
-// (16-byte aligned); `flag` is one shared int.
-// ---------------------------------------------------------------------------
-template <int PB, class S>
-__device__ int chol_diag_block(S H, int t0, int jb, const float* panel, float* D, float* linv,
-                               bool update) {
-  constexpr int LD = PB + 4;
-  const int lane = threadIdx.x & 31;
-  float row[PB];
-#pragma unroll
-  for (int t = 0; t < PB; ++t) {
-    float v = (lane < jb) ? ((t <= lane) ? H.at(t0 + lane, t0 + t) : 0.f) : (t == lane ? 1.f : 0.f);
-    if (update && lane < jb && t <= lane) {
-      // rank-PB update of the block from the previous panel's factor rows
-      float acc = 0.f;
-#pragma unroll
-      for (int u = 0; u < PB; ++u) acc = fmaf(panel[(t0 + lane) * LD + u], panel[(t0 + t) * LD + u], acc);
-      v -= acc;
-    }
-    row[t] = v;
-  }
-  int ok = 1;
-#pragma unroll
-  for (int j = 0; j < PB; ++j) {
-    const float dj = __shfl_sync(0xffffffffu, row[j], j);
-    ok &= (dj > 0.f);
-    const float l = sqrtf(dj > 0.f ? dj : 1.f);
-    const float inv = 1.f / l;
-    row[j] = (lane == j) ? l : ((lane > j) ? row[j] * inv : row[j]);
-#pragma unroll
-    for (int t = j + 1; t < PB; ++t) {
-      const float ltj = __shfl_sync(0xffffffffu, row[j], t);
-      if (lane >= t) row[t] = fmaf(-row[j], ltj, row[t]);
-    }
-  }
-  if (lane < PB) {
-#pragma unroll
-    for (int t = 0; t < PB; ++t) D[lane * LD + t] = (t <= lane) ? row[t] : 0.f;
-  }
-  __syncwarp();
-  // inverse of the block, column `lane`, by forward substitution
-  if (lane < PB) {
-    float x[PB];
-#pragma unroll
-    for (int i = 0; i < PB; ++i) {
-      float v = 0.f;
-      if (i == lane) {
-        v = 1.f / D[i * LD + i];
-      } else if (i > lane) {
-        float acc = 0.f;
-#pragma unroll
-        for (int u = 0; u < i; ++u)
-          if (u >= lane) acc = fmaf(D[i * LD + u], x[u], acc);
-        v = -acc / D[i * LD + i];
-      }
-      x[i] = v;
-      linv[i * (PB + 1) + lane] = v;
-    }
-  }
-  return __all_sync(0xffffffffu, ok);
-}
-
-template <int NT, int PB, class S>
-__device__ bool shifted_cholesky_pd_nb(S H, int n, float c, float* panel, int* flag, int slot = -1) {
-  constexpr int NW = NT / 32;
-  constexpr int LD = PB + 4;
-  constexpr int TB = PB / 4;                  // 4x4 tile rows covered by the next diagonal block
-  constexpr int SKIP = TB * (TB + 1) / 2;     // its tiles, done by warp 0
-  static_assert(PB == 8 || PB == 16, "panel width");
-  // with a single warp the lookahead block and the trailing update run one
-  // after the other (they touch disjoint entries)
-  constexpr int TW = NT == 32 ? 0 : 32;       // first thread of the trailing update
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  float* linv = panel + n * LD;               // 2 x PB x (PB + 1), double buffered
-  float* D = linv + 2 * PB * (PB + 1);        // PB x LD scratch of the diagonal factor
-  PHASE_INIT();
-  for (int r = warp; r < n; r += NW)
-    for (int cc = lane; cc <= r; cc += 32) {
-      float& h = H.at(r, cc);
-      h = (r == cc ? c : 0.f) - h;
-    }
-  __syncthreads();
-  if (warp == 0) {
-    const int ok = chol_diag_block<PB>(H, 0, min(PB, n), panel, D, linv, false);
-    if (lane == 0) *flag = ok;
-  }
-  __syncthreads();
-  PHASE(slot, 12);
-  int buf = 0;
-  for (int j0 = 0; j0 < n; j0 += PB) {
-    if (!*flag) return false;
-    const int jb = min(PB, n - j0);
-    const float* li = linv + buf * PB * (PB + 1);
-    // rows below: L(i, :) = H(i, :) L11^{-T}
-    for (int i = j0 + jb + tid; i < n; i += NT) {
-      float h[PB];
-#pragma unroll
-      for (int u = 0; u < PB; ++u) h[u] = (u < jb) ? H.at(i, j0 + u) : 0.f;
-      float v[PB];
-#pragma unroll
-      for (int t = 0; t < PB; ++t) {
-        float acc = 0.f;
-#pragma unroll
-        for (int u = 0; u <= t; ++u) acc = fmaf(h[u], li[t * (PB + 1) + u], acc);
-        v[t] = (t < jb) ? acc : 0.f;
-      }
-#pragma unroll
-      for (int t = 0; t < PB; t += 4)
-        *reinterpret_cast<float4*>(panel + i * LD + t) = make_float4(v[t], v[t + 1], v[t + 2], v[t + 3]);
-    }
-    __syncthreads();
-    PHASE(slot, 14);
-    const int t0 = j0 + jb;
-    if (t0 >= n) break;
-    if (warp == 0) {
-      // lookahead: update and factor the next diagonal block
-      const int ok = chol_diag_block<PB>(H, t0, min(PB, n - t0), panel, D,
-                                         linv + (buf ^ 1) * PB * (PB + 1), true);
-      if (lane == 0) *flag = ok;
-    }
-    if (NT == 32) __syncwarp();
-    if (NT == 32 || warp > 0) {
-      // trailing rank-PB update of everything else, 4x4 register tiles
-      const int tr = (n - t0 + 3) >> 2;
-      const int ntiles = tr * (tr + 1) / 2;
-      for (int tt = SKIP + (tid - TW); tt < ntiles; tt += NT - TW) {
-        int a = (int)((sqrtf(8.f * tt + 1.f) - 1.f) * 0.5f);
-        while (((a + 1) * (a + 2)) / 2 <= tt) ++a;
-        while ((a * (a + 1)) / 2 > tt) --a;
-        const int b = tt - (a * (a + 1)) / 2;
-        const int r0 = t0 + 4 * a, c0 = t0 + 4 * b;
-        float acc[4][4];
-#pragma unroll
-        for (int i = 0; i < 4; ++i)
-#pragma unroll
-          for (int j = 0; j < 4; ++j) acc[i][j] = 0.f;
-#pragma unroll
-        for (int u = 0; u < PB; u += 4) {
-          float4 pr[4], pc[4];
-#pragma unroll
-          for (int i = 0; i < 4; ++i) {
-            const int r = min(r0 + i, n - 1), cc = min(c0 + i, n - 1);
-            pr[i] = *reinterpret_cast<const float4*>(panel + r * LD + u);
-            pc[i] = *reinterpret_cast<const float4*>(panel + cc * LD + u);
-          }
-#pragma unroll
-          for (int i = 0; i < 4; ++i)
-#pragma unroll
-            for (int j = 0; j < 4; ++j) {
-              float v = acc[i][j];
-              v = fmaf(pr[i].x, pc[j].x, v);
-              v = fmaf(pr[i].y, pc[j].y, v);
-              v = fmaf(pr[i].z, pc[j].z, v);
-              v = fmaf(pr[i].w, pc[j].w, v);
-              acc[i][j] = v;
-            }
-        }
-#pragma unroll
-        for (int i = 0; i < 4; ++i) {
-          const int r = r0 + i;
-          if (r >= n) break;
-#pragma unroll
-          for (int j = 0; j < 4; ++j) {
-            const int cc = c0 + j;
-            if (cc <= r && cc < n) {
-              float& hh = H.at(r, cc);
-              hh -= acc[i][j];
-            }
-          }
-        }
-      }
-    }
-    __syncthreads();
-    PHASE(slot, 15);
-    buf ^= 1;
-  }
-  return true;
-}
-
-// ---------------------------------------------------------------------------
 // y = G x for G symmetric in the lower triangle (n <= 32 * RMAX * NT/32...):
 // warp w takes rows r = w, w + NW, ...; for row r lane l reads G(r, c),
 // c = l + 32 t <= r (contiguous), adds G(r, c) x_c to the row sum and
@@ -497,8 +183,12 @@ __device__ void symv_lower(S G, int n, const float* x, float* y, float* part) {
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   float colp[CT];
   float rs[RT];
+  float xv[CT];
 #pragma unroll
-  for (int t = 0; t < CT; ++t) colp[t] = 0.f;
+  for (int t = 0; t < CT; ++t) {
+    colp[t] = 0.f;
+    xv[t] = (lane + 32 * t < n) ? x[lane + 32 * t] : 0.f;
+  }
 #pragma unroll
   for (int q = 0; q < RT; ++q) {
     rs[q] = 0.f;
@@ -510,7 +200,7 @@ __device__ void symv_lower(S G, int n, const float* x, float* y, float* part) {
         const int cc = lane + 32 * t;
         if (cc <= r) {
           const float g = ABS ? fabsf(G.at(r, cc)) : G.at(r, cc);
-          rs[q] = fmaf(g, x[cc], rs[q]);
+          rs[q] = fmaf(g, xv[t], rs[q]);
           if (cc < r) colp[t] = fmaf(g, xr, colp[t]);
         }
       }
