@@ -273,11 +273,13 @@ eig_big_kernel(ScaleLaunch a, const float* __restrict__ Gall, BigWorkspace ws) {
       const float n8 = (float)((nn + 7) & ~7);
       const float margin = n8 * n8 * FLT_EPSILON * (thr + gbound);
       const float c = thr - margin;
+      PHASE(3, 6);
       if (c > 0.f &&
           regchol_pd<NT, NMAX>(Gacc, nn, c, false, nullptr, nullptr, 0, panel, s.red)) {
         skipped = true;
         k = 0;
       }
+      PHASE(3, 7);
     }
   }
   PHASE(3, 1);
@@ -290,7 +292,7 @@ eig_big_kernel(ScaleLaunch a, const float* __restrict__ Gall, BigWorkspace ws) {
     float* Wm = Y + (size_t)kLzMaxK * nn;
     k = lanczos_certified<NT, NMAX, kEigCT, kEigRT>(Gacc, Gacc, nn, thr, gbound, Qs,
                                                     min(nn, kLzMaxJ), U, Wm, warm, kwarm,
-                                                    0x1234567u + 977u * b, s, z, panel, &ku, 3);
+                                                    0x1234567u + 977u * b, s, z, panel, &ku, 4);
     lanczos_ok = k >= 0;
     PHASE(3, 5);
     if (lanczos_ok) {

@@ -338,6 +338,7 @@ __device__ int lanczos_certified(SG Gs, SR Gr, int n, float thr, float gbound, f
     U[(size_t)q * n + r] = v;
   }
   __syncthreads();
+  PHASE(slot, 12);
   // W = G U, B = U^T W, rho
   for (int q = 0; q < ku; ++q) {
     for (int e = tid; e < n; e += NT) z.x[e] = U[(size_t)q * n + e];
@@ -361,6 +362,7 @@ __device__ int lanczos_certified(SG Gs, SR Gr, int n, float thr, float gbound, f
     part = fmaf(rr, rr, part);
   }
   const float rho = sqrtf(block_sum<NT>(part, s.red));
+  PHASE(slot, 13);
   // kept pairs: Rayleigh quotients, count above thr; pairs above thr first
   int kk = 0;
   for (int q = 0; q < ku; ++q) {
@@ -392,6 +394,7 @@ __device__ int lanczos_certified(SG Gs, SR Gr, int n, float thr, float gbound, f
   __syncthreads();
   PHASE(slot, 11);
   if (!regchol_pd<NT, NMAX>(Gr, n, c0, true, U8, W8, ku, panel + 16 * n8, s.red)) return -1;
+  PHASE(slot, 14);
   *ku_out = ku;
   return kk;
 }

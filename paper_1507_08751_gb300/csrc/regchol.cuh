@@ -16,8 +16,8 @@
 // Per panel of 8 columns (right-looking, Sec. 4.2.9 of the same book):
 //   1. the owners of the panel's tiles write them to a column-major strip
 //      in shared memory (double-buffered),
-//   2. every warp factors the 8x8 diagonal block in registers (lane = row;
-//      all warps get the same answer, so no barrier is needed before 3),
+//   2. every thread factors the 8x8 diagonal block in its registers (all
+//      get the same answer, so no barrier is needed before 3),
 //   3. each row below solves for its 8 factor entries (one thread per row),
 //   4. every thread subtracts the rank-8 product from its active tiles.
 // Two CTA barriers per panel; no shared-memory traffic for the trailing
@@ -35,10 +35,10 @@
 
 namespace msllr {
 
-// shared scratch (floats) of regchol_pd: two 8 x n8 strips and one 8 x 9
-// factor block per warp
+// shared scratch (floats) of regchol_pd: two 8 x n8 strips and one packed
+// 8 x 8 factor per warp
 __host__ __device__ constexpr int regchol_scratch_floats(int nmax, int nt) {
-  return 16 * nmax + (nt / 32) * 72;
+  return 16 * nmax + (nt / 32) * 36;
 }
 
 __device__ __forceinline__ int regchol_tri_row(int e) {
@@ -68,7 +68,7 @@ __device__ bool regchol_pd(SX src, int n, float c0, bool frob, const float* U, c
   const int n8 = (n + 7) & ~7, nb = n8 >> 2;
   const int ntile = nb >= 3 ? (nb - 2) * (nb - 1) / 2 : 0;
   float* S = scr;                   // strips: S[(buf * 8 + u) * n8 + r]
-  float* Lw = S + 16 * n8 + warp * 72;
+  float* Lw = S + 16 * n8 + warp * 36;  // this warp's copy of the diagonal factor
 
   float v[SL][16];
   int ta[SL], tb[SL];
@@ -165,32 +165,37 @@ __device__ bool regchol_pd(SX src, int n, float c0, bool frob, const float* U, c
         }
     }
     __syncthreads();
-    // 8x8 diagonal block, factored by every warp (lane l < 8 holds row l)
-    float row[8];
+    // 8x8 diagonal block, factored by every thread in registers from
+    // broadcast loads (packed lower triangle, the diagonal replaced by the
+    // reciprocal pivots); rsqrt (a few ulp) instead of sqrt and a division
+    // keeps the chain of 8 dependent pivots short, and its error stays far
+    // inside the backward-error margin
+    float L[36];
 #pragma unroll
-    for (int t = 0; t < 8; ++t) row[t] = (lane < 8 && t <= lane) ? Sb[t * n8 + j0 + lane] : 0.f;
+    for (int t = 0; t < 8; ++t)
+#pragma unroll
+      for (int u = 0; u <= t; ++u) L[t * (t + 1) / 2 + u] = Sb[u * n8 + j0 + t];
     bool ok = true;
 #pragma unroll
     for (int j = 0; j < 8; ++j) {
-      const float dj = __shfl_sync(0xffffffffu, row[j], j);
+      const float dj = L[j * (j + 1) / 2 + j];
       ok = ok && (dj > 0.f);
-      // rsqrt (a few ulp) instead of sqrt and a division: the chain of 8
-      // dependent pivots is the serial part of every panel, and the error
-      // stays far inside the backward-error margin
       const float inv = rsqrtf(dj > 0.f ? dj : 1.f);
-      const float l = dj * inv;
-      row[j] = (lane == j) ? l : ((lane > j) ? row[j] * inv : row[j]);
+      L[j * (j + 1) / 2 + j] = inv;
 #pragma unroll
-      for (int t = j + 1; t < 8; ++t) {
-        const float ltj = __shfl_sync(0xffffffffu, row[j], t);
-        if (lane >= t) row[t] = fmaf(-row[j], ltj, row[t]);
-      }
+      for (int i = j + 1; i < 8; ++i) L[i * (i + 1) / 2 + j] *= inv;
+#pragma unroll
+      for (int i = j + 1; i < 8; ++i)
+#pragma unroll
+        for (int t = j + 1; t <= i; ++t)
+          L[i * (i + 1) / 2 + t] = fmaf(-L[i * (i + 1) / 2 + j], L[t * (t + 1) / 2 + j],
+                                        L[i * (i + 1) / 2 + t]);
     }
     if (!ok) return false;
-    if (lane < 8) {
+    // one copy of the factor per warp frees the registers for the solve
+    if (lane == 0) {
 #pragma unroll
-      for (int t = 0; t < 8; ++t) Lw[lane * 9 + t] = row[t];
-      Lw[lane * 9 + 8] = 1.f / row[lane];  // off the critical chain
+      for (int e = 0; e < 36; ++e) Lw[e] = L[e];
     }
     __syncwarp();
     // rows below the block: L21 = A21 L11^{-T}
@@ -200,8 +205,8 @@ __device__ bool regchol_pd(SX src, int n, float c0, bool frob, const float* U, c
       for (int t = 0; t < 8; ++t) {
         float acc = Sb[t * n8 + r];
 #pragma unroll
-        for (int u = 0; u < t; ++u) acc = fmaf(-x[u], Lw[t * 9 + u], acc);
-        x[t] = acc * Lw[t * 9 + 8];
+        for (int u = 0; u < t; ++u) acc = fmaf(-x[u], Lw[t * (t + 1) / 2 + u], acc);
+        x[t] = acc * Lw[t * (t + 1) / 2 + t];
       }
 #pragma unroll
       for (int t = 0; t < 8; ++t) Sb[t * n8 + r] = x[t];
