@@ -166,14 +166,11 @@ gram_reduce_kernel(const float* __restrict__ part, float* __restrict__ G, int nn
   }
 }
 
-constexpr int kEigCT = kEigMax / 32;                   // symv column slots per lane
-constexpr int kEigRT = kEigMax / (kEigThreads / 32);   // symv rows per warp
-constexpr int kEigPart = (kEigThreads / 32) * 32 * kEigCT;
-// panel region: Cholesky panel, or Lanczos Q (kLzMaxJ x n) followed by the symv scratch
-constexpr int kEigPanelFloats =
-    (lz_cert_floats(kEigMax, kEigThreads) > kLzMaxJ * kEigMax + kEigPart)
-        ? lz_cert_floats(kEigMax, kEigThreads)
-        : kLzMaxJ * kEigMax + kEigPart;
+// panel region: Lanczos Q (kLzMaxJ x n), or the certificate's staging and
+// Cholesky scratch, or the V_f staging
+constexpr int kEigPanelFloats = (lz_cert_floats(kEigMax, kEigThreads) > kLzMaxJ * kEigMax)
+                                    ? lz_cert_floats(kEigMax, kEigThreads)
+                                    : kLzMaxJ * kEigMax;
 
 size_t eig_smem_bytes(int nn) {
   return sizeof(float) * ((((size_t)nn * (nn + 1) / 2 + 3) & ~(size_t)3) + kEigPanelFloats +
@@ -198,7 +195,7 @@ __device__ bool power_above(S G, int n, float thr, EigScratch& s, LzScratch& z) 
   for (int it = 0; it < 3; ++it) {
     for (int e = tid; e < n; e += NT) z.x[e] /= nrm;
     __syncthreads();
-    symv_lower<NT, kEigCT, kEigRT>(G, n, z.x, z.w, z.part);
+    symv_rows<NT, kEigMax>(G, n, z.x, z.w);
     float p1 = 0.f, p2 = 0.f;
     for (int e = tid; e < n; e += NT) {
       p1 = fmaf(z.x[e], z.w[e], p1);
@@ -240,10 +237,10 @@ eig_big_kernel(ScaleLaunch a, const float* __restrict__ Gall, BigWorkspace ws) {
   s.cnt = reinterpret_cast<int*>(s.xs + NT);
   s.red = reinterpret_cast<float*>(s.cnt + NT);
   LzScratch z;
-  // Lanczos Q and the symv scratch share the panel region with the Cholesky
-  // panel; they are never live together
+  // Lanczos Q shares the panel region with the certificate scratch; they
+  // are never live together
   float* Qs = panel;
-  lz_bind<NT>(z, s.red + 64, NMAX, kLzMaxJ, panel + kLzMaxJ * NMAX);
+  lz_bind<NT>(z, s.red + 64, NMAX, kLzMaxJ);
   PHASE_INIT();
   LowerPacked Gacc{Gp};
   auto load_g = [&]() {
@@ -258,56 +255,64 @@ eig_big_kernel(ScaleLaunch a, const float* __restrict__ Gall, BigWorkspace ws) {
   float tr = 0.f;
   for (int i = tid; i < nn; i += NT) tr += Gacc.at(i, i);
   tr = block_sum<NT>(tr, s.red);
-  const float rs = gershgorin_lower<NT, kEigCT, kEigRT>(Gacc, nn, z.x, z.w, z.part, s.red);
+  const float rs = gershgorin_lower<NT, NMAX>(Gacc, nn, z.x, z.w, s.red);
   const float gbound = fminf(tr, rs);
   const bool full = (a.m == a.M && a.n == a.N);
   const int kwarm = (a.warm_start && (full || !a.shift)) ? min(ws.kwarm[b], kLzMaxK) : 0;
-  bool skipped = false;
-  int k = -1;
-  if (a.skip_bound) {
-    if (gbound <= thr) {
-      skipped = true;
-      k = 0;
-    } else if (kwarm == 0 && !power_above(Gacc, nn, thr, s, z)) {
-      // certified lambda_max(G) < tau^2 by Cholesky of (tau^2 - margin) I - G
-      const float n8 = (float)((nn + 7) & ~7);
-      const float margin = n8 * n8 * FLT_EPSILON * (thr + gbound);
-      const float c = thr - margin;
-      PHASE(3, 6);
-      if (c > 0.f &&
-          regchol_pd<NT, NMAX>(Gacc, nn, c, false, nullptr, nullptr, 0, panel, s.red)) {
+  bool skipped = false, lanczos_ok = false;
+  int k = -1, ku = 0;
+  // Two certificates share one Cholesky call site: attempt 0 tests
+  // lambda_max(G) < tau^2 (zero rank), attempt 1 certifies the Lanczos pairs
+  // by the deflated matrix.
+  const int n8 = (nn + 7) & ~7;
+  float* U = Y;
+  float* Wm = Y + (size_t)kLzMaxK * nn;
+  for (int attempt = 0; attempt < 2 && k < 0 && a.skip_bound; ++attempt) {
+    float c0;
+    int kk = 0;
+    if (attempt == 0) {
+      if (gbound <= thr) {
         skipped = true;
         k = 0;
+        break;
       }
-      PHASE(3, 7);
+      if (kwarm > 0 || power_above(Gacc, nn, thr, s, z)) continue;
+      // certified lambda_max(G) < tau^2 by Cholesky of (tau^2 - margin) I - G
+      c0 = thr - (float)n8 * (float)n8 * FLT_EPSILON * (thr + gbound);
+      if (!(c0 > 0.f)) continue;
+      PHASE(3, 6);
+    } else {
+      PHASE(3, 1);
+      const float* warm = ws.warm + (size_t)b * kLzMaxK * nn;
+      kk = lanczos_candidates<NT, NMAX>(Gacc, nn, thr, gbound, Qs,
+                                                        min(nn, kLzMaxJ), U, Wm, warm, kwarm,
+                                                        0x1234567u + 977u * b, s, z, panel, &ku,
+                                                        &c0, 4);
+      PHASE(3, 5);
+      if (kk < 0) break;
+    }
+    const bool pd = regchol_pd<NT, NMAX>(Gacc, nn, c0, attempt == 1, panel, panel + 8 * n8,
+                                         attempt == 1 ? ku : 0, panel + 16 * n8, s.red,
+                                         3 + attempt);
+    PHASE(3, 7 + attempt);
+    if (pd) {
+      k = kk;
+      skipped = attempt == 0;
+      lanczos_ok = attempt == 1;
     }
   }
-  PHASE(3, 1);
-  bool lanczos_ok = false;
-  int ku = 0;
-  if (k < 0 && a.skip_bound) {
-    // Lanczos + residual + deflated-Cholesky certificate
-    const float* warm = ws.warm + (size_t)b * kLzMaxK * nn;
-    float* U = Y;
-    float* Wm = Y + (size_t)kLzMaxK * nn;
-    k = lanczos_certified<NT, NMAX, kEigCT, kEigRT>(Gacc, Gacc, nn, thr, gbound, Qs,
-                                                    min(nn, kLzMaxJ), U, Wm, warm, kwarm,
-                                                    0x1234567u + 977u * b, s, z, panel, &ku, 4);
-    lanczos_ok = k >= 0;
-    PHASE(3, 5);
-    if (lanczos_ok) {
-      // keep the Ritz vectors for the next call's warm start
-      float* wdst = ws.warm + (size_t)b * kLzMaxK * nn;
-      for (int e = tid; e < nn * ku; e += NT) wdst[e] = U[e];
-      if (tid == 0) ws.kwarm[b] = ku;
-      // V_f (row-major, ld nn) for the rebuild, staged through shared memory
-      for (int e = tid; e < nn * k; e += NT) panel[e] = U[e];
-      __syncthreads();
-      for (int e = tid; e < nn * k; e += NT) {
-        const int i = e / k, q = e - i * k;
-        const float sig = sqrtf(s.lam[q]);
-        Y[(size_t)i * nn + q] = panel[(size_t)q * nn + i] * sqrtf(fmaxf(1.f - a.tau / sig, 0.f));
-      }
+  if (lanczos_ok) {
+    // keep the Ritz vectors for the next call's warm start
+    float* wdst = ws.warm + (size_t)b * kLzMaxK * nn;
+    for (int e = tid; e < nn * ku; e += NT) wdst[e] = U[e];
+    if (tid == 0) ws.kwarm[b] = ku;
+    // V_f (row-major, ld nn) for the rebuild, staged through shared memory
+    for (int e = tid; e < nn * k; e += NT) panel[e] = U[e];
+    __syncthreads();
+    for (int e = tid; e < nn * k; e += NT) {
+      const int i = e / k, q = e - i * k;
+      const float sig = sqrtf(s.lam[q]);
+      Y[(size_t)i * nn + q] = panel[(size_t)q * nn + i] * sqrtf(fmaxf(1.f - a.tau / sig, 0.f));
     }
   }
   if (k < 0) {

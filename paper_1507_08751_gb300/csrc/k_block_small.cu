@@ -76,15 +76,13 @@ __global__ void __launch_bounds__(NT) blocksvt_small_kernel(ScaleLaunch a) {
   s.xs = s.hi + NT;
   s.cnt = reinterpret_cast<int*>(s.xs + NT);
   s.red = reinterpret_cast<float*>(s.cnt + NT);
-  // Lanczos region: Q (NMAX x JCAP), U and W (NMAX x kLzMaxK each), symv scratch
+  // Lanczos region: Q (NMAX x JCAP), U and W (NMAX x kLzMaxK each)
   constexpr int JCAP = NMAX < kLzMaxJ ? NMAX : kLzMaxJ;
-  constexpr int CT = (NMAX + 31) / 32, RT = NMAX / (NT / 32);
   float* Qs = s.red + 64;
   float* Us = Qs + NMAX * JCAP;
   float* Ws = Us + NMAX * kLzMaxK;
-  float* part = Ws + NMAX * kLzMaxK;
   LzScratch z;
-  lz_bind<NT>(z, part + (NT / 32) * 32 * CT, NMAX, JCAP, part);
+  lz_bind<NT>(z, Ws + NMAX * kLzMaxK, NMAX, JCAP);
 
   // gather A = A1 + A2 on the shifted grid; ||C||_F^2
   const int melem = a.m * a.n;
@@ -102,6 +100,8 @@ __global__ void __launch_bounds__(NT) blocksvt_small_kernel(ScaleLaunch a) {
   if constexpr (NT == 32) __syncwarp();
   PHASE(SLOT, 0);
   const float thr = a.tau * a.tau;
+  const int n8 = (nn + 7) & ~7;
+  float c_skip = 0.f;  // shift of the zero-rank Cholesky test (0: no test)
   int k = 0;
   bool skipped = false;
   float gbound = fro;  // trace(G) >= lambda_max(G)
@@ -139,34 +139,48 @@ __global__ void __launch_bounds__(NT) blocksvt_small_kernel(ScaleLaunch a) {
         skipped = true;
       } else {
         // certified lambda_max(G) < tau^2 by Cholesky of (tau^2 - margin) I - G
-        const int n8 = (nn + 7) & ~7;
-        const float margin = (float)(n8 * n8) * FLT_EPSILON * (thr + rs);
-        const float c = thr - margin;
-        if (c > 0.f &&
-            regchol_pd<NT, NMAX>(LowerFull{G, ldg}, nn, c, false, nullptr, nullptr, 0, panel, s.red))
-          skipped = true;
-        __syncthreads();
+        c_skip = thr - (float)(n8 * n8) * FLT_EPSILON * (thr + rs);
       }
     }
   }
   PHASE(SLOT, 2);
+  // Two certificates share one Cholesky call site: attempt 0 tests
+  // lambda_max(G) < tau^2 (zero rank), attempt 1 certifies the Lanczos pairs
+  // by the deflated matrix (G stays intact for the fallback).
   bool lanczos_ok = false;
-  if (!skipped && a.skip_bound) {
-    // certified Lanczos (G stays intact for the fallback)
-    int ku = 0;
-    k = lanczos_certified<NT, NMAX, CT, RT>(LowerFull{G, ldg}, LowerFull{G, ldg}, nn, thr, gbound,
-                                            Qs, nn < JCAP ? nn : JCAP, Us, Ws, nullptr, 0,
-                                            0x51ED27u + 131u * blockIdx.x, s, z, panel, &ku);
-    lanczos_ok = k >= 0;
-    if (lanczos_ok) {
-      for (int e = tid; e < nn * k; e += NT) {
-        const int i = e / k, q = e - i * k;
-        Y[i * ldy + q] = Us[q * nn + i];
-      }
-      __syncthreads();
+  // (blocks of width <= 16: the Householder path below is cheaper than
+  // Lanczos for candidates that fail the zero-rank test)
+  constexpr int kAttempts = NMAX <= 16 ? 1 : 2;
+  for (int attempt = 0; attempt < kAttempts && !skipped && a.skip_bound; ++attempt) {
+    float c0 = c_skip;
+    int kk = 0, ku = 0;
+    if (attempt == 0) {
+      if (!(c_skip > 0.f)) continue;
     } else {
-      k = 0;
+      kk = lanczos_candidates<NT, NMAX>(LowerFull{G, ldg}, nn, thr, gbound, Qs,
+                                                nn < JCAP ? nn : JCAP, Us, Ws, nullptr, 0,
+                                                0x51ED27u + 131u * blockIdx.x, s, z, panel, &ku,
+                                                &c0, 5 + SLOT);
+      PHASE(SLOT, 10);
+      if (kk < 0) break;
     }
+    const bool pd = regchol_pd<NT, NMAX>(LowerFull{G, ldg}, nn, c0, attempt == 1, panel,
+                                         panel + 8 * n8, attempt == 1 ? ku : 0, panel + 16 * n8,
+                                         s.red, attempt == 1 ? 5 + SLOT : -1);
+    __syncthreads();
+    PHASE(SLOT, 8 + attempt);
+    if (pd) {
+      skipped = attempt == 0;
+      lanczos_ok = attempt == 1;
+      k = kk;
+    }
+  }
+  if (lanczos_ok) {
+    for (int e = tid; e < nn * k; e += NT) {
+      const int i = e / k, q = e - i * k;
+      Y[i * ldy + q] = Us[q * nn + i];
+    }
+    __syncthreads();
   }
   PHASE(SLOT, 7);
   if (!skipped && !lanczos_ok) {
@@ -241,10 +255,9 @@ __global__ void __launch_bounds__(NT) blocksvt_small_kernel(ScaleLaunch a) {
 template <int NT, int NMAX>
 size_t small_smem_bytes(int mm, int nn) {
   constexpr int JCAP = NMAX < kLzMaxJ ? NMAX : kLzMaxJ;
-  constexpr int CT = (NMAX + 31) / 32;
   return sizeof(float) * ((size_t)2 * mm * nn + (size_t)nn * (2 * nn + 2) + lz_cert_floats(NMAX, NT) +
                           4 + 9 * NMAX + 4 * NT + 64 + NMAX * JCAP + 2 * NMAX * kLzMaxK +
-                          (NT / 32) * 32 * CT + lz_scratch_floats(NMAX, JCAP));
+                          lz_scratch_floats(NMAX, JCAP));
 }
 
 template <int NT, int NMAX>

@@ -41,37 +41,33 @@ __host__ __device__ constexpr int lz_cert_floats(int nmax, int nt) {
 struct LzScratch {
   float* x;      // [n] current Lanczos vector q_j
   float* w;      // [n] G q_j, then the next residual
-  float* qprev;  // [n] q_{j-1}
   float* alpha;  // [kLzMaxJ]
   float* beta;   // [kLzMaxJ]
-  float* h;      // [kLzMaxJ + 8] reorthogonalisation coefficients
+  float* h;      // [2 * kLzMaxJ + 8] projection coefficients (two passes)
   float* ty;     // [jcap * kLzMaxK] eigenvectors of T_J (row i, column q)
   float* lu;     // [4 * jcap * kLzMaxK] inverse-iteration LU factors
   unsigned* piv; // [2 * kLzMaxK] pivot bits
   float* Bm;     // [kLzMaxK * kLzMaxK] U^T G U
-  float* part;   // symv scratch (NW * 32 * CT floats)
   int jcap;      // row capacity of ty / lu (>= Lanczos steps)
 };
 
 // floats of LzScratch for a given n capacity and J capacity
 __host__ __device__ constexpr int lz_scratch_floats(int nmax, int jcap) {
-  return 3 * nmax + 2 * kLzMaxJ + (kLzMaxJ + 8) + jcap * kLzMaxK + 4 * jcap * kLzMaxK +
+  return 2 * nmax + 2 * kLzMaxJ + (2 * kLzMaxJ + 8) + jcap * kLzMaxK + 4 * jcap * kLzMaxK +
          2 * kLzMaxK + kLzMaxK * kLzMaxK;
 }
 
 template <int NT>
-__device__ void lz_bind(LzScratch& z, float* base, int nmax, int jcap, float* part) {
+__device__ void lz_bind(LzScratch& z, float* base, int nmax, int jcap) {
   z.x = base;
   z.w = z.x + nmax;
-  z.qprev = z.w + nmax;
-  z.alpha = z.qprev + nmax;
+  z.alpha = z.w + nmax;
   z.beta = z.alpha + kLzMaxJ;
   z.h = z.beta + kLzMaxJ;
-  z.ty = z.h + kLzMaxJ + 8;
+  z.ty = z.h + 2 * kLzMaxJ + 8;
   z.lu = z.ty + jcap * kLzMaxK;
   z.piv = reinterpret_cast<unsigned*>(z.lu + 4 * jcap * kLzMaxK);
   z.Bm = reinterpret_cast<float*>(z.piv + 2 * kLzMaxK);
-  z.part = part;
   z.jcap = jcap;
 }
 
@@ -85,27 +81,91 @@ __device__ __forceinline__ float lz_hash(uint32_t seed, int i) {
   return (float)(h >> 8) * (2.f / 16777216.f) - 1.f;
 }
 
-// Orthogonalise the shared vector w (n) against Q's columns 0..nq-1 (column
-// j at Q + j*n, shared) twice, classical Gram-Schmidt per pass.
-template <int NT>
-__device__ void lz_reorth(float* w, const float* Q, int n, int nq, float* h) {
+// y = G x with TPR threads per row (G symmetric in lower storage, n <= NMAX,
+// x and y shared, y must not alias x).  Each thread walks its part of row r
+// in two ranges, G(r, c) for c <= r and G(c, r) above, so every element of
+// the row is read once and the only reduction is a shuffle inside the TPR
+// lanes of the row.  Ends with a CTA barrier.
+template <int NT, int NMAX, bool ABS = false, class S>
+__device__ void symv_rows(S G, int n, const float* x, float* y) {
+  constexpr int TPR = (NT / NMAX >= 2) ? 2 : 1;
+  const int tid = threadIdx.x, p = tid % TPR;
+  // the row loop is uniform across the CTA so that every lane reaches the
+  // shuffle below
+  for (int r0 = 0; r0 < n; r0 += NT / TPR) {
+    const int r = r0 + tid / TPR;
+    float a0 = 0.f, a1 = 0.f;
+    if (r < n) {
+      int c = p;
+      for (; c + TPR <= r; c += 2 * TPR) {
+        const float g0 = G.at(r, c), g1 = G.at(r, c + TPR);
+        a0 = fmaf(ABS ? fabsf(g0) : g0, x[c], a0);
+        a1 = fmaf(ABS ? fabsf(g1) : g1, x[c + TPR], a1);
+      }
+      if (c <= r) {
+        const float g = G.at(r, c);
+        a0 = fmaf(ABS ? fabsf(g) : g, x[c], a0);
+        c += TPR;
+      }
+      for (; c + TPR < n; c += 2 * TPR) {
+        const float g0 = G.at(c, r), g1 = G.at(c + TPR, r);
+        a0 = fmaf(ABS ? fabsf(g0) : g0, x[c], a0);
+        a1 = fmaf(ABS ? fabsf(g1) : g1, x[c + TPR], a1);
+      }
+      if (c < n) {
+        const float g = G.at(c, r);
+        a0 = fmaf(ABS ? fabsf(g) : g, x[c], a0);
+      }
+    }
+    float acc = a0 + a1;
+    if constexpr (TPR == 2) acc += __shfl_xor_sync(0xffffffffu, acc, 1);
+    if (p == 0 && r < n) y[r] = acc;
+  }
+  __syncthreads();
+}
+
+// w <- (I - Q Q^T) w twice (classical Gram-Schmidt, two passes) over Q's
+// columns 0..nq-1 (column i at Q + i*n, shared).  h1 and h2 receive the two
+// passes' coefficients; returns ||w||^2 after the second pass.  Small n:
+// one thread per coefficient (skewed walk, conflict-free); large n: one
+// warp per coefficient.
+template <int NT, int NMAX>
+__device__ float lz_project(float* w, const float* Q, int n, int nq, float* h1, float* h2,
+                            float* red) {
   constexpr int NW = NT / 32;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  float part = 0.f;
+#pragma unroll
   for (int pass = 0; pass < 2; ++pass) {
-    for (int i = warp; i < nq; i += NW) {
-      float d = 0.f;
-      for (int e = lane; e < n; e += 32) d = fmaf(Q[i * n + e], w[e], d);
-      d = warp_sum(d);
-      if (lane == 0) h[i] = d;
+    float* h = pass == 0 ? h1 : h2;
+    if constexpr (NMAX <= 64) {
+      for (int i = tid; i < nq; i += NT) {
+        float d = 0.f;
+        int e = i % n;
+        for (int t = 0; t < n; ++t) {
+          d = fmaf(Q[i * n + e], w[e], d);
+          if (++e == n) e = 0;
+        }
+        h[i] = d;
+      }
+    } else {
+      for (int i = warp; i < nq; i += NW) {
+        float d = 0.f;
+        for (int e = lane; e < n; e += 32) d = fmaf(Q[i * n + e], w[e], d);
+        d = warp_sum(d);
+        if (lane == 0) h[i] = d;
+      }
     }
     __syncthreads();
     for (int e = tid; e < n; e += NT) {
       float v = w[e];
       for (int i = 0; i < nq; ++i) v = fmaf(-h[i], Q[i * n + e], v);
       w[e] = v;
+      if (pass == 1) part = fmaf(v, v, part);
     }
     __syncthreads();
   }
+  return block_sum<NT>(part, red);
 }
 
 // Inverse iteration on T (s.d, s.e, size J) for the k shifts s.shf[0..k),
@@ -210,34 +270,40 @@ __device__ int lz_ritz(int J, float thr, EigScratch& s, LzScratch& z, float* tno
 }
 
 // Gershgorin bound max_i sum_j |A_ij| of a symmetric matrix in lower storage:
-// the row sums are |A| times a vector of ones (conflict-free symv pattern).
-template <int NT, int CT, int RT, class S>
-__device__ float gershgorin_lower(S A, int n, float* ones, float* sums, float* part, float* red) {
+// the row sums are |A| times a vector of ones.
+template <int NT, int NMAX, class S>
+__device__ float gershgorin_lower(S A, int n, float* ones, float* sums, float* red) {
   for (int e = threadIdx.x; e < n; e += NT) ones[e] = 1.f;
   __syncthreads();
-  symv_lower<NT, CT, RT, S, true>(A, n, ones, sums, part);
+  symv_rows<NT, NMAX, true>(A, n, ones, sums);
   float m = 0.f;
   for (int e = threadIdx.x; e < n; e += NT) m = fmaxf(m, sums[e]);
   return block_max<NT>(m, red);
 }
 
 // The whole Lanczos + certificate path.
-//  Gs  G in lower storage, read only (the Lanczos operator);
-//  Gr  G in lower storage, read only (source for P G P; may equal Gs).
+//  Gs  G in lower storage, read only (the Lanczos operator).
 //  Q   shared scratch of jmax * n floats (column j at Q + j*n), jmax <= n.
 //  U, Wm  scratch of kLzMaxK * n floats each (column-major, any memory).
 //  warm / kwarm: previous Ritz vectors (column-major n x kwarm) or kwarm = 0.
 //  gbound: an upper bound of ||G||_2.
 //  panel: lz_cert_floats(NMAX, NT) floats of 16-byte aligned shared
 //      scratch for the certificate (may alias Q and the symv scratch).
-// On success returns k >= 0 (pairs above thr) with s.lam[0..k) and the
-// vectors in U's columns 0..k-1 (U holds ku >= k kept pairs, *ku_out = ku).
-// Returns -1 when the caller must fall back.  G is never modified.
-template <int NT, int NMAX, int CT, int RT, class SG, class SR>
-__device__ int lanczos_certified(SG Gs, SR Gr, int n, float thr, float gbound, float* Q,
-                                 int jmax, float* U, float* Wm, const float* warm, int kwarm,
-                                 uint32_t seed, EigScratch& s, LzScratch& z, float* panel,
-                                 int* ku_out, int slot = -1) {
+// Steps 1-3 and the set-up of step 4.  On success returns k >= 0 (pairs
+// above thr) with s.lam[0..k), the vectors in U's columns 0..k-1 (U holds
+// ku >= k kept pairs, *ku_out = ku), U and What = W - U sym(B) / 2 staged at
+// panel and panel + 8 n8 (n8 = roundup(n, 8)) and the certificate shift
+// in *c0_out: the pairs are certified iff
+//   regchol_pd<NT, NMAX>(G, n, *c0_out, true, panel, panel + 8 n8, ku,
+//                        panel + 16 n8, red)
+// holds (one call site per kernel keeps the code size and the register
+// allocation of that routine in one place).  Returns -1 when the caller
+// must fall back.  G is never modified.
+template <int NT, int NMAX, class SG>
+__device__ int lanczos_candidates(SG Gs, int n, float thr, float gbound, float* Q, int jmax,
+                                  float* U, float* Wm, const float* warm, int kwarm,
+                                  uint32_t seed, EigScratch& s, LzScratch& z, float* panel,
+                                  int* ku_out, float* c0_out, int slot = -1) {
   constexpr int NW = NT / 32;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   PHASE_INIT();
@@ -252,33 +318,22 @@ __device__ int lanczos_certified(SG Gs, SR Gr, int n, float thr, float gbound, f
     z.x[e] = v;
     part = fmaf(v, v, part);
   }
-  const float nrm = sqrtf(block_sum<NT>(part, s.red));
-  for (int e = tid; e < n; e += NT) {
-    z.x[e] /= nrm;
-    Q[e] = z.x[e];
-    z.qprev[e] = 0.f;
-  }
+  const float inrm = 1.f / sqrtf(block_sum<NT>(part, s.red));
+  for (int e = tid; e < n; e += NT) Q[e] = z.x[e] * inrm;
   __syncthreads();
   const int jmin = min(jmax, kwarm > 0 ? kwarm + 3 : 8);
   int J = 0, k = -1;
   float tn = 0.f;
-  float beta_prev = 0.f;
   uint32_t restart = 1;
   PHASE(slot, 6);
   for (int j = 0; j < jmax; ++j) {
-    symv_lower<NT, CT, RT>(Gs, n, z.x, z.w, z.part);
+    // w = G q_j, then w <- w - Q_j Q_j^T w twice: alpha_j is the q_j
+    // coefficient of the two passes, beta_j = ||w|| (full reorthogonalisation)
+    symv_rows<NT, NMAX>(Gs, n, Q + (size_t)j * n, z.w);
     PHASE(slot, 7);
-    part = 0.f;
-    for (int e = tid; e < n; e += NT) part = fmaf(z.x[e], z.w[e], part);
-    const float a = block_sum<NT>(part, s.red);
-    for (int e = tid; e < n; e += NT) z.w[e] = z.w[e] - a * z.x[e] - beta_prev * z.qprev[e];
-    __syncthreads();
-    PHASE(slot, 8);
-    lz_reorth<NT>(z.w, Q, n, j + 1, z.h);
+    float b = sqrtf(lz_project<NT, NMAX>(z.w, Q, n, j + 1, z.h, z.h + kLzMaxJ, s.red));
+    const float a = z.h[j] + z.h[kLzMaxJ + j];
     PHASE(slot, 9);
-    part = 0.f;
-    for (int e = tid; e < n; e += NT) part = fmaf(z.w[e], z.w[e], part);
-    float b = sqrtf(block_sum<NT>(part, s.red));
     if (tid == 0) {
       z.alpha[j] = a;
       z.beta[j] = b;
@@ -292,23 +347,13 @@ __device__ int lanczos_certified(SG Gs, SR Gr, int n, float thr, float gbound, f
         for (int e = tid; e < n; e += NT) z.w[e] = lz_hash(seed + 7919u * restart, e);
         ++restart;
         __syncthreads();
-        lz_reorth<NT>(z.w, Q, n, j + 1, z.h);
-        part = 0.f;
-        for (int e = tid; e < n; e += NT) part = fmaf(z.w[e], z.w[e], part);
-        const float bn = sqrtf(block_sum<NT>(part, s.red));
+        const float bn = sqrtf(lz_project<NT, NMAX>(z.w, Q, n, j + 1, z.h, z.h + kLzMaxJ, s.red));
         if (!(bn > 0.f)) break;
         if (tid == 0) z.beta[j] = 0.f;
         b = bn;
-        beta_prev = 0.f;
-      } else {
-        beta_prev = b;
       }
-      for (int e = tid; e < n; e += NT) {
-        z.qprev[e] = z.x[e];
-        const float q = z.w[e] / b;
-        z.x[e] = q;
-        Q[(j + 1) * n + e] = q;
-      }
+      const float ib = 1.f / b;
+      for (int e = tid; e < n; e += NT) Q[(size_t)(j + 1) * n + e] = z.w[e] * ib;
       __syncthreads();
     }
     PHASE(slot, 10);
@@ -343,7 +388,7 @@ __device__ int lanczos_certified(SG Gs, SR Gr, int n, float thr, float gbound, f
   for (int q = 0; q < ku; ++q) {
     for (int e = tid; e < n; e += NT) z.x[e] = U[(size_t)q * n + e];
     __syncthreads();
-    symv_lower<NT, CT, RT>(Gs, n, z.x, z.w, z.part);
+    symv_rows<NT, NMAX>(Gs, n, z.x, z.w);
     for (int e = tid; e < n; e += NT) Wm[(size_t)q * n + e] = z.w[e];
     __syncthreads();
   }
@@ -393,9 +438,8 @@ __device__ int lanczos_certified(SG Gs, SR Gr, int n, float thr, float gbound, f
   }
   __syncthreads();
   PHASE(slot, 11);
-  if (!regchol_pd<NT, NMAX>(Gr, n, c0, true, U8, W8, ku, panel + 16 * n8, s.red)) return -1;
-  PHASE(slot, 14);
   *ku_out = ku;
+  *c0_out = c0;
   return kk;
 }
 

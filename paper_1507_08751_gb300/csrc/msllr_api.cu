@@ -191,8 +191,8 @@ int msllr_create(msllr_ctx** out, int device, size_t hbm_budget_bytes, void* cud
   if (cudaEventCreateWithFlags(&ctx->ev_fork, cudaEventDisableTiming) != cudaSuccess)
     return bail(fail(ctx, MSLLR_ECUDA, "cudaEventCreate"));
   if (getenv("MSLLR_PHASE_TIMING")) {
-    if (cudaMalloc(&ctx->d_phase, 5 * 16 * 2 * sizeof(unsigned long long)) != cudaSuccess ||
-        cudaMemset(ctx->d_phase, 0, 5 * 16 * 2 * sizeof(unsigned long long)) != cudaSuccess ||
+    if (cudaMalloc(&ctx->d_phase, 8 * 16 * 2 * sizeof(unsigned long long)) != cudaSuccess ||
+        cudaMemset(ctx->d_phase, 0, 8 * 16 * 2 * sizeof(unsigned long long)) != cudaSuccess ||
         set_phase_buffer_small(ctx->d_phase) != cudaSuccess ||
         set_phase_buffer_big(ctx->d_phase) != cudaSuccess)
       return bail(fail(ctx, MSLLR_ECUDA, "phase timing buffer"));
@@ -212,10 +212,11 @@ int msllr_destroy(msllr_ctx* ctx) {
   if (ctx->graph) cudaGraphExecDestroy(ctx->graph);
   if (ctx->ws) cudaFree(ctx->ws);
   if (ctx->d_phase) {
-    unsigned long long h[5 * 16 * 2];
+    unsigned long long h[8 * 16 * 2];
     if (cudaMemcpy(h, ctx->d_phase, sizeof h, cudaMemcpyDeviceToHost) == cudaSuccess) {
-      static const char* names[5] = {"small32", "small64", "small128", "eig_big", "eig_lanczos"};
-      for (int k = 0; k < 5; ++k) {
+      static const char* names[8] = {"small32", "small64", "small128", "eig_big", "eig_lanczos",
+                                     "lz32", "lz64", "lz128"};
+      for (int k = 0; k < 8; ++k) {
         fprintf(stderr, "[msllr phase] %s:", names[k]);
         for (int p = 0; p < 16; ++p)
           if (h[(k * 16 + p) * 2 + 1])

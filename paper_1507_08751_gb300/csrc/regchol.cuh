@@ -16,8 +16,9 @@
 // Per panel of 8 columns (right-looking, Sec. 4.2.9 of the same book):
 //   1. the owners of the panel's tiles write them to a column-major strip
 //      in shared memory (double-buffered),
-//   2. every thread factors the 8x8 diagonal block in its registers (all
-//      get the same answer, so no barrier is needed before 3),
+//   2. every warp factors the 8x8 diagonal block (all get the same answer,
+//      so no barrier is needed before 3): in every thread's registers for
+//      small CTAs, by shuffles across 8 lanes where registers are scarce,
 //   3. each row below solves for its 8 factor entries (one thread per row),
 //   4. every thread subtracts the rank-8 product from its active tiles.
 // Two CTA barriers per panel; no shared-memory traffic for the trailing
@@ -57,9 +58,9 @@ __device__ __forceinline__ int regchol_tri_row(int e) {
 // Returns false when c <= 0.  `scr` holds regchol_scratch_floats(NMAX, NT)
 // floats (16-byte aligned); `red` is block_sum scratch.  src is not
 // modified.  All threads of the CTA must call; the answer is uniform.
-template <int NT, int NMAX, class SX>
+template <int NT, int NMAX, class SX, bool REGF = (NT <= 128)>
 __device__ bool regchol_pd(SX src, int n, float c0, bool frob, const float* U, const float* Wh,
-                           int ku, float* scr, float* red) {
+                           int ku, float* scr, float* red, int slot = -1) {
   static_assert(NMAX % 8 == 0 && NT % 32 == 0, "shape");
   constexpr int NB = NMAX / 4;
   constexpr int TMAX = NB >= 3 ? (NB - 2) * (NB - 1) / 2 : 1;
@@ -141,6 +142,7 @@ __device__ bool regchol_pd(SX src, int n, float c0, bool frob, const float* U, c
   }
   if (!(c > 0.f)) return false;
   __syncthreads();
+  PHASE_INIT();
   if (tid < 8) S[tid * n8 + tid] += c;
 #pragma unroll
   for (int s = 0; s < SL; ++s)
@@ -165,37 +167,66 @@ __device__ bool regchol_pd(SX src, int n, float c0, bool frob, const float* U, c
         }
     }
     __syncthreads();
-    // 8x8 diagonal block, factored by every thread in registers from
-    // broadcast loads (packed lower triangle, the diagonal replaced by the
-    // reciprocal pivots); rsqrt (a few ulp) instead of sqrt and a division
-    // keeps the chain of 8 dependent pivots short, and its error stays far
-    // inside the backward-error margin
-    float L[36];
-#pragma unroll
-    for (int t = 0; t < 8; ++t)
-#pragma unroll
-      for (int u = 0; u <= t; ++u) L[t * (t + 1) / 2 + u] = Sb[u * n8 + j0 + t];
+    // 8x8 diagonal block into this warp's packed copy Lw (lower triangle,
+    // the diagonal replaced by the reciprocal pivots).  Every warp factors
+    // it; rsqrt (a few ulp) instead of sqrt and a division keeps the chain
+    // of 8 dependent pivots short, and its error stays far inside the
+    // backward-error margin.
     bool ok = true;
+    if constexpr (REGF) {
+      // every thread holds the whole block (broadcast loads): no shuffles
+      float L[36];
 #pragma unroll
-    for (int j = 0; j < 8; ++j) {
-      const float dj = L[j * (j + 1) / 2 + j];
-      ok = ok && (dj > 0.f);
-      const float inv = rsqrtf(dj > 0.f ? dj : 1.f);
-      L[j * (j + 1) / 2 + j] = inv;
+      for (int t = 0; t < 8; ++t)
 #pragma unroll
-      for (int i = j + 1; i < 8; ++i) L[i * (i + 1) / 2 + j] *= inv;
+        for (int u = 0; u <= t; ++u) L[t * (t + 1) / 2 + u] = Sb[u * n8 + j0 + t];
 #pragma unroll
-      for (int i = j + 1; i < 8; ++i)
+      for (int j = 0; j < 8; ++j) {
+        const float dj = L[j * (j + 1) / 2 + j];
+        ok = ok && (dj > 0.f);
+        const float inv = rsqrtf(dj > 0.f ? dj : 1.f);
+        L[j * (j + 1) / 2 + j] = inv;
 #pragma unroll
-        for (int t = j + 1; t <= i; ++t)
-          L[i * (i + 1) / 2 + t] = fmaf(-L[i * (i + 1) / 2 + j], L[t * (t + 1) / 2 + j],
-                                        L[i * (i + 1) / 2 + t]);
-    }
-    if (!ok) return false;
-    // one copy of the factor per warp frees the registers for the solve
-    if (lane == 0) {
+        for (int i = j + 1; i < 8; ++i) L[i * (i + 1) / 2 + j] *= inv;
 #pragma unroll
-      for (int e = 0; e < 36; ++e) Lw[e] = L[e];
+        for (int i = j + 1; i < 8; ++i)
+#pragma unroll
+          for (int t = j + 1; t <= i; ++t)
+            L[i * (i + 1) / 2 + t] = fmaf(-L[i * (i + 1) / 2 + j], L[t * (t + 1) / 2 + j],
+                                          L[i * (i + 1) / 2 + t]);
+      }
+      if (!ok) return false;
+      if (lane == 0) {
+#pragma unroll
+        for (int e = 0; e < 36; ++e) Lw[e] = L[e];
+      }
+    } else {
+      // lane l < 8 holds row l (fewer registers, shuffles on the chain)
+      float row[8];
+#pragma unroll
+      for (int t = 0; t < 8; ++t) row[t] = (lane < 8 && t <= lane) ? Sb[t * n8 + j0 + lane] : 0.f;
+      float myinv = 1.f;
+#pragma unroll
+      for (int j = 0; j < 8; ++j) {
+        const float dj = __shfl_sync(0xffffffffu, row[j], j);
+        ok = ok && (dj > 0.f);
+        const float inv = rsqrtf(dj > 0.f ? dj : 1.f);
+        if (lane == j) myinv = inv;
+        if (lane > j) row[j] *= inv;
+#pragma unroll
+        for (int t = j + 1; t < 8; ++t) {
+          const float ltj = __shfl_sync(0xffffffffu, row[j], t);
+          if (lane >= t) row[t] = fmaf(-row[j], ltj, row[t]);
+        }
+      }
+      if (!ok) return false;
+      if (lane < 8) {
+        const int base = lane * (lane + 1) / 2;
+#pragma unroll
+        for (int t = 0; t < 8; ++t)
+          if (t < lane) Lw[base + t] = row[t];
+        Lw[base + lane] = myinv;
+      }
     }
     __syncwarp();
     // rows below the block: L21 = A21 L11^{-T}
@@ -231,6 +262,7 @@ __device__ bool regchol_pd(SX src, int n, float c0, bool frob, const float* U, c
       }
     }
   }
+  PHASE(slot, 15);
   return true;
 }
 

@@ -168,68 +168,6 @@ __device__ void tridiagonalize(S G, int n, EigScratch& s) {
   __syncthreads();
 }
 
-// ---------------------------------------------------------------------------
-// y = G x for G symmetric in the lower triangle (n <= 32 * RMAX * NT/32...):
-// warp w takes rows r = w, w + NW, ...; for row r lane l reads G(r, c),
-// c = l + 32 t <= r (contiguous), adds G(r, c) x_c to the row sum and
-// G(r, c) x_r to its private partial of column c (the transposed half).
-// Row sums are reduced across lanes in one interleaved butterfly, column
-// partials across warps through `part` (NW * 32 * CT floats of shared
-// scratch, CT = ceil(n / 32)).  x and y are shared; y must not alias x.
-// ---------------------------------------------------------------------------
-template <int NT, int CT, int RT, class S, bool ABS = false>
-__device__ void symv_lower(S G, int n, const float* x, float* y, float* part) {
-  constexpr int NW = NT / 32;
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  float colp[CT];
-  float rs[RT];
-  float xv[CT];
-#pragma unroll
-  for (int t = 0; t < CT; ++t) {
-    colp[t] = 0.f;
-    xv[t] = (lane + 32 * t < n) ? x[lane + 32 * t] : 0.f;
-  }
-#pragma unroll
-  for (int q = 0; q < RT; ++q) {
-    rs[q] = 0.f;
-    const int r = warp + q * NW;
-    if (r < n) {
-      const float xr = x[r];
-#pragma unroll
-      for (int t = 0; t < CT; ++t) {
-        const int cc = lane + 32 * t;
-        if (cc <= r) {
-          const float g = ABS ? fabsf(G.at(r, cc)) : G.at(r, cc);
-          rs[q] = fmaf(g, xv[t], rs[q]);
-          if (cc < r) colp[t] = fmaf(g, xr, colp[t]);
-        }
-      }
-    }
-  }
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1)
-#pragma unroll
-    for (int q = 0; q < RT; ++q) rs[q] += __shfl_xor_sync(0xffffffffu, rs[q], o);
-#pragma unroll
-  for (int t = 0; t < CT; ++t) part[(warp * CT + t) * 32 + lane] = colp[t];
-  __syncthreads();
-  for (int cc = tid; cc < n; cc += NT) {
-    float acc = 0.f;
-    const int t = cc >> 5, l = cc & 31;
-    for (int w = 0; w < NW; ++w) acc += part[(w * CT + t) * 32 + l];
-    y[cc] = acc;
-  }
-  __syncthreads();
-  if (lane == 0) {
-#pragma unroll
-    for (int q = 0; q < RT; ++q) {
-      const int r = warp + q * NW;
-      if (r < n) y[r] += rs[q];
-    }
-  }
-  __syncthreads();
-}
-
 // Number of eigenvalues of T (d, e2 = e^2) strictly below x (Sturm count via
 // the LDL^T pivots of T - xI; tiny pivots are replaced by -pivmin).
 __device__ __forceinline__ int sturm_below(const float* d, const float* e2, int n, float x,
