@@ -107,19 +107,46 @@ __global__ void __launch_bounds__(NT) blocksvt_small_kernel(ScaleLaunch a) {
   float gbound = fro;  // trace(G) >= lambda_max(G)
   if (a.skip_bound && fro <= thr) skipped = true;
   if (!skipped) {
-    const int ntri = nn * (nn + 1) / 2;
-    for (int e = tid; e < ntri; e += NT) {
-      const int i = tri_row(e), j = e - (i * (i + 1)) / 2;
-      float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f;
-      int r = 0;
-      for (; r + 3 < mm; r += 4) {
-        a0 = fmaf(C[r * ldc + i], C[r * ldc + j], a0);
-        a1 = fmaf(C[(r + 1) * ldc + i], C[(r + 1) * ldc + j], a1);
-        a2 = fmaf(C[(r + 2) * ldc + i], C[(r + 2) * ldc + j], a2);
-        a3 = fmaf(C[(r + 3) * ldc + i], C[(r + 3) * ldc + j], a3);
+    if ((nn & 3) == 0) {
+      // 4x4 register tiles of the lower triangle: per row of C one 128-bit
+      // load for the tile's rows and one for its columns, 16 FMAs
+      const int nt = nn >> 2, ntiles = nt * (nt + 1) / 2;
+      for (int t = tid; t < ntiles; t += NT) {
+        const int ta = tri_row(t), tb = t - (ta * (ta + 1)) / 2;
+        float acc[4][4] = {};
+        const float* ci = C + 4 * ta;
+        const float* cj = C + 4 * tb;
+#pragma unroll 4
+        for (int r = 0; r < mm; ++r) {
+          const float4 x = *reinterpret_cast<const float4*>(ci + r * ldc);
+          const float4 y = *reinterpret_cast<const float4*>(cj + r * ldc);
+          const float xv[4] = {x.x, x.y, x.z, x.w}, yv[4] = {y.x, y.y, y.z, y.w};
+#pragma unroll
+          for (int u = 0; u < 4; ++u)
+#pragma unroll
+            for (int v = 0; v < 4; ++v) acc[u][v] = fmaf(xv[u], yv[v], acc[u][v]);
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+#pragma unroll
+          for (int v = 0; v < 4; ++v)
+            if (ta > tb || v <= u) G[(4 * ta + u) * ldg + 4 * tb + v] = acc[u][v];
       }
-      for (; r < mm; ++r) a0 = fmaf(C[r * ldc + i], C[r * ldc + j], a0);
-      G[i * ldg + j] = (a0 + a1) + (a2 + a3);
+    } else {
+      const int ntri = nn * (nn + 1) / 2;
+      for (int e = tid; e < ntri; e += NT) {
+        const int i = tri_row(e), j = e - (i * (i + 1)) / 2;
+        float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f;
+        int r = 0;
+        for (; r + 3 < mm; r += 4) {
+          a0 = fmaf(C[r * ldc + i], C[r * ldc + j], a0);
+          a1 = fmaf(C[(r + 1) * ldc + i], C[(r + 1) * ldc + j], a1);
+          a2 = fmaf(C[(r + 2) * ldc + i], C[(r + 2) * ldc + j], a2);
+          a3 = fmaf(C[(r + 3) * ldc + i], C[(r + 3) * ldc + j], a3);
+        }
+        for (; r < mm; ++r) a0 = fmaf(C[r * ldc + i], C[r * ldc + j], a0);
+        G[i * ldg + j] = (a0 + a1) + (a2 + a3);
+      }
     }
     __syncthreads();
     PHASE(SLOT, 1);
