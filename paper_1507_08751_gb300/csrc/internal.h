@@ -35,7 +35,7 @@ struct ScaleLaunch {
 
 // Device workspace needed by the wide-block path for one scale.
 struct BigWorkspace {
-  float* G;      // nblocks * nn * nn
+  float* G;      // nblocks * nn * nn; block b at b * nn * nn, lower triangle packed row by row
   float* part;   // nblocks * chunks * ntiles * 64 * 64 (when chunks > 1)
   float* Y;      // nblocks * ystride: eigenvectors / Lanczos scratch per block
   int* k;        // nblocks

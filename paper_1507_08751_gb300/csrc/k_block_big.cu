@@ -132,7 +132,7 @@ gram_tiles_kernel(ScaleLaunch a, float* __restrict__ G, float* __restrict__ part
 #pragma unroll
       for (int y = 0; y < 4; ++y) {
         const int j = c0 + tx * 4 + y;
-        if (j < nn) Gb[(size_t)i * nn + j] = acc[x][y];
+        if (j <= i) Gb[(size_t)i * (i + 1) / 2 + j] = acc[x][y];
       }
     }
   } else {
@@ -162,7 +162,7 @@ gram_reduce_kernel(const float* __restrict__ part, float* __restrict__ G, int nn
     float s = 0.f;
     for (int c = 0; c < chunks; ++c)
       s += part[(((size_t)b * chunks + c) * ntiles + t) * (kTile * kTile) + e];
-    G[(size_t)b * nn * nn + (size_t)i * nn + j] = s;
+    if (j <= i) G[(size_t)b * nn * nn + (size_t)i * (i + 1) / 2 + j] = s;
   }
 }
 
@@ -243,9 +243,16 @@ eig_big_kernel(ScaleLaunch a, const float* __restrict__ Gall, BigWorkspace ws) {
   lz_bind<NT>(z, s.red + 64, NMAX, kLzMaxJ);
   PHASE_INIT();
   LowerPacked Gacc{Gp};
+  // G arrives packed (lower triangle, row by row): a straight copy
   auto load_g = [&]() {
-    for (int i = warp; i < nn; i += NW)
-      for (int j = lane; j <= i; j += 32) Gacc.at(i, j) = Gg[(size_t)i * nn + j];
+    const int ntri = nn * (nn + 1) / 2;
+    if ((ntri & 3) == 0 && ((reinterpret_cast<uintptr_t>(Gg) & 15) == 0)) {
+      const float4* src = reinterpret_cast<const float4*>(Gg);
+      float4* dst = reinterpret_cast<float4*>(Gp);
+      for (int e = tid; e < ntri / 4; e += NT) dst[e] = src[e];
+    } else {
+      for (int e = tid; e < ntri; e += NT) Gp[e] = Gg[e];
+    }
     __syncthreads();
   };
   load_g();
@@ -266,7 +273,6 @@ eig_big_kernel(ScaleLaunch a, const float* __restrict__ Gall, BigWorkspace ws) {
   // by the deflated matrix.
   const int n8 = (nn + 7) & ~7;
   float* U = Y;
-  float* Wm = Y + (size_t)kLzMaxK * nn;
   for (int attempt = 0; attempt < 2 && k < 0 && a.skip_bound; ++attempt) {
     float c0;
     int kk = 0;
@@ -285,7 +291,7 @@ eig_big_kernel(ScaleLaunch a, const float* __restrict__ Gall, BigWorkspace ws) {
       PHASE(3, 1);
       const float* warm = ws.warm + (size_t)b * kLzMaxK * nn;
       kk = lanczos_candidates<NT, NMAX>(Gacc, nn, thr, gbound, Qs,
-                                                        min(nn, kLzMaxJ), U, Wm, warm, kwarm,
+                                                        min(nn, kLzMaxJ), U, warm, kwarm,
                                                         0x1234567u + 977u * b, s, z, panel, &ku,
                                                         &c0, 4);
       PHASE(3, 5);

@@ -76,13 +76,12 @@ __global__ void __launch_bounds__(NT) blocksvt_small_kernel(ScaleLaunch a) {
   s.xs = s.hi + NT;
   s.cnt = reinterpret_cast<int*>(s.xs + NT);
   s.red = reinterpret_cast<float*>(s.cnt + NT);
-  // Lanczos region: Q (NMAX x JCAP), U and W (NMAX x kLzMaxK each)
+  // Lanczos region: Q (NMAX x JCAP), U (NMAX x kLzMaxK)
   constexpr int JCAP = NMAX < kLzMaxJ ? NMAX : kLzMaxJ;
   float* Qs = s.red + 64;
   float* Us = Qs + NMAX * JCAP;
-  float* Ws = Us + NMAX * kLzMaxK;
   LzScratch z;
-  lz_bind<NT>(z, Ws + NMAX * kLzMaxK, NMAX, JCAP);
+  lz_bind<NT>(z, Us + NMAX * kLzMaxK, NMAX, JCAP);
 
   // gather A = A1 + A2 on the shifted grid; ||C||_F^2
   const int melem = a.m * a.n;
@@ -185,7 +184,7 @@ __global__ void __launch_bounds__(NT) blocksvt_small_kernel(ScaleLaunch a) {
       if (!(c_skip > 0.f)) continue;
     } else {
       kk = lanczos_candidates<NT, NMAX>(LowerFull{G, ldg}, nn, thr, gbound, Qs,
-                                                nn < JCAP ? nn : JCAP, Us, Ws, nullptr, 0,
+                                                nn < JCAP ? nn : JCAP, Us, nullptr, 0,
                                                 0x51ED27u + 131u * blockIdx.x, s, z, panel, &ku,
                                                 &c0, 5 + SLOT);
       PHASE(SLOT, 10);
@@ -283,7 +282,7 @@ template <int NT, int NMAX>
 size_t small_smem_bytes(int mm, int nn) {
   constexpr int JCAP = NMAX < kLzMaxJ ? NMAX : kLzMaxJ;
   return sizeof(float) * ((size_t)2 * mm * nn + (size_t)nn * (2 * nn + 2) + lz_cert_floats(NMAX, NT) +
-                          4 + 9 * NMAX + 4 * NT + 64 + NMAX * JCAP + 2 * NMAX * kLzMaxK +
+                          4 + 9 * NMAX + 4 * NT + 64 + NMAX * JCAP + NMAX * kLzMaxK +
                           lz_scratch_floats(NMAX, JCAP));
 }
 

@@ -124,6 +124,45 @@ __device__ void symv_rows(S G, int n, const float* x, float* y) {
   __syncthreads();
 }
 
+// Y = G X for 8 vectors at once (X, Y shared, n x 8 row-major, 16-byte
+// aligned): every element of G is read once per row walk for all 8
+// products.  Same row split as symv_rows; ends with a CTA barrier.
+template <int NT, int NMAX, class S>
+__device__ void symm_rows8(S G, int n, const float* X, float* Yo) {
+  constexpr int TPR = (NT / NMAX >= 2) ? 2 : 1;
+  const int tid = threadIdx.x, p = tid % TPR;
+  for (int r0 = 0; r0 < n; r0 += NT / TPR) {
+    const int r = r0 + tid / TPR;
+    float acc[8];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) acc[q] = 0.f;
+    if (r < n) {
+      for (int c = p; c < n; c += TPR) {
+        const float g = c <= r ? G.at(r, c) : G.at(c, r);
+        const float4 x0 = *reinterpret_cast<const float4*>(X + c * 8);
+        const float4 x1 = *reinterpret_cast<const float4*>(X + c * 8 + 4);
+        acc[0] = fmaf(g, x0.x, acc[0]);
+        acc[1] = fmaf(g, x0.y, acc[1]);
+        acc[2] = fmaf(g, x0.z, acc[2]);
+        acc[3] = fmaf(g, x0.w, acc[3]);
+        acc[4] = fmaf(g, x1.x, acc[4]);
+        acc[5] = fmaf(g, x1.y, acc[5]);
+        acc[6] = fmaf(g, x1.z, acc[6]);
+        acc[7] = fmaf(g, x1.w, acc[7]);
+      }
+    }
+    if constexpr (TPR == 2) {
+#pragma unroll
+      for (int q = 0; q < 8; ++q) acc[q] += __shfl_xor_sync(0xffffffffu, acc[q], 1);
+    }
+    if (p == 0 && r < n) {
+      *reinterpret_cast<float4*>(Yo + r * 8) = make_float4(acc[0], acc[1], acc[2], acc[3]);
+      *reinterpret_cast<float4*>(Yo + r * 8 + 4) = make_float4(acc[4], acc[5], acc[6], acc[7]);
+    }
+  }
+  __syncthreads();
+}
+
 // w <- (I - Q Q^T) w twice (classical Gram-Schmidt, two passes) over Q's
 // columns 0..nq-1 (column i at Q + i*n, shared).  h1 and h2 receive the two
 // passes' coefficients; returns ||w||^2 after the second pass.  Small n:
@@ -284,7 +323,8 @@ __device__ float gershgorin_lower(S A, int n, float* ones, float* sums, float* r
 // The whole Lanczos + certificate path.
 //  Gs  G in lower storage, read only (the Lanczos operator).
 //  Q   shared scratch of jmax * n floats (column j at Q + j*n), jmax <= n.
-//  U, Wm  scratch of kLzMaxK * n floats each (column-major, any memory).
+//  U   receives the kept Ritz vectors (kLzMaxK * n floats, column-major,
+//      any memory).
 //  warm / kwarm: previous Ritz vectors (column-major n x kwarm) or kwarm = 0.
 //  gbound: an upper bound of ||G||_2.
 //  panel: lz_cert_floats(NMAX, NT) floats of 16-byte aligned shared
@@ -301,7 +341,7 @@ __device__ float gershgorin_lower(S A, int n, float* ones, float* sums, float* r
 // must fall back.  G is never modified.
 template <int NT, int NMAX, class SG>
 __device__ int lanczos_candidates(SG Gs, int n, float thr, float gbound, float* Q, int jmax,
-                                  float* U, float* Wm, const float* warm, int kwarm,
+                                  float* U, const float* warm, int kwarm,
                                   uint32_t seed, EigScratch& s, LzScratch& z, float* panel,
                                   int* ku_out, float* c0_out, int slot = -1) {
   constexpr int NW = NT / 32;
@@ -375,36 +415,65 @@ __device__ int lanczos_candidates(SG Gs, int n, float thr, float gbound, float* 
     if (k > kLzMaxK) return -1;
   }
   const int ku = k;
-  // U = Q_J Y (n x ku)
-  for (int e = tid; e < n * ku; e += NT) {
-    const int q = e / n, r = e - q * n;
+  // U = Q_J Y (n x ku) into the caller's U and, row-major n x 8 with zero
+  // columns beyond ku, into X8 (shared; Q may alias the panel, so the values
+  // wait in registers for the barrier)
+  static_assert(8 * NMAX <= 4 * NT, "staging split");
+  float* X8 = panel + 16 * NMAX;
+  float* Y8 = panel + 24 * NMAX;
+  float uv[4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const int e = tid + i * NT, r = e >> 3, q = e & 7;
     float v = 0.f;
-    for (int jj = 0; jj < J; ++jj) v = fmaf(Q[jj * n + r], z.ty[jj * kLzMaxK + q], v);
-    U[(size_t)q * n + r] = v;
+    if (r < n && q < ku)
+      for (int jj = 0; jj < J; ++jj) v = fmaf(Q[jj * n + r], z.ty[jj * kLzMaxK + q], v);
+    uv[i] = v;
+  }
+  __syncthreads();
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const int e = tid + i * NT, r = e >> 3, q = e & 7;
+    if (r < n) {
+      X8[e] = uv[i];
+      if (q < ku) U[(size_t)q * n + r] = uv[i];
+    }
   }
   __syncthreads();
   PHASE(slot, 12);
-  // W = G U, B = U^T W, rho
-  for (int q = 0; q < ku; ++q) {
-    for (int e = tid; e < n; e += NT) z.x[e] = U[(size_t)q * n + e];
-    __syncthreads();
-    symv_rows<NT, NMAX>(Gs, n, z.x, z.w);
-    for (int e = tid; e < n; e += NT) Wm[(size_t)q * n + e] = z.w[e];
-    __syncthreads();
-  }
-  for (int pq = warp; pq < ku * ku; pq += NW) {
-    const int p = pq / ku, q = pq - p * ku;
-    float d = 0.f;
-    for (int e = lane; e < n; e += 32) d = fmaf(U[(size_t)p * n + e], Wm[(size_t)q * n + e], d);
-    d = warp_sum(d);
-    if (lane == 0) z.Bm[p * kLzMaxK + q] = d;
+  // W = G U (all columns in one pass over G), B = U^T W, rho
+  symm_rows8<NT, NMAX>(Gs, n, X8, Y8);
+  for (int pr = warp; pr < ku; pr += NW) {
+    float d[8];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) d[q] = 0.f;
+    for (int r = lane; r < n; r += 32) {
+      const float x = X8[r * 8 + pr];
+      const float4 y0 = *reinterpret_cast<const float4*>(Y8 + r * 8);
+      const float4 y1 = *reinterpret_cast<const float4*>(Y8 + r * 8 + 4);
+      d[0] = fmaf(x, y0.x, d[0]);
+      d[1] = fmaf(x, y0.y, d[1]);
+      d[2] = fmaf(x, y0.z, d[2]);
+      d[3] = fmaf(x, y0.w, d[3]);
+      d[4] = fmaf(x, y1.x, d[4]);
+      d[5] = fmaf(x, y1.y, d[5]);
+      d[6] = fmaf(x, y1.z, d[6]);
+      d[7] = fmaf(x, y1.w, d[7]);
+    }
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      const float t = warp_sum(d[q]);
+      if (lane == 0 && q < ku) z.Bm[pr * kLzMaxK + q] = t;
+    }
   }
   __syncthreads();
   part = 0.f;
-  for (int e = tid; e < n * ku; e += NT) {
-    const int q = e / n, r = e - q * n;
-    const float rr = Wm[(size_t)q * n + r] - z.Bm[q * kLzMaxK + q] * U[(size_t)q * n + r];
-    part = fmaf(rr, rr, part);
+  for (int e = tid; e < 8 * n; e += NT) {
+    const int q = e & 7;
+    if (q < ku) {
+      const float rr = Y8[e] - z.Bm[q * kLzMaxK + q] * X8[e];
+      part = fmaf(rr, rr, part);
+    }
   }
   const float rho = sqrtf(block_sum<NT>(part, s.red));
   PHASE(slot, 13);
@@ -428,10 +497,10 @@ __device__ int lanczos_candidates(SG Gs, int n, float thr, float gbound, float* 
     const int q = e / n8, r = e - q * n8;
     float u = 0.f, w = 0.f;
     if (r < n) {
-      u = U[(size_t)q * n + r];
-      w = Wm[(size_t)q * n + r];
+      u = X8[r * 8 + q];
+      w = Y8[r * 8 + q];
       for (int p = 0; p < ku; ++p)
-        w = fmaf(-0.25f * (z.Bm[p * kLzMaxK + q] + z.Bm[q * kLzMaxK + p]), U[(size_t)p * n + r], w);
+        w = fmaf(-0.25f * (z.Bm[p * kLzMaxK + q] + z.Bm[q * kLzMaxK + p]), X8[r * 8 + p], w);
     }
     U8[e] = u;
     W8[e] = w;
