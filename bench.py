@@ -119,6 +119,11 @@ def peaks():
     return p
 
 
+# DRAM bytes (read + write) per launch from one ncu capture of the kernel as
+# it stands (profiles/eig_big_video16384x256.md); kernels not listed: null.
+NCU_TRAFFIC_BYTES = {"eig_big[scale 3: 256x256]": 8779520}
+
+
 def kernel_roofline(stats, scales, M, N, pk):
     """Roofline of the kernel kind x scale with the largest summed device time
     (CUDA events around every launch of the profiled job)."""
@@ -157,6 +162,7 @@ def kernel_roofline(stats, scales, M, N, pk):
                 "frac": round(ach / pk["hbm_gbs"], 4), "traffic": None,
                 "peak_src": pk["src"]}
     roof["kernel"] = f"{kind}[scale {i}: {m}x{nsz}]"
+    roof["traffic"] = NCU_TRAFFIC_BYTES.get(roof["kernel"])
     roof["avg_launch_us"] = round(avg_s * 1e6, 2)
     total = sum(sum(v) for v in stats["kernel_ms"].values())
     roof["time_share"] = round(ms / total, 4) if total else None
