@@ -156,7 +156,8 @@ def kernel_roofline(stats, scales, M, N, pk):
                 "peak_src": "152 SM x 128 FP32 lanes x 2 x max SM clock"}
     else:
         per = {"consensus": (L + 2) * 4 * MN, "soft1x1": 16 * MN, "fused_small": 16 * MN,
-               "rebuild": 16 * MN, "gram_reduce": 0, "advance": 8, "misc": 8 * MN}[kind]
+               "rebuild": 16 * MN, "gram_reduce": 0, "advance": 8, "misc": 8 * MN,
+               "eig_fallback": 0}[kind]
         ach = per / avg_s / 1e9
         roof = {"bound": "hbm", "achieved": round(ach, 1), "peak": pk["hbm_gbs"], "unit": "GB/s",
                 "frac": round(ach / pk["hbm_gbs"], 4), "traffic": None,

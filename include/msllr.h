@@ -49,8 +49,9 @@ typedef enum msllr_status {
  * 0 shift advance, 1 consensus residual, 2 1x1 soft threshold, 3 fused
  * narrow-block SVT, 4 wide-block Gram tiles, 5 Gram partial-sum reduce,
  * 6 wide-block eigen-solve, 7 wide-block rebuild, 8 set-up and output
- * kernels (finiteness check, state init, X/U output). */
-#define MSLLR_KERNEL_KINDS 9
+ * kernels (finiteness check, state init, X/U output), 9 wide-block
+ * Householder fallback (blocks the certified paths did not settle). */
+#define MSLLR_KERNEL_KINDS 10
 
 /* Widest block (min(m_i, n_i)) the block-SVT kernels accept; the full-matrix
  * scale obeys the same limit on min(M, N). */

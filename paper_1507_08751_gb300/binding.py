@@ -27,7 +27,7 @@ MSLLR_EBUSY = 6
 MAX_SCALES = 8
 MAX_BLOCK_WIDTH = 256
 KERNEL_KINDS = ("advance", "consensus", "soft1x1", "fused_small", "gram", "gram_reduce",
-                "eig_big", "rebuild", "misc")
+                "eig_big", "rebuild", "misc", "eig_fallback")
 
 STATUS_NAMES = {0: "MSLLR_OK", 1: "MSLLR_EINVAL", 2: "MSLLR_ENOMEM", 3: "MSLLR_ECUDA",
                 4: "MSLLR_ETIMEOUT", 5: "MSLLR_ENONFINITE", 6: "MSLLR_EBUSY"}

@@ -55,6 +55,7 @@ enum KernelKind {
   KK_EIG,
   KK_REBUILD,
   KK_MISC,
+  KK_EIG_FALLBACK,
   KK_COUNT
 };
 

@@ -1,11 +1,14 @@
 // Block SVT for wide blocks (64 < min(m, n) <= 256, or m*n > 8192), which
-// includes the full-matrix scale of eq:bsvt.  Three phases per scale:
+// includes the full-matrix scale of eq:bsvt.  Phases per scale:
 //   1. gram_tiles: G_b = C_b^T C_b for every block, tiled 64x64 over the
 //      lower triangle and split over row chunks (partial sums reduced in a
-//      fixed order, so results are deterministic);
-//   2. eig_big: one CTA per block -- skip bound (Sec. 8), certified rank and
-//      top eigenpairs of G_b (symeig.cuh), output V_b diag(sqrt(f));
-//   3. rebuild: Z'_b = (C_b V_f) V_f^T in row slabs, scattered through
+//      fixed order, so results are deterministic), stored packed;
+//   2. eig_big: one CTA per block -- skip bound (Sec. 8), certified zero
+//      rank or certified Lanczos eigenpairs of G_b (lanczos.cuh,
+//      regchol.cuh), output V_b diag(sqrt(f));
+//   3. eig_fallback: the Householder path (symeig.cuh) for the blocks step 2
+//      could not certify;
+//   4. rebuild: Z'_b = (C_b V_f) V_f^T in row slabs, scattered through
 //      Shift_{-s}, with the fused dual update W' = 2 Z' - A of eq:admm.
 #include <math.h>
 
@@ -321,33 +324,82 @@ eig_big_kernel(ScaleLaunch a, const float* __restrict__ Gall, BigWorkspace ws) {
       Y[(size_t)i * nn + q] = panel[(size_t)q * nn + i] * sqrtf(fmaxf(1.f - a.tau / sig, 0.f));
     }
   }
-  if (k < 0) {
-    // Householder fallback
-    if (tid == 0 && ws.kwarm) ws.kwarm[b] = 0;
-    tridiagonalize<NT>(Gacc, nn, s);
-    PHASE(3, 2);
-    float tn = 0.f;
-    k = top_eigenvalues<NT>(nn, thr, s, &tn);
-    PHASE(3, 3);
-    if (k > 0) top_eigenvectors<NT, NMAX>(Gacc, nn, k, tn, s, Y, nn, 3);
-    PHASE(3, 4);
-    if (k > 0) {
-      // V_f = V diag(sqrt(f)), f = 1 - tau/sigma
-      for (int e = tid; e < nn * k; e += NT) {
-        const int i = e / k, q = e - i * k;
-        const float sig = sqrtf(s.lam[q]);
-        Y[(size_t)i * nn + q] *= sqrtf(fmaxf(1.f - a.tau / sig, 0.f));
+  if (tid == 0) {
+    // k < 0: not settled here; eig_fallback_kernel takes the block
+    ws.k[b] = k;
+    if (k < 0) {
+      if (ws.kwarm) ws.kwarm[b] = 0;
+    } else {
+      if (a.rank_out) a.rank_out[b] = k;
+      if (a.cnt) {
+        if (skipped) atomicAdd(a.cnt, 1ull);
+        if (k == 0) atomicAdd(a.cnt + 1, 1ull);
+        if (lanczos_ok) atomicAdd(a.cnt + 2, 1ull);
       }
+      if (a.nuc_acc && k > 0) {
+        double t = 0.0;
+        for (int q = 0; q < k; ++q) t += (double)fmaxf(sqrtf(s.lam[q]) - a.tau, 0.f);
+        atomicAdd(a.nuc_acc, t);
+      }
+    }
+  }
+}
+
+// Householder path for the blocks eig_big_kernel left unsettled (ws.k < 0):
+// tridiagonalisation, Sturm multisection and inverse iteration on the
+// packed G (symeig.cuh).  Kept out of eig_big_kernel so that the common
+// paths run from a smaller instruction footprint; CTAs of settled blocks
+// return at once.
+__global__ void __launch_bounds__(kEigThreads)
+eig_fallback_kernel(ScaleLaunch a, const float* __restrict__ Gall, BigWorkspace ws) {
+  const int b = blockIdx.x;
+  if (ws.k[b] >= 0) return;
+  extern __shared__ float sm[];
+  constexpr int NT = kEigThreads, NMAX = kEigMax;
+  const int tid = threadIdx.x;
+  const int nn = a.m >= a.n ? a.n : a.m;
+  const float* Gg = Gall + (size_t)b * nn * nn;
+  float* Y = ws.Y + (size_t)b * ws.ystride;
+  float* Gp = sm;
+  float* scr = Gp + (((nn * (nn + 1)) / 2 + 3) & ~3);
+  EigScratch s;
+  s.d = scr;
+  s.e = s.d + NMAX;
+  s.e2 = s.e + NMAX;
+  s.beta = s.e2 + NMAX;
+  s.vbuf = s.beta + NMAX;
+  s.pbuf = s.vbuf + NMAX;
+  s.lam = s.pbuf + NMAX;
+  s.shf = s.lam + NMAX;
+  s.clus = reinterpret_cast<int*>(s.shf + NMAX);
+  s.lo = reinterpret_cast<float*>(s.clus + NMAX);
+  s.hi = s.lo + NT;
+  s.xs = s.hi + NT;
+  s.cnt = reinterpret_cast<int*>(s.xs + NT);
+  s.red = reinterpret_cast<float*>(s.cnt + NT);
+  const int ntri = nn * (nn + 1) / 2;
+  for (int e = tid; e < ntri; e += NT) Gp[e] = Gg[e];
+  __syncthreads();
+  LowerPacked Gacc{Gp};
+  const float thr = a.tau * a.tau;
+  tridiagonalize<NT>(Gacc, nn, s);
+  float tn = 0.f;
+  const int k = top_eigenvalues<NT>(nn, thr, s, &tn);
+  if (k > 0) {
+    top_eigenvectors<NT, NMAX>(Gacc, nn, k, tn, s, Y, nn, -1);
+    // V_f = V diag(sqrt(f)), f = 1 - tau/sigma
+    for (int e = tid; e < nn * k; e += NT) {
+      const int i = e / k, q = e - i * k;
+      const float sig = sqrtf(s.lam[q]);
+      Y[(size_t)i * nn + q] *= sqrtf(fmaxf(1.f - a.tau / sig, 0.f));
     }
   }
   if (tid == 0) {
     ws.k[b] = k;
     if (a.rank_out) a.rank_out[b] = k;
     if (a.cnt) {
-      if (skipped) atomicAdd(a.cnt, 1ull);
       if (k == 0) atomicAdd(a.cnt + 1, 1ull);
-      if (lanczos_ok) atomicAdd(a.cnt + 2, 1ull);
-      else if (!skipped) atomicAdd(a.cnt + 3, 1ull);
+      atomicAdd(a.cnt + 3, 1ull);
     }
     if (a.nuc_acc && k > 0) {
       double t = 0.0;
@@ -355,6 +407,11 @@ eig_big_kernel(ScaleLaunch a, const float* __restrict__ Gall, BigWorkspace ws) {
       atomicAdd(a.nuc_acc, t);
     }
   }
+}
+
+size_t fallback_smem_bytes(int nn) {
+  return sizeof(float) * ((((size_t)nn * (nn + 1) / 2 + 3) & ~(size_t)3) + 9 * kEigMax +
+                          4 * kEigThreads + 64);
 }
 
 // Z' = (C V_f) V_f^T for a slab of `rs` rows of C, W' = 2 Z' - A.
@@ -489,6 +546,9 @@ cudaError_t configure_big_kernels() {
   cudaError_t e = cudaFuncSetAttribute(eig_big_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)eig_smem_bytes(kEigMax));
   if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(eig_fallback_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)fallback_smem_bytes(kEigMax));
+  if (e != cudaSuccess) return e;
   return cudaFuncSetAttribute(rebuild_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                               100 * 1024);
 }
@@ -519,6 +579,9 @@ cudaError_t launch_big(const ScaleLaunch& s, const BigWorkspace& ws, cudaStream_
     if (cudaError_t e_ = cudaEventRecord(after_gram, st)) return e_;
   PROF_BEFORE(KK_EIG)
   eig_big_kernel<<<d.nblocks, kEigThreads, eig_smem_bytes(d.nn), st>>>(s, ws.G, ws);
+  PROF_AFTER()
+  PROF_BEFORE(KK_EIG_FALLBACK)
+  eig_fallback_kernel<<<d.nblocks, kEigThreads, fallback_smem_bytes(d.nn), st>>>(s, ws.G, ws);
   PROF_AFTER()
   const int rs = kRebElems / d.nn;
   const int slabs = (d.mm + rs - 1) / rs;
