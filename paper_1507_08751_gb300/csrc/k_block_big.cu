@@ -216,8 +216,8 @@ __device__ bool power_above(S G, int n, float thr, EigScratch& s, LzScratch& z) 
 __global__ void __launch_bounds__(kEigThreads)
 eig_big_kernel(ScaleLaunch a, const float* __restrict__ Gall, BigWorkspace ws) {
   extern __shared__ float sm[];
-  constexpr int NT = kEigThreads, NMAX = kEigMax, NW = NT / 32;
-  const int b = blockIdx.x, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  constexpr int NT = kEigThreads, NMAX = kEigMax;
+  const int b = blockIdx.x, tid = threadIdx.x;
   const int nn = a.m >= a.n ? a.n : a.m;
   const float* Gg = Gall + (size_t)b * nn * nn;
   float* Y = ws.Y + (size_t)b * ws.ystride;

@@ -23,6 +23,8 @@
 
 #include <float.h>
 
+#include <type_traits>
+
 #include "common.cuh"
 #include "regchol.cuh"
 #include "symeig.cuh"
@@ -90,36 +92,84 @@ template <int NT, int NMAX, bool ABS = false, class S>
 __device__ void symv_rows(S G, int n, const float* x, float* y) {
   constexpr int TPR = (NT / NMAX >= 2) ? 2 : 1;
   const int tid = threadIdx.x, p = tid % TPR;
-  // the row loop is uniform across the CTA so that every lane reaches the
-  // shuffle below
-  for (int r0 = 0; r0 < n; r0 += NT / TPR) {
-    const int r = r0 + tid / TPR;
-    float a0 = 0.f, a1 = 0.f;
-    if (r < n) {
-      int c = p;
-      for (; c + TPR <= r; c += 2 * TPR) {
-        const float g0 = G.at(r, c), g1 = G.at(r, c + TPR);
-        a0 = fmaf(ABS ? fabsf(g0) : g0, x[c], a0);
-        a1 = fmaf(ABS ? fabsf(g1) : g1, x[c + TPR], a1);
+  if constexpr (std::is_same<S, LowerPacked>::value && NT == 512) {
+    // packed storage: warp w takes rows 32 (w & 7) + lane and half (w >> 3)
+    // of the columns.  All lanes of a warp walk the same column c, so the
+    // loads T(r) + c (c <= r) and T(c) + r (c > r), T(i) = i (i + 1) / 2,
+    // hit distinct banks, and x[c] is a broadcast.  Left of the warp's row
+    // band the row part is contiguous, right of it the column part advances
+    // by c + 1; only the 32 columns of the band need both forms.
+    const float* g = G.g;
+    const int lane = tid & 31, warp = tid >> 5;
+    const int b0 = 32 * (warp & 7), half = warp >> 3;
+    const int r = b0 + lane;
+    const int cs = (n + 1) >> 1;
+    const int c_lo = half ? cs : 0, c_hi = half ? n : cs;
+    float acc = 0.f;
+    if (b0 < n) {
+      const int rr = r < n ? r : n - 1;  // lanes past n compute a dummy row
+      const int tr = (rr * (rr + 1)) / 2;
+      float a0 = 0.f, a1 = 0.f;
+      int c = c_lo;
+      const int e1 = min(c_hi, b0);
+      for (; c + 1 < e1; c += 2) {
+        a0 = fmaf(ABS ? fabsf(g[tr + c]) : g[tr + c], x[c], a0);
+        a1 = fmaf(ABS ? fabsf(g[tr + c + 1]) : g[tr + c + 1], x[c + 1], a1);
       }
-      if (c <= r) {
-        const float g = G.at(r, c);
-        a0 = fmaf(ABS ? fabsf(g) : g, x[c], a0);
-        c += TPR;
+      if (c < e1) {
+        a0 = fmaf(ABS ? fabsf(g[tr + c]) : g[tr + c], x[c], a0);
+        ++c;
       }
-      for (; c + TPR < n; c += 2 * TPR) {
-        const float g0 = G.at(c, r), g1 = G.at(c + TPR, r);
-        a0 = fmaf(ABS ? fabsf(g0) : g0, x[c], a0);
-        a1 = fmaf(ABS ? fabsf(g1) : g1, x[c + TPR], a1);
+      const int e2 = min(c_hi, b0 + 32);
+      for (; c < e2; ++c) {
+        const int idx = c <= rr ? tr + c : (c * (c + 1)) / 2 + rr;
+        a0 = fmaf(ABS ? fabsf(g[idx]) : g[idx], x[c], a0);
       }
-      if (c < n) {
-        const float g = G.at(c, r);
-        a0 = fmaf(ABS ? fabsf(g) : g, x[c], a0);
+      int idx = (c * (c + 1)) / 2 + rr;
+      for (; c + 1 < c_hi; c += 2) {
+        const int i1 = idx + c + 1;
+        a0 = fmaf(ABS ? fabsf(g[idx]) : g[idx], x[c], a0);
+        a1 = fmaf(ABS ? fabsf(g[i1]) : g[i1], x[c + 1], a1);
+        idx = i1 + c + 2;
       }
+      if (c < c_hi) a0 = fmaf(ABS ? fabsf(g[idx]) : g[idx], x[c], a0);
+      acc = a0 + a1;
     }
-    float acc = a0 + a1;
-    if constexpr (TPR == 2) acc += __shfl_xor_sync(0xffffffffu, acc, 1);
-    if (p == 0 && r < n) y[r] = acc;
+    if (half && r < n) y[r] = acc;
+    __syncthreads();
+    if (!half && r < n) y[r] += acc;
+  } else {
+    // the row loop is uniform across the CTA so that every lane reaches the
+    // shuffle below
+    for (int r0 = 0; r0 < n; r0 += NT / TPR) {
+      const int r = r0 + tid / TPR;
+      float a0 = 0.f, a1 = 0.f;
+      if (r < n) {
+        int c = p;
+        for (; c + TPR <= r; c += 2 * TPR) {
+          const float g0 = G.at(r, c), g1 = G.at(r, c + TPR);
+          a0 = fmaf(ABS ? fabsf(g0) : g0, x[c], a0);
+          a1 = fmaf(ABS ? fabsf(g1) : g1, x[c + TPR], a1);
+        }
+        if (c <= r) {
+          const float g = G.at(r, c);
+          a0 = fmaf(ABS ? fabsf(g) : g, x[c], a0);
+          c += TPR;
+        }
+        for (; c + TPR < n; c += 2 * TPR) {
+          const float g0 = G.at(c, r), g1 = G.at(c + TPR, r);
+          a0 = fmaf(ABS ? fabsf(g0) : g0, x[c], a0);
+          a1 = fmaf(ABS ? fabsf(g1) : g1, x[c + TPR], a1);
+        }
+        if (c < n) {
+          const float g = G.at(c, r);
+          a0 = fmaf(ABS ? fabsf(g) : g, x[c], a0);
+        }
+      }
+      float acc = a0 + a1;
+      if constexpr (TPR == 2) acc += __shfl_xor_sync(0xffffffffu, acc, 1);
+      if (p == 0 && r < n) y[r] = acc;
+    }
   }
   __syncthreads();
 }
