@@ -76,10 +76,10 @@ __global__ void __launch_bounds__(NT) blocksvt_small_kernel(ScaleLaunch a) {
   s.xs = s.hi + NT;
   s.cnt = reinterpret_cast<int*>(s.xs + NT);
   s.red = reinterpret_cast<float*>(s.cnt + NT);
-  // Lanczos region: Q (NMAX x JCAP), U (NMAX x kLzMaxK)
+  // Lanczos region: Q (lz_ldq x JCAP), U (NMAX x kLzMaxK)
   constexpr int JCAP = NMAX < kLzMaxJ ? NMAX : kLzMaxJ;
   float* Qs = s.red + 64;
-  float* Us = Qs + NMAX * JCAP;
+  float* Us = Qs + lz_ldq<NMAX>(NMAX) * JCAP;
   LzScratch z;
   lz_bind<NT>(z, Us + NMAX * kLzMaxK, NMAX, JCAP);
 
@@ -282,7 +282,7 @@ template <int NT, int NMAX>
 size_t small_smem_bytes(int mm, int nn) {
   constexpr int JCAP = NMAX < kLzMaxJ ? NMAX : kLzMaxJ;
   return sizeof(float) * ((size_t)2 * mm * nn + (size_t)nn * (2 * nn + 2) + lz_cert_floats(NMAX, NT) +
-                          4 + 9 * NMAX + 4 * NT + 64 + NMAX * JCAP + NMAX * kLzMaxK +
+                          4 + 9 * NMAX + 4 * NT + 64 + lz_ldq<NMAX>(NMAX) * JCAP + NMAX * kLzMaxK +
                           lz_scratch_floats(NMAX, JCAP));
 }
 

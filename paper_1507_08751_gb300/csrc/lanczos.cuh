@@ -34,7 +34,14 @@ namespace msllr {
 constexpr int kLzMaxJ = 32;  // Lanczos steps
 constexpr int kLzMaxK = 8;   // Ritz pairs kept (above 0.95 tau^2)
 
-// shared scratch (floats) of the certificate step of lanczos_certified
+// leading dimension of the Lanczos basis in shared memory: padded for the
+// thread-per-coefficient projection of small blocks
+template <int NMAX>
+__host__ __device__ constexpr int lz_ldq(int n) {
+  return NMAX <= 64 ? n + 1 : n;
+}
+
+// shared scratch (floats) of the certificate step of lanczos_candidates
 __host__ __device__ constexpr int lz_cert_floats(int nmax, int nt) {
   return 16 * nmax + regchol_scratch_floats(nmax, nt);
 }
@@ -214,13 +221,13 @@ __device__ void symm_rows8(S G, int n, const float* X, float* Yo) {
 }
 
 // w <- (I - Q Q^T) w twice (classical Gram-Schmidt, two passes) over Q's
-// columns 0..nq-1 (column i at Q + i*n, shared).  h1 and h2 receive the two
-// passes' coefficients; returns ||w||^2 after the second pass.  Small n:
-// one thread per coefficient (skewed walk, conflict-free); large n: one
-// warp per coefficient.
+// columns 0..nq-1 (column i at Q + i*ldq, shared).  h1 and h2 receive the
+// two passes' coefficients; returns ||w||^2 after the second pass.  Small
+// n: one thread per coefficient with four partial sums (ldq = n + 1 keeps
+// the threads on distinct banks); large n: one warp per coefficient.
 template <int NT, int NMAX>
-__device__ float lz_project(float* w, const float* Q, int n, int nq, float* h1, float* h2,
-                            float* red) {
+__device__ float lz_project(float* w, const float* Q, int ldq, int n, int nq, float* h1,
+                            float* h2, float* red) {
   constexpr int NW = NT / 32;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   float part = 0.f;
@@ -229,18 +236,22 @@ __device__ float lz_project(float* w, const float* Q, int n, int nq, float* h1, 
     float* h = pass == 0 ? h1 : h2;
     if constexpr (NMAX <= 64) {
       for (int i = tid; i < nq; i += NT) {
-        float d = 0.f;
-        int e = i % n;
-        for (int t = 0; t < n; ++t) {
-          d = fmaf(Q[i * n + e], w[e], d);
-          if (++e == n) e = 0;
+        const float* qi = Q + i * ldq;
+        float d0 = 0.f, d1 = 0.f, d2 = 0.f, d3 = 0.f;
+        int e = 0;
+        for (; e + 3 < n; e += 4) {
+          d0 = fmaf(qi[e], w[e], d0);
+          d1 = fmaf(qi[e + 1], w[e + 1], d1);
+          d2 = fmaf(qi[e + 2], w[e + 2], d2);
+          d3 = fmaf(qi[e + 3], w[e + 3], d3);
         }
-        h[i] = d;
+        for (; e < n; ++e) d0 = fmaf(qi[e], w[e], d0);
+        h[i] = (d0 + d1) + (d2 + d3);
       }
     } else {
       for (int i = warp; i < nq; i += NW) {
         float d = 0.f;
-        for (int e = lane; e < n; e += 32) d = fmaf(Q[i * n + e], w[e], d);
+        for (int e = lane; e < n; e += 32) d = fmaf(Q[i * ldq + e], w[e], d);
         d = warp_sum(d);
         if (lane == 0) h[i] = d;
       }
@@ -248,7 +259,7 @@ __device__ float lz_project(float* w, const float* Q, int n, int nq, float* h1, 
     __syncthreads();
     for (int e = tid; e < n; e += NT) {
       float v = w[e];
-      for (int i = 0; i < nq; ++i) v = fmaf(-h[i], Q[i * n + e], v);
+      for (int i = 0; i < nq; ++i) v = fmaf(-h[i], Q[i * ldq + e], v);
       w[e] = v;
       if (pass == 1) part = fmaf(v, v, part);
     }
@@ -372,7 +383,8 @@ __device__ float gershgorin_lower(S A, int n, float* ones, float* sums, float* r
 
 // The whole Lanczos + certificate path.
 //  Gs  G in lower storage, read only (the Lanczos operator).
-//  Q   shared scratch of jmax * n floats (column j at Q + j*n), jmax <= n.
+//  Q   shared scratch of jmax * lz_ldq<NMAX>(n) floats (column j at
+//      Q + j * lz_ldq<NMAX>(n)), jmax <= n.
 //  U   receives the kept Ritz vectors (kLzMaxK * n floats, column-major,
 //      any memory).
 //  warm / kwarm: previous Ritz vectors (column-major n x kwarm) or kwarm = 0.
@@ -409,6 +421,7 @@ __device__ int lanczos_candidates(SG Gs, int n, float thr, float gbound, float* 
     part = fmaf(v, v, part);
   }
   const float inrm = 1.f / sqrtf(block_sum<NT>(part, s.red));
+  const int ldq = lz_ldq<NMAX>(n);
   for (int e = tid; e < n; e += NT) Q[e] = z.x[e] * inrm;
   __syncthreads();
   const int jmin = min(jmax, kwarm > 0 ? kwarm + 3 : 8);
@@ -419,9 +432,9 @@ __device__ int lanczos_candidates(SG Gs, int n, float thr, float gbound, float* 
   for (int j = 0; j < jmax; ++j) {
     // w = G q_j, then w <- w - Q_j Q_j^T w twice: alpha_j is the q_j
     // coefficient of the two passes, beta_j = ||w|| (full reorthogonalisation)
-    symv_rows<NT, NMAX>(Gs, n, Q + (size_t)j * n, z.w);
+    symv_rows<NT, NMAX>(Gs, n, Q + (size_t)j * ldq, z.w);
     PHASE(slot, 7);
-    float b = sqrtf(lz_project<NT, NMAX>(z.w, Q, n, j + 1, z.h, z.h + kLzMaxJ, s.red));
+    float b = sqrtf(lz_project<NT, NMAX>(z.w, Q, ldq, n, j + 1, z.h, z.h + kLzMaxJ, s.red));
     const float a = z.h[j] + z.h[kLzMaxJ + j];
     PHASE(slot, 9);
     if (tid == 0) {
@@ -437,13 +450,13 @@ __device__ int lanczos_candidates(SG Gs, int n, float thr, float gbound, float* 
         for (int e = tid; e < n; e += NT) z.w[e] = lz_hash(seed + 7919u * restart, e);
         ++restart;
         __syncthreads();
-        const float bn = sqrtf(lz_project<NT, NMAX>(z.w, Q, n, j + 1, z.h, z.h + kLzMaxJ, s.red));
+        const float bn = sqrtf(lz_project<NT, NMAX>(z.w, Q, ldq, n, j + 1, z.h, z.h + kLzMaxJ, s.red));
         if (!(bn > 0.f)) break;
         if (tid == 0) z.beta[j] = 0.f;
         b = bn;
       }
       const float ib = 1.f / b;
-      for (int e = tid; e < n; e += NT) Q[(size_t)(j + 1) * n + e] = z.w[e] * ib;
+      for (int e = tid; e < n; e += NT) Q[(size_t)(j + 1) * ldq + e] = z.w[e] * ib;
       __syncthreads();
     }
     PHASE(slot, 10);
@@ -477,7 +490,7 @@ __device__ int lanczos_candidates(SG Gs, int n, float thr, float gbound, float* 
     const int e = tid + i * NT, r = e >> 3, q = e & 7;
     float v = 0.f;
     if (r < n && q < ku)
-      for (int jj = 0; jj < J; ++jj) v = fmaf(Q[jj * n + r], z.ty[jj * kLzMaxK + q], v);
+      for (int jj = 0; jj < J; ++jj) v = fmaf(Q[jj * ldq + r], z.ty[jj * kLzMaxK + q], v);
     uv[i] = v;
   }
   __syncthreads();
