@@ -8,8 +8,9 @@
 //      regchol.cuh), output V_b diag(sqrt(f));
 //   3. eig_fallback: the Householder path (symeig.cuh) for the blocks step 2
 //      could not certify;
-//   4. rebuild: Z'_b = (C_b V_f) V_f^T in row slabs, scattered through
-//      Shift_{-s}, with the fused dual update W' = 2 Z' - A of eq:admm.
+//   4. rebuild: Z'_b = (C_b V_f) V_f^T, scattered through Shift_{-s}, with
+//      the fused dual update W' = 2 Z' - A of eq:admm (warp per row for
+//      ranks up to 8, row slabs above).
 #include <math.h>
 
 #include "common.cuh"
@@ -414,10 +415,72 @@ size_t fallback_smem_bytes(int nn) {
                           4 * kEigThreads + 64);
 }
 
-// Z' = (C V_f) V_f^T for a slab of `rs` rows of C, W' = 2 Z' - A.
+// Z' = (C V_f) V_f^T, W' = 2 Z' - A for blocks of rank k <= kRowK: one warp
+// per row of C, a lane per 32nd column.  Row i: P = C_i V_f by lane partial
+// sums and k warp reductions, Z'_i = P V_f^T; V_f (transposed) is staged once
+// per CTA.  Every load of C and store of Z', W' is a warp-wide row segment.
+constexpr int kRowK = 8;
+constexpr int kRowsPerCta = 32;  // 8 warps x 4 rows
+__global__ void __launch_bounds__(kRebThreads, 4)
+rebuild_rows_kernel(ScaleLaunch a, const float* __restrict__ Yall, size_t ystride,
+                    const int* __restrict__ kin) {
+  __shared__ float Vt[kRowK * kEigMax];
+  const int b = blockIdx.y;
+  const int k = kin[b];
+  if (k > kRowK) return;  // rebuild_kernel takes the block
+  const BlockGeom g = make_geom(a, b);
+  const int mm = g.mm(), nn = g.nn();
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const float* Yb = Yall + (size_t)b * ystride;
+  for (int i = tid; i < nn; i += kRebThreads)
+    for (int q = 0; q < k; ++q) Vt[q * nn + i] = Yb[(size_t)i * nn + q];
+  __syncthreads();
+  constexpr int RPW = kRowsPerCta / (kRebThreads / 32);
+  const int row0 = blockIdx.x * kRowsPerCta + warp * RPW;
+  for (int rr = 0; rr < RPW; ++rr) {
+    const int i = row0 + rr;
+    if (i >= mm) break;
+    float av[kEigMax / 32];
+#pragma unroll
+    for (int t = 0; t < kEigMax / 32; ++t) {
+      const int c = lane + 32 * t;
+      av[t] = c < nn ? load_a(a, c_offset(g, i, c)) : 0.f;
+    }
+    float P[kRowK];
+#pragma unroll
+    for (int q = 0; q < kRowK; ++q) {
+      P[q] = 0.f;
+      if (q < k) {
+#pragma unroll
+        for (int t = 0; t < kEigMax / 32; ++t) {
+          const int c = lane + 32 * t;
+          if (c < nn) P[q] = fmaf(av[t], Vt[q * nn + c], P[q]);
+        }
+        P[q] = warp_sum(P[q]);
+      }
+    }
+#pragma unroll
+    for (int t = 0; t < kEigMax / 32; ++t) {
+      const int c = lane + 32 * t;
+      if (c < nn) {
+        float z = 0.f;
+#pragma unroll
+        for (int q = 0; q < kRowK; ++q)
+          if (q < k) z = fmaf(P[q], Vt[q * nn + c], z);
+        const size_t off = c_offset(g, i, c);
+        a.Zout[off] = z;
+        if (a.Wout) a.Wout[off] = 2.f * z - av[t];
+      }
+    }
+  }
+}
+
+// Z' = (C V_f) V_f^T for a slab of `rs` rows of C, W' = 2 Z' - A: blocks of
+// rank above kRowK.
 __global__ void __launch_bounds__(kRebThreads)
 rebuild_kernel(ScaleLaunch a, const float* __restrict__ Yall, size_t ystride,
                const int* __restrict__ kin, int rs) {
+  if (kin[blockIdx.y] <= kRowK) return;  // rebuild_rows_kernel took the block
   extern __shared__ float sm[];
   const int b = blockIdx.y, tid = threadIdx.x;
   const BlockGeom g = make_geom(a, b);
@@ -586,6 +649,10 @@ cudaError_t launch_big(const ScaleLaunch& s, const BigWorkspace& ws, cudaStream_
   const int rs = kRebElems / d.nn;
   const int slabs = (d.mm + rs - 1) / rs;
   const size_t smem = sizeof(float) * ((size_t)rs * d.nn + (size_t)(d.nn + 1) * kKC + (size_t)rs * kKC);
+  PROF_BEFORE(KK_REBUILD)
+  rebuild_rows_kernel<<<dim3((d.mm + kRowsPerCta - 1) / kRowsPerCta, d.nblocks), kRebThreads, 0,
+                        st>>>(s, ws.Y, ws.ystride, ws.k);
+  PROF_AFTER()
   PROF_BEFORE(KK_REBUILD)
   rebuild_kernel<<<dim3(slabs, d.nblocks), kRebThreads, smem, st>>>(s, ws.Y, ws.ystride, ws.k, rs);
   PROF_AFTER()
