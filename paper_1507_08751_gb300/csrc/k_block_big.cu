@@ -78,10 +78,10 @@ __device__ __forceinline__ float load_a(const ScaleLaunch& a, size_t off) {
   return v;
 }
 
-__global__ void __launch_bounds__(kGramThreads)
+__global__ void __launch_bounds__(kGramThreads, 5)
 gram_tiles_kernel(ScaleLaunch a, float* __restrict__ G, float* __restrict__ part, int chunks) {
-  __shared__ float As[32][kTile + 4];
-  __shared__ float Bs[32][kTile + 4];
+  __shared__ __align__(16) float As[32][kTile + 4];
+  __shared__ __align__(16) float Bs[32][kTile + 4];
   const int t = blockIdx.x, chunk = blockIdx.y, b = blockIdx.z;
   int ta = (int)((sqrtf(8.f * t + 1.f) - 1.f) * 0.5f);
   while (((ta + 1) * (ta + 2)) / 2 <= t) ++ta;
@@ -115,11 +115,9 @@ gram_tiles_kernel(ScaleLaunch a, float* __restrict__ G, float* __restrict__ part
     __syncthreads();
 #pragma unroll 8
     for (int rr = 0; rr < 32; ++rr) {
-      float av[4], bv[4];
-#pragma unroll
-      for (int x = 0; x < 4; ++x) av[x] = As[rr][ty * 4 + x];
-#pragma unroll
-      for (int y = 0; y < 4; ++y) bv[y] = Bs[rr][tx * 4 + y];
+      const float4 a4 = *reinterpret_cast<const float4*>(&As[rr][ty * 4]);
+      const float4 b4 = *reinterpret_cast<const float4*>(&Bs[rr][tx * 4]);
+      const float av[4] = {a4.x, a4.y, a4.z, a4.w}, bv[4] = {b4.x, b4.y, b4.z, b4.w};
 #pragma unroll
       for (int x = 0; x < 4; ++x)
 #pragma unroll
