@@ -418,8 +418,8 @@ size_t fallback_smem_bytes(int nn) {
 // sums and k warp reductions, Z'_i = P V_f^T; V_f (transposed) is staged once
 // per CTA.  Every load of C and store of Z', W' is a warp-wide row segment.
 constexpr int kRowK = 8;
-constexpr int kRowsPerCta = 32;  // 8 warps x 4 rows
-__global__ void __launch_bounds__(kRebThreads, 4)
+constexpr int kRowsPerCta = 48;  // 8 warps x 6 rows: one wave at 3 CTAs per SM
+__global__ void __launch_bounds__(kRebThreads, 3)
 rebuild_rows_kernel(ScaleLaunch a, const float* __restrict__ Yall, size_t ystride,
                     const int* __restrict__ kin) {
   __shared__ float Vt[kRowK * kEigMax];
@@ -434,15 +434,24 @@ rebuild_rows_kernel(ScaleLaunch a, const float* __restrict__ Yall, size_t ystrid
     for (int q = 0; q < k; ++q) Vt[q * nn + i] = Yb[(size_t)i * nn + q];
   __syncthreads();
   constexpr int RPW = kRowsPerCta / (kRebThreads / 32);
+  constexpr int CPL = kEigMax / 32;  // columns per lane
   const int row0 = blockIdx.x * kRowsPerCta + warp * RPW;
+  // the next row's inputs are loaded while the current row is finished
+  float nx[CPL];
+#pragma unroll
+  for (int t = 0; t < CPL; ++t) {
+    const int c = lane + 32 * t;
+    nx[t] = (row0 < mm && c < nn) ? load_a(a, c_offset(g, row0, c)) : 0.f;
+  }
   for (int rr = 0; rr < RPW; ++rr) {
     const int i = row0 + rr;
     if (i >= mm) break;
-    float av[kEigMax / 32];
+    float av[CPL];
 #pragma unroll
-    for (int t = 0; t < kEigMax / 32; ++t) {
+    for (int t = 0; t < CPL; ++t) {
+      av[t] = nx[t];
       const int c = lane + 32 * t;
-      av[t] = c < nn ? load_a(a, c_offset(g, i, c)) : 0.f;
+      nx[t] = (rr + 1 < RPW && i + 1 < mm && c < nn) ? load_a(a, c_offset(g, i + 1, c)) : 0.f;
     }
     float P[kRowK];
 #pragma unroll
