@@ -34,7 +34,7 @@ __device__ __forceinline__ int tri_row(int e) {
 }
 
 template <int NT, int NMAX>
-__global__ void __launch_bounds__(NT) blocksvt_small_kernel(ScaleLaunch a) {
+__global__ void __launch_bounds__(NT, NT == 32 ? 24 : 1) blocksvt_small_kernel(ScaleLaunch a) {
   extern __shared__ float sm[];
   const int tid = threadIdx.x;
   constexpr int SLOT = NT == 32 ? 0 : (NT == 64 ? 1 : 2);
@@ -76,7 +76,9 @@ __global__ void __launch_bounds__(NT) blocksvt_small_kernel(ScaleLaunch a) {
   s.xs = s.hi + NT;
   s.cnt = reinterpret_cast<int*>(s.xs + NT);
   s.red = reinterpret_cast<float*>(s.cnt + NT);
-  // Lanczos region: Q (lz_ldq x JCAP), U (NMAX x kLzMaxK)
+  // Lanczos region: Q (lz_ldq x JCAP), U (NMAX x kLzMaxK); none for blocks
+  // of width <= 16, which skip Lanczos (kAttempts == 1)
+  constexpr int kAttempts = NMAX <= 16 ? 1 : 2;
   constexpr int JCAP = NMAX < kLzMaxJ ? NMAX : kLzMaxJ;
   float* Qs = s.red + 64;
   float* Us = Qs + lz_ldq<NMAX>(NMAX) * JCAP;
@@ -176,17 +178,16 @@ __global__ void __launch_bounds__(NT) blocksvt_small_kernel(ScaleLaunch a) {
   bool lanczos_ok = false;
   // (blocks of width <= 16: the Householder path below is cheaper than
   // Lanczos for candidates that fail the zero-rank test)
-  constexpr int kAttempts = NMAX <= 16 ? 1 : 2;
   for (int attempt = 0; attempt < kAttempts && !skipped && a.skip_bound; ++attempt) {
     float c0 = c_skip;
     int kk = 0, ku = 0;
     if (attempt == 0) {
       if (!(c_skip > 0.f)) continue;
-    } else {
+    } else if constexpr (kAttempts == 2) {
       kk = lanczos_candidates<NT, NMAX>(LowerFull{G, ldg}, nn, thr, gbound, Qs,
-                                                nn < JCAP ? nn : JCAP, Us, nullptr, 0,
-                                                0x51ED27u + 131u * blockIdx.x, s, z, panel, &ku,
-                                                &c0, 5 + SLOT);
+                                        nn < JCAP ? nn : JCAP, Us, nullptr, 0,
+                                        0x51ED27u + 131u * blockIdx.x, s, z, panel, &ku, &c0,
+                                        5 + SLOT);
       PHASE(SLOT, 10);
       if (kk < 0) break;
     }
@@ -281,9 +282,11 @@ __global__ void __launch_bounds__(NT) blocksvt_small_kernel(ScaleLaunch a) {
 template <int NT, int NMAX>
 size_t small_smem_bytes(int mm, int nn) {
   constexpr int JCAP = NMAX < kLzMaxJ ? NMAX : kLzMaxJ;
+  constexpr size_t lz = NMAX <= 16 ? 0
+                                   : (size_t)lz_ldq<NMAX>(NMAX) * JCAP + NMAX * kLzMaxK +
+                                         lz_scratch_floats(NMAX, JCAP);
   return sizeof(float) * ((size_t)2 * mm * nn + (size_t)nn * (2 * nn + 2) + lz_cert_floats(NMAX, NT) +
-                          4 + 9 * NMAX + 4 * NT + 64 + lz_ldq<NMAX>(NMAX) * JCAP + NMAX * kLzMaxK +
-                          lz_scratch_floats(NMAX, JCAP));
+                          4 + 9 * NMAX + 4 * NT + 64 + lz);
 }
 
 template <int NT, int NMAX>
