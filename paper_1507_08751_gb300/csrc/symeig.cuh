@@ -126,17 +126,36 @@ __device__ void tridiagonalize(S G, int n, EigScratch& s) {
       s.beta[j] = b;
     }
     __syncthreads();
-    // p = b * A v on the trailing block A = G[j+1:, j+1:]
-    for (int r = warp; r < len; r += NW) {
-      const int R = j + 1 + r;
-      float acc = 0.f;
-      for (int c = lane; c < len; c += 32) {
-        const int Cc = j + 1 + c;
-        const float a = (c <= r) ? G.at(R, Cc) : G.at(Cc, R);
-        acc = fmaf(a, s.vbuf[c], acc);
+    // p = b * A v on the trailing block A = G[j+1:, j+1:]: one thread per
+    // row when the block is narrow enough, else one warp per row
+    if (len <= NT) {
+      const int r = tid;
+      if (r < len) {
+        const int R = j + 1 + r;
+        float a0 = 0.f, a1 = 0.f;
+        int c = 0;
+        for (; c + 1 <= r; c += 2) {
+          a0 = fmaf(G.at(R, j + 1 + c), s.vbuf[c], a0);
+          a1 = fmaf(G.at(R, j + 2 + c), s.vbuf[c + 1], a1);
+        }
+        for (; c < len; ++c) {
+          const int Cc = j + 1 + c;
+          a0 = fmaf(c <= r ? G.at(R, Cc) : G.at(Cc, R), s.vbuf[c], a0);
+        }
+        s.pbuf[r] = b * (a0 + a1);
       }
-      acc = warp_sum(acc);
-      if (lane == 0) s.pbuf[r] = b * acc;
+    } else {
+      for (int r = warp; r < len; r += NW) {
+        const int R = j + 1 + r;
+        float acc = 0.f;
+        for (int c = lane; c < len; c += 32) {
+          const int Cc = j + 1 + c;
+          const float a = (c <= r) ? G.at(R, Cc) : G.at(Cc, R);
+          acc = fmaf(a, s.vbuf[c], acc);
+        }
+        acc = warp_sum(acc);
+        if (lane == 0) s.pbuf[r] = b * acc;
+      }
     }
     __syncthreads();
     float kp = 0.f;
@@ -146,12 +165,24 @@ __device__ void tridiagonalize(S G, int n, EigScratch& s) {
     for (int i = tid; i < len; i += NT) s.pbuf[i] = fmaf(-K, s.vbuf[i], s.pbuf[i]);
     __syncthreads();
     // A <- A - v w^T - w v^T (lower triangle)
-    for (int r = warp; r < len; r += NW) {
-      const int R = j + 1 + r;
-      const float vr = s.vbuf[r], wr = s.pbuf[r];
-      for (int c = lane; c <= r; c += 32) {
-        float& g = G.at(R, j + 1 + c);
-        g = g - vr * s.pbuf[c] - wr * s.vbuf[c];
+    if (len <= NT) {
+      const int r = tid;
+      if (r < len) {
+        const int R = j + 1 + r;
+        const float vr = s.vbuf[r], wr = s.pbuf[r];
+        for (int c = 0; c <= r; ++c) {
+          float& g = G.at(R, j + 1 + c);
+          g = g - vr * s.pbuf[c] - wr * s.vbuf[c];
+        }
+      }
+    } else {
+      for (int r = warp; r < len; r += NW) {
+        const int R = j + 1 + r;
+        const float vr = s.vbuf[r], wr = s.pbuf[r];
+        for (int c = lane; c <= r; c += 32) {
+          float& g = G.at(R, j + 1 + c);
+          g = g - vr * s.pbuf[c] - wr * s.vbuf[c];
+        }
       }
     }
     __syncthreads();
