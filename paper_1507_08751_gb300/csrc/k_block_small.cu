@@ -33,8 +33,43 @@ __device__ __forceinline__ int tri_row(int e) {
   return i;
 }
 
+// Shared-memory layout of blocksvt_small_kernel (floats, 16-byte aligned
+// offsets), shared by the kernel and the launcher.
+//   C   mm x nn block                          [oC]
+//   S   EigScratch (9 NMAX + 4 NT + 64)        [oS]
+//   G   nn x (nn + 1) Gram matrix              [oG]
+//   L   certificate scratch, then (widths > 16) the Lanczos basis Q, the
+//       Ritz vectors U and the Lanczos scalars [oL, oQ, oU, oZ .. oEnd)
+//   Y   Householder eigenvectors (nn x nn): aliases L, which is dead on
+//       that path
+//   P   C V diag(f) (mm x nn, rebuild only): aliases G when it fits there,
+//       else appended at oEnd
 template <int NT, int NMAX>
-__global__ void __launch_bounds__(NT, NT == 32 ? 24 : 1) blocksvt_small_kernel(ScaleLaunch a) {
+struct SmallLayout {
+  static constexpr bool kLz = NMAX > 16;  // narrower blocks skip Lanczos
+  static constexpr int JCAP = NMAX < kLzMaxJ ? NMAX : kLzMaxJ;
+  int oC, oS, oG, oL, oQ, oU, oZ, oEnd, oP, total;
+  __host__ __device__ static int al(int x) { return (x + 3) & ~3; }
+  __host__ __device__ SmallLayout(int mm, int nn) {
+    oC = 0;
+    oS = al(mm * nn);
+    oG = al(oS + 9 * NMAX + 4 * NT + 64);
+    oL = al(oG + nn * (nn + 1));
+    oQ = al(oL + lz_cert_floats(NMAX, NT));
+    oU = kLz ? oQ + lz_ldq<NMAX>(NMAX) * JCAP : oQ;
+    oZ = kLz ? oU + NMAX * kLzMaxK : oU;
+    oEnd = kLz ? al(oZ + lz_scratch_floats(NMAX, JCAP)) : oQ;
+    oP = mm * nn <= nn * (nn + 1) ? oG : oEnd;
+    total = oP == oG ? oEnd : oEnd + mm * nn;
+  }
+};
+static_assert(16 * 16 <= lz_cert_floats(16, 32), "Y alias (16)");
+static_assert(32 * 32 <= lz_cert_floats(32, 64), "Y alias (32)");
+static_assert(64 * 64 <= lz_cert_floats(64, 128) + 65 * 32 + 64 * kLzMaxK, "Y alias (64)");
+
+template <int NT, int NMAX>
+__global__ void __launch_bounds__(NT, NT == 32 ? 24 : (NT == 128 ? 3 : 1))
+blocksvt_small_kernel(ScaleLaunch a) {
   extern __shared__ float sm[];
   const int tid = threadIdx.x;
   constexpr int SLOT = NT == 32 ? 0 : (NT == 64 ? 1 : 2);
@@ -54,13 +89,13 @@ __global__ void __launch_bounds__(NT, NT == 32 ? 24 : 1) blocksvt_small_kernel(S
   const int mm = g.mm(), nn = g.nn();
   const int ldc = nn, ldg = nn + 1, ldy = nn;
 
-  float* C = sm;
-  float* G = C + mm * nn;
-  float* Y = G + nn * ldg;
-  float* P = Y + nn * (nn + 1);  // Y region holds nn x (nn + 1)
-  const int panel_off = (int)(P - sm) + mm * nn;
-  float* panel = sm + ((panel_off + 3) & ~3);  // certificate scratch, 16-byte aligned (absolute offset)
-  float* scr = panel + lz_cert_floats(NMAX, NT);
+  const SmallLayout<NT, NMAX> lay(mm, nn);
+  float* C = sm + lay.oC;
+  float* G = sm + lay.oG;
+  float* Y = sm + lay.oL;
+  float* P = sm + lay.oP;
+  float* panel = sm + lay.oL;  // certificate scratch
+  float* scr = sm + lay.oS;
   EigScratch s;
   s.d = scr;
   s.e = s.d + NMAX;
@@ -78,12 +113,12 @@ __global__ void __launch_bounds__(NT, NT == 32 ? 24 : 1) blocksvt_small_kernel(S
   s.red = reinterpret_cast<float*>(s.cnt + NT);
   // Lanczos region: Q (lz_ldq x JCAP), U (NMAX x kLzMaxK); none for blocks
   // of width <= 16, which skip Lanczos (kAttempts == 1)
-  constexpr int kAttempts = NMAX <= 16 ? 1 : 2;
-  constexpr int JCAP = NMAX < kLzMaxJ ? NMAX : kLzMaxJ;
-  float* Qs = s.red + 64;
-  float* Us = Qs + lz_ldq<NMAX>(NMAX) * JCAP;
+  constexpr int kAttempts = SmallLayout<NT, NMAX>::kLz ? 2 : 1;
+  constexpr int JCAP = SmallLayout<NT, NMAX>::JCAP;
+  float* Qs = sm + lay.oQ;
+  float* Us = sm + lay.oU;
   LzScratch z;
-  lz_bind<NT>(z, Us + NMAX * kLzMaxK, NMAX, JCAP);
+  lz_bind<NT>(z, sm + lay.oZ, NMAX, JCAP);
 
   // gather A = A1 + A2 on the shifted grid; ||C||_F^2
   const int melem = a.m * a.n;
@@ -202,13 +237,6 @@ __global__ void __launch_bounds__(NT, NT == 32 ? 24 : 1) blocksvt_small_kernel(S
       k = kk;
     }
   }
-  if (lanczos_ok) {
-    for (int e = tid; e < nn * k; e += NT) {
-      const int i = e / k, q = e - i * k;
-      Y[i * ldy + q] = Us[q * nn + i];
-    }
-    __syncthreads();
-  }
   PHASE(SLOT, 7);
   if (!skipped && !lanczos_ok) {
     LowerFull Gacc{G, ldg};
@@ -239,6 +267,10 @@ __global__ void __launch_bounds__(NT, NT == 32 ? 24 : 1) blocksvt_small_kernel(S
     }
     return;
   }
+  // eigenvector q, entry c, at Vb[c * vsc + q * vsq]: the Ritz vectors in
+  // place (column-major) or the Householder output Y (row-major)
+  const float* Vb = lanczos_ok ? Us : Y;
+  const int vsc = lanczos_ok ? 1 : ldy, vsq = lanczos_ok ? nn : 1;
   // f_j = 1 - tau / sigma_j for the k eigenpairs above the threshold
   if (tid < k) {
     const float sig = sqrtf(s.lam[tid]);
@@ -250,7 +282,7 @@ __global__ void __launch_bounds__(NT, NT == 32 ? 24 : 1) blocksvt_small_kernel(S
   for (int e = tid; e < mm * k; e += NT) {
     const int i = e / k, q = e - i * k;
     float acc = 0.f;
-    for (int c = 0; c < nn; ++c) acc = fmaf(C[i * ldc + c], Y[c * ldy + q], acc);
+    for (int c = 0; c < nn; ++c) acc = fmaf(C[i * ldc + c], Vb[c * vsc + q * vsq], acc);
     P[i * nn + q] = acc * s.xs[q];
   }
   __syncthreads();
@@ -259,7 +291,7 @@ __global__ void __launch_bounds__(NT, NT == 32 ? 24 : 1) blocksvt_small_kernel(S
     const int r = e / a.n, c = e - r * a.n;
     const int i = transposed ? c : r, col = transposed ? r : c;
     float z = 0.f;
-    for (int q = 0; q < k; ++q) z = fmaf(P[i * nn + q], Y[col * ldy + q], z);
+    for (int q = 0; q < k; ++q) z = fmaf(P[i * nn + q], Vb[col * vsc + q * vsq], z);
     const size_t off = g.offset(r, c);
     a.Zout[off] = z;
     if (a.Wout) a.Wout[off] = 2.f * z - C[i * ldc + col];
@@ -281,12 +313,7 @@ __global__ void __launch_bounds__(NT, NT == 32 ? 24 : 1) blocksvt_small_kernel(S
 
 template <int NT, int NMAX>
 size_t small_smem_bytes(int mm, int nn) {
-  constexpr int JCAP = NMAX < kLzMaxJ ? NMAX : kLzMaxJ;
-  constexpr size_t lz = NMAX <= 16 ? 0
-                                   : (size_t)lz_ldq<NMAX>(NMAX) * JCAP + NMAX * kLzMaxK +
-                                         lz_scratch_floats(NMAX, JCAP);
-  return sizeof(float) * ((size_t)2 * mm * nn + (size_t)nn * (2 * nn + 2) + lz_cert_floats(NMAX, NT) +
-                          4 + 9 * NMAX + 4 * NT + 64 + lz);
+  return sizeof(float) * (size_t)SmallLayout<NT, NMAX>(mm, nn).total;
 }
 
 template <int NT, int NMAX>
