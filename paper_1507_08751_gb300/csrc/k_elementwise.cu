@@ -11,6 +11,7 @@
 
 #include "common.cuh"
 #include "internal.h"
+#include "../../include/msllr.h"
 
 namespace msllr {
 
@@ -35,13 +36,19 @@ consensus_kernel(const float* __restrict__ Y, const float* __restrict__ W, float
     const size_t n4 = MN >> 2;
     for (size_t i = i0; i < n4; i += stride) {
       float4 acc = reinterpret_cast<const float4*>(Y)[i];
-      for (int j = 0; j < L; ++j) {
-        const float4 w = reinterpret_cast<const float4*>(W + (size_t)j * MN)[i];
-        acc.x -= w.x;
-        acc.y -= w.y;
-        acc.z -= w.z;
-        acc.w -= w.w;
-      }
+      // unrolled to the scale limit so that all L loads are in flight at once
+      float4 w[MSLLR_MAX_SCALES];
+#pragma unroll
+      for (int j = 0; j < MSLLR_MAX_SCALES; ++j)
+        if (j < L) w[j] = reinterpret_cast<const float4*>(W + (size_t)j * MN)[i];
+#pragma unroll
+      for (int j = 0; j < MSLLR_MAX_SCALES; ++j)
+        if (j < L) {
+          acc.x -= w[j].x;
+          acc.y -= w[j].y;
+          acc.z -= w[j].z;
+          acc.w -= w[j].w;
+        }
       acc.x *= invL;
       acc.y *= invL;
       acc.z *= invL;
