@@ -418,8 +418,8 @@ size_t fallback_smem_bytes(int nn) {
 // sums and k warp reductions, Z'_i = P V_f^T; V_f (transposed) is staged once
 // per CTA.  Every load of C and store of Z', W' is a warp-wide row segment.
 constexpr int kRowK = 8;
-constexpr int kRowsPerCta = 48;  // 8 warps x 6 rows: one wave at 3 CTAs per SM
-__global__ void __launch_bounds__(kRebThreads, 3)
+constexpr int kRowsPerCta = 32;  // 8 warps x 4 rows: one wave at 4 CTAs per SM
+__global__ void __launch_bounds__(kRebThreads, 4)
 rebuild_rows_kernel(ScaleLaunch a, const float* __restrict__ Yall, size_t ystride,
                     const int* __restrict__ kin) {
   __shared__ float Vt[kRowK * kEigMax];

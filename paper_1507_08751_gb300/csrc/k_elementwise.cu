@@ -26,9 +26,13 @@ int ew_grid(size_t n_items) {
   return (int)(g < cap ? (g > 0 ? g : 1) : cap);
 }
 
+static_assert(MSLLR_MAX_SCALES == 8, "consensus dispatch covers 1..8 scales");
+
+template <int LC>  // the scale count, a compile-time constant so that all loads are in flight
 __global__ void __launch_bounds__(kEwThreads)
 consensus_kernel(const float* __restrict__ Y, const float* __restrict__ W, float* __restrict__ R,
-                 const uint8_t* __restrict__ mask, int L, size_t MN) {
+                 const uint8_t* __restrict__ mask, size_t MN) {
+  constexpr int L = LC;
   const float invL = 1.f / (float)L;
   const size_t stride = (size_t)gridDim.x * blockDim.x;
   const size_t i0 = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -36,19 +40,16 @@ consensus_kernel(const float* __restrict__ Y, const float* __restrict__ W, float
     const size_t n4 = MN >> 2;
     for (size_t i = i0; i < n4; i += stride) {
       float4 acc = reinterpret_cast<const float4*>(Y)[i];
-      // unrolled to the scale limit so that all L loads are in flight at once
-      float4 w[MSLLR_MAX_SCALES];
+      float4 w[L];
 #pragma unroll
-      for (int j = 0; j < MSLLR_MAX_SCALES; ++j)
-        if (j < L) w[j] = reinterpret_cast<const float4*>(W + (size_t)j * MN)[i];
+      for (int j = 0; j < L; ++j) w[j] = reinterpret_cast<const float4*>(W + (size_t)j * MN)[i];
 #pragma unroll
-      for (int j = 0; j < MSLLR_MAX_SCALES; ++j)
-        if (j < L) {
-          acc.x -= w[j].x;
-          acc.y -= w[j].y;
-          acc.z -= w[j].z;
-          acc.w -= w[j].w;
-        }
+      for (int j = 0; j < L; ++j) {
+        acc.x -= w[j].x;
+        acc.y -= w[j].y;
+        acc.z -= w[j].z;
+        acc.w -= w[j].w;
+      }
       acc.x *= invL;
       acc.y *= invL;
       acc.z *= invL;
@@ -241,7 +242,24 @@ cudaError_t launch_consensus(const float* Y, const float* W, float* R, const uin
                              size_t MN, cudaStream_t st, Prof* prof) {
   if (prof) prof->scale = 0;
   if (prof) if (cudaError_t e = prof->before(st, KK_CONSENSUS)) return e;
-  consensus_kernel<<<ew_grid((MN + 3) / 4), kEwThreads, 0, st>>>(Y, W, R, mask, L, MN);
+  const int grid = ew_grid((MN + 3) / 4);
+  switch (L) {
+#define MSLLR_CONSENSUS_CASE(n) \
+  case n:                      \
+    consensus_kernel<n><<<grid, kEwThreads, 0, st>>>(Y, W, R, mask, MN); \
+    break;
+    MSLLR_CONSENSUS_CASE(1)
+    MSLLR_CONSENSUS_CASE(2)
+    MSLLR_CONSENSUS_CASE(3)
+    MSLLR_CONSENSUS_CASE(4)
+    MSLLR_CONSENSUS_CASE(5)
+    MSLLR_CONSENSUS_CASE(6)
+    MSLLR_CONSENSUS_CASE(7)
+    MSLLR_CONSENSUS_CASE(8)
+#undef MSLLR_CONSENSUS_CASE
+    default:
+      return cudaErrorInvalidValue;
+  }
   if (prof) if (cudaError_t e = prof->after(st)) return e;
   return cudaGetLastError();
 }
