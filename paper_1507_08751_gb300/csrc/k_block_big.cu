@@ -347,12 +347,9 @@ eig_big_kernel(ScaleLaunch a, const float* __restrict__ Gall, BigWorkspace ws) {
 // Householder path for the blocks eig_big_kernel left unsettled (ws.k < 0):
 // tridiagonalisation, Sturm multisection and inverse iteration on the
 // packed G (symeig.cuh).  Kept out of eig_big_kernel so that the common
-// paths run from a smaller instruction footprint; CTAs of settled blocks
-// return at once.
-__global__ void __launch_bounds__(kEigThreads)
-eig_fallback_kernel(ScaleLaunch a, const float* __restrict__ Gall, BigWorkspace ws) {
-  const int b = blockIdx.x;
-  if (ws.k[b] >= 0) return;
+// paths run from a smaller instruction footprint.
+__device__ __forceinline__ void eig_fallback_block(const ScaleLaunch& a, const float* __restrict__ Gall,
+                                                   const BigWorkspace& ws, int b) {
   extern __shared__ float sm[];
   constexpr int NT = kEigThreads, NMAX = kEigMax;
   const int tid = threadIdx.x;
@@ -405,6 +402,18 @@ eig_fallback_kernel(ScaleLaunch a, const float* __restrict__ Gall, BigWorkspace 
       for (int q = 0; q < k; ++q) t += (double)fmaxf(sqrtf(s.lam[q]) - a.tau, 0.f);
       atomicAdd(a.nuc_acc, t);
     }
+  }
+}
+
+// A few CTAs stride over the blocks (the fallback is rare, and a launch that
+// finds nothing to do then holds few SMs); one CTA per block when the
+// certified paths are off.
+__global__ void __launch_bounds__(kEigThreads)
+eig_fallback_kernel(ScaleLaunch a, const float* __restrict__ Gall, BigWorkspace ws, int nblocks) {
+  for (int b = blockIdx.x; b < nblocks; b += gridDim.x) {
+    if (ws.k[b] >= 0) continue;
+    eig_fallback_block(a, Gall, ws, b);
+    __syncthreads();
   }
 }
 
@@ -483,16 +492,17 @@ rebuild_rows_kernel(ScaleLaunch a, const float* __restrict__ Yall, size_t ystrid
 }
 
 // Z' = (C V_f) V_f^T for a slab of `rs` rows of C, W' = 2 Z' - A: blocks of
-// rank above kRowK.
-__global__ void __launch_bounds__(kRebThreads)
-rebuild_kernel(ScaleLaunch a, const float* __restrict__ Yall, size_t ystride,
-               const int* __restrict__ kin, int rs) {
-  if (kin[blockIdx.y] <= kRowK) return;  // rebuild_rows_kernel took the block
+// rank above kRowK (only the Householder path produces them).  The CTAs
+// stride over the (slab, block) items, so that a launch with nothing to do
+// holds few SMs.
+__device__ __forceinline__ void rebuild_slab(const ScaleLaunch& a, const float* __restrict__ Yall,
+                                             size_t ystride, const int* __restrict__ kin, int rs,
+                                             int slab, int b) {
   extern __shared__ float sm[];
-  const int b = blockIdx.y, tid = threadIdx.x;
+  const int tid = threadIdx.x;
   const BlockGeom g = make_geom(a, b);
   const int mm = g.mm(), nn = g.nn();
-  const int r0 = blockIdx.x * rs;
+  const int r0 = slab * rs;
   const int rows = min(rs, mm - r0);
   const int k = kin[b];
   float* Cs = sm;                          // rows x nn
@@ -556,6 +566,17 @@ rebuild_kernel(ScaleLaunch a, const float* __restrict__ Yall, size_t ystride,
       a.Zout[off] = acc[t];
       if (a.Wout) a.Wout[off] = 2.f * acc[t] - Cs[e];
     }
+  }
+}
+
+__global__ void __launch_bounds__(kRebThreads)
+rebuild_kernel(ScaleLaunch a, const float* __restrict__ Yall, size_t ystride,
+               const int* __restrict__ kin, int rs, int slabs, int nblocks) {
+  for (int w = blockIdx.x; w < slabs * nblocks; w += gridDim.x) {
+    const int b = w / slabs;
+    if (kin[b] <= kRowK) continue;  // rebuild_rows_kernel took the block
+    rebuild_slab(a, Yall, ystride, kin, rs, w - b * slabs, b);
+    __syncthreads();
   }
 }
 
@@ -651,7 +672,9 @@ cudaError_t launch_big(const ScaleLaunch& s, const BigWorkspace& ws, cudaStream_
   eig_big_kernel<<<d.nblocks, kEigThreads, eig_smem_bytes(d.nn), st>>>(s, ws.G, ws);
   PROF_AFTER()
   PROF_BEFORE(KK_EIG_FALLBACK)
-  eig_fallback_kernel<<<d.nblocks, kEigThreads, fallback_smem_bytes(d.nn), st>>>(s, ws.G, ws);
+  const int fb_grid = s.skip_bound ? (d.nblocks < 4 ? d.nblocks : 4) : d.nblocks;
+  eig_fallback_kernel<<<fb_grid, kEigThreads, fallback_smem_bytes(d.nn), st>>>(s, ws.G, ws,
+                                                                               d.nblocks);
   PROF_AFTER()
   const int rs = kRebElems / d.nn;
   const int slabs = (d.mm + rs - 1) / rs;
@@ -661,7 +684,10 @@ cudaError_t launch_big(const ScaleLaunch& s, const BigWorkspace& ws, cudaStream_
                         st>>>(s, ws.Y, ws.ystride, ws.k);
   PROF_AFTER()
   PROF_BEFORE(KK_REBUILD)
-  rebuild_kernel<<<dim3(slabs, d.nblocks), kRebThreads, smem, st>>>(s, ws.Y, ws.ystride, ws.k, rs);
+  const int slab_items = slabs * d.nblocks;
+  const int reb_grid = s.skip_bound ? (slab_items < 152 ? slab_items : 152) : slab_items;
+  rebuild_kernel<<<reb_grid, kRebThreads, smem, st>>>(s, ws.Y, ws.ystride, ws.k, rs, slabs,
+                                                      d.nblocks);
   PROF_AFTER()
 #undef PROF_BEFORE
 #undef PROF_AFTER
