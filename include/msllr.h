@@ -187,6 +187,55 @@ int msllr_decompose_host(msllr_ctx* ctx, const float* Y, int M, int N, int ld,
                          const uint8_t* mask, const msllr_params* params,
                          float* X_out, float* Z_out, msllr_stats* stats);
 
+/* ---- serving queue ------------------------------------------------------
+ * Independent decompositions of one context run in submission order on a
+ * worker thread of the library, so that a caller can keep submitting while
+ * earlier jobs run (the jobs and their sizes are those of msllr_decompose,
+ * eq:admm with the Sec. 9 cycle spin; the queue itself is plumbing around
+ * it).  A job's inputs (Y, mask, block sizes, lambda, params) are copied at
+ * submission; its outputs go to the caller's HOST buffers, which must stay
+ * valid until msllr_poll reports the job done or msllr_wait returns.  While
+ * jobs are queued or running, msllr_decompose, msllr_decompose_host and
+ * msllr_blocksvt on the same context return MSLLR_EBUSY.  Destroying the
+ * context lets the running job finish and drops the queued ones. */
+
+/* Jobs that may wait in the queue of one context. */
+#define MSLLR_SERVE_QUEUE 64
+
+typedef struct msllr_job {
+  const float* Y;          /* host, M x N row-major with row stride ld       */
+  int M, N, ld;
+  int L;                   /* scales, 1..MSLLR_MAX_SCALES                     */
+  const int* block_m;      /* L block heights (divide M)                      */
+  const int* block_n;      /* L block widths (divide N)                       */
+  const double* lambda;    /* L weights, or NULL for the eq:lambda default   */
+  double rho;              /* ADMM penalty, > 0                               */
+  int iters;
+  uint64_t seed;           /* cycle-spin shift sequence                       */
+  const uint8_t* mask;     /* host M x N (row stride N), 1 = observed, or NULL */
+  const msllr_params* params;  /* or NULL; its device-state pointers must be NULL */
+  float* X_out;            /* host L x M x N: the decomposition X_i           */
+  float* Z_out;            /* host L x M x N block-low-rank Z_i, or NULL      */
+  msllr_stats* stats;      /* host, or NULL                                   */
+} msllr_job;
+
+/* Queue a job; *job_id identifies it for msllr_poll / msllr_wait.  Checks
+ * the arguments (EINVAL) and admits the job only if its device footprint
+ * (workspace plus input and output copies) fits the context's HBM budget
+ * (ENOMEM); EBUSY when MSLLR_SERVE_QUEUE jobs are already waiting. */
+int msllr_submit(msllr_ctx* ctx, const msllr_job* job, uint64_t* job_id);
+
+/* *done = 1 once the job has finished, 0 before.  When it reports done the
+ * job leaves the queue's table and the call returns the job's own status
+ * (OK, or the error the decomposition returned, message in
+ * msllr_last_error); EINVAL for an unknown or already collected id. */
+int msllr_poll(msllr_ctx* ctx, uint64_t job_id, int* done);
+
+/* Wait up to timeout_ms (< 0: without limit) for the job, then return its
+ * status as msllr_poll does; ETIMEOUT if it has not finished by then (the
+ * job stays queued and can be waited for again). */
+int msllr_wait(msllr_ctx* ctx, uint64_t job_id, int timeout_ms);
+
 /* Bytes of the fixed device scratch used by msllr_blocksvt_noalloc. */
 #define MSLLR_NOALLOC_SCRATCH_BYTES (32 * 1024 * 1024)
 

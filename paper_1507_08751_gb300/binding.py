@@ -36,8 +36,10 @@ STATUS_NAMES = {0: "MSLLR_OK", 1: "MSLLR_EINVAL", 2: "MSLLR_ENOMEM", 3: "MSLLR_E
 EXPORTS = (
     "msllr_params_default", "msllr_create", "msllr_destroy", "msllr_last_error",
     "msllr_shift_table", "msllr_lambda_default", "msllr_blocksvt", "msllr_decompose",
-    "msllr_decompose_host", "msllr_blocksvt_noalloc",
+    "msllr_decompose_host", "msllr_blocksvt_noalloc", "msllr_submit", "msllr_poll",
+    "msllr_wait",
 )
+SERVE_QUEUE = 64
 NOALLOC_SCRATCH_BYTES = 32 * 1024 * 1024
 
 
@@ -99,6 +101,27 @@ class Stats(ctypes.Structure):
         }
 
 
+class Job(ctypes.Structure):
+    _fields_ = [
+        ("Y", ctypes.c_void_p),
+        ("M", ctypes.c_int),
+        ("N", ctypes.c_int),
+        ("ld", ctypes.c_int),
+        ("L", ctypes.c_int),
+        ("block_m", ctypes.c_void_p),
+        ("block_n", ctypes.c_void_p),
+        ("lambda_", ctypes.c_void_p),
+        ("rho", ctypes.c_double),
+        ("iters", ctypes.c_int),
+        ("seed", ctypes.c_uint64),
+        ("mask", ctypes.c_void_p),
+        ("params", ctypes.c_void_p),
+        ("X_out", ctypes.c_void_p),
+        ("Z_out", ctypes.c_void_p),
+        ("stats", ctypes.c_void_p),
+    ]
+
+
 _lib = None
 
 
@@ -123,6 +146,9 @@ def lib():
         L.msllr_decompose.argtypes = dec
         L.msllr_decompose_host.argtypes = dec
         L.msllr_blocksvt_noalloc.argtypes = [vp, vp, ci, ci, ci, ci, ci, cd, ci, ci, vp, vp]
+        L.msllr_submit.argtypes = [vp, ctypes.POINTER(Job), ctypes.POINTER(cu64)]
+        L.msllr_poll.argtypes = [vp, cu64, ctypes.POINTER(ci)]
+        L.msllr_wait.argtypes = [vp, cu64, ci]
         for name in EXPORTS:
             getattr(L, name)
         _lib = L
@@ -253,3 +279,61 @@ class Context:
         return self._decompose(lib().msllr_decompose_host, hp(Y, np.float32), M, N, N, scales,
                                lambdas, rho, iters, seed, hp(mask, np.uint8), params,
                                hp(X_out, np.float32), hp(Z_out, np.float32))
+
+    # -- serving queue ---------------------------------------------------------
+    def msllr_submit(self, Y, scales, X_out, lambdas=None, rho=1.0, iters=100, seed=0,
+                     mask=None, params=None, Z_out=None):
+        """Queue a decomposition of the host array Y (NumPy float32); X_out (and Z_out)
+        are host arrays filled when the job completes.  Returns the job id."""
+        def hp(a, dt):
+            if a is None:
+                return None
+            if a.dtype != dt or not a.flags["C_CONTIGUOUS"]:
+                raise MsllrError(MSLLR_EINVAL, f"host array must be contiguous {dt}")
+            return a.ctypes.data
+        M, N = Y.shape
+        L = len(scales)
+        bm = _int_array([s[0] for s in scales])
+        bn = _int_array([s[1] for s in scales])
+        lam = _double_array(lambdas)
+        p = params if params is not None else msllr_params_default()
+        st = Stats()
+        job = Job(Y=hp(Y, np.float32), M=M, N=N, ld=N, L=L,
+                  block_m=ctypes.cast(bm, ctypes.c_void_p),
+                  block_n=ctypes.cast(bn, ctypes.c_void_p),
+                  lambda_=ctypes.cast(lam, ctypes.c_void_p) if lam is not None else None,
+                  rho=float(rho), iters=int(iters), seed=int(seed), mask=hp(mask, np.uint8),
+                  params=ctypes.cast(ctypes.pointer(p), ctypes.c_void_p),
+                  X_out=hp(X_out, np.float32), Z_out=hp(Z_out, np.float32),
+                  stats=ctypes.cast(ctypes.pointer(st), ctypes.c_void_p))
+        jid = ctypes.c_uint64()
+        _check(lib().msllr_submit(self._ctx, ctypes.byref(job), ctypes.byref(jid)), self._ctx)
+        # the output buffers and the stats struct must outlive the job
+        if not hasattr(self, "_jobs"):
+            self._jobs = {}
+        self._jobs[jid.value] = (X_out, Z_out, st)
+        return jid.value
+
+    def msllr_poll(self, job_id):
+        """None while the job runs; its stats dict once it has finished (raises
+        MsllrError if the job failed)."""
+        done = ctypes.c_int()
+        code = lib().msllr_poll(self._ctx, ctypes.c_uint64(job_id), ctypes.byref(done))
+        keep = getattr(self, "_jobs", {})
+        if done.value:
+            _, _, st = keep.pop(job_id, (None, None, None))
+            _check(code, self._ctx)
+            return st.to_dict() if st is not None else {}
+        _check(code, self._ctx)
+        return None
+
+    def msllr_wait(self, job_id, timeout_ms=-1):
+        """Wait for the job; returns its stats dict (MsllrError with MSLLR_ETIMEOUT if it
+        has not finished within timeout_ms)."""
+        code = lib().msllr_wait(self._ctx, ctypes.c_uint64(job_id), int(timeout_ms))
+        keep = getattr(self, "_jobs", {})
+        if code == MSLLR_ETIMEOUT:
+            _check(code, self._ctx)
+        _, _, st = keep.pop(job_id, (None, None, None))
+        _check(code, self._ctx)
+        return st.to_dict() if st is not None else {}

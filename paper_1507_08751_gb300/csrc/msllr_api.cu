@@ -6,7 +6,15 @@
 #include <stdlib.h>
 #include <string.h>
 
+#include <atomic>
+#include <chrono>
+#include <condition_variable>
+#include <deque>
+#include <memory>
+#include <mutex>
 #include <string>
+#include <thread>
+#include <unordered_map>
 #include <vector>
 
 #include "../../include/msllr.h"
@@ -24,6 +32,28 @@ namespace msllr {
 // Error message of calls made without a context (msllr_last_error(NULL)).
 void set_contextless_error(const char* msg) { g_last_error = msg; }
 }  // namespace msllr
+
+// One job of the serving queue: its inputs are copied at submission, its
+// outputs point into the caller's host memory.
+struct ServeJob {
+  uint64_t id = 0;
+  int M = 0, N = 0, L = 0;
+  std::vector<float> Y;
+  std::vector<uint8_t> mask;
+  std::vector<int> bm, bn;
+  std::vector<double> lam;
+  double rho = 1.0;
+  int iters = 0;
+  uint64_t seed = 0;
+  msllr_params p{};
+  bool has_p = false;
+  float* X_out = nullptr;
+  float* Z_out = nullptr;
+  msllr_stats* stats = nullptr;
+  int status = MSLLR_OK;
+  bool done = false;
+  std::string err;
+};
 
 struct msllr_ctx {
   int device = 0;
@@ -51,6 +81,21 @@ struct msllr_ctx {
   cudaEvent_t ev_join[MSLLR_MAX_SCALES] = {};
   cudaEvent_t ev_gate[MSLLR_MAX_SCALES] = {};
 
+  // error message; written under err_mu (the serving worker runs concurrently)
+  std::mutex err_mu;
+
+  // serving queue: one worker thread runs the submitted jobs in order
+  std::mutex q_mu;
+  std::condition_variable q_cv;     // wakes the worker
+  std::condition_variable done_cv;  // a job finished
+  std::deque<std::shared_ptr<ServeJob>> queue;
+  std::unordered_map<uint64_t, std::shared_ptr<ServeJob>> jobs;
+  uint64_t next_job = 1;
+  std::thread worker;
+  bool worker_started = false;
+  bool stop = false;
+  std::atomic<int> in_flight{0};
+
   // cached graph of one iteration
   cudaGraphExec_t graph = nullptr;
   std::vector<char> graph_key;
@@ -61,9 +106,21 @@ struct msllr_ctx {
 namespace {
 
 int fail(msllr_ctx* ctx, int code, const std::string& msg) {
-  if (ctx) ctx->err = msg;
-  else g_last_error = msg;
+  if (ctx) {
+    std::lock_guard<std::mutex> lk(ctx->err_mu);
+    ctx->err = msg;
+  } else {
+    g_last_error = msg;
+  }
   return code;
+}
+
+// calls that use the context's stream and workspace directly are refused
+// while serving jobs are queued or running
+int busy(msllr_ctx* ctx) {
+  return ctx->in_flight.load() > 0
+             ? fail(ctx, MSLLR_EBUSY, "serving jobs are in flight on this context")
+             : MSLLR_OK;
 }
 
 #define CK(call)                                                                       \
@@ -207,6 +264,14 @@ int msllr_create(msllr_ctx** out, int device, size_t hbm_budget_bytes, void* cud
 
 int msllr_destroy(msllr_ctx* ctx) {
   if (!ctx) return MSLLR_OK;
+  if (ctx->worker_started) {
+    {
+      std::lock_guard<std::mutex> lk(ctx->q_mu);
+      ctx->stop = true;  // the running job completes, queued ones are dropped
+    }
+    ctx->q_cv.notify_all();
+    ctx->worker.join();
+  }
   cudaSetDevice(ctx->device);
   if (ctx->stream) cudaStreamSynchronize(ctx->stream);
   if (ctx->graph) cudaGraphExecDestroy(ctx->graph);
@@ -247,7 +312,12 @@ int msllr_destroy(msllr_ctx* ctx) {
 }
 
 const char* msllr_last_error(const msllr_ctx* ctx) {
-  return ctx ? ctx->err.c_str() : g_last_error.c_str();
+  if (!ctx) return g_last_error.c_str();
+  // a copy per calling thread: the serving worker may set a new message
+  static thread_local std::string copy;
+  std::lock_guard<std::mutex> lk(const_cast<msllr_ctx*>(ctx)->err_mu);
+  copy = ctx->err;
+  return copy.c_str();
 }
 
 int msllr_shift_table(uint64_t seed, int iters, int M, int N, int32_t* out) {
@@ -267,6 +337,7 @@ int msllr_lambda_default(int M, int N, int m, int n, double* out) {
 int msllr_blocksvt(msllr_ctx* ctx, const float* A, float* Z, int M, int N, int ld, int bm, int bn,
                    double tau, int shift_r, int shift_c, int* block_rank_out) {
   if (!ctx) return fail(nullptr, MSLLR_EINVAL, "ctx is NULL");
+  if (int r = busy(ctx)) return r;
   if (!A || !Z || M <= 0 || N <= 0 || ld < N)
     return fail(ctx, MSLLR_EINVAL, "msllr_blocksvt: bad matrix arguments");
   if (!(tau >= 0.0) || !isfinite(tau)) return fail(ctx, MSLLR_EINVAL, "tau must be finite and >= 0");
@@ -572,12 +643,102 @@ int decompose_device(msllr_ctx* ctx, const float* Y, int M, int N, int ld, int L
   return MSLLR_OK;
 }
 
+
+// Runs one serving job: device slabs for its inputs and outputs, the
+// decomposition, the copies back into the caller's host buffers.
+int run_job(msllr_ctx* ctx, ServeJob& j) {
+  const size_t MN = (size_t)j.M * j.N;
+  float* dY = nullptr;
+  float* dX = nullptr;
+  float* dZ = nullptr;
+  uint8_t* dmask = nullptr;
+  auto cleanup = [&]() {
+    if (dY) cudaFree(dY);
+    if (dX) cudaFree(dX);
+    if (dZ) cudaFree(dZ);
+    if (dmask) cudaFree(dmask);
+  };
+  CK(cudaSetDevice(ctx->device));
+  if (cudaMalloc(&dY, sizeof(float) * MN) != cudaSuccess ||
+      cudaMalloc(&dX, sizeof(float) * j.L * MN) != cudaSuccess ||
+      (j.Z_out && cudaMalloc(&dZ, sizeof(float) * j.L * MN) != cudaSuccess) ||
+      (!j.mask.empty() && cudaMalloc(&dmask, MN) != cudaSuccess)) {
+    cudaGetLastError();
+    cleanup();
+    return fail(ctx, MSLLR_ENOMEM, "serving job: device buffers");
+  }
+  cudaError_t e = cudaMemcpyAsync(dY, j.Y.data(), sizeof(float) * MN, cudaMemcpyHostToDevice,
+                                  ctx->stream);
+  if (e == cudaSuccess && dmask)
+    e = cudaMemcpyAsync(dmask, j.mask.data(), MN, cudaMemcpyHostToDevice, ctx->stream);
+  if (e != cudaSuccess) {
+    cleanup();
+    return fail(ctx, MSLLR_ECUDA, std::string("serving job: host to device copy: ") +
+                                      cudaGetErrorString(e));
+  }
+  int r = decompose_device(ctx, dY, j.M, j.N, j.N, j.L, j.bm.data(), j.bn.data(),
+                           j.lam.empty() ? nullptr : j.lam.data(), j.rho, j.iters, j.seed, dmask,
+                           j.has_p ? &j.p : nullptr, dX, dZ, j.stats);
+  if (r == MSLLR_OK) {
+    e = cudaMemcpyAsync(j.X_out, dX, sizeof(float) * j.L * MN, cudaMemcpyDeviceToHost,
+                        ctx->stream);
+    if (e == cudaSuccess && j.Z_out)
+      e = cudaMemcpyAsync(j.Z_out, dZ, sizeof(float) * j.L * MN, cudaMemcpyDeviceToHost,
+                          ctx->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+    if (e != cudaSuccess)
+      r = fail(ctx, MSLLR_ECUDA, std::string("serving job: device to host copy: ") +
+                                     cudaGetErrorString(e));
+  }
+  cleanup();
+  return r;
+}
+
+// The serving worker: takes the queued jobs in submission order until the
+// context is destroyed.
+void serve_loop(msllr_ctx* ctx) {
+  for (;;) {
+    std::shared_ptr<ServeJob> job;
+    {
+      std::unique_lock<std::mutex> lk(ctx->q_mu);
+      ctx->q_cv.wait(lk, [&] { return ctx->stop || !ctx->queue.empty(); });
+      if (ctx->stop) return;
+      job = ctx->queue.front();
+      ctx->queue.pop_front();
+    }
+    const int r = run_job(ctx, *job);
+    std::string msg;
+    if (r != MSLLR_OK) {
+      std::lock_guard<std::mutex> lk(ctx->err_mu);
+      msg = ctx->err;
+    }
+    {
+      std::lock_guard<std::mutex> lk(ctx->q_mu);
+      job->status = r;
+      job->err = msg;
+      job->done = true;
+      ctx->in_flight.fetch_sub(1);
+    }
+    ctx->done_cv.notify_all();
+  }
+}
+
+// a finished job leaves the table and hands its status (and message) back
+int collect(msllr_ctx* ctx, std::unordered_map<uint64_t, std::shared_ptr<ServeJob>>::iterator it) {
+  const int st = it->second->status;
+  const std::string msg = it->second->err;
+  ctx->jobs.erase(it);
+  return st == MSLLR_OK ? MSLLR_OK : fail(ctx, st, msg);
+}
+
 }  // namespace
 
 int msllr_decompose(msllr_ctx* ctx, const float* Y, int M, int N, int ld, int L,
                     const int* block_m, const int* block_n, const double* lambda, double rho,
                     int iters, uint64_t seed, const uint8_t* mask, const msllr_params* params,
                     float* X_out, float* Z_out, msllr_stats* stats) {
+  if (ctx)
+    if (int r = busy(ctx)) return r;
   return decompose_device(ctx, Y, M, N, ld, L, block_m, block_n, lambda, rho, iters, seed, mask,
                           params, X_out, Z_out, stats);
 }
@@ -587,6 +748,7 @@ int msllr_decompose_host(msllr_ctx* ctx, const float* Y, int M, int N, int ld, i
                          int iters, uint64_t seed, const uint8_t* mask, const msllr_params* params,
                          float* X_out, float* Z_out, msllr_stats* stats) {
   if (!ctx) return fail(nullptr, MSLLR_EINVAL, "ctx is NULL");
+  if (int r = busy(ctx)) return r;
   if (!Y || !X_out || M <= 0 || N <= 0 || ld < N || L <= 0 || L > MSLLR_MAX_SCALES)
     return fail(ctx, MSLLR_EINVAL, "msllr_decompose_host: bad arguments");
   if (params && (params->Z_init || params->U_init || params->U_out))
@@ -631,6 +793,91 @@ int msllr_decompose_host(msllr_ctx* ctx, const float* Y, int M, int N, int ld, i
   }
   cleanup();
   return r;
+}
+
+int msllr_submit(msllr_ctx* ctx, const msllr_job* job, uint64_t* job_id) {
+  if (!ctx) return fail(nullptr, MSLLR_EINVAL, "ctx is NULL");
+  if (!job || !job_id) return fail(ctx, MSLLR_EINVAL, "msllr_submit: job and job_id are required");
+  const int M = job->M, N = job->N, L = job->L;
+  if (!job->Y || !job->X_out || M <= 0 || N <= 0 || job->ld < N || L <= 0 ||
+      L > MSLLR_MAX_SCALES || !job->block_m || !job->block_n || job->iters < 0 ||
+      !(job->rho > 0.0) || !isfinite(job->rho))
+    return fail(ctx, MSLLR_EINVAL, "msllr_submit: bad job arguments");
+  if (job->params && (job->params->Z_init || job->params->U_init || job->params->U_out))
+    return fail(ctx, MSLLR_EINVAL, "msllr_submit: jobs take no device state pointers");
+  for (int i = 0; i < L; ++i)
+    if (int r = check_blocks(ctx, M, N, job->block_m[i], job->block_n[i])) return r;
+  // admission: the job's workspace plus its input and output slabs must fit
+  // the context's HBM budget
+  const size_t MN = (size_t)M * N;
+  const size_t need = plan(nullptr, M, N, L, job->block_m, job->block_n, job->mask != nullptr).total +
+                      sizeof(float) * MN * (1 + (size_t)L * (job->Z_out ? 2 : 1)) +
+                      (job->mask ? MN : 0);
+  if (ctx->budget && need > ctx->budget)
+    return fail(ctx, MSLLR_ENOMEM, "msllr_submit: job needs " + std::to_string(need) +
+                                       " bytes, above the HBM budget");
+  auto j = std::make_shared<ServeJob>();
+  j->M = M;
+  j->N = N;
+  j->L = L;
+  j->Y.resize(MN);
+  for (int r = 0; r < M; ++r)
+    memcpy(j->Y.data() + (size_t)r * N, job->Y + (size_t)r * job->ld, sizeof(float) * N);
+  if (job->mask) j->mask.assign(job->mask, job->mask + MN);
+  j->bm.assign(job->block_m, job->block_m + L);
+  j->bn.assign(job->block_n, job->block_n + L);
+  if (job->lambda) j->lam.assign(job->lambda, job->lambda + L);
+  j->rho = job->rho;
+  j->iters = job->iters;
+  j->seed = job->seed;
+  if (job->params) {
+    j->p = *job->params;
+    j->has_p = true;
+  }
+  j->X_out = job->X_out;
+  j->Z_out = job->Z_out;
+  j->stats = job->stats;
+  {
+    std::lock_guard<std::mutex> lk(ctx->q_mu);
+    if ((int)ctx->queue.size() >= MSLLR_SERVE_QUEUE)
+      return fail(ctx, MSLLR_EBUSY, "msllr_submit: the serving queue is full");
+    j->id = ctx->next_job++;
+    ctx->jobs[j->id] = j;
+    ctx->queue.push_back(j);
+    ctx->in_flight.fetch_add(1);
+    if (!ctx->worker_started) {
+      ctx->worker = std::thread(serve_loop, ctx);
+      ctx->worker_started = true;
+    }
+  }
+  ctx->q_cv.notify_one();
+  *job_id = j->id;
+  return MSLLR_OK;
+}
+
+int msllr_poll(msllr_ctx* ctx, uint64_t job_id, int* done) {
+  if (!ctx) return fail(nullptr, MSLLR_EINVAL, "ctx is NULL");
+  if (!done) return fail(ctx, MSLLR_EINVAL, "msllr_poll: done is required");
+  std::lock_guard<std::mutex> lk(ctx->q_mu);
+  auto it = ctx->jobs.find(job_id);
+  if (it == ctx->jobs.end()) return fail(ctx, MSLLR_EINVAL, "msllr_poll: unknown job id");
+  *done = it->second->done ? 1 : 0;
+  return *done ? collect(ctx, it) : MSLLR_OK;
+}
+
+int msllr_wait(msllr_ctx* ctx, uint64_t job_id, int timeout_ms) {
+  if (!ctx) return fail(nullptr, MSLLR_EINVAL, "ctx is NULL");
+  std::unique_lock<std::mutex> lk(ctx->q_mu);
+  auto it = ctx->jobs.find(job_id);
+  if (it == ctx->jobs.end()) return fail(ctx, MSLLR_EINVAL, "msllr_wait: unknown job id");
+  std::shared_ptr<ServeJob> j = it->second;
+  auto ready = [&] { return j->done; };
+  if (timeout_ms < 0) {
+    ctx->done_cv.wait(lk, ready);
+  } else if (!ctx->done_cv.wait_for(lk, std::chrono::milliseconds(timeout_ms), ready)) {
+    return fail(ctx, MSLLR_ETIMEOUT, "msllr_wait: job not finished within the timeout");
+  }
+  return collect(ctx, ctx->jobs.find(job_id));
 }
 
 }  // extern "C"
