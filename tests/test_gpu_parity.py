@@ -176,6 +176,32 @@ def test_decompose_video_shaped_matches_oracle(ctx):
     assert np.all(err <= TOL), err
 
 
+def test_decompose_one_sided_partitions_matches_oracle(ctx):
+    """One-sided partitions (Sec. 2: blocks spanning whole rows, the group
+    prox of 1 x N rows and the block norm of m x N strips) next to the 1x1
+    and full-matrix scales, against the oracle."""
+    rng = np.random.default_rng(1507087517)
+    M, N = 256, 128
+    rows = np.zeros((M, N))
+    active = rng.random(M) < 0.05
+    rows[active] = rng.standard_normal((active.sum(), N))
+    strips = np.zeros((M, N))
+    for p in range(M // 8):
+        if rng.random() < 0.1:
+            strips[8 * p:8 * p + 8] = np.outer(rng.standard_normal(8), rng.standard_normal(N))
+    Y = rows + strips + 0.5 * np.outer(rng.standard_normal(M), rng.standard_normal(N)) \
+        + 0.01 * rng.standard_normal((M, N))
+    Y32 = Y.astype(np.float32)
+    scales = [(1, 1), (1, N), (8, N), (M, N)]
+    lam = [O.lambda_default(M, N, m, n) for m, n in scales]
+    iters, seed = 80, 11
+    X, Z, stats = _run_decompose(ctx, Y32, scales, lam, iters, seed)
+    ref = O.admm(Y32.astype(np.float64), scales, lam, 1.0, iters,
+                 shifts=O.shift_table(seed, iters, M, N))
+    err = O.relerr(X, ref["X"], Y32)
+    assert np.all(err <= TOL), err
+
+
 def test_decompose_masked_matches_oracle(ctx):
     """Sec. 10.4 masked X-update on a ratings-like input."""
     Y32, mask = synth.ratings(5, 128, 96, density=0.3)
