@@ -18,7 +18,10 @@ design notes):
   * the returned X_i is the X-update of eq:admm applied to the final (Z, U),
     so that sum_i X_i = Y holds exactly (up to rounding);
   * masked X-update (Sec. 10.4): the residual term is zero at unobserved
-    entries, and Y there is ignored.
+    entries, and Y there is ignored;
+  * the noise scale of Sec. 2.1 (the whole matrix reshaped to one MN x 1
+    block, whose nuclear norm is the Frobenius norm) is written as the block
+    size (0, 0); its default weight is eq:lambda with m = MN, n = 1.
 """
 
 from __future__ import annotations
@@ -65,7 +68,11 @@ def shift_table(seed: int, iters: int, M: int, N: int) -> np.ndarray:
 
 def lambda_default(M: int, N: int, m: int, n: int) -> float:
     """eq:lambda as used in the experiments (Sec. 10):
-    lambda_i = sqrt(m_i) + sqrt(n_i) + sqrt(log(M N / max(m_i, n_i)))."""
+    lambda_i = sqrt(m_i) + sqrt(n_i) + sqrt(log(M N / max(m_i, n_i))).
+    The noise scale (0, 0) is the MN x 1 block: sqrt(MN) + 1 (Sec. 4 notes
+    the sqrt(MN) scaling)."""
+    if (m, n) == (0, 0):
+        m, n = M * N, 1
     return math.sqrt(m) + math.sqrt(n) + math.sqrt(math.log(M * N / max(m, n)))
 
 
@@ -117,8 +124,12 @@ def soft_threshold(a: np.ndarray, tau: float) -> np.ndarray:
 
 def _blocks(A: np.ndarray, m: int, n: int) -> np.ndarray:
     """R_b for every block b of the m x n partition (Sec. 2, Fig. Rop):
-    block (p, q) is A[p*m:(p+1)*m, q*n:(q+1)*n]; returns shape (nb, m, n)."""
+    block (p, q) is A[p*m:(p+1)*m, q*n:(q+1)*n]; returns shape (nb, m, n).
+    The noise scale (0, 0) is the one block R_noise(A), the whole matrix
+    reshaped to MN x 1 (Sec. 2.1)."""
     M, N = A.shape
+    if (m, n) == (0, 0):
+        return A.reshape(1, M * N, 1)
     if M % m or N % n:
         raise ValueError(f"block {m}x{n} does not divide {M}x{N}")
     return A.reshape(M // m, m, N // n, n).transpose(0, 2, 1, 3).reshape(-1, m, n)
@@ -127,6 +138,8 @@ def _blocks(A: np.ndarray, m: int, n: int) -> np.ndarray:
 def _unblocks(B: np.ndarray, M: int, N: int) -> np.ndarray:
     """sum_b R_b^T(B_b): the adjoint of ``_blocks`` (blocks do not overlap)."""
     nb, m, n = B.shape
+    if (nb, m, n) == (1, M * N, 1) and (M, N) != (M * N, 1):
+        return B.reshape(M, N)  # the noise block R_noise^T
     return B.reshape(M // m, N // n, m, n).transpose(0, 2, 1, 3).reshape(M, N)
 
 

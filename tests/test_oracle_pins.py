@@ -422,3 +422,57 @@ def test_planted_shift_direction_is_caught(monkeypatch):
     monkeypatch.setattr(O, "shift", bad_shift)
     with pytest.raises(AssertionError):
         test_shift_matches_definition_by_loops()
+
+
+# --------------------------------------------------------------------------
+# Noise scale (Sec. 2.1): the whole matrix as one MN x 1 block
+# --------------------------------------------------------------------------
+
+def test_noise_scale_is_the_vector_shrink():
+    """The SVD of an MN x 1 block has the single singular value ||A||_F with
+    u = vec(A)/||A||_F and v = 1, so its SVT is A max(1 - tau/||A||_F, 0)."""
+    rng = np.random.default_rng(31)
+    A = rng.standard_normal((12, 5))
+    nrm = np.sqrt((A * A).sum())
+    for tau in (0.3 * nrm, 0.99 * nrm, 1.5 * nrm):
+        Z = O.block_svt(A, 0, 0, tau)
+        np.testing.assert_allclose(Z, A * max(1.0 - tau / nrm, 0.0), rtol=1e-12, atol=1e-14)
+    assert O.block_nuclear_norm(A, 0, 0) == pytest.approx(nrm, rel=1e-13)
+    assert O.block_dual_norm(A, 0, 0) == pytest.approx(nrm, rel=1e-13)
+
+
+def test_noise_scale_prox_is_optimal_brute_force():
+    """prox of tau ||.||_F: no perturbation of the returned Z lowers
+    0.5 ||Z - A||^2 + tau ||Z||_F (random directions, small and large)."""
+    rng = np.random.default_rng(32)
+    A = rng.standard_normal((3, 2))
+    tau = 0.7
+    Z = O.block_svt(A, 0, 0, tau)
+    f = lambda X: 0.5 * ((X - A) ** 2).sum() + tau * np.sqrt((X * X).sum())
+    f0 = f(Z)
+    for _ in range(2000):
+        d = rng.standard_normal(A.shape) * 10.0 ** rng.uniform(-4, 0)
+        assert f(Z + d) >= f0 - 1e-12
+
+
+def test_noise_scale_lambda_default():
+    assert O.lambda_default(64, 32, 0, 0) == pytest.approx(np.sqrt(64 * 32) + 1.0, rel=1e-15)
+
+
+def test_admm_with_noise_scale_keeps_the_invariants():
+    """sum_i X_i = Y and U' = X + U - Z' with a noise scale among the scales."""
+    rng = np.random.default_rng(33)
+    M, N = 32, 16
+    Y = np.outer(rng.standard_normal(M), rng.standard_normal(N)) + 0.1 * rng.standard_normal((M, N))
+    scales = [(1, 1), (8, 8), (M, N), (0, 0)]
+    lam = [O.lambda_default(M, N, m, n) for m, n in scales]
+    out = O.admm(Y, scales, lam, 1.0, 40, shifts=O.shift_table(7, 40, M, N))
+    np.testing.assert_allclose(out["X"].sum(0), Y, atol=1e-12)
+    L = len(scales)
+    Z = np.zeros((L, M, N)); U = np.zeros((L, M, N))
+    s = O.shift_table(7, 1, M, N)[0]
+    X, Zn, Un = O.admm_step(Y, Z, U, scales, lam, s)
+    np.testing.assert_allclose(Un, X + U - Zn, atol=1e-13)
+    # the noise scale's first prox: Y/L shrunk by its Frobenius norm
+    A = Y / L
+    np.testing.assert_allclose(Zn[3], A * max(1 - lam[3] / np.linalg.norm(A), 0), atol=1e-13)
