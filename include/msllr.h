@@ -134,8 +134,16 @@ int msllr_shift_table(uint64_t seed, int iters, int M, int N, int32_t* out);
 
 /* Default regularisation eq:lambda (Sec. 4, as used in Sec. 10):
  *   lambda = sqrt(m) + sqrt(n) + sqrt(log(M N / max(m, n))).
+ * For the noise scale (m = n = 0, see MSLLR_NOISE_SCALE) the block is
+ * MN x 1: lambda = sqrt(M N) + 1.
  * Errors: EINVAL when the block does not fit in the matrix. */
 int msllr_lambda_default(int M, int N, int m, int n, double* out);
+
+/* Block size (m, n) = (0, 0) selects the noise scale of Sec. 2.1: the whole
+ * matrix reshaped to one MN x 1 block, whose nuclear norm is the Frobenius
+ * norm, so that its SVT is A max(1 - tau / ||A||_F, 0).  Accepted wherever a
+ * block size is (not by msllr_blocksvt_noalloc). */
+#define MSLLR_NOISE_SCALE 0
 
 /* One block-wise singular value threshold, eq:bsvt (Sec. 7), under the
  * circular shift s = (shift_r, shift_c) of Sec. 9:
@@ -145,8 +153,8 @@ int msllr_lambda_default(int M, int N, int m, int n, double* out);
  * stride `ld` (>= N) elements; A and Z must not overlap.  If
  * `block_rank_out` is not NULL it receives, per block in row-major block
  * order, the number of singular values above tau (device int32,
- * (M/bm)*(N/bn) entries).  Errors: EINVAL (bm, bn do not divide M, N;
- * min(bm, bn) > MSLLR_MAX_BLOCK_WIDTH; tau < 0), ECUDA. */
+ * (M/bm)*(N/bn) entries; one for the noise scale).  Errors: EINVAL (bm, bn
+ * do not divide M, N; min(bm, bn) > MSLLR_MAX_BLOCK_WIDTH; tau < 0), ECUDA. */
 int msllr_blocksvt(msllr_ctx* ctx, const float* A, float* Z, int M, int N, int ld,
                    int bm, int bn, double tau, int shift_r, int shift_c,
                    int* block_rank_out);
@@ -159,7 +167,8 @@ int msllr_blocksvt(msllr_ctx* ctx, const float* A, float* Z, int M, int N, int l
  * starting from Z_i = U_i = 0 (or params->Z_init / U_init).
  *  Y        device, M x N, row stride ld (>= N).
  *  block_m, block_n   host arrays of L block sizes; each must divide M, N;
- *           min(m_i, n_i) <= MSLLR_MAX_BLOCK_WIDTH.
+ *           min(m_i, n_i) <= MSLLR_MAX_BLOCK_WIDTH; (0, 0) is the noise
+ *           scale (MSLLR_NOISE_SCALE).
  *  lambda   host array of L values > 0, or NULL for msllr_lambda_default.
  *  rho      > 0.
  *  seed     seeds the shift table (msllr_shift_table).
@@ -248,7 +257,7 @@ int msllr_wait(msllr_ctx* ctx, uint64_t job_id, int timeout_ms);
  * It needs no msllr_ctx.
  *
  * Computes exactly what msllr_blocksvt computes, with the same argument
- * meaning, on the stream `cuda_stream` (a cudaStream_t, or NULL for the
+ * meaning (block sizes that divide the matrix; not the noise scale), on the stream `cuda_stream` (a cudaStream_t, or NULL for the
  * legacy default stream) of the current CUDA device, and returns after
  * that stream has finished the work.  Its workspace is one fixed array of
  * MSLLR_NOALLOC_SCRATCH_BYTES in device memory that every GPU loading the

@@ -31,6 +31,7 @@ struct ScaleLaunch {
   double* nuc_acc;         // device, += sum over blocks of sum_j (sigma_j - tau)_+, or null
   unsigned long long* cnt; // device [4]: blocks skipped by a bound, blocks of rank 0,
                            // blocks solved by certified Lanczos, by Householder; or null
+  double* norm_acc;        // device scratch double (noise scale: ||A||_F^2)
 };
 
 // Device workspace needed by the wide-block path for one scale.
@@ -93,7 +94,7 @@ struct Prof {
 };
 
 // Path selection.
-enum class ScalePath { Elementwise, Small, Big };
+enum class ScalePath { Elementwise, Small, Big, Noise };  // Noise: block (0, 0), Sec. 2.1
 ScalePath choose_path(int m, int n);
 // Bytes of BigWorkspace a scale needs (0 for the other paths).
 size_t big_workspace_bytes(int M, int N, int m, int n);

@@ -16,6 +16,7 @@
 namespace msllr {
 
 cudaError_t launch_soft1x1(const ScaleLaunch& s, cudaStream_t st, Prof* prof);
+cudaError_t launch_noise(const ScaleLaunch& s, cudaStream_t st, Prof* prof);
 cudaError_t launch_big(const ScaleLaunch& s, const BigWorkspace& ws, cudaStream_t st, Prof* prof,
                        cudaEvent_t after_gram);
 
@@ -348,6 +349,7 @@ cudaError_t configure_kernels() {
 }
 
 ScalePath choose_path(int m, int n) {
+  if (m == 0 && n == 0) return ScalePath::Noise;
   if (m == 1 && n == 1) return ScalePath::Elementwise;
   const int nn = m < n ? m : n;
   const long long area = (long long)m * n;
@@ -360,6 +362,8 @@ cudaError_t launch_scale(const ScaleLaunch& s, const BigWorkspace& ws, cudaStrea
   switch (choose_path(s.m, s.n)) {
     case ScalePath::Elementwise:
       return launch_soft1x1(s, st, prof);
+    case ScalePath::Noise:
+      return launch_noise(s, st, prof);
     case ScalePath::Small: {
       const int nn = s.m < s.n ? s.m : s.n;
       if (nn <= 16) return launch_small_t<32, 16>(s, st, prof);

@@ -1,6 +1,7 @@
 // Element-wise kernels of the ADMM (eq:admm, Sec. 7): the consensus
 // residual of the X-update, the 1x1-scale soft threshold (eq:bsvt for 1x1
-// blocks) with its fused dual update, and the output X-update.
+// blocks) and the noise-scale shrink (Sec. 2.1) with their fused dual
+// updates, and the output X-update.
 //
 // ADMM state kept in HBM per scale: Z_i and W_i = Z_i - U_i.  With the
 // consensus residual R = (1/L)(Y - sum_j W_j) (zero at unobserved entries,
@@ -236,6 +237,58 @@ copy_dense_kernel(const float* __restrict__ src, int M, int N, int ld, float* __
   }
 }
 
+// Noise scale (Sec. 2.1): the whole matrix is one MN x 1 block, whose only
+// singular value is ||A||_F, so its SVT is A max(1 - tau / ||A||_F, 0).
+// Pass 1 sums ||A||^2 in FP64 (A = A1 + A2); pass 2 applies the shrink with
+// the fused dual update.  The cycle-spin shift is irrelevant (a permutation
+// of the entries).
+__global__ void __launch_bounds__(kEwThreads)
+noise_norm_kernel(const float* __restrict__ A1, const float* __restrict__ A2, int M, int N, int ld,
+                  double* __restrict__ acc) {
+  __shared__ double red[kEwThreads / 32];
+  const size_t MN = (size_t)M * N;
+  const size_t stride = (size_t)gridDim.x * blockDim.x;
+  double t = 0.0;
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < MN; i += stride) {
+    const size_t r = i / (size_t)N, off = r * (size_t)ld + (i - r * (size_t)N);
+    float a = A1[off];
+    if (A2) a += A2[off];
+    t = fma((double)a, (double)a, t);
+  }
+  t = warp_sum_d(t);
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  if (lane == 0) red[w] = t;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double s = 0.0;
+    for (int k = 0; k < kEwThreads / 32; ++k) s += red[k];
+    atomicAdd(acc, s);
+  }
+}
+
+__global__ void __launch_bounds__(kEwThreads)
+noise_shrink_kernel(const float* A1, const float* __restrict__ A2, float* Zout, float* Wout, int M,
+                    int N, int ld, float tau, const double* __restrict__ acc, int* rank_out,
+                    double* nuc_acc, unsigned long long* cnt) {
+  const double nrm = sqrt(*acc);
+  const float f = nrm > (double)tau ? (float)(1.0 - (double)tau / nrm) : 0.f;
+  const size_t MN = (size_t)M * N;
+  const size_t stride = (size_t)gridDim.x * blockDim.x;
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < MN; i += stride) {
+    const size_t r = i / (size_t)N, off = r * (size_t)ld + (i - r * (size_t)N);
+    float a = A1[off];
+    if (A2) a += A2[off];
+    const float z = f * a;
+    Zout[off] = z;
+    if (Wout) Wout[off] = 2.f * z - a;
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    if (rank_out) rank_out[0] = f > 0.f;
+    if (nuc_acc && nrm > (double)tau) atomicAdd(nuc_acc, nrm - (double)tau);
+    if (cnt && !(f > 0.f)) atomicAdd(cnt + 1, 1ull);
+  }
+}
+
 }  // namespace
 
 cudaError_t launch_consensus(const float* Y, const float* W, float* R, const uint8_t* mask, int L,
@@ -260,6 +313,21 @@ cudaError_t launch_consensus(const float* Y, const float* W, float* R, const uin
     default:
       return cudaErrorInvalidValue;
   }
+  if (prof) if (cudaError_t e = prof->after(st)) return e;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_noise(const ScaleLaunch& s, cudaStream_t st, Prof* prof) {
+  if (!s.norm_acc) return cudaErrorInvalidValue;
+  const size_t MN = (size_t)s.M * s.N;
+  if (prof) if (cudaError_t e = prof->before(st, KK_SOFT1X1)) return e;
+  if (cudaError_t e = cudaMemsetAsync(s.norm_acc, 0, sizeof(double), st)) return e;
+  noise_norm_kernel<<<ew_grid(MN), kEwThreads, 0, st>>>(s.A1, s.A2, s.M, s.N, s.ld, s.norm_acc);
+  if (prof) if (cudaError_t e = prof->after(st)) return e;
+  if (prof) if (cudaError_t e = prof->before(st, KK_SOFT1X1)) return e;
+  noise_shrink_kernel<<<ew_grid(MN), kEwThreads, 0, st>>>(s.A1, s.A2, s.Zout, s.Wout, s.M, s.N,
+                                                          s.ld, s.tau, s.norm_acc, s.rank_out,
+                                                          s.nuc_acc, s.cnt);
   if (prof) if (cudaError_t e = prof->after(st)) return e;
   return cudaGetLastError();
 }

@@ -68,6 +68,7 @@ struct msllr_ctx {
   // small device scalars
   int* d_small = nullptr;          // [0] iter, [1..2] cur shift, [3] nonfinite flag, [4..5] tmp shift
   double* d_acc = nullptr;         // [0..MAX) nuc per scale, [MAX] primal residual^2
+  double* d_noise = nullptr;       // [MAX] noise-scale ||A||_F^2 scratch
   unsigned long long* d_cnt = nullptr;  // [2*MAX]
   int* d_table = nullptr;
   size_t table_cap = 0;
@@ -146,8 +147,11 @@ void fill_shift_table(uint64_t seed, int offset, int iters, int M, int N, int32_
 }
 
 double lambda_of(int M, int N, int m, int n) {
-  const double mx = m > n ? m : n;
-  return sqrt((double)m) + sqrt((double)n) + sqrt(log((double)M * (double)N / mx));
+  // the noise scale (0, 0) is one MN x 1 block
+  const double bm = (m == 0 && n == 0) ? (double)M * (double)N : (double)m;
+  const double bn = (m == 0 && n == 0) ? 1.0 : (double)n;
+  const double mx = bm > bn ? bm : bn;
+  return sqrt(bm) + sqrt(bn) + sqrt(log((double)M * (double)N / mx));
 }
 
 size_t align_up(size_t x) { return (x + 255) & ~(size_t)255; }
@@ -181,6 +185,7 @@ int ensure_ws(msllr_ctx* ctx, size_t bytes) {
 }
 
 int check_blocks(msllr_ctx* ctx, int M, int N, int m, int n) {
+  if (m == 0 && n == 0) return MSLLR_OK;  // the noise scale (Sec. 2.1)
   if (m <= 0 || n <= 0 || m > M || n > N || M % m || N % n)
     return fail(ctx, MSLLR_EINVAL,
                 "block " + std::to_string(m) + "x" + std::to_string(n) + " does not divide " +
@@ -256,6 +261,7 @@ int msllr_create(msllr_ctx** out, int device, size_t hbm_budget_bytes, void* cud
   }
   if (cudaMalloc(&ctx->d_small, 64 * sizeof(int)) != cudaSuccess ||
       cudaMalloc(&ctx->d_acc, (MSLLR_MAX_SCALES + 8) * sizeof(double)) != cudaSuccess ||
+      cudaMalloc(&ctx->d_noise, MSLLR_MAX_SCALES * sizeof(double)) != cudaSuccess ||
       cudaMalloc(&ctx->d_cnt, 4 * MSLLR_MAX_SCALES * sizeof(unsigned long long)) != cudaSuccess)
     return bail(fail(ctx, MSLLR_ENOMEM, "cudaMalloc of context scalars"));
   *out = ctx;
@@ -297,6 +303,7 @@ int msllr_destroy(msllr_ctx* ctx) {
   }
   if (ctx->d_small) cudaFree(ctx->d_small);
   if (ctx->d_acc) cudaFree(ctx->d_acc);
+  if (ctx->d_noise) cudaFree(ctx->d_noise);
   if (ctx->d_cnt) cudaFree(ctx->d_cnt);
   if (ctx->d_table) cudaFree(ctx->d_table);
   for (int i = 0; i < MSLLR_MAX_SCALES; ++i) {
@@ -328,7 +335,8 @@ int msllr_shift_table(uint64_t seed, int iters, int M, int N, int32_t* out) {
 }
 
 int msllr_lambda_default(int M, int N, int m, int n, double* out) {
-  if (!out || m <= 0 || n <= 0 || m > M || n > N)
+  const bool noise = m == 0 && n == 0;
+  if (!out || M <= 0 || N <= 0 || (!noise && (m <= 0 || n <= 0 || m > M || n > N)))
     return fail(nullptr, MSLLR_EINVAL, "msllr_lambda_default: bad arguments");
   *out = lambda_of(M, N, m, n);
   return MSLLR_OK;
@@ -365,6 +373,7 @@ int msllr_blocksvt(msllr_ctx* ctx, const float* A, float* Z, int M, int N, int l
   s.tau = (float)tau;
   s.skip_bound = 1;
   s.rank_out = block_rank_out;
+  s.norm_acc = ctx->d_noise;
   BigWorkspace w = carve_big_workspace(ctx->ws, M, N, bm, bn);
   CK(launch_scale(s, w, ctx->stream, nullptr));
   CK(cudaStreamSynchronize(ctx->stream));
@@ -450,6 +459,7 @@ int enqueue_iteration(msllr_ctx* ctx, const Layout& lay, int M, int N, int L, co
       s.rank_out = nullptr;
       s.nuc_acc = stats ? ctx->d_acc + i : nullptr;
       s.cnt = stats ? ctx->d_cnt + 4 * i : nullptr;
+      s.norm_acc = ctx->d_noise + i;
       prof->scale = i;
       const bool gate = fork && wide && i > 0;
       if (prof->per_scale) {
@@ -615,7 +625,7 @@ int decompose_device(msllr_ctx* ctx, const float* Y, int M, int N, int ld, int L
     for (int i = 0; i < L; ++i) {
       stats->scale_nuclear[i] = acc[i];
       obj += lam[i] * acc[i];
-      stats->blocks[i] = (long long)(M / bm[i]) * (N / bn[i]);
+      stats->blocks[i] = (bm[i] == 0 && bn[i] == 0) ? 1 : (long long)(M / bm[i]) * (N / bn[i]);
       stats->blocks_skipped[i] = (long long)cnt[4 * i];
       stats->blocks_zero[i] = (long long)cnt[4 * i + 1];
       stats->blocks_lanczos[i] = (long long)cnt[4 * i + 2];

@@ -47,7 +47,8 @@ def test_shift_table_bit_exact_against_oracle(built):
 
 
 def test_lambda_default_matches_eq_lambda(built):
-    for M, N, m, n in [(64, 64, 1, 1), (16384, 256, 16, 16), (16384, 256, 16384, 256), (30, 50, 3, 5)]:
+    for M, N, m, n in [(64, 64, 1, 1), (16384, 256, 16, 16), (16384, 256, 16384, 256), (30, 50, 3, 5),
+                       (16384, 256, 0, 0)]:
         assert B.msllr_lambda_default(M, N, m, n) == pytest.approx(O.lambda_default(M, N, m, n),
                                                                     rel=1e-14)
     with pytest.raises(B.MsllrError) as e:

@@ -101,6 +101,49 @@ def test_blocksvt_matches_oracle(ctx, M, N, m, n, shift):
     assert not bad.any(), f"{bad.sum()} blocks with a wrong rank"
 
 
+def test_blocksvt_noise_scale_matches_oracle(ctx):
+    """Block size (0, 0): the noise scale of Sec. 2.1, one MN x 1 block,
+    whose SVT shrinks the whole matrix by its Frobenius norm; below and above
+    the threshold, with a row stride."""
+    rng = np.random.default_rng(41)
+    M, N, ld = 300, 200, 208
+    Ap = np.zeros((M, ld), np.float32)
+    Ap[:, :N] = rng.standard_normal((M, N)).astype(np.float32)
+    A64 = Ap[:, :N].astype(np.float64)
+    nrm = np.linalg.norm(A64)
+    for tau in (0.4 * nrm, 1.2 * nrm):
+        Z = torch.full((M, ld), 7.0, dtype=torch.float32, device="cuda")
+        rank = torch.full((1,), -1, dtype=torch.int32, device="cuda")
+        ctx.msllr_blocksvt(dev(Ap), Z, 0, 0, tau, (5, 9), rank_out=rank, N=N)
+        torch.cuda.synchronize()
+        want = O.block_svt(A64, 0, 0, tau)
+        got = Z.cpu().numpy()[:, :N].astype(np.float64)
+        err = np.linalg.norm(got - want) / max(np.linalg.norm(want), 1e-6 * nrm)
+        assert err <= TOL, f"relative error {err:.3e}"
+        assert int(rank.item()) == int(tau < nrm)
+        assert np.all(Z.cpu().numpy()[:, N:] == 7.0)  # padding untouched
+
+
+def test_decompose_with_noise_scale_matches_oracle(ctx):
+    """Multi-scale low rank + noise (Sec. 2.1): a noise scale next to the
+    1x1, 8x8 and full-matrix scales, against the oracle."""
+    rng = np.random.default_rng(42)
+    M, N = 128, 96
+    Y = np.outer(rng.standard_normal(M), rng.standard_normal(N))
+    Y += (rng.random((M, N)) < 0.02) * rng.standard_normal((M, N)) * 3
+    Y += 0.2 * rng.standard_normal((M, N))
+    Y32 = Y.astype(np.float32)
+    scales = [(1, 1), (8, 8), (M, N), (0, 0)]
+    lam = [O.lambda_default(M, N, m, n) for m, n in scales]
+    iters, seed = 100, 13
+    X, Z, stats = _run_decompose(ctx, Y32, scales, lam, iters, seed)
+    ref = O.admm(Y32.astype(np.float64), scales, lam, 1.0, iters,
+                 shifts=O.shift_table(seed, iters, M, N))
+    err = O.relerr(X, ref["X"], Y32)
+    assert np.all(err <= TOL), err
+    assert stats["blocks"][3] == 1
+
+
 def test_blocksvt_1x1_is_soft_threshold_bit_exact(ctx):
     """1x1 blocks: the kernel's soft threshold equals the FP32 textbook
     formula bit for bit (the oracle restates it in FP64)."""
