@@ -50,12 +50,17 @@ typedef enum msllr_status {
  * narrow-block SVT, 4 wide-block Gram tiles, 5 Gram partial-sum reduce,
  * 6 wide-block eigen-solve, 7 wide-block rebuild, 8 set-up and output
  * kernels (finiteness check, state init, X/U output), 9 wide-block
- * Householder fallback (blocks the certified paths did not settle). */
-#define MSLLR_KERNEL_KINDS 10
+ * Householder fallback (blocks the certified paths did not settle),
+ * 10 subspace iteration of blocks wider than 256 (G V, orthonormalisation,
+ * Rayleigh-Ritz), 11 their tiled Cholesky certificate. */
+#define MSLLR_KERNEL_KINDS 12
 
 /* Widest block (min(m_i, n_i)) the block-SVT kernels accept; the full-matrix
- * scale obeys the same limit on min(M, N). */
-#define MSLLR_MAX_BLOCK_WIDTH 256
+ * scale obeys the same limit on min(M, N).  Blocks up to 256 wide are solved
+ * by one CTA each; wider ones (e.g. the full-matrix scale of a 1024 x 1024
+ * matrix) by certified subspace iteration spread over many CTAs, where a
+ * block's thresholded rank is at most 16. */
+#define MSLLR_MAX_BLOCK_WIDTH 4096
 
 typedef struct msllr_ctx msllr_ctx;
 
@@ -108,6 +113,10 @@ typedef struct msllr_stats {
    * params->profile was set (else 0). */
   long long kernel_launches[MSLLR_KERNEL_KINDS][MSLLR_MAX_SCALES];
   double kernel_ms[MSLLR_KERNEL_KINDS][MSLLR_MAX_SCALES];
+  /* blocks wider than 256 whose certificate (no singular value above tau
+   * outside the kept Ritz pairs) failed at the last iteration; their
+   * thresholded rank is taken from the Ritz pairs.  0 in normal runs. */
+  long long blocks_uncertified[MSLLR_MAX_SCALES];
 } msllr_stats;
 
 /* Fill *p with the defaults.  Returns MSLLR_EINVAL if p is NULL. */

@@ -25,10 +25,10 @@ MSLLR_ETIMEOUT = 4
 MSLLR_ENONFINITE = 5
 MSLLR_EBUSY = 6
 MAX_SCALES = 8
-MAX_BLOCK_WIDTH = 256
+MAX_BLOCK_WIDTH = 4096
 NOISE_SCALE = (0, 0)  # block size of the noise scale (Sec. 2.1)
 KERNEL_KINDS = ("advance", "consensus", "soft1x1", "fused_small", "gram", "gram_reduce",
-                "eig_big", "rebuild", "misc", "eig_fallback")
+                "eig_big", "rebuild", "misc", "eig_fallback", "subspace", "certificate")
 
 STATUS_NAMES = {0: "MSLLR_OK", 1: "MSLLR_EINVAL", 2: "MSLLR_ENOMEM", 3: "MSLLR_ECUDA",
                 4: "MSLLR_ETIMEOUT", 5: "MSLLR_ENONFINITE", 6: "MSLLR_EBUSY"}
@@ -79,6 +79,7 @@ class Stats(ctypes.Structure):
         ("launches", ctypes.c_longlong),
         ("kernel_launches", (ctypes.c_longlong * MAX_SCALES) * len(KERNEL_KINDS)),
         ("kernel_ms", (ctypes.c_double * MAX_SCALES) * len(KERNEL_KINDS)),
+        ("blocks_uncertified", ctypes.c_longlong * MAX_SCALES),
     ]
 
     def to_dict(self):
@@ -99,6 +100,7 @@ class Stats(ctypes.Structure):
             "kernel_launches": {k: list(self.kernel_launches[i][:max(L, 1)])
                                 for i, k in enumerate(KERNEL_KINDS)},
             "kernel_ms": {k: list(self.kernel_ms[i][:max(L, 1)]) for i, k in enumerate(KERNEL_KINDS)},
+            "blocks_uncertified": list(self.blocks_uncertified[:L]),
         }
 
 

@@ -43,6 +43,14 @@ struct BigWorkspace {
   float* warm;   // nblocks * 8 * nn: previous Ritz vectors (warm start)
   int* kwarm;    // nblocks: how many of them (0 = none)
   size_t ystride;
+  // blocks wider than 256 (k_block_huge.cu): G is a full square there
+  float* H;      // nblocks * nn * nn: certificate matrix, factored in place
+  float* tstat;  // nblocks * ntiles * 2: per-tile diagonal sums, sums of squares
+  float* V;      // nblocks * nn * 32: subspace basis (kept across calls)
+  float* Wv;     // nblocks * nn * 32: G V
+  float* U;      // nblocks * nn * 16: Ritz vectors
+  float* GU;     // nblocks * nn * 16: G U, then What
+  void* hb;      // nblocks per-block states
 };
 
 // Kernel kinds, for launch counting and per-kernel CUDA-event timing.
@@ -57,6 +65,8 @@ enum KernelKind {
   KK_REBUILD,
   KK_MISC,
   KK_EIG_FALLBACK,
+  KK_SUBSPACE,  // wide blocks over 256: G V, orthonormalisation, Rayleigh-Ritz
+  KK_CERT,      // wide blocks over 256: the tiled Cholesky certificate
   KK_COUNT
 };
 
@@ -94,11 +104,18 @@ struct Prof {
 };
 
 // Path selection.
-enum class ScalePath { Elementwise, Small, Big, Noise };  // Noise: block (0, 0), Sec. 2.1
+// Noise: block (0, 0), Sec. 2.1; Huge: min(m, n) > 256
+enum class ScalePath { Elementwise, Small, Big, Noise, Huge };
 ScalePath choose_path(int m, int n);
 // Bytes of BigWorkspace a scale needs (0 for the other paths).
 size_t big_workspace_bytes(int M, int N, int m, int n);
 BigWorkspace carve_big_workspace(void* base, int M, int N, int m, int n);
+// The wide path above 256 (k_block_huge.cu).
+size_t huge_workspace_bytes(int M, int N, int m, int n);
+BigWorkspace carve_huge_workspace(void* base, int M, int N, int m, int n);
+cudaError_t reset_huge_basis(const BigWorkspace& w, int M, int N, int m, int n, cudaStream_t st);
+cudaError_t launch_huge(const ScaleLaunch& s, const BigWorkspace& ws, cudaStream_t st, Prof* prof,
+                        cudaEvent_t after_gram);
 // Zero the warm-start counts of a scale's workspace (start of a decomposition).
 cudaError_t reset_warm_start(const BigWorkspace& w, int M, int N, int m, int n, cudaStream_t st);
 

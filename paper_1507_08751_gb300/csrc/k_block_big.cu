@@ -588,6 +588,7 @@ static size_t y_stride(int nn) {
 }
 
 size_t big_workspace_bytes(int M, int N, int m, int n) {
+  if (choose_path(m, n) == ScalePath::Huge) return huge_workspace_bytes(M, N, m, n);
   if (choose_path(m, n) != ScalePath::Big) return 0;
   const BigDims d = big_dims(M, N, m, n);
   size_t bytes = 0;
@@ -607,6 +608,7 @@ static char* align256(char* p) {
 
 BigWorkspace carve_big_workspace(void* base, int M, int N, int m, int n) {
   BigWorkspace w{};
+  if (choose_path(m, n) == ScalePath::Huge) return carve_huge_workspace(base, M, N, m, n);
   if (!base || choose_path(m, n) != ScalePath::Big) return w;
   const BigDims d = big_dims(M, N, m, n);
   char* p = align256((char*)base);
@@ -628,6 +630,7 @@ BigWorkspace carve_big_workspace(void* base, int M, int N, int m, int n) {
 }
 
 cudaError_t reset_warm_start(const BigWorkspace& w, int M, int N, int m, int n, cudaStream_t st) {
+  if (choose_path(m, n) == ScalePath::Huge) return reset_huge_basis(w, M, N, m, n, st);
   if (!w.kwarm) return cudaSuccess;
   const BigDims d = big_dims(M, N, m, n);
   return cudaMemsetAsync(w.kwarm, 0, sizeof(int) * (size_t)d.nblocks, st);

@@ -354,6 +354,7 @@ ScalePath choose_path(int m, int n) {
   const int nn = m < n ? m : n;
   const long long area = (long long)m * n;
   if (nn <= 64 && area <= 8192) return ScalePath::Small;
+  if (nn > 256) return ScalePath::Huge;
   return ScalePath::Big;
 }
 
@@ -370,6 +371,8 @@ cudaError_t launch_scale(const ScaleLaunch& s, const BigWorkspace& ws, cudaStrea
       if (nn <= 32) return launch_small_t<64, 32>(s, st, prof);
       return launch_small_t<128, 64>(s, st, prof);
     }
+    case ScalePath::Huge:
+      return launch_huge(s, ws, st, prof, after_gram);
     case ScalePath::Big:
     default:
       return launch_big(s, ws, st, prof, after_gram);

@@ -196,7 +196,8 @@ int check_blocks(msllr_ctx* ctx, int M, int N, int m, int n) {
                 "block " + std::to_string(m) + "x" + std::to_string(n) +
                     " is wider than MSLLR_MAX_BLOCK_WIDTH");
   const long long nblocks = (long long)(M / m) * (N / n);
-  if (choose_path(m, n) == ScalePath::Big && nblocks > 65535)
+  const ScalePath path = choose_path(m, n);
+  if ((path == ScalePath::Big || path == ScalePath::Huge) && nblocks > 65535)
     return fail(ctx, MSLLR_EINVAL, "too many wide blocks in one scale (max 65535)");
   return MSLLR_OK;
 }
@@ -262,7 +263,7 @@ int msllr_create(msllr_ctx** out, int device, size_t hbm_budget_bytes, void* cud
   if (cudaMalloc(&ctx->d_small, 64 * sizeof(int)) != cudaSuccess ||
       cudaMalloc(&ctx->d_acc, (MSLLR_MAX_SCALES + 8) * sizeof(double)) != cudaSuccess ||
       cudaMalloc(&ctx->d_noise, MSLLR_MAX_SCALES * sizeof(double)) != cudaSuccess ||
-      cudaMalloc(&ctx->d_cnt, 4 * MSLLR_MAX_SCALES * sizeof(unsigned long long)) != cudaSuccess)
+      cudaMalloc(&ctx->d_cnt, 8 * MSLLR_MAX_SCALES * sizeof(unsigned long long)) != cudaSuccess)
     return bail(fail(ctx, MSLLR_ENOMEM, "cudaMalloc of context scalars"));
   *out = ctx;
   return MSLLR_OK;
@@ -375,6 +376,7 @@ int msllr_blocksvt(msllr_ctx* ctx, const float* A, float* Z, int M, int N, int l
   s.rank_out = block_rank_out;
   s.norm_acc = ctx->d_noise;
   BigWorkspace w = carve_big_workspace(ctx->ws, M, N, bm, bn);
+  CK(reset_warm_start(w, M, N, bm, bn, ctx->stream));
   CK(launch_scale(s, w, ctx->stream, nullptr));
   CK(cudaStreamSynchronize(ctx->stream));
   return MSLLR_OK;
@@ -435,7 +437,8 @@ int enqueue_iteration(msllr_ctx* ctx, const Layout& lay, int M, int N, int L, co
   bool gated[MSLLR_MAX_SCALES] = {};
   for (int pass = 0; pass < 2; ++pass) {
     for (int i = 0; i < L; ++i) {
-      const bool wide = choose_path(bm[i], bn[i]) == ScalePath::Big;
+      const ScalePath path = choose_path(bm[i], bn[i]);
+      const bool wide = path == ScalePath::Big || path == ScalePath::Huge;
       if ((pass == 0) != wide) continue;
       cudaStream_t st = (i == 0 || !fork) ? ctx->stream : (wide ? ctx->side_hi[i] : ctx->side[i]);
       if (i > 0 && fork) CK(cudaStreamWaitEvent(st, ctx->ev_fork, 0));
@@ -458,7 +461,7 @@ int enqueue_iteration(msllr_ctx* ctx, const Layout& lay, int M, int N, int L, co
       s.warm_start = 1;
       s.rank_out = nullptr;
       s.nuc_acc = stats ? ctx->d_acc + i : nullptr;
-      s.cnt = stats ? ctx->d_cnt + 4 * i : nullptr;
+      s.cnt = stats ? ctx->d_cnt + 8 * i : nullptr;
       s.norm_acc = ctx->d_noise + i;
       prof->scale = i;
       const bool gate = fork && wide && i > 0;
@@ -554,7 +557,7 @@ int decompose_device(msllr_ctx* ctx, const float* Y, int M, int N, int ld, int L
   CK(launch_init_state(p.Z_init, p.U_init, lay.Z, lay.W, L, lay.MN, st, &prof));
   for (int i = 0; i < L; ++i) CK(reset_warm_start(lay.big[i], M, N, bm[i], bn[i], st));
   CK(cudaMemsetAsync(ctx->d_acc, 0, (MSLLR_MAX_SCALES + 8) * sizeof(double), st));
-  CK(cudaMemsetAsync(ctx->d_cnt, 0, 4 * MSLLR_MAX_SCALES * sizeof(unsigned long long), st));
+  CK(cudaMemsetAsync(ctx->d_cnt, 0, 8 * MSLLR_MAX_SCALES * sizeof(unsigned long long), st));
 
   // iterations 0 .. iters-2 (graph replay), the last one with statistics
   const int plain_iters = iters > 0 ? iters - 1 : 0;
@@ -613,7 +616,7 @@ int decompose_device(msllr_ctx* ctx, const float* Y, int M, int N, int ld, int L
   if (Z_out)
     CK(cudaMemcpyAsync(Z_out, lay.Z, sizeof(float) * L * lay.MN, cudaMemcpyDeviceToDevice, st));
   double acc[MSLLR_MAX_SCALES + 8];
-  unsigned long long cnt[4 * MSLLR_MAX_SCALES];
+  unsigned long long cnt[8 * MSLLR_MAX_SCALES];
   CK(cudaMemcpyAsync(acc, ctx->d_acc, sizeof acc, cudaMemcpyDeviceToHost, st));
   CK(cudaMemcpyAsync(cnt, ctx->d_cnt, sizeof cnt, cudaMemcpyDeviceToHost, st));
   CK(cudaStreamSynchronize(st));
@@ -626,10 +629,11 @@ int decompose_device(msllr_ctx* ctx, const float* Y, int M, int N, int ld, int L
       stats->scale_nuclear[i] = acc[i];
       obj += lam[i] * acc[i];
       stats->blocks[i] = (bm[i] == 0 && bn[i] == 0) ? 1 : (long long)(M / bm[i]) * (N / bn[i]);
-      stats->blocks_skipped[i] = (long long)cnt[4 * i];
-      stats->blocks_zero[i] = (long long)cnt[4 * i + 1];
-      stats->blocks_lanczos[i] = (long long)cnt[4 * i + 2];
-      stats->blocks_householder[i] = (long long)cnt[4 * i + 3];
+      stats->blocks_skipped[i] = (long long)cnt[8 * i];
+      stats->blocks_zero[i] = (long long)cnt[8 * i + 1];
+      stats->blocks_lanczos[i] = (long long)cnt[8 * i + 2];
+      stats->blocks_householder[i] = (long long)cnt[8 * i + 3];
+      stats->blocks_uncertified[i] = (long long)cnt[8 * i + 4];
       stats->lambda[i] = lam[i];
     }
     stats->objective = obj;

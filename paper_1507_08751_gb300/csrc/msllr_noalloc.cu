@@ -46,8 +46,8 @@ extern "C" int msllr_blocksvt_noalloc(const float* A, float* Z, int M, int N, in
     return err(MSLLR_EINVAL, "msllr_blocksvt_noalloc: tau must be finite and >= 0");
   if (bm <= 0 || bn <= 0 || bm > M || bn > N || M % bm || N % bn)
     return err(MSLLR_EINVAL, "msllr_blocksvt_noalloc: block does not divide the matrix");
-  if ((bm < bn ? bm : bn) > MSLLR_MAX_BLOCK_WIDTH)
-    return err(MSLLR_EINVAL, "msllr_blocksvt_noalloc: block wider than MSLLR_MAX_BLOCK_WIDTH");
+  if ((bm < bn ? bm : bn) > 256)
+    return err(MSLLR_EINVAL, "msllr_blocksvt_noalloc: blocks wider than 256 need msllr_blocksvt");
   if (choose_path(bm, bn) == ScalePath::Big && (long long)(M / bm) * (N / bn) > 65535)
     return err(MSLLR_EINVAL, "msllr_blocksvt_noalloc: too many wide blocks (max 65535)");
   const char* a0 = (const char*)A;
