@@ -31,6 +31,9 @@ WORKLOAD = "video-16384x256-L5-s1_16_64_256_full"
 M_DEF, N_DEF, ITERS_DEF = 16384, 256, 300
 SEED = 1507087510
 METRIC = "BlockSVT-ADMM iter/s (video 16384x256, L=5, 300 iters/job)"
+# Batching/serving-shaped jobs (dyadic scales 1, 4, 16, 64, 256 and the full
+# matrix): their full-matrix scale goes through the wide-block path.
+JOBS = {"job1024": (1024, 1024, 200), "job2048": (2048, 2048, 200), "job4096x512": (4096, 512, 200)}
 
 
 def parse():
@@ -42,6 +45,9 @@ def parse():
     ap.add_argument("--iters", type=int, default=ITERS_DEF)
     ap.add_argument("--M", type=int, default=M_DEF)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--workload", default="video", choices=["video"] + sorted(JOBS),
+                    help="video (default, the headline line) or a batching/serving-shaped "
+                         "job whose full-matrix scale is wider than 256")
     return ap.parse_args()
 
 
@@ -122,6 +128,7 @@ def peaks():
 # DRAM bytes (read + write) per launch from one ncu capture of the kernel as
 # it stands (profiles/eig_big_video16384x256.md); kernels not listed: null.
 NCU_TRAFFIC_BYTES = {"eig_big[scale 3: 256x256]": 8781056}
+ITERS_OF = {}
 
 
 def kernel_roofline(stats, scales, M, N, pk):
@@ -148,6 +155,15 @@ def kernel_roofline(stats, scales, M, N, pk):
         roof = {"bound": "alu", "achieved": round(ach, 3), "peak": round(pk["fp32_tflops"], 1),
                 "unit": "TFLOP/s", "frac": round(ach / pk["fp32_tflops"], 4), "traffic": None,
                 "peak_src": "152 SM x 128 FP32 lanes x 2 x max SM clock"}
+    elif kind == "certificate":
+        # tiled Cholesky of an nn x nn matrix per block: nn^3 / 3 flop per
+        # iteration, over all of that iteration's panel and update launches
+        per_iter_launches = n / max(1, ITERS_OF.get("cur", 1))
+        flops = nblocks * nn ** 3 / 3 / per_iter_launches
+        ach = flops / avg_s / 1e12
+        roof = {"bound": "alu", "achieved": round(ach, 4), "peak": round(pk["fp32_tflops"], 1),
+                "unit": "TFLOP/s", "frac": round(ach / pk["fp32_tflops"], 5), "traffic": None,
+                "peak_src": "152 SM x 128 FP32 lanes x 2 x max SM clock"}
     elif kind == "eig_big":
         flops = nblocks * (4 * nn ** 3 // 3)
         ach = flops / avg_s / 1e12
@@ -157,7 +173,7 @@ def kernel_roofline(stats, scales, M, N, pk):
     else:
         per = {"consensus": (L + 2) * 4 * MN, "soft1x1": 16 * MN, "fused_small": 16 * MN,
                "rebuild": 16 * MN, "gram_reduce": 0, "advance": 8, "misc": 8 * MN,
-               "eig_fallback": 0}[kind]
+               "eig_fallback": 0, "subspace": 0, "certificate": 0}[kind]
         ach = per / avg_s / 1e9
         roof = {"bound": "hbm", "achieved": round(ach, 1), "peak": pk["hbm_gbs"], "unit": "GB/s",
                 "frac": round(ach / pk["hbm_gbs"], 4), "traffic": None,
@@ -258,7 +274,17 @@ def ours(a):
     dev = torch.device("cuda", local)
 
     # per-rank independent job (replicas: the method has no cross-GPU step)
-    Y32, comps, scales = synth.video(seed=SEED + 1 + rank, M=a.M, N=256)
+    if a.workload == "video":
+        Y32, comps, scales = synth.video(seed=SEED + 1 + rank, M=a.M, N=256)
+        metric, workload = METRIC, WORKLOAD
+    else:
+        Mj, Nj, it_j = JOBS[a.workload]
+        if a.iters == ITERS_DEF:
+            a.iters = it_j
+        Y32, scales = synth.job(SEED + 1 + rank, Mj, Nj, 6)
+        metric = f"BlockSVT-ADMM iter/s ({a.workload}: {Mj}x{Nj}, L={len(scales)}, {a.iters} iters/job)"
+        workload = f"{a.workload}-L{len(scales)}-s" + "_".join(str(m) for m, _ in scales[:-1]) + "_full"
+    ITERS_OF["cur"] = a.iters
     M, N = Y32.shape
     L = len(scales)
     stream = torch.cuda.Stream(device=dev)
@@ -325,7 +351,7 @@ def ours(a):
            "steps": e_steps}
 
     cpu = None
-    if rank == 0 and world == 1 and not a.no_cpu_baseline:
+    if rank == 0 and world == 1 and not a.no_cpu_baseline and a.workload == "video":
         try:
             cpu = cpu_baseline(a.M)
         except Exception as ex:  # noqa: BLE001
@@ -333,14 +359,15 @@ def ours(a):
 
     if rank == 0:
         line = {
-            "metric": METRIC, "value": round(value, 2), "unit": "iter/s", "n_gpus": world,
+            "metric": metric, "value": round(value, 2), "unit": "iter/s", "n_gpus": world,
             "steps": a.steps, "warmup": a.warmup,
             "ms_per_step": round(1e3 * t_s / a.steps, 3), "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "M": M, "N": N, "L": L,
+            "config": {"workload": workload, "M": M, "N": N, "L": L,
                        "scales": [f"{m}x{n}" for m, n in scales], "iters_per_job": a.iters,
                        "parallelism": f"replicas{world}", "step": "one decomposition job",
-                       "l2": "ADMM state 11 x 16.8 MB = 185 MB > 126 MB L2"},
+                       "l2": f"ADMM state {2 * L + 1} x {4 * M * N / 1e6:.1f} MB"
+                             f" = {(2 * L + 1) * 4 * M * N / 1e6:.0f} MB vs 126 MB L2"},
             "blocks_per_s": round(value * nblocks, 1),
             "e2e": e2e,
             "gpu_launches": int(launches_per_step * a.steps),
@@ -352,6 +379,7 @@ def ours(a):
             "zero_rank_blocks_last_iter": stats["blocks_zero"],
             "lanczos_blocks_last_iter": stats["blocks_lanczos"],
             "householder_blocks_last_iter": stats["blocks_householder"],
+            "uncertified_blocks_last_iter": stats["blocks_uncertified"],
             "clocks": ck,
             "cpu_baseline": cpu,
         }

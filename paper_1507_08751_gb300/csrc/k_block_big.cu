@@ -405,9 +405,8 @@ __device__ __forceinline__ void eig_fallback_block(const ScaleLaunch& a, const f
   }
 }
 
-// A few CTAs stride over the blocks (the fallback is rare, and a launch that
-// finds nothing to do then holds few SMs); one CTA per block when the
-// certified paths are off.
+// At most 32 CTAs stride over the blocks (a launch that finds nothing to do
+// then holds few SMs); one CTA per block when the certified paths are off.
 __global__ void __launch_bounds__(kEigThreads)
 eig_fallback_kernel(ScaleLaunch a, const float* __restrict__ Gall, BigWorkspace ws, int nblocks) {
   for (int b = blockIdx.x; b < nblocks; b += gridDim.x) {
@@ -675,7 +674,10 @@ cudaError_t launch_big(const ScaleLaunch& s, const BigWorkspace& ws, cudaStream_
   eig_big_kernel<<<d.nblocks, kEigThreads, eig_smem_bytes(d.nn), st>>>(s, ws.G, ws);
   PROF_AFTER()
   PROF_BEFORE(KK_EIG_FALLBACK)
-  const int fb_grid = s.skip_bound ? (d.nblocks < 4 ? d.nblocks : 4) : d.nblocks;
+  // up to 32 CTAs stride over the blocks: enough for scales where many
+  // blocks need the Householder path (blocks of rank above 8, or with an
+  // eigenvalue just below tau^2), few idle SMs where almost none do
+  const int fb_grid = s.skip_bound ? (d.nblocks < 32 ? d.nblocks : 32) : d.nblocks;
   eig_fallback_kernel<<<fb_grid, kEigThreads, fallback_smem_bytes(d.nn), st>>>(s, ws.G, ws,
                                                                                d.nblocks);
   PROF_AFTER()

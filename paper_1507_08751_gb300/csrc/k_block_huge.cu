@@ -40,7 +40,7 @@ constexpr int kHP = 32;          // subspace width
 constexpr int kHK = 16;          // most Ritz pairs kept per block
 constexpr int kHThreads = 256;   // tile kernels
 constexpr int kHBlockThreads = 512;  // per-block kernels
-constexpr int kHGvRows = 32;     // rows of W per CTA in W = G V
+constexpr int kHGvRows = 8;      // rows of W per CTA in W = G V
 
 // per-block state of the wide path
 struct HugeBlock {
@@ -282,47 +282,45 @@ __device__ __forceinline__ bool huge_active(const HugeBlock& h) {
 }
 
 // ---------------------------------------------------------------------------
-// 2. W = G V for kHGvRows rows of one block (V, W: nn x kHP row-major).
+// 2. W = G V for kHGvRows rows of one block (V, W: nn x kHP row-major): one
+// output per thread, the K loop in chunks of 64 through shared memory.
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(kHThreads)
 huge_gv_kernel(const float* __restrict__ G, const float* __restrict__ V, float* __restrict__ W,
                int nn, const HugeBlock* __restrict__ hb) {
-  __shared__ float Gs[kHGvRows][33];
-  __shared__ __align__(16) float Vs[32][kHP];
+  constexpr int KC = 64;
+  static_assert(kHGvRows * kHP == kHThreads, "one output per thread");
+  __shared__ float Gs[kHGvRows][KC + 1];
+  __shared__ float Vs[KC][kHP];
   const int b = blockIdx.y;
   if (!huge_active(hb[b])) return;
   const int r0 = blockIdx.x * kHGvRows, tid = threadIdx.x;
-  const int row = tid >> 3, cq = (tid & 7) * 4;
+  const int row = tid / kHP, col = tid % kHP;
   const float* Gb = G + (size_t)b * nn * nn;
   const float* Vb = V + (size_t)b * nn * kHP;
-  float acc[4] = {0.f, 0.f, 0.f, 0.f};
-  for (int l0 = 0; l0 < nn; l0 += 32) {
+  float acc = 0.f;
+  for (int l0 = 0; l0 < nn; l0 += KC) {
 #pragma unroll
-    for (int j = 0; j < 4; ++j) {
+    for (int j = 0; j < (kHGvRows * KC) / kHThreads; ++j) {
       const int e = tid + j * kHThreads;
-      const int rr = e >> 5, cc = e & 31;
+      const int rr = e / KC, cc = e % KC;
       const int gr = r0 + rr, gl = l0 + cc;
       Gs[rr][cc] = (gr < nn && gl < nn) ? Gb[(size_t)gr * nn + gl] : 0.f;
+    }
+#pragma unroll
+    for (int j = 0; j < (KC * kHP) / kHThreads; ++j) {
+      const int e = tid + j * kHThreads;
+      const int rr = e / kHP, cc = e % kHP;
       const int vl = l0 + rr;
       Vs[rr][cc] = (vl < nn) ? Vb[(size_t)vl * kHP + cc] : 0.f;
     }
     __syncthreads();
-#pragma unroll 8
-    for (int kk = 0; kk < 32; ++kk) {
-      const float gv = Gs[row][kk];
-      const float4 v4 = *reinterpret_cast<const float4*>(&Vs[kk][cq]);
-      acc[0] = fmaf(gv, v4.x, acc[0]);
-      acc[1] = fmaf(gv, v4.y, acc[1]);
-      acc[2] = fmaf(gv, v4.z, acc[2]);
-      acc[3] = fmaf(gv, v4.w, acc[3]);
-    }
+#pragma unroll 16
+    for (int kk = 0; kk < KC; ++kk) acc = fmaf(Gs[row][kk], Vs[kk][col], acc);
     __syncthreads();
   }
   const int r = r0 + row;
-  if (r < nn) {
-    float* dst = W + (size_t)b * nn * kHP + (size_t)r * kHP + cq;
-    *reinterpret_cast<float4*>(dst) = make_float4(acc[0], acc[1], acc[2], acc[3]);
-  }
+  if (r < nn) W[(size_t)b * nn * kHP + (size_t)r * kHP + col] = acc;
 }
 
 // S = X^T Y over the nn rows of two nn x kHP row-major matrices (Y = X
@@ -616,13 +614,13 @@ huge_rr_kernel(const float* __restrict__ V, const float* __restrict__ W, float* 
       k += th > thr;
     }
     // converged: every kept pair's residual is small against tau^2, or at
-    // the rounding level of its own eigenvalue
+    // the rounding level of G V (set by the largest eigenvalue)
     int conv = 1;
-    float trb = 0.f;
+    float trb = 0.f, th0 = 0.f;
+    for (int q = 0; q < ku; ++q) th0 = fmaxf(th0, Bm[q * kHK + q]);
     for (int q = 0; q < ku; ++q) {
-      const float th = Bm[q * kHK + q];
-      trb += th;
-      if (rq[q] > fmaxf(3e-4f * thr, 2e-6f * th)) conv = 0;
+      trb += Bm[q * kHK + q];
+      if (rq[q] > fmaxf(3e-4f * thr, 1e-5f * th0)) conv = 0;
     }
     // Certificate shift: lambda_max(P G P) < c proves, by Cauchy interlacing,
     // that G has at most ku eigenvalues above c (and the ku Ritz values above
