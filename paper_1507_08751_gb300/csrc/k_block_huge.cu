@@ -53,6 +53,7 @@ struct HugeBlock {
   int k;         // pairs above tau
   int conv;      // Rayleigh-Ritz residual test passed
   int chol_fail; // the tiled Cholesky met a non-positive pivot
+  int orth_fail; // a CholQR factorisation broke down (basis restarted)
 };
 enum : int { kHsSkip = 1, kHsIter = 2, kHsCert = 3, kHsNoCert = 4 };
 
@@ -265,6 +266,7 @@ huge_prep_kernel(const float* __restrict__ tstat, int ntiles, HugeBlock* __restr
     h.k = 0;
     h.conv = 0;
     h.chol_fail = 0;
+    h.orth_fail = 0;
     h.c = 0.f;
   }
 }
@@ -278,7 +280,7 @@ __global__ void huge_init_basis_kernel(float* __restrict__ V, size_t total) {
 }
 
 __device__ __forceinline__ bool huge_active(const HugeBlock& h) {
-  return h.status == kHsIter && !h.conv;
+  return h.status == kHsIter && !h.conv && !h.orth_fail;
 }
 
 // ---------------------------------------------------------------------------
@@ -405,68 +407,116 @@ __device__ bool huge_chol32(float* Sm, float shift, float* Rm, float* Ri, int* f
   return ok;
 }
 
-// Out = (X + mu X2) R^{-1}, row by row (warp per row, lane per column); Out
-// may alias X (each warp reads its whole row before writing it).
-__device__ void huge_apply_rinv(const float* X, const float* X2, float mu, const float* Ri,
-                                float* Out, int nn) {
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  constexpr int NW = kHBlockThreads / 32;
-  for (int r = warp; r < nn; r += NW) {
-    float x = X[(size_t)r * kHP + lane];
-    if (X2) x = fmaf(mu, X2[(size_t)r * kHP + lane], x);
-    float o = 0.f;
-#pragma unroll
-    for (int a = 0; a < kHP; ++a) {
-      const float xa = __shfl_sync(0xffffffffu, x, a);
-      if (a <= lane) o = fmaf(xa, Ri[a * 33 + lane], o);
-    }
-    __syncwarp();
-    Out[(size_t)r * kHP + lane] = o;
-  }
-  __syncthreads();
-}
-
-
-// Orthonormal basis of span(W + mu V) into V: shifted CholQR, then CholQR
-// twice.  mu = 1e-4 ||W||_F (a shift of G by mu I) keeps W + mu V of full
-// rank when G is (numerically) of rank below kHP.
-__global__ void __launch_bounds__(kHBlockThreads)
-huge_orth_kernel(float* __restrict__ V, float* __restrict__ W, int nn, HugeBlock* __restrict__ hb) {
-  __shared__ float Xs[64 * 33];
+// Orthonormal basis of span(W + mu V) into V by shifted CholQR and two plain
+// CholQR passes, spread over the rows: four sweeps, each a launch over
+// (row chunk of kHOrthRows, block).  Sweep p (p >= 1) first sums the chunk
+// partials of S from sweep p - 1 in chunk order and factors S (+ shift for
+// p = 1) = R^T R in every CTA (all CTAs get the same R^{-1}); then each CTA
+// maps its rows: sweep 0 X = W + mu V, sweep 1 X = (W + mu V) R^{-1},
+// sweeps 2, 3 X = W R^{-1} (sweeps 1, 2 write W, sweep 3 writes V), and
+// sweeps 0-2 write the partial S = X^T X of their rows.  mu = 1e-4 ||G||_F
+// (a shift of G by mu I) keeps W + mu V of full rank when G is (numerically)
+// of rank below kHP.  A failed factorisation marks the block (orth_fail) and
+// restarts its basis.
+constexpr int kHOrthRows = 32;
+__global__ void __launch_bounds__(kHThreads)
+huge_orth_sweep_kernel(float* __restrict__ V, float* __restrict__ W, const float* __restrict__ pin,
+                       float* __restrict__ pout, int nn, int pass, HugeBlock* __restrict__ hb) {
+  constexpr int NT = kHThreads, PER = kHOrthRows * kHP / NT;
+  __shared__ float Xin[kHOrthRows * 33];
   __shared__ float Sm[kHP * 33];
   __shared__ float Rm[kHP * 33];
   __shared__ float Ri[kHP * 33];
-  __shared__ float red[32];
   __shared__ int flag;
-  const int b = blockIdx.x, tid = threadIdx.x;
-  if (!huge_active(hb[b])) return;
+  const int chunk = blockIdx.x, b = blockIdx.y, tid = threadIdx.x;
+  const int nchunks = gridDim.x;
+  {
+    const HugeBlock& h = hb[b];
+    if (!huge_active(h)) return;
+  }
   float* Vb = V + (size_t)b * nn * kHP;
   float* Wb = W + (size_t)b * nn * kHP;
-  float part = 0.f;
-  for (size_t e = tid; e < (size_t)nn * kHP; e += kHBlockThreads) part = fmaf(Wb[e], Wb[e], part);
-  const float mu = 1e-4f * sqrtf(block_sum<kHBlockThreads>(part, red));
+  const int r0 = chunk * kHOrthRows;
+  const float mu = 1e-4f * hb[b].gF;
+  // this CTA's rows (loads in flight during the factorisation)
+  float x[PER];
+#pragma unroll
+  for (int j = 0; j < PER; ++j) {
+    const int e = tid + j * NT;
+    const int r = r0 + (e >> 5), cc = e & 31;
+    float v = 0.f;
+    if (r < nn) {
+      v = Wb[(size_t)r * kHP + cc];
+      if (pass <= 1) v = fmaf(mu, Vb[(size_t)r * kHP + cc], v);
+    }
+    x[j] = v;
+  }
   bool ok = true;
-  for (int pass = 0; pass < 3 && ok; ++pass) {
-    huge_xty(Wb, pass == 0 ? Vb : nullptr, pass == 0 ? mu : 0.f, nullptr, nn, Xs, Xs, Sm);
+  if (pass >= 1) {
+    const float* pb = pin + (size_t)b * nchunks * (kHP * kHP);
+    for (int e = tid; e < kHP * kHP; e += NT) {
+      float t = 0.f;
+      for (int c = 0; c < nchunks; ++c) t += pb[(size_t)c * (kHP * kHP) + e];
+      Sm[(e >> 5) * 33 + (e & 31)] = t;
+    }
+    __syncthreads();
     float shift = 0.f;
-    if (pass == 0) {
+    if (pass == 1) {
       float tr = 0.f;
       for (int i = 0; i < kHP; ++i) tr += Sm[i * 33 + i];
       shift = 11.f * (float)((double)nn * kHP + kHP * (kHP + 1)) * FLT_EPSILON * tr;
     }
     ok = huge_chol32(Sm, shift, Rm, Ri, &flag);
-    if (ok) huge_apply_rinv(Wb, pass == 0 ? Vb : nullptr, pass == 0 ? mu : 0.f, Ri,
-                            pass == 2 ? Vb : Wb, nn);
   }
   if (!ok) {
-    // breakdown: restart the basis on the next call; this call's block stays
-    // without pairs and is counted as uncertified
-    for (size_t e = tid; e < (size_t)nn * kHP; e += kHBlockThreads)
-      Vb[e] = huge_hash((uint32_t)(e / kHP) + 977u * b, (uint32_t)(e % kHP) + 0xB0Bu);
-    if (tid == 0) {
-      hb[b].status = kHsNoCert;
-      hb[b].ku = 0;
-      hb[b].k = 0;
+    for (int j = 0; j < PER; ++j) {
+      const int e = tid + j * NT;
+      const int r = r0 + (e >> 5), cc = e & 31;
+      if (r < nn) Vb[(size_t)r * kHP + cc] = huge_hash((uint32_t)r + 977u * b, (uint32_t)cc + 0xB0Bu);
+    }
+    if (chunk == 0 && tid == 0) hb[b].orth_fail = 1;
+    return;
+  }
+#pragma unroll
+  for (int j = 0; j < PER; ++j) {
+    const int e = tid + j * NT;
+    Xin[(e >> 5) * 33 + (e & 31)] = x[j];
+  }
+  __syncthreads();
+  if (pass >= 1) {
+    float o[PER];
+#pragma unroll
+    for (int j = 0; j < PER; ++j) {
+      const int e = tid + j * NT;
+      const int rr = e >> 5, cc = e & 31;
+      float t = 0.f;
+#pragma unroll
+      for (int a = 0; a < kHP; ++a)
+        if (a <= cc) t = fmaf(Xin[rr * 33 + a], Ri[a * 33 + cc], t);
+      o[j] = t;
+    }
+    __syncthreads();
+    float* dst = pass == 3 ? Vb : Wb;
+#pragma unroll
+    for (int j = 0; j < PER; ++j) {
+      const int e = tid + j * NT;
+      const int rr = e >> 5, cc = e & 31;
+      Xin[rr * 33 + cc] = o[j];
+      if (r0 + rr < nn) dst[(size_t)(r0 + rr) * kHP + cc] = o[j];
+    }
+    __syncthreads();
+  }
+  if (pass <= 2) {
+    // partial S of this chunk: thread t owns entries t, t + NT, ...
+    float* pb = pout + ((size_t)b * nchunks + chunk) * (kHP * kHP);
+#pragma unroll
+    for (int j = 0; j < (kHP * kHP) / NT; ++j) {
+      const int e = tid + j * NT;
+      const int a = e >> 5, c = e & 31;
+      float t = 0.f;
+#pragma unroll 8
+      for (int rr = 0; rr < kHOrthRows; ++rr) t = fmaf(Xin[rr * 33 + a], Xin[rr * 33 + c], t);
+      pb[e] = t;
     }
   }
 }
@@ -535,9 +585,15 @@ huge_rr_kernel(const float* __restrict__ V, const float* __restrict__ W, float* 
   float Bacc[kHK];
 #pragma unroll
   for (int p = 0; p < kHK; ++p) Bacc[p] = 0.f;
+  // the next row's loads are issued before the current row is used
+  float vn = warp < nn ? Vb[(size_t)warp * kHP + lane] : 0.f;
+  float wn = warp < nn ? Wb[(size_t)warp * kHP + lane] : 0.f;
   for (int r = warp; r < nn; r += NW) {
-    const float v = Vb[(size_t)r * kHP + lane];
-    const float wv = Wb[(size_t)r * kHP + lane];
+    const float v = vn, wv = wn;
+    if (r + NW < nn) {
+      vn = Vb[(size_t)(r + NW) * kHP + lane];
+      wn = Wb[(size_t)(r + NW) * kHP + lane];
+    }
     float u = 0.f, g = 0.f;
 #pragma unroll 8
     for (int a = 0; a < kHP; ++a) {
@@ -571,11 +627,16 @@ huge_rr_kernel(const float* __restrict__ V, const float* __restrict__ W, float* 
   __syncthreads();
   // residuals and What
   float racc = 0.f, wacc = 0.f;
+  float un = 0.f, gn = 0.f;
+  if (lane < ku && warp < nn) {
+    un = Ub[(size_t)warp * kHK + lane];
+    gn = Gb[(size_t)warp * kHK + lane];
+  }
   for (int r = warp; r < nn; r += NW) {
-    float u = 0.f, g = 0.f;
-    if (lane < ku) {
-      u = Ub[(size_t)r * kHK + lane];
-      g = Gb[(size_t)r * kHK + lane];
+    const float u = un, g = gn;
+    if (lane < ku && r + NW < nn) {
+      un = Ub[(size_t)(r + NW) * kHK + lane];
+      gn = Gb[(size_t)(r + NW) * kHK + lane];
     }
     float wh = g;
 #pragma unroll
@@ -614,13 +675,15 @@ huge_rr_kernel(const float* __restrict__ V, const float* __restrict__ W, float* 
       k += th > thr;
     }
     // converged: every kept pair's residual is small against tau^2, or at
-    // the rounding level of G V (set by the largest eigenvalue)
+    // the rounding level of G V (set by the largest eigenvalue).  Pairs just
+    // above tau converge slowly; they need this accuracy all the same, since
+    // the consensus step carries their error into every scale.
     int conv = 1;
     float trb = 0.f, th0 = 0.f;
     for (int q = 0; q < ku; ++q) th0 = fmaxf(th0, Bm[q * kHK + q]);
     for (int q = 0; q < ku; ++q) {
       trb += Bm[q * kHK + q];
-      if (rq[q] > fmaxf(3e-4f * thr, 1e-5f * th0)) conv = 0;
+      if (rq[q] > fmaxf(3e-4f * thr, 4e-6f * th0)) conv = 0;
     }
     // Certificate shift: lambda_max(P G P) < c proves, by Cauchy interlacing,
     // that G has at most ku eigenvalues above c (and the ku Ritz values above
@@ -1010,14 +1073,22 @@ cudaError_t launch_huge(const ScaleLaunch& s, const BigWorkspace& ws, cudaStream
   const bool warm = s.warm_start && (full || !s.shift);
   const int rounds[3] = {warm ? 2 : 6, 6, 12};
   const dim3 gv_grid((nn + kHGvRows - 1) / kHGvRows, B);
+  const int orth_chunks = (nn + kHOrthRows - 1) / kHOrthRows;
   for (int r = 0; r < 3; ++r) {
     for (int st_i = 0; st_i < rounds[r]; ++st_i) {
       PROF_BEFORE(KK_SUBSPACE)
       huge_gv_kernel<<<gv_grid, kHThreads, 0, st>>>(ws.G, ws.V, ws.Wv, nn, hb);
       PROF_AFTER()
-      PROF_BEFORE(KK_SUBSPACE)
-      huge_orth_kernel<<<B, kHBlockThreads, 0, st>>>(ws.V, ws.Wv, nn, hb);
-      PROF_AFTER()
+      for (int pass = 0; pass < 4; ++pass) {
+        // S partials alternate between the two halves of the Gram partial
+        // buffer (free once G is formed)
+        float* pa = ws.part;
+        float* pb = ws.part + (size_t)B * orth_chunks * (kHP * kHP);
+        PROF_BEFORE(KK_SUBSPACE)
+        huge_orth_sweep_kernel<<<dim3(orth_chunks, B), kHThreads, 0, st>>>(
+            ws.V, ws.Wv, (pass & 1) ? pa : pb, (pass & 1) ? pb : pa, nn, pass, hb);
+        PROF_AFTER()
+      }
     }
     PROF_BEFORE(KK_SUBSPACE)
     huge_gv_kernel<<<gv_grid, kHThreads, 0, st>>>(ws.G, ws.V, ws.Wv, nn, hb);
