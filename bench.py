@@ -155,6 +155,18 @@ def kernel_roofline(stats, scales, M, N, pk):
         roof = {"bound": "alu", "achieved": round(ach, 3), "peak": round(pk["fp32_tflops"], 1),
                 "unit": "TFLOP/s", "frac": round(ach / pk["fp32_tflops"], 4), "traffic": None,
                 "peak_src": "152 SM x 128 FP32 lanes x 2 x max SM clock"}
+    elif kind == "subspace":
+        # W = G V launches read G (4 nn^2 bytes per block); per iteration the
+        # wide path launches sum(steps) + 3 of them among 5 sum(steps) + 3
+        # subspace launches (steps 2 or 6, 6, 12).  Every launch is counted
+        # as active: an upper bound when blocks converge in an early round.
+        full = (m, nsz) == (M, N)
+        steps = (2 if full else 6) + 6 + 12
+        per = (steps + 3) / (5 * steps + 3) * 4 * nn * nn * nblocks
+        ach = per / avg_s / 1e9
+        roof = {"bound": "hbm", "achieved": round(ach, 1), "peak": pk["hbm_gbs"], "unit": "GB/s",
+                "frac": round(ach / pk["hbm_gbs"], 4), "traffic": None,
+                "peak_src": pk["src"], "note": "G V launches counted as all active (upper bound)"}
     elif kind == "certificate":
         # tiled Cholesky of an nn x nn matrix per block: nn^3 / 3 flop per
         # iteration, over all of that iteration's panel and update launches
