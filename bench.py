@@ -45,9 +45,12 @@ def parse():
     ap.add_argument("--iters", type=int, default=ITERS_DEF)
     ap.add_argument("--M", type=int, default=M_DEF)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", default="video", choices=["video"] + sorted(JOBS),
-                    help="video (default, the headline line) or a batching/serving-shaped "
-                         "job whose full-matrix scale is wider than 256")
+    ap.add_argument("--serve-jobs", type=int, default=24)
+    ap.add_argument("--serve-rate", type=float, default=50.0)
+    ap.add_argument("--workload", default="video", choices=["video", "serve"] + sorted(JOBS),
+                    help="video (default, the headline line), a batching-shaped job whose "
+                         "full-matrix scale is wider than 256, or serve (p50/p99 latency of "
+                         "queued jobs under Poisson arrivals)")
     return ap.parse_args()
 
 
@@ -401,10 +404,92 @@ def ours(a):
         dist.destroy_process_group()
 
 
+# ---------------------------------------------------------------- serving ----
+
+SERVE_SIZES = [(256, 256), (1024, 1024), (4096, 512), (8192, 512), (2048, 2048)]
+
+
+def serve(a):
+    """Serving: jobs of the serving mix (sizes above, 3-6 dyadic scales, 30 %
+    rating-like with a 5 % observed mask) arrive as a Poisson stream and go
+    through msllr_submit / msllr_wait on one context (host buffers, copies
+    inside); latency = result in host memory - arrival."""
+    import numpy as np
+
+    from paper_1507_08751_gb300 import binding as B
+    from paper_1507_08751_gb300 import synth
+
+    if int(os.environ.get("RANK", "0")) != 0:
+        return
+    iters = a.iters if a.iters != ITERS_DEF else 200
+    rng = np.random.default_rng(SEED + 77)
+    jobs = []
+    for j in range(a.serve_jobs):
+        M, N = SERVE_SIZES[int(rng.integers(len(SERVE_SIZES)))]
+        L = int(rng.integers(3, 7))
+        if rng.random() < 0.3:
+            Y, mask = synth.ratings(SEED + 100 + j, M, N, density=0.05)
+            scales = synth.dyadic_scales(M, N, L)
+        else:
+            Y, scales = synth.job(SEED + 100 + j, M, N, L)
+            mask = None
+        jobs.append((Y, scales, mask))
+    arrivals = np.cumsum(rng.exponential(1.0 / a.serve_rate, a.serve_jobs))
+    outs = [np.empty((len(sc), *Y.shape), np.float32) for Y, sc, _ in jobs]
+    ctx = B.Context(0)
+    for Y, sc, mask in jobs[:3]:  # warm-up: kernels loaded, workspace grown
+        ctx.msllr_decompose_host(Y, sc, np.empty((len(sc), *Y.shape), np.float32), iters=2,
+                                 mask=mask)
+    n = len(jobs)
+    ids, t_arr = [None] * n, [None] * n
+    clocks = ClockSampler(0)
+    clocks.start()
+    t0 = time.perf_counter()
+
+    def submitter():
+        for j, (Y, sc, mask) in enumerate(jobs):
+            dt = t0 + arrivals[j] - time.perf_counter()
+            if dt > 0:
+                time.sleep(dt)
+            t_arr[j] = time.perf_counter()
+            ids[j] = ctx.msllr_submit(Y, sc, outs[j], iters=iters, seed=SEED + j, mask=mask)
+
+    th = threading.Thread(target=submitter)
+    th.start()
+    lat = []
+    for j in range(n):
+        while ids[j] is None:
+            time.sleep(0.0005)
+        ctx.msllr_wait(ids[j])
+        lat.append(time.perf_counter() - t_arr[j])
+    th.join()
+    t_total = time.perf_counter() - t0
+    ck = clocks.stop()
+    ctx.close()
+    lat_s = sorted(lat)
+    p50 = float(np.percentile(lat_s, 50))
+    p99 = float(np.percentile(lat_s, 99))
+    line = {
+        "metric": f"serve p50 latency (Poisson {a.serve_rate:g} jobs/s, {n} jobs, {iters} iters/job)",
+        "value": round(p50, 4), "unit": "s", "n_gpus": 1, "steps": 1, "warmup": 3,
+        "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic",
+        "config": {"workload": "serve-mix", "sizes": [f"{m}x{n_}" for m, n_ in SERVE_SIZES],
+                   "scales": "3-6 dyadic", "rating_like": 0.3, "arrival_rate": a.serve_rate,
+                   "jobs": n, "iters_per_job": iters, "queue": "msllr_submit, one worker"},
+        "p50_s": round(p50, 4), "p99_s": round(p99, 4),
+        "aggregate_iter_s": round(n * iters / t_total, 2),
+        "makespan_s": round(t_total, 3), "clocks": ck,
+    }
+    print(json.dumps(line), flush=True)
+
+
 def main():
     a = parse()
     if a.impl == "reference":
         reference_arm(a)
+    elif a.workload == "serve":
+        serve(a)
     else:
         ours(a)
 
