@@ -18,6 +18,10 @@ Parity status per function (what pins each one is listed in the tests):
                         with random cycle spinning: parity unpinned against
                         the paper (it prints no numbers), pinned only by the
                         per-iteration invariants sum_i X_i = Y and U' = A - Z'.
+  spin_set /           pinned (exact translation equivariance over the full
+  block_svt_spun        set, identity at tau = 0, brute force by explicit
+                        block windows, single-shift special case; the
+                        averaged ADMM is translation equivariant)
 """
 
 from .msllr_oracle import (  # noqa: F401
@@ -30,6 +34,8 @@ from .msllr_oracle import (  # noqa: F401
     svt,
     soft_threshold,
     block_svt,
+    spin_set,
+    block_svt_spun,
     block_nuclear_norm,
     block_dual_norm,
     consensus_residual,

@@ -21,7 +21,10 @@ design notes):
     entries, and Y there is ignored;
   * the noise scale of Sec. 2.1 (the whole matrix reshaped to one MN x 1
     block, whose nuclear norm is the Frobenius norm) is written as the block
-    size (0, 0); its default weight is eq:lambda with m = MN, n = 1.
+    size (0, 0); its default weight is eq:lambda with m = MN, n = 1;
+  * averaged cycle spinning (Sec. 9): the set S of a scale is all shifts
+    modulo its block size, or a sub-lattice of it, offset by the iteration's
+    random shift when that is on.
 """
 
 from __future__ import annotations
@@ -159,6 +162,31 @@ def block_svt(A: np.ndarray, m: int, n: int, tau: float,
     return _unblocks(Zb, M, N)
 
 
+def spin_set(m: int, n: int, g: int):
+    """Shifts averaged by cycle spinning at a scale of m x n blocks (Sec. 9:
+    S is the set of all shifts the application allows).  Shifts that differ
+    by whole blocks give the same partition, so all distinct shifts are
+    {0..m-1} x {0..n-1}; ``g`` >= max(m, n) takes all of them.  A smaller g
+    takes the sub-lattice of steps m/g_r, n/g_c (g_r = min(g, m), g_c =
+    min(g, n), which must divide m and n): invariance to shifts by multiples
+    of those steps.  g <= 1 gives {(0, 0)}."""
+    if g <= 1:
+        return [(0, 0)]
+    gr, gc = min(g, m), min(g, n)
+    if m % gr or n % gc:
+        raise ValueError("spin grid must divide the block size")
+    return [(a * (m // gr), b * (n // gc)) for a in range(gr) for b in range(gc)]
+
+
+def block_svt_spun(A: np.ndarray, m: int, n: int, tau: float, shifts) -> np.ndarray:
+    """Cycle-spun BlockSVT (Sec. 9, the averaged Z-update):
+        (1/|S|) sum_{s in S} Shift_{-s}(BlockSVT_tau(Shift_s(A)))."""
+    out = np.zeros_like(A, dtype=np.float64)
+    for s in shifts:
+        out += unshift(block_svt(shift(A, s), m, n, tau), s)
+    return out / len(shifts)
+
+
 def block_nuclear_norm(X: np.ndarray, m: int, n: int) -> float:
     """||X||_(i) = sum_b ||R_b(X)||_* (Sec. 3)."""
     return float(np.linalg.svd(_blocks(X, m, n), compute_uv=False).sum())
@@ -190,30 +218,39 @@ def x_update(Y, Z, U, mask=None):
     return (Z - U) + consensus_residual(Y, Z, U, mask)[None]
 
 
-def admm_step(Y, Z, U, scales, taus, s, mask=None):
+def admm_step(Y, Z, U, scales, taus, s, mask=None, spin=None):
     """One iteration of eq:admm with the Sec. 9 random-shift Z-update:
         X_i <- (Z_i - U_i) + (1/L)(Y - sum_j (Z_j - U_j))
         Z_i <- Shift_{-s}(BlockSVT_{tau_i}(Shift_s(X_i + U_i)))
         U_i <- U_i - (Z_i - X_i)
     ``s`` is one (s_r, s_c) pair shared by all scales, or an (L, 2) array
-    with one pair per scale.  Returns (X, Z_new, U_new)."""
+    with one pair per scale.  With ``spin`` (a list of shift sets, one per
+    scale, from ``spin_set``) the Z-update is the averaged one of Sec. 9 over
+    the shifts s + t, t in the scale's set.  Returns (X, Z_new, U_new)."""
     X = x_update(Y, Z, U, mask)
     s = np.asarray(s).reshape(-1, 2)
     Znew = np.empty_like(Z)
     for i, (m, n) in enumerate(scales):
         si = s[i] if s.shape[0] > 1 else s[0]
+        if spin is not None and len(spin[i]) > 1:
+            S = [(int(si[0]) + t[0], int(si[1]) + t[1]) for t in spin[i]]
+            Znew[i] = block_svt_spun(X[i] + U[i], m, n, taus[i], S)
+            continue
         Znew[i] = unshift(block_svt(shift(X[i] + U[i], si), m, n, taus[i]), si)
     Unew = U - (Znew - X)
     return X, Znew, Unew
 
 
 def admm(Y, scales, lambdas, rho=1.0, iters=100, shifts=None, mask=None,
-         Z0=None, U0=None, history=False):
+         Z0=None, U0=None, history=False, spin_grid=0):
     """Solve eq:cvx (or its masked form, Sec. 10.4) by ``iters`` iterations of
     eq:admm, starting from Z = U = 0 unless (Z0, U0) are given.
 
     ``shifts``: None (no cycle spinning) or an array with one shift per
     iteration, shape (iters, 2) or (iters, L, 2).
+    ``spin_grid``: g > 1 averages every scale's Z-update over ``spin_set``
+    (Sec. 9); the 1x1, full-matrix and noise scales commute with every shift
+    and keep the single update.
     Returns a dict with X (the X-update applied to the final Z, U), Z, U and,
     if ``history``, per-iteration objective sum_i lambda_i ||Z_i||_(i) and
     primal residual ||X - Z||_F."""
@@ -227,9 +264,13 @@ def admm(Y, scales, lambdas, rho=1.0, iters=100, shifts=None, mask=None,
     Z = np.zeros((L, M, N)) if Z0 is None else np.array(Z0, dtype=np.float64)
     U = np.zeros((L, M, N)) if U0 is None else np.array(U0, dtype=np.float64)
     obj, pres = [], []
+    spin = None
+    if spin_grid > 1:
+        spin = [[(0, 0)] if (m, n) in ((1, 1), (M, N), (0, 0)) else spin_set(m, n, spin_grid)
+                for (m, n) in scales]
     for k in range(iters):
         s = (0, 0) if shifts is None else shifts[k]
-        X, Z, U = admm_step(Y, Z, U, scales, taus, s, mask)
+        X, Z, U = admm_step(Y, Z, U, scales, taus, s, mask, spin)
         if history:
             obj.append(sum(lam * block_nuclear_norm(Z[i], *scales[i])
                            for i, lam in enumerate(lambdas)))

@@ -476,3 +476,96 @@ def test_admm_with_noise_scale_keeps_the_invariants():
     # the noise scale's first prox: Y/L shrunk by its Frobenius norm
     A = Y / L
     np.testing.assert_allclose(Zn[3], A * max(1 - lam[3] / np.linalg.norm(A), 0), atol=1e-13)
+
+
+# --------------------------------------------------------------------------
+# Averaged cycle spinning (Sec. 9): the Z-update averaged over a set of shifts.
+# --------------------------------------------------------------------------
+
+def _spun_by_windows(A, m, n, tau, shifts):
+    """The same average written without shifting arrays: for every shift s
+    and every block of the shifted grid, take the SVT of the block read
+    through explicit wrapped row/column indices and add 1/|S| of it back at
+    those indices."""
+    M, N = A.shape
+    out = np.zeros_like(A)
+    for (sr, sc) in shifts:
+        for p in range(M // m):
+            for q in range(N // n):
+                rows = [(p * m + i + sr) % M for i in range(m)]
+                cols = [(q * n + j + sc) % N for j in range(n)]
+                B = A[np.ix_(rows, cols)]
+                U, s, Vh = np.linalg.svd(B)
+                Zb = (U[:, :len(s)] * np.maximum(s - tau, 0)) @ Vh[:len(s)]
+                for i, r in enumerate(rows):
+                    for j, c in enumerate(cols):
+                        out[r, c] += Zb[i, j] / len(shifts)
+    return out
+
+
+def test_spin_set_sizes_and_lattice():
+    assert O.spin_set(4, 4, 0) == [(0, 0)]
+    assert O.spin_set(4, 4, 1) == [(0, 0)]
+    assert sorted(O.spin_set(4, 4, 2)) == [(0, 0), (0, 2), (2, 0), (2, 2)]
+    assert len(O.spin_set(4, 8, 64)) == 32          # every shift modulo the block
+    assert O.spin_set(1, 8, 4) == [(0, 0), (0, 2), (0, 4), (0, 6)]
+    with pytest.raises(ValueError):
+        O.spin_set(6, 6, 4)
+
+
+def test_spun_block_svt_brute_force_windows():
+    rng = np.random.default_rng(21)
+    A = rng.standard_normal((8, 12))
+    for (m, n, g) in ((4, 4, 4), (4, 6, 2), (2, 3, 8)):
+        S = O.spin_set(m, n, g)
+        S = [(s[0] + 3, s[1] + 5) for s in S]        # offset by a random shift
+        tau = 0.6
+        np.testing.assert_allclose(O.block_svt_spun(A, m, n, tau, S),
+                                   _spun_by_windows(A, m, n, tau, S), atol=1e-12)
+
+
+def test_spun_block_svt_is_translation_equivariant_over_all_shifts():
+    """Averaging over every shift modulo the block makes the operator commute
+    with every translation (the purpose of cycle spinning, Sec. 9)."""
+    rng = np.random.default_rng(22)
+    A = rng.standard_normal((12, 8))
+    m, n = 4, 4
+    S = O.spin_set(m, n, 4)
+    f = lambda X: O.block_svt_spun(X, m, n, 0.8, S)
+    for t in ((1, 0), (0, 3), (5, 7)):
+        np.testing.assert_allclose(f(O.shift(A, t)), O.shift(f(A), t), atol=1e-12)
+    # a single shift is not equivariant: the check has teeth
+    g = lambda X: O.block_svt(X, m, n, 0.8)
+    assert np.abs(g(O.shift(A, (1, 0))) - O.shift(g(A), (1, 0))).max() > 1e-3
+
+
+def test_spun_block_svt_special_cases():
+    rng = np.random.default_rng(23)
+    A = rng.standard_normal((8, 8))
+    # tau = 0: every term is the identity, so the average is A (weights 1/|S|)
+    np.testing.assert_allclose(O.block_svt_spun(A, 4, 4, 0.0, O.spin_set(4, 4, 4)), A,
+                               atol=1e-12)
+    # one shift: the random-shift update of Sec. 9
+    s = (3, 6)
+    np.testing.assert_allclose(O.block_svt_spun(A, 4, 4, 0.5, [s]),
+                               O.unshift(O.block_svt(O.shift(A, s), 4, 4, 0.5), s), atol=1e-12)
+    # full-matrix and 1x1 blocks commute with shifts: averaging changes nothing
+    np.testing.assert_allclose(O.block_svt_spun(A, 8, 8, 0.5, [(1, 2), (5, 3)]),
+                               O.svt(A, 0.5), atol=1e-12)
+    np.testing.assert_allclose(O.block_svt_spun(A, 1, 1, 0.5, [(1, 2), (5, 3)]),
+                               O.soft_threshold(A, 0.5), atol=1e-12)
+
+
+def test_spun_admm_is_translation_equivariant_and_keeps_invariants():
+    """With the full shift set and no random shift the averaged ADMM commutes
+    with translations of Y; sum_i X_i = Y holds at every iterate."""
+    Y, comps, scales = synth.tiny_64()
+    Y = Y[:32, :32].astype(np.float64)
+    scales = [(1, 1), (4, 4), (8, 8), (32, 32)]
+    lam = [O.lambda_default(32, 32, m, n) for m, n in scales]
+    r1 = O.admm(Y, scales, lam, 1.0, 6, spin_grid=8)
+    t = (5, 11)
+    r2 = O.admm(O.shift(Y, t), scales, lam, 1.0, 6, spin_grid=8)
+    for i in range(len(scales)):
+        np.testing.assert_allclose(r2["X"][i], O.shift(r1["X"][i], t), atol=1e-9)
+    np.testing.assert_allclose(r1["X"].sum(0), Y, atol=1e-10)
