@@ -270,7 +270,10 @@ def admm(Y, scales, lambdas, rho=1.0, iters=100, shifts=None, mask=None,
                 for (m, n) in scales]
     for k in range(iters):
         s = (0, 0) if shifts is None else shifts[k]
-        X, Z, U = admm_step(Y, Z, U, scales, taus, s, mask, spin)
+        if spin is None:
+            X, Z, U = admm_step(Y, Z, U, scales, taus, s, mask)
+        else:
+            X, Z, U = admm_step(Y, Z, U, scales, taus, s, mask, spin=spin)
         if history:
             obj.append(sum(lam * block_nuclear_norm(Z[i], *scales[i])
                            for i, lam in enumerate(lambdas)))
