@@ -89,6 +89,19 @@ typedef struct msllr_params {
                           2: scales run concurrently as usual and each
                           scale's whole segment is timed (kind 6 for wide
                           scales, 3 for the others).  Default 0.            */
+  int spin_grid;       /* averaged cycle spinning (Sec. 9).  0 or 1 (default):
+                          one shift per iteration.  g > 1: every scale of
+                          m x n blocks (not 1x1, not the full matrix, not the
+                          noise scale) averages its Z-update over the shifts
+                          s + (a m / g_r, b n / g_c), 0 <= a < g_r, 0 <= b <
+                          g_c, g_r = min(g, m), g_c = min(g, n) (which must
+                          divide m and n; else EINVAL), s the iteration's
+                          random shift (0 with cycle_spin = 0).  g >= the
+                          block size averages over every distinct shift:
+                          the update then commutes with translations.  Costs
+                          g_r g_c block SVTs per scale and iteration; block
+                          counts in msllr_stats add up over the shifts and
+                          scale_nuclear is their mean.                      */
 } msllr_params;
 
 /* Per-run diagnostics, all taken at the last iteration. */

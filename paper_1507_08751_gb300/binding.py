@@ -60,6 +60,7 @@ class Params(ctypes.Structure):
         ("U_init", ctypes.c_void_p),
         ("U_out", ctypes.c_void_p),
         ("profile", ctypes.c_int),
+        ("spin_grid", ctypes.c_int),
     ]
 
 

@@ -23,6 +23,7 @@ struct ScaleLaunch {
   int M, N, ld;            // matrix shape and row stride of A1, A2, Zout, Wout
   int m, n;                // block shape
   const int* shift;        // device int[2]: current (s_r, s_c)
+  int shift_add_r, shift_add_c;  // added to the shift (averaged cycle spinning)
   float tau;
   int skip_bound;
   int warm_start;          // wide blocks: start Lanczos from the previous call's Ritz
@@ -146,5 +147,11 @@ cudaError_t launch_nonfinite(const float* Y, int M, int N, int ld, int* flag, cu
                              Prof* prof = nullptr);
 cudaError_t launch_copy_dense(const float* src, int M, int N, int ld, float* dst, cudaStream_t st,
                               Prof* prof = nullptr);
+// Averaged cycle spinning: acc = w T (first) or acc += w T; then Z = acc,
+// W = 2 acc - (Z + R) (the fused dual update of eq:admm on the average).
+cudaError_t launch_spin_accum(float* acc, const float* T, float w, bool first, size_t MN,
+                              cudaStream_t st, Prof* prof = nullptr);
+cudaError_t launch_spin_finish(float* Z, float* W, const float* R, size_t MN, cudaStream_t st,
+                               Prof* prof = nullptr);
 
 }  // namespace msllr

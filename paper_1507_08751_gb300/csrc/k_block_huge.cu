@@ -88,8 +88,8 @@ __device__ __forceinline__ BlockGeom huge_geom(const ScaleLaunch& a, int b) {
   g.p = b / nbn;
   g.q = b - g.p * nbn;
   const bool full = (a.m == a.M && a.n == a.N);
-  g.sr = (a.shift && !full) ? a.shift[0] : 0;
-  g.sc = (a.shift && !full) ? a.shift[1] : 0;
+  g.sr = (a.shift && !full) ? (a.shift[0] + a.shift_add_r) % a.M : 0;
+  g.sc = (a.shift && !full) ? (a.shift[1] + a.shift_add_c) % a.N : 0;
   return g;
 }
 

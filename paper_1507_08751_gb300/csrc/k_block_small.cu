@@ -85,8 +85,8 @@ blocksvt_small_kernel(ScaleLaunch a) {
   g.p = blockIdx.x / nbn;
   g.q = blockIdx.x - g.p * nbn;
   const bool full = (a.m == a.M && a.n == a.N);  // SVT commutes with permutations
-  g.sr = (a.shift && !full) ? a.shift[0] : 0;
-  g.sc = (a.shift && !full) ? a.shift[1] : 0;
+  g.sr = (a.shift && !full) ? (a.shift[0] + a.shift_add_r) % a.M : 0;
+  g.sc = (a.shift && !full) ? (a.shift[1] + a.shift_add_c) % a.N : 0;
   const int mm = g.mm(), nn = g.nn();
   const int ldc = nn, ldg = nn + 1, ldy = nn;
 

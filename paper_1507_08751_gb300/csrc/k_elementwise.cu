@@ -395,4 +395,43 @@ cudaError_t launch_copy_dense(const float* src, int M, int N, int ld, float* dst
 #undef MISC_BEFORE
 #undef MISC_AFTER
 
+// Averaged cycle spinning (Sec. 9): the Z-updates of the shifts of a scale
+// are summed with weight 1/|S| into acc (the scale's W slot, free once the
+// consensus step has read it), then Z = acc and W = 2 acc - A, A = Z + R.
+__global__ void __launch_bounds__(kEwThreads)
+spin_accum_kernel(float* __restrict__ acc, const float* __restrict__ T, float w, int first,
+                  size_t MN) {
+  for (size_t e = blockIdx.x * (size_t)kEwThreads + threadIdx.x; e < MN;
+       e += (size_t)gridDim.x * kEwThreads)
+    acc[e] = first ? w * T[e] : fmaf(w, T[e], acc[e]);
+}
+
+__global__ void __launch_bounds__(kEwThreads)
+spin_finish_kernel(float* __restrict__ Z, float* __restrict__ W, const float* __restrict__ R,
+                   size_t MN) {
+  for (size_t e = blockIdx.x * (size_t)kEwThreads + threadIdx.x; e < MN;
+       e += (size_t)gridDim.x * kEwThreads) {
+    const float a = Z[e] + R[e];
+    const float z = W[e];
+    Z[e] = z;
+    W[e] = 2.f * z - a;
+  }
+}
+
+cudaError_t launch_spin_accum(float* acc, const float* T, float w, bool first, size_t MN,
+                              cudaStream_t st, Prof* prof) {
+  if (prof) if (cudaError_t e = prof->before(st, KK_MISC)) return e;
+  spin_accum_kernel<<<ew_grid(MN), kEwThreads, 0, st>>>(acc, T, w, first ? 1 : 0, MN);
+  if (prof) if (cudaError_t e = prof->after(st)) return e;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_spin_finish(float* Z, float* W, const float* R, size_t MN, cudaStream_t st,
+                               Prof* prof) {
+  if (prof) if (cudaError_t e = prof->before(st, KK_MISC)) return e;
+  spin_finish_kernel<<<ew_grid(MN), kEwThreads, 0, st>>>(Z, W, R, MN);
+  if (prof) if (cudaError_t e = prof->after(st)) return e;
+  return cudaGetLastError();
+}
+
 }  // namespace msllr

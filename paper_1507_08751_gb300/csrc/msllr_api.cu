@@ -15,6 +15,7 @@
 #include <string>
 #include <thread>
 #include <unordered_map>
+#include <utility>
 #include <vector>
 
 #include "../../include/msllr.h"
@@ -388,6 +389,7 @@ struct Layout {
   size_t MN;
   float* Z;
   float* W;
+  float* T;  // averaged cycle spinning: one M x N Z-update per scale, or null
   float* R;
   float* Yd;
   uint8_t* mask;
@@ -396,7 +398,8 @@ struct Layout {
 };
 
 // Offsets of every buffer inside the workspace (base may be null to size it).
-Layout plan(void* base, int M, int N, int L, const int* bm, const int* bn, bool masked) {
+Layout plan(void* base, int M, int N, int L, const int* bm, const int* bn, bool masked,
+            bool spin) {
   Layout lay;
   lay.MN = (size_t)M * N;
   char* b = (char*)base;
@@ -409,6 +412,7 @@ Layout plan(void* base, int M, int N, int L, const int* bm, const int* bn, bool 
   lay.Z = (float*)take(sizeof(float) * L * lay.MN);
   lay.W = (float*)take(sizeof(float) * L * lay.MN);
   lay.R = (float*)take(sizeof(float) * lay.MN);
+  lay.T = spin ? (float*)take(sizeof(float) * L * lay.MN) : nullptr;
   lay.Yd = (float*)take(sizeof(float) * lay.MN);
   lay.mask = masked ? (uint8_t*)take(lay.MN) : nullptr;
   for (int i = 0; i < L; ++i) {
@@ -418,6 +422,23 @@ Layout plan(void* base, int M, int N, int L, const int* bm, const int* bn, bool 
   }
   lay.total = off + 256;
   return lay;
+}
+
+// Shift offsets averaged at a scale (Sec. 9, msllr_params.spin_grid); one
+// zero offset where the scale is not spun.
+std::vector<std::pair<int, int>> spin_offsets(int M, int N, int m, int n, int g) {
+  std::vector<std::pair<int, int>> out;
+  const ScalePath path = choose_path(m, n);
+  const bool spun = g > 1 && (path == ScalePath::Small || path == ScalePath::Big ||
+                              path == ScalePath::Huge) && !(m == M && n == N);
+  if (!spun) {
+    out.push_back({0, 0});
+    return out;
+  }
+  const int gr = g < m ? g : m, gc = g < n ? g : n;
+  for (int a = 0; a < gr; ++a)
+    for (int b = 0; b < gc; ++b) out.push_back({a * (m / gr), b * (n / gc)});
+  return out;
 }
 
 int enqueue_iteration(msllr_ctx* ctx, const Layout& lay, int M, int N, int L, const int* bm,
@@ -445,6 +466,7 @@ int enqueue_iteration(msllr_ctx* ctx, const Layout& lay, int M, int N, int L, co
       if (pass == 1 && fork)
         for (int j = 0; j < L; ++j)
           if (gated[j]) CK(cudaStreamWaitEvent(st, ctx->ev_gate[j], 0));
+      const auto offs = spin_offsets(M, N, bm[i], bn[i], p.spin_grid);
       ScaleLaunch s{};
       s.A1 = lay.Z + (size_t)i * lay.MN;
       s.A2 = lay.R;
@@ -455,7 +477,7 @@ int enqueue_iteration(msllr_ctx* ctx, const Layout& lay, int M, int N, int L, co
       s.ld = N;
       s.m = bm[i];
       s.n = bn[i];
-      s.shift = p.cycle_spin ? ctx->d_small + 1 : nullptr;
+      s.shift = (p.cycle_spin || offs.size() > 1) ? ctx->d_small + 1 : nullptr;
       s.tau = taus[i];
       s.skip_bound = p.skip_bound;
       s.warm_start = 1;
@@ -465,15 +487,36 @@ int enqueue_iteration(msllr_ctx* ctx, const Layout& lay, int M, int N, int L, co
       s.norm_acc = ctx->d_noise + i;
       prof->scale = i;
       const bool gate = fork && wide && i > 0;
+      // one block SVT, or the average over the scale's shift set
+      auto run_scale = [&]() -> int {
+        if (offs.size() == 1) {
+          CK(launch_scale(s, lay.big[i], st, prof, gate ? ctx->ev_gate[i] : nullptr));
+          return MSLLR_OK;
+        }
+        float* acc = lay.W + (size_t)i * lay.MN;
+        float* T = lay.T + (size_t)i * lay.MN;
+        const float w = 1.f / (float)offs.size();
+        for (size_t j = 0; j < offs.size(); ++j) {
+          ScaleLaunch sj = s;
+          sj.shift_add_r = offs[j].first;
+          sj.shift_add_c = offs[j].second;
+          sj.Zout = T;
+          sj.Wout = nullptr;
+          CK(launch_scale(sj, lay.big[i], st, prof, (gate && j == 0) ? ctx->ev_gate[i] : nullptr));
+          CK(launch_spin_accum(acc, T, w, j == 0, lay.MN, st, prof));
+        }
+        CK(launch_spin_finish(lay.Z + (size_t)i * lay.MN, acc, lay.R, lay.MN, st, prof));
+        return MSLLR_OK;
+      };
       if (prof->per_scale) {
         // concurrent profile: one event pair around the scale's whole segment
         CK(prof->before(st, wide ? KK_EIG : KK_FUSED));
         prof->timing = false;
-        CK(launch_scale(s, lay.big[i], st, prof, gate ? ctx->ev_gate[i] : nullptr));
+        if (int r = run_scale()) return r;
         prof->timing = true;
         CK(prof->after(st));
       } else {
-        CK(launch_scale(s, lay.big[i], st, prof, gate ? ctx->ev_gate[i] : nullptr));
+        if (int r = run_scale()) return r;
       }
       gated[i] = gate;
       if (i > 0 && fork) CK(cudaEventRecord(ctx->ev_join[i], st));
@@ -500,6 +543,14 @@ int decompose_device(msllr_ctx* ctx, const float* Y, int M, int N, int ld, int L
   msllr_params_default(&p);
   if (params) p = *params;
   if (p.iter_offset < 0) return fail(ctx, MSLLR_EINVAL, "iter_offset must be >= 0");
+  if (p.spin_grid < 0) return fail(ctx, MSLLR_EINVAL, "spin_grid must be >= 0");
+  for (int i = 0; i < L && p.spin_grid > 1; ++i) {
+    const int m = bm[i], n = bn[i];
+    if (m <= 0 || n <= 0) continue;
+    const int gr = p.spin_grid < m ? p.spin_grid : m, gc = p.spin_grid < n ? p.spin_grid : n;
+    if (m % gr || n % gc)
+      return fail(ctx, MSLLR_EINVAL, "spin_grid must divide every block size it spins");
+  }
   Prof prof;
   prof.timing = p.profile != 0;
   prof.per_scale = p.profile == 2;
@@ -520,9 +571,10 @@ int decompose_device(msllr_ctx* ctx, const float* Y, int M, int N, int ld, int L
     taus[i] = (float)(lam[i] / rho);
   }
   CK(cudaSetDevice(ctx->device));
-  const Layout sizing = plan(nullptr, M, N, L, bm, bn, mask != nullptr);
+  const bool spin = p.spin_grid > 1;
+  const Layout sizing = plan(nullptr, M, N, L, bm, bn, mask != nullptr, spin);
   if (int r = ensure_ws(ctx, sizing.total)) return r;
-  const Layout lay = plan(ctx->ws, M, N, L, bm, bn, mask != nullptr);
+  const Layout lay = plan(ctx->ws, M, N, L, bm, bn, mask != nullptr, spin);
   cudaStream_t st = ctx->stream;
 
   // inputs: finiteness check, dense copies
@@ -572,7 +624,7 @@ int decompose_device(msllr_ctx* ctx, const float* Y, int M, int N, int ld, int L
     put(bm, sizeof(int) * L);
     put(bn, sizeof(int) * L);
     put(taus, sizeof(float) * L);
-    const int flags[3] = {p.skip_bound, p.cycle_spin, mask != nullptr};
+    const int flags[4] = {p.skip_bound, p.cycle_spin, mask != nullptr, p.spin_grid};
     put(flags, sizeof flags);
     void* wsp = ctx->ws;
     put(&wsp, sizeof wsp);
@@ -626,8 +678,10 @@ int decompose_device(msllr_ctx* ctx, const float* Y, int M, int N, int ld, int L
     stats->L = L;
     double obj = 0.0;
     for (int i = 0; i < L; ++i) {
-      stats->scale_nuclear[i] = acc[i];
-      obj += lam[i] * acc[i];
+      // averaged cycle spinning sums the nuclear norms of all the shifts
+      const double nspin = (double)spin_offsets(M, N, bm[i], bn[i], p.spin_grid).size();
+      stats->scale_nuclear[i] = acc[i] / nspin;
+      obj += lam[i] * acc[i] / nspin;
       stats->blocks[i] = (bm[i] == 0 && bn[i] == 0) ? 1 : (long long)(M / bm[i]) * (N / bn[i]);
       stats->blocks_skipped[i] = (long long)cnt[8 * i];
       stats->blocks_zero[i] = (long long)cnt[8 * i + 1];
@@ -824,7 +878,8 @@ int msllr_submit(msllr_ctx* ctx, const msllr_job* job, uint64_t* job_id) {
   // admission: the job's workspace plus its input and output slabs must fit
   // the context's HBM budget
   const size_t MN = (size_t)M * N;
-  const size_t need = plan(nullptr, M, N, L, job->block_m, job->block_n, job->mask != nullptr).total +
+  const bool spin = job->params && job->params->spin_grid > 1;
+  const size_t need = plan(nullptr, M, N, L, job->block_m, job->block_n, job->mask != nullptr, spin).total +
                       sizeof(float) * MN * (1 + (size_t)L * (job->Z_out ? 2 : 1)) +
                       (job->mask ? MN : 0);
   if (ctx->budget && need > ctx->budget)

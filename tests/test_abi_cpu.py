@@ -60,6 +60,16 @@ def test_params_default(built):
     p = B.msllr_params_default()
     assert (p.skip_bound, p.cycle_spin, p.use_graph, p.iter_offset) == (1, 1, 1, 0)
     assert not p.Z_init and not p.U_init and not p.U_out
+    assert p.profile == 0 and p.spin_grid == 0
+
+
+def test_params_struct_matches_header_field_order():
+    """The ctypes mirror lists the header's msllr_params fields in order."""
+    src = open(os.path.join(ROOT, "include", "msllr.h")).read()
+    body = src[src.index("typedef struct msllr_params"):src.index("} msllr_params;")]
+    body = re.sub(r"/\*.*?\*/", "", body, flags=re.S)
+    names = re.findall(r"^\s+(?:const\s+)?\w+\*?\s+\*?(\w+);", body, re.M)
+    assert names == [f[0] for f in B.Params._fields_]
 
 
 def test_create_without_device_fails_loudly(built):
