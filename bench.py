@@ -45,6 +45,8 @@ def parse():
     ap.add_argument("--iters", type=int, default=ITERS_DEF)
     ap.add_argument("--M", type=int, default=M_DEF)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--spin-grid", type=int, default=0,
+                    help="averaged cycle spinning (Sec. 9) over a g x g shift lattice per scale")
     ap.add_argument("--serve-jobs", type=int, default=24)
     ap.add_argument("--serve-rate", type=float, default=50.0)
     ap.add_argument("--workload", default="video", choices=["video", "serve"] + sorted(JOBS),
@@ -309,6 +311,10 @@ def ours(a):
     torch.cuda.synchronize()
 
     def step(params=None):
+        if params is None and a.spin_grid > 1:
+            params = B.msllr_params_default()
+        if params is not None:
+            params.spin_grid = a.spin_grid
         return ctx.msllr_decompose(Yd, scales, X, iters=a.iters, seed=SEED, params=params)
 
     for _ in range(a.warmup):
@@ -355,11 +361,15 @@ def ours(a):
     # end to end through the host API: pinned host Y in, X out, copies timed
     Yh = torch.from_numpy(Y32).pin_memory()
     Xh = torch.empty((L, M, N), dtype=torch.float32).pin_memory()
-    ctx.msllr_decompose_host(Yh, scales, Xh, iters=a.iters, seed=SEED)
+    hp = None
+    if a.spin_grid > 1:
+        hp = B.msllr_params_default()
+        hp.spin_grid = a.spin_grid
+    ctx.msllr_decompose_host(Yh, scales, Xh, iters=a.iters, seed=SEED, params=hp)
     e_steps = max(1, min(a.steps, 3))
     t0 = time.perf_counter()
     for _ in range(e_steps):
-        ctx.msllr_decompose_host(Yh, scales, Xh, iters=a.iters, seed=SEED)
+        ctx.msllr_decompose_host(Yh, scales, Xh, iters=a.iters, seed=SEED, params=hp)
     t_e2e = time.perf_counter() - t0
     e2e = {"value": round(a.iters * e_steps / t_e2e, 2), "unit": "iter/s",
            "h2d_bytes_per_step": 4 * M * N, "d2h_bytes_per_step": 4 * L * M * N,
@@ -378,7 +388,8 @@ def ours(a):
             "steps": a.steps, "warmup": a.warmup,
             "ms_per_step": round(1e3 * t_s / a.steps, 3), "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": workload, "M": M, "N": N, "L": L,
+            "config": {"workload": workload + (f"-spin{a.spin_grid}" if a.spin_grid > 1 else ""),
+                       "M": M, "N": N, "L": L,
                        "scales": [f"{m}x{n}" for m, n in scales], "iters_per_job": a.iters,
                        "parallelism": f"replicas{world}", "step": "one decomposition job",
                        "l2": f"ADMM state {2 * L + 1} x {4 * M * N / 1e6:.1f} MB"
