@@ -274,6 +274,29 @@ def reference_arm(a):
 
 # -------------------------------------------------------------- our arm ----
 
+def replica_seed(rank):
+    """Each rank decomposes its own job (replicas: the method has no step that
+    exchanges data between GPUs)."""
+    return SEED + 1 + rank
+
+
+def job_time_over_ranks(t_s, world, device):
+    """The whole-job time is the slowest rank's timed region (max over ranks);
+    one rank returns its own."""
+    if world <= 1:
+        return t_s
+    import torch
+    import torch.distributed as dist
+    tt = torch.tensor([t_s], dtype=torch.float64, device=device)
+    dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+    return float(tt.item())
+
+
+def whole_job_value(world, iters, steps, t_s):
+    """Iterations processed by all ranks per second of the max-over-ranks time."""
+    return world * iters * steps / t_s
+
+
 def ours(a):
     import numpy as np
     import torch
@@ -292,13 +315,13 @@ def ours(a):
 
     # per-rank independent job (replicas: the method has no cross-GPU step)
     if a.workload == "video":
-        Y32, comps, scales = synth.video(seed=SEED + 1 + rank, M=a.M, N=256)
+        Y32, comps, scales = synth.video(seed=replica_seed(rank), M=a.M, N=256)
         metric, workload = METRIC, WORKLOAD
     else:
         Mj, Nj, it_j = JOBS[a.workload]
         if a.iters == ITERS_DEF:
             a.iters = it_j
-        Y32, scales = synth.job(SEED + 1 + rank, Mj, Nj, 6)
+        Y32, scales = synth.job(replica_seed(rank), Mj, Nj, 6)
         metric = f"BlockSVT-ADMM iter/s ({a.workload}: {Mj}x{Nj}, L={len(scales)}, {a.iters} iters/job)"
         workload = f"{a.workload}-L{len(scales)}-s" + "_".join(str(m) for m, _ in scales[:-1]) + "_full"
     ITERS_OF["cur"] = a.iters
@@ -335,13 +358,9 @@ def ours(a):
     if world > 1:
         dist.barrier()
     ck = clocks.stop()
-    t_s = e0.elapsed_time(e1) / 1e3
-    if world > 1:
-        tt = torch.tensor([t_s], device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        t_s = float(tt.item())
+    t_s = job_time_over_ranks(e0.elapsed_time(e1) / 1e3, world, dev)
     launches_per_step = stats["launches"]
-    value = world * a.iters * a.steps / t_s
+    value = whole_job_value(world, a.iters, a.steps, t_s)
     nblocks = sum((M // m) * (N // n) for m, n in scales)
 
     # profiled job: per-kernel CUDA events on the launching stream
