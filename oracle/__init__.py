@@ -18,6 +18,9 @@ Parity status per function (what pins each one is listed in the tests):
                         with random cycle spinning: parity unpinned against
                         the paper (it prints no numbers), pinned only by the
                         per-iteration invariants sum_i X_i = Y and U' = A - Z'.
+  blocks3d / block_svt_3d   pinned (inverse of its adjoint, reduction to the
+                        2-D partition when a block spans whole frame rows,
+                        brute force by explicit pixel indices)
   spin_set /           pinned (exact translation equivariance over the full
   block_svt_spun        set, identity at tau = 0, brute force by explicit
                         block windows, single-shift special case; the
@@ -36,6 +39,10 @@ from .msllr_oracle import (  # noqa: F401
     block_svt,
     spin_set,
     block_svt_spun,
+    blocks3d,
+    unblocks3d,
+    shift3d,
+    block_svt_3d,
     block_nuclear_norm,
     block_dual_norm,
     consensus_residual,

@@ -162,6 +162,48 @@ def block_svt(A: np.ndarray, m: int, n: int, tau: float,
     return _unblocks(Zb, M, N)
 
 
+# --------------------------------------------------------------------------
+# Spatio-temporal blocks (Sec. 10.2: the video partitions 4x4x4 and
+# 16x16x16).  The M x N video matrix has one column per frame and row
+# y * W + x for pixel (y, x) of an H x W frame (M = H W).  A bh x bw x bt
+# block of the video cube is reshaped by R_b into a (bh bw) x bt matrix,
+# pixels in row-major order within the patch (Sec. 2, the block reshape
+# operator).
+# --------------------------------------------------------------------------
+
+def blocks3d(A: np.ndarray, H: int, W: int, bh: int, bw: int, bt: int, s3=(0, 0, 0)) -> np.ndarray:
+    """R_b of every bh x bw x bt block of the video cube of A, after the
+    circular shift s3 = (s_y, s_x, s_t) of the cube (Sec. 9 in three
+    dimensions); returns shape (nb, bh*bw, bt)."""
+    M, T = A.shape
+    if M != H * W or H % bh or W % bw or T % bt:
+        raise ValueError("spatio-temporal block does not divide the video")
+    V = A.reshape(H, W, T)
+    V = np.roll(V, shift=(-int(s3[0]), -int(s3[1]), -int(s3[2])), axis=(0, 1, 2))
+    V = V.reshape(H // bh, bh, W // bw, bw, T // bt, bt)
+    return V.transpose(0, 2, 4, 1, 3, 5).reshape(-1, bh * bw, bt)
+
+
+def unblocks3d(B: np.ndarray, H: int, W: int, T: int, bh: int, bw: int, bt: int,
+               s3=(0, 0, 0)) -> np.ndarray:
+    """The adjoint (and inverse) of ``blocks3d``: embed every block back and
+    undo the shift; returns the (H W) x T matrix."""
+    V = B.reshape(H // bh, W // bw, T // bt, bh, bw, bt).transpose(0, 3, 1, 4, 2, 5)
+    V = V.reshape(H, W, T)
+    V = np.roll(V, shift=(int(s3[0]), int(s3[1]), int(s3[2])), axis=(0, 1, 2))
+    return V.reshape(H * W, T)
+
+
+def block_svt_3d(A: np.ndarray, H: int, W: int, bh: int, bw: int, bt: int, tau: float,
+                 s3=(0, 0, 0)) -> np.ndarray:
+    """eq:bsvt with spatio-temporal blocks: SVT of every (bh bw) x bt block
+    matrix (full FP64 SVD), embedded back."""
+    B = blocks3d(A, H, W, bh, bw, bt, s3)
+    U, sv, Vh = np.linalg.svd(B, full_matrices=False)
+    Zb = (U * np.maximum(sv - tau, 0.0)[:, None, :]) @ Vh
+    return unblocks3d(Zb, H, W, A.shape[1], bh, bw, bt, s3)
+
+
 def spin_set(m: int, n: int, g: int):
     """Shifts averaged by cycle spinning at a scale of m x n blocks (Sec. 9:
     S is the set of all shifts the application allows).  Shifts that differ
@@ -218,7 +260,14 @@ def x_update(Y, Z, U, mask=None):
     return (Z - U) + consensus_residual(Y, Z, U, mask)[None]
 
 
-def admm_step(Y, Z, U, scales, taus, s, mask=None, spin=None):
+def shift3d(s, W: int, T: int):
+    """The iteration's shift (s_r, s_c) read on the video cube: the row shift
+    names a pixel, (s_y, s_x) = divmod(s_r, W), and s_c a frame shift."""
+    sy, sx = divmod(int(s[0]), W)
+    return (sy, sx, int(s[1]) % T)
+
+
+def admm_step(Y, Z, U, scales, taus, s, mask=None, spin=None, frame=None):
     """One iteration of eq:admm with the Sec. 9 random-shift Z-update:
         X_i <- (Z_i - U_i) + (1/L)(Y - sum_j (Z_j - U_j))
         Z_i <- Shift_{-s}(BlockSVT_{tau_i}(Shift_s(X_i + U_i)))
@@ -226,12 +275,21 @@ def admm_step(Y, Z, U, scales, taus, s, mask=None, spin=None):
     ``s`` is one (s_r, s_c) pair shared by all scales, or an (L, 2) array
     with one pair per scale.  With ``spin`` (a list of shift sets, one per
     scale, from ``spin_set``) the Z-update is the averaged one of Sec. 9 over
-    the shifts s + t, t in the scale's set.  Returns (X, Z_new, U_new)."""
+    the shifts s + t, t in the scale's set.  A scale given as (bh, bw, bt)
+    is a spatio-temporal partition of the video cube of frame ``frame`` =
+    (H, W) (Sec. 10.2), shifted by ``shift3d``.  Returns (X, Z_new, U_new)."""
     X = x_update(Y, Z, U, mask)
     s = np.asarray(s).reshape(-1, 2)
     Znew = np.empty_like(Z)
-    for i, (m, n) in enumerate(scales):
+    for i, sc in enumerate(scales):
+        m, n = sc[0], sc[-1]
         si = s[i] if s.shape[0] > 1 else s[0]
+        if len(scales[i]) == 3:
+            bh, bw, bt = scales[i]
+            H, W = frame
+            Znew[i] = block_svt_3d(X[i] + U[i], H, W, bh, bw, bt, taus[i],
+                                   shift3d(si, W, Y.shape[1]))
+            continue
         if spin is not None and len(spin[i]) > 1:
             S = [(int(si[0]) + t[0], int(si[1]) + t[1]) for t in spin[i]]
             Znew[i] = block_svt_spun(X[i] + U[i], m, n, taus[i], S)
@@ -242,12 +300,13 @@ def admm_step(Y, Z, U, scales, taus, s, mask=None, spin=None):
 
 
 def admm(Y, scales, lambdas, rho=1.0, iters=100, shifts=None, mask=None,
-         Z0=None, U0=None, history=False, spin_grid=0):
+         Z0=None, U0=None, history=False, spin_grid=0, frame=None):
     """Solve eq:cvx (or its masked form, Sec. 10.4) by ``iters`` iterations of
     eq:admm, starting from Z = U = 0 unless (Z0, U0) are given.
 
     ``shifts``: None (no cycle spinning) or an array with one shift per
     iteration, shape (iters, 2) or (iters, L, 2).
+    ``frame``: (H, W) when some scales are spatio-temporal (bh, bw, bt).
     ``spin_grid``: g > 1 averages every scale's Z-update over ``spin_set``
     (Sec. 9); the 1x1, full-matrix and noise scales commute with every shift
     and keep the single update.
@@ -266,16 +325,20 @@ def admm(Y, scales, lambdas, rho=1.0, iters=100, shifts=None, mask=None,
     obj, pres = [], []
     spin = None
     if spin_grid > 1:
-        spin = [[(0, 0)] if (m, n) in ((1, 1), (M, N), (0, 0)) else spin_set(m, n, spin_grid)
-                for (m, n) in scales]
+        spin = [[(0, 0)] if len(sc) == 3 or tuple(sc) in ((1, 1), (M, N), (0, 0))
+                else spin_set(sc[0], sc[1], spin_grid) for sc in scales]
     for k in range(iters):
         s = (0, 0) if shifts is None else shifts[k]
-        if spin is None:
-            X, Z, U = admm_step(Y, Z, U, scales, taus, s, mask)
-        else:
-            X, Z, U = admm_step(Y, Z, U, scales, taus, s, mask, spin=spin)
+        extra = {}
+        if spin is not None:
+            extra["spin"] = spin
+        if frame is not None:
+            extra["frame"] = frame
+        X, Z, U = admm_step(Y, Z, U, scales, taus, s, mask, **extra)
         if history:
-            obj.append(sum(lam * block_nuclear_norm(Z[i], *scales[i])
+            obj.append(sum(lam * (block_nuclear_norm(Z[i], *scales[i]) if len(scales[i]) == 2
+                                  else float(np.linalg.svd(blocks3d(Z[i], *frame, *scales[i]),
+                                                           compute_uv=False).sum()))
                            for i, lam in enumerate(lambdas)))
             pres.append(float(np.linalg.norm(X - Z)))
     out = {"X": x_update(Y, Z, U, mask), "Z": Z, "U": U}

@@ -569,3 +569,86 @@ def test_spun_admm_is_translation_equivariant_and_keeps_invariants():
     for i in range(len(scales)):
         np.testing.assert_allclose(r2["X"][i], O.shift(r1["X"][i], t), atol=1e-9)
     np.testing.assert_allclose(r1["X"].sum(0), Y, atol=1e-10)
+
+
+# --------------------------------------------------------------------------
+# Spatio-temporal blocks (Sec. 10.2): bh x bw x bt video blocks reshaped to
+# (bh bw) x bt matrices.
+# --------------------------------------------------------------------------
+
+def test_blocks3d_round_trip_and_shape():
+    rng = np.random.default_rng(31)
+    H, W, T = 8, 12, 16
+    A = rng.standard_normal((H * W, T))
+    for (bh, bw, bt, s3) in ((4, 4, 4, (0, 0, 0)), (2, 6, 8, (3, 5, 11)), (8, 12, 16, (1, 2, 3))):
+        B = O.blocks3d(A, H, W, bh, bw, bt, s3)
+        assert B.shape == ((H // bh) * (W // bw) * (T // bt), bh * bw, bt)
+        np.testing.assert_array_equal(O.unblocks3d(B, H, W, T, bh, bw, bt, s3), A)
+
+
+def test_block3d_by_explicit_pixel_indices():
+    """Brute force: block (py, px, pt) of the shifted cube holds, at row
+    i * bw + j and column k, the entry of pixel ((py bh + i + sy) mod H,
+    (px bw + j + sx) mod W) in frame (pt bt + k + st) mod T."""
+    rng = np.random.default_rng(32)
+    H, W, T, bh, bw, bt, s3 = 6, 8, 6, 3, 4, 2, (4, 7, 5)
+    A = rng.standard_normal((H * W, T))
+    B = O.blocks3d(A, H, W, bh, bw, bt, s3)
+    b = 0
+    for py in range(H // bh):
+        for px in range(W // bw):
+            for pt in range(T // bt):
+                for i in range(bh):
+                    for j in range(bw):
+                        for k in range(bt):
+                            y = (py * bh + i + s3[0]) % H
+                            x = (px * bw + j + s3[1]) % W
+                            t = (pt * bt + k + s3[2]) % T
+                            assert B[b, i * bw + j, k] == A[y * W + x, t]
+                b += 1
+
+
+def test_block_svt_3d_reduces_to_2d_when_blocks_span_frame_rows():
+    """A bh x W x bt block covers bh whole frame rows: its rows are the
+    contiguous matrix rows y0 W .. (y0 + bh) W - 1, so the spatio-temporal
+    BlockSVT equals the 2-D one with (bh W) x bt blocks."""
+    rng = np.random.default_rng(33)
+    H, W, T = 8, 6, 12
+    A = rng.standard_normal((H * W, T))
+    for (bh, bt, tau) in ((2, 4, 0.7), (4, 6, 1.5), (8, 12, 3.0)):
+        np.testing.assert_allclose(O.block_svt_3d(A, H, W, bh, W, bt, tau),
+                                   O.block_svt(A, bh * W, bt, tau), atol=1e-12)
+
+
+def test_block_svt_3d_singular_values_closed_form():
+    rng = np.random.default_rng(34)
+    H, W, T = 8, 8, 8
+    A = rng.standard_normal((H * W, T))
+    tau = 1.1
+    Z = O.block_svt_3d(A, H, W, 4, 4, 4, tau, (1, 3, 2))
+    sa = np.linalg.svd(O.blocks3d(A, H, W, 4, 4, 4, (1, 3, 2)), compute_uv=False)
+    sz = np.linalg.svd(O.blocks3d(Z, H, W, 4, 4, 4, (1, 3, 2)), compute_uv=False)
+    np.testing.assert_allclose(sz, np.maximum(sa - tau, 0.0), atol=1e-12)
+
+
+def test_spatio_temporal_admm_reduces_to_2d_and_keeps_invariants():
+    """ADMM with a bh x W x bt scale and shifts off is the 2-D ADMM with
+    (bh W) x bt blocks; with shifts on (the row shift read as a pixel shift)
+    sum_i X_i = Y holds."""
+    rng = np.random.default_rng(35)
+    H, W, T = 8, 4, 16
+    Y = rng.standard_normal((H * W, T))
+    M, N = Y.shape
+    s3d = [(1, 1), (2, W, 4), (M, N)]
+    s2d = [(1, 1), (2 * W, 4), (M, N)]
+    lam = [O.lambda_default(M, N, 1, 1), O.lambda_default(M, N, 2 * W, 4),
+           O.lambda_default(M, N, M, N)]
+    r3 = O.admm(Y, s3d, lam, 1.0, 15, frame=(H, W))
+    r2 = O.admm(Y, s2d, lam, 1.0, 15)
+    np.testing.assert_allclose(r3["X"], r2["X"], atol=1e-12)
+    sh = O.shift_table(3, 10, M, N)
+    r = O.admm(Y, [(1, 1), (2, 2, 4), (4, 4, 8), (M, N)],
+               [1.0, 2.0, 3.0, 6.0], 1.0, 10, shifts=sh, frame=(H, W), history=True)
+    np.testing.assert_allclose(r["X"].sum(0), Y, atol=1e-10)
+    assert np.all(np.isfinite(r["objective"]))
+    assert O.shift3d((13, 5), W, T) == (3, 1, 5)
