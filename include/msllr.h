@@ -118,7 +118,10 @@ typedef struct msllr_stats {
   long long blocks_zero[MSLLR_MAX_SCALES];    /* blocks whose certified rank
                                                  above tau was 0 (incl. skip) */
   double lambda[MSLLR_MAX_SCALES];            /* lambda_i actually used       */
-  long long blocks_lanczos[MSLLR_MAX_SCALES]; /* eigenpairs by certified Lanczos */
+  long long blocks_lanczos[MSLLR_MAX_SCALES]; /* eigenpairs by certified Lanczos
+                                                 (blocks up to 256 wide) or by
+                                                 certified subspace iteration
+                                                 (wider blocks)               */
   long long blocks_householder[MSLLR_MAX_SCALES]; /* by the Householder path   */
   long long launches;                         /* kernels launched by the call */
   /* per kernel kind (see MSLLR_KERNEL_KINDS) and scale (kinds 0, 1 and 8
