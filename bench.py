@@ -316,7 +316,8 @@ def ours(a):
     # per-rank independent job (replicas: the method has no cross-GPU step)
     if a.workload == "video":
         Y32, comps, scales = synth.video(seed=replica_seed(rank), M=a.M, N=256)
-        metric, workload = METRIC, WORKLOAD
+        metric = METRIC if a.iters == ITERS_DEF else METRIC.replace(f"{ITERS_DEF} iters", f"{a.iters} iters")
+        workload = WORKLOAD
     else:
         Mj, Nj, it_j = JOBS[a.workload]
         if a.iters == ITERS_DEF:
