@@ -116,7 +116,7 @@ class ClockSampler:
 
 # ------------------------------------------------------------------ peaks ----
 
-def peaks():
+def peaks(n_sm):
     p = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "src": "fallback"}
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -125,14 +125,17 @@ def peaks():
         p["sm_max_mhz"] = float(d.get("sm_max_mhz", 2070.0))
     except (OSError, KeyError, ValueError):
         p["sm_max_mhz"] = 2070.0
-    # FP32 CUDA-core peak: 152 SMs x 128 FP32 lanes x 2 flop (FMA) x max SM clock
-    p["fp32_tflops"] = 152 * 128 * 2 * p["sm_max_mhz"] * 1e6 / 1e12
+    # FP32 CUDA-core peak: SMs x 128 FP32 lanes x 2 flop (FMA) x max SM clock
+    p["n_sm"] = n_sm
+    p["fp32_tflops"] = n_sm * 128 * 2 * p["sm_max_mhz"] * 1e6 / 1e12
+    p["fp32_src"] = f"derived: {n_sm} SM x 128 FP32 lanes x 2 x {p['sm_max_mhz']:.0f} MHz"
     return p
 
 
-# DRAM bytes (read + write) per launch from one ncu capture of the kernel as
-# it stands (profiles/eig_big_video16384x256.md); kernels not listed: null.
-NCU_TRAFFIC_BYTES = {"eig_big[scale 3: 256x256]": 8781056}
+# DRAM bytes (read + write) per launch of a kernel, from one ncu capture of
+# the kernel as it stands (key: kernel kind and scale); kernels not listed
+# report traffic null.
+NCU_TRAFFIC_BYTES = {}
 ITERS_OF = {}
 
 
@@ -159,7 +162,7 @@ def kernel_roofline(stats, scales, M, N, pk):
         ach = flops / avg_s / 1e12
         roof = {"bound": "alu", "achieved": round(ach, 3), "peak": round(pk["fp32_tflops"], 1),
                 "unit": "TFLOP/s", "frac": round(ach / pk["fp32_tflops"], 4), "traffic": None,
-                "peak_src": "152 SM x 128 FP32 lanes x 2 x max SM clock"}
+                "peak_src": pk["fp32_src"]}
     elif kind == "subspace":
         # W = G V launches read G (4 nn^2 bytes per block); per iteration the
         # wide path launches sum(steps) + 3 of them among 5 sum(steps) + 3
@@ -180,13 +183,24 @@ def kernel_roofline(stats, scales, M, N, pk):
         ach = flops / avg_s / 1e12
         roof = {"bound": "alu", "achieved": round(ach, 4), "peak": round(pk["fp32_tflops"], 1),
                 "unit": "TFLOP/s", "frac": round(ach / pk["fp32_tflops"], 5), "traffic": None,
-                "peak_src": "152 SM x 128 FP32 lanes x 2 x max SM clock"}
-    elif kind == "eig_big":
-        flops = nblocks * (4 * nn ** 3 // 3)
+                "peak_src": pk["fp32_src"]}
+    elif kind in ("eig_big", "eig_fallback"):
+        # flops of the steps the kernel ran (counted on the device over every
+        # launch of the profiled job), per launch
+        key = "flops" if kind == "eig_big" else "flops_fallback"
+        flops = stats[key][i] / n
         ach = flops / avg_s / 1e12
         roof = {"bound": "alu", "achieved": round(ach, 4), "peak": round(pk["fp32_tflops"], 1),
                 "unit": "TFLOP/s", "frac": round(ach / pk["fp32_tflops"], 5), "traffic": None,
-                "peak_src": "152 SM x 128 FP32 lanes x 2 x max SM clock"}
+                "peak_src": pk["fp32_src"], "flops_per_launch": int(flops)}
+    elif kind == "fused_small":
+        # HBM bound by design (16 MN bytes per launch); the counted flops of
+        # the blocks that run an eigen-solve give its ALU fraction beside it
+        ach = 16 * MN / avg_s / 1e9
+        alu = stats["flops"][i] / n / avg_s / 1e12
+        roof = {"bound": "hbm", "achieved": round(ach, 1), "peak": pk["hbm_gbs"], "unit": "GB/s",
+                "frac": round(ach / pk["hbm_gbs"], 4), "traffic": None, "peak_src": pk["src"],
+                "alu_frac": round(alu / pk["fp32_tflops"], 5)}
     else:
         per = {"consensus": (L + 2) * 4 * MN, "soft1x1": 16 * MN, "fused_small": 16 * MN,
                "rebuild": 16 * MN, "gram_reduce": 0, "advance": 8, "misc": 8 * MN,
@@ -201,6 +215,47 @@ def kernel_roofline(stats, scales, M, N, pk):
     total = sum(sum(v) for v in stats["kernel_ms"].values())
     roof["time_share"] = round(ms / total, 4) if total else None
     return roof, best
+
+
+def scale_rooflines(stats, scales, M, N, iters, pk):
+    """One roofline row per step of the iteration, from the profiled job in
+    which every kernel ran alone, bracketed by CUDA events on its stream:
+    the consensus residual (a1: reads Y and L W_j, writes R) and every scale
+    (its kernels' summed time; algorithmic bytes 16 MN: reads Z_i and R,
+    writes Z_i and W_i).  Scales with an eigen-solve also get their ALU
+    fraction: Gram flops (wide blocks: mm nn (nn + 1) per block) plus the
+    eigen-solve flops the kernels counted for the steps they ran."""
+    MN = M * N
+    L = len(scales)
+    hbm, fp32 = pk["hbm_gbs"], pk["fp32_tflops"]
+    ms, nl = stats["kernel_ms"], stats["kernel_launches"]
+    rows = []
+    if nl["consensus"][0]:
+        t = ms["consensus"][0] / nl["consensus"][0] / 1e3
+        byt = (L + 2) * 4 * MN
+        rows.append({"step": "consensus", "us": round(t * 1e6, 2), "bytes": byt,
+                     "bound": "hbm", "frac": round(byt / t / 1e9 / hbm, 4)})
+    skip = ("advance", "consensus", "misc")
+    for i, (m, n) in enumerate(scales):
+        kinds = [k for k in ms if k not in skip and ms[k][i] > 0]
+        t = sum(ms[k][i] for k in kinds) / iters / 1e3
+        if t <= 0:
+            continue
+        byt = 16 * MN
+        row = {"step": f"scale {m}x{n}", "us": round(t * 1e6, 2), "bytes": byt,
+               "hbm_frac": round(byt / t / 1e9 / hbm, 4),
+               "kernels_us": {k: round(ms[k][i] / iters * 1e3, 2) for k in kinds}}
+        fl = (stats["flops"][i] + stats["flops_fallback"][i]) / iters
+        if "gram" in kinds:
+            mm, nn = max(m, n), min(m, n)
+            fl += (M // m) * (N // n) * mm * nn * (nn + 1)
+        if fl > 0:
+            row["flops"] = int(fl)
+            row["alu_frac"] = round(fl / t / 1e12 / fp32, 5)
+        row["bound"] = "alu" if row.get("alu_frac", 0) > row["hbm_frac"] else "hbm"
+        row["frac"] = max(row.get("alu_frac", 0), row["hbm_frac"])
+        rows.append(row)
+    return rows
 
 
 # --------------------------------------------------------------- CPU legs ----
@@ -223,15 +278,21 @@ for k in range({n_it}):
     t0 = time.perf_counter()
     X, Z, U = O.admm_step(Y, Z, U, scales, lam, sh[k])
     times.append(time.perf_counter() - t0)
+if {save!r}:
+    np.save({save!r}, O.x_update(Y, Z, U).astype(np.float64))
 print(json.dumps({{"times": times}}))
 """
 
 
-def run_oracle_iters(M, n_it, threads):
+def run_oracle_iters(M, n_it, threads, save=""):
+    """n_it FP64 oracle iterations of the video workload (the benchmark's
+    rank-0 input, same shift-table seed) in a subprocess with `threads` BLAS
+    threads; with `save`, the X-update after the last iteration is written
+    there (.npy)."""
     env = dict(os.environ)
     for v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
         env[v] = str(threads)
-    code = CPU_SNIPPET.format(root=ROOT, M=M, seed=SEED, n_it=n_it)
+    code = CPU_SNIPPET.format(root=ROOT, M=M, seed=SEED, n_it=n_it, save=save)
     r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env,
                        timeout=1800)
     if r.returncode != 0:
@@ -239,13 +300,23 @@ def run_oracle_iters(M, n_it, threads):
     return json.loads(r.stdout.strip().splitlines()[-1])["times"]
 
 
-def cpu_baseline(M):
+PARITY_ITERS = 5
+
+
+def cpu_baseline(M, save):
+    """The oracle timed on the host cores: PARITY_ITERS iterations with every
+    core as BLAS threads (the first one discarded from the timing; its X is
+    the parity leg's reference), and 2 iterations on one core."""
     cores = os.cpu_count() or 1
-    times = run_oracle_iters(M, 3, cores)
+    times = run_oracle_iters(M, PARITY_ITERS, cores, save=save)
     t = sum(times[1:]) / max(1, len(times) - 1)
+    t1 = run_oracle_iters(M, 2, 1)
     return {"value": round(1.0 / t, 4), "unit": "iter/s", "cores": cores, "kind": "oracle",
-            "sample": f"3 FP64 ADMM iterations of the {M}x256 video workload (first discarded), "
-                      f"numpy/LAPACK with {cores} BLAS threads"}
+            "sample": f"{PARITY_ITERS} FP64 ADMM iterations of the {M}x256 video workload (first "
+                      f"discarded), numpy/LAPACK with {cores} BLAS threads",
+            "one_core": {"value": round(1.0 / t1[-1], 4),
+                         "unit": "iter/s", "cores": 1,
+                         "sample": "2 FP64 ADMM iterations (first discarded), 1 BLAS thread"}}
 
 
 def reference_arm(a):
@@ -368,8 +439,18 @@ def ours(a):
     p = B.msllr_params_default()
     p.profile = 1
     pstats = step(p)
-    pk = peaks()
+    pk = peaks(torch.cuda.get_device_properties(dev).multi_processor_count)
     roof, best = kernel_roofline(pstats, scales, M, N, pk)
+    per_scale = scale_rooflines(pstats, scales, M, N, a.iters, pk)
+    t_iter = t_s / (a.steps * a.iters)
+    b_survey, b_layout = (4 * L + 1) * 4 * M * N, (5 * L + 3) * 4 * M * N
+    iteration = {"us": round(t_iter * 1e6, 2),
+                 "bytes_state_form": b_survey, "bytes_this_layout": b_layout,
+                 "hbm_frac_state_form": round(b_survey / t_iter / 1e9 / pk["hbm_gbs"], 4),
+                 "hbm_frac_this_layout": round(b_layout / t_iter / 1e9 / pk["hbm_gbs"], 4)}
+    if roof is not None:
+        roof["per_scale"] = per_scale
+        roof["iteration"] = iteration
 
     # concurrent per-scale segment times (profile mode 2)
     p2 = B.msllr_params_default()
@@ -395,12 +476,30 @@ def ours(a):
            "h2d_bytes_per_step": 4 * M * N, "d2h_bytes_per_step": 4 * L * M * N,
            "steps": e_steps}
 
-    cpu = None
+    cpu, parity = None, None
     if rank == 0 and world == 1 and not a.no_cpu_baseline and a.workload == "video":
+        import tempfile
+        ref_path = os.path.join(tempfile.mkdtemp(prefix="msllr_bench_"), "x_oracle.npy")
         try:
-            cpu = cpu_baseline(a.M)
+            cpu = cpu_baseline(a.M, ref_path)
         except Exception as ex:  # noqa: BLE001
             cpu = {"error": str(ex)[-300:]}
+        if os.path.exists(ref_path):
+            # parity on the timed input: the same job for PARITY_ITERS
+            # iterations on the GPU against the oracle's X after as many
+            Xp = torch.empty((L, M, N), dtype=torch.float32, device=dev)
+            ctx.msllr_decompose(Yd, scales, Xp, iters=PARITY_ITERS, seed=SEED)
+            torch.cuda.synchronize()
+            Xo = np.load(ref_path)
+            Xg = Xp.cpu().numpy().astype(np.float64)
+            floor = 1e-6 * np.linalg.norm(Y32.astype(np.float64))
+            err = [float(np.linalg.norm(Xg[i] - Xo[i]) / max(np.linalg.norm(Xo[i]), floor))
+                   for i in range(L)]
+            parity = {"iters": PARITY_ITERS, "max_relerr": max(err),
+                      "relerr_per_scale": [float(f"{e:.3e}") for e in err], "tol": 1e-4,
+                      "ok": max(err) <= 1e-4,
+                      "reference": "FP64 oracle, same input and shift table"}
+            os.remove(ref_path)
 
     if rank == 0:
         line = {
@@ -428,6 +527,7 @@ def ours(a):
             "uncertified_blocks_last_iter": stats["blocks_uncertified"],
             "clocks": ck,
             "cpu_baseline": cpu,
+            "parity": parity,
         }
         print(json.dumps(line), flush=True)
     ctx.close()

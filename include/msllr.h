@@ -104,7 +104,9 @@ typedef struct msllr_params {
                           scale_nuclear is their mean.                      */
 } msllr_params;
 
-/* Per-run diagnostics, all taken at the last iteration. */
+/* Per-run diagnostics, taken at the last iteration; when params->profile is
+ * set, the block counts (blocks_skipped .. blocks_householder,
+ * blocks_uncertified) and flops are summed over all iterations instead. */
 typedef struct msllr_stats {
   int iters;                                  /* iterations run               */
   int L;                                      /* scales                       */
@@ -133,6 +135,15 @@ typedef struct msllr_stats {
    * outside the kept Ritz pairs) failed at the last iteration; their
    * thresholded rank is taken from the Ritz pairs.  0 in normal runs. */
   long long blocks_uncertified[MSLLR_MAX_SCALES];
+  /* FP32 flops of the block eigen-solve steps that ran, each step counted
+   * at its algorithmic cost (a multiply-add is 2 flops): zero-rank and
+   * deflated Cholesky certificates n^3/3, Lanczos and power steps,
+   * Householder tridiagonalisation 4n^3/3.  `flops`: the fused narrow-block
+   * kernel (its Gram and rebuild included) or the wide-block eigen kernel;
+   * `flops_fallback`: the wide-block Householder fallback kernel.  Blocks up
+   * to 256 wide; 0 for the other paths. */
+  long long flops[MSLLR_MAX_SCALES];
+  long long flops_fallback[MSLLR_MAX_SCALES];
 } msllr_stats;
 
 /* Fill *p with the defaults.  Returns MSLLR_EINVAL if p is NULL. */
@@ -147,8 +158,9 @@ int msllr_create(msllr_ctx** out, int device, size_t hbm_budget_bytes, void* cud
 /* Destroy a context and free everything it holds.  NULL is accepted. */
 int msllr_destroy(msllr_ctx* ctx);
 
-/* Last error message of the context (or of the last context-less call when
- * ctx is NULL).  Valid until the next call on the same context. */
+/* Last error message of the context, or, when ctx is NULL, of the calling
+ * host thread's last failed context-less call.  Valid until the next call on
+ * the same context (or, for NULL, the next context-less call of the thread). */
 const char* msllr_last_error(const msllr_ctx* ctx);
 
 /* Shift table of the random cycle spinning (Sec. 9): for k = 0..iters-1,
@@ -267,7 +279,9 @@ int msllr_poll(msllr_ctx* ctx, uint64_t job_id, int* done);
 
 /* Wait up to timeout_ms (< 0: without limit) for the job, then return its
  * status as msllr_poll does; ETIMEOUT if it has not finished by then (the
- * job stays queued and can be waited for again). */
+ * job stays queued and can be waited for again).  EINVAL for an unknown id,
+ * and when another thread's msllr_poll or msllr_wait collected the job while
+ * this call waited (a job's status is handed out once). */
 int msllr_wait(msllr_ctx* ctx, uint64_t job_id, int timeout_ms);
 
 /* Bytes of the fixed device scratch used by msllr_blocksvt_noalloc. */
@@ -275,16 +289,16 @@ int msllr_wait(msllr_ctx* ctx, uint64_t job_id, int timeout_ms);
 
 /* msllr_blocksvt without any device allocation.  The paper has no
  * counterpart: this entry point exists for callers that cannot call
- * cudaMalloc -- code running while a CUDA graph is being captured (where
- * allocation is not allowed), processes whose device memory is handed out
- * by their own pool and must not be touched by libraries, and loops that
- * cannot afford the device-wide synchronisation cudaMalloc/cudaFree imply.
- * It needs no msllr_ctx.
+ * cudaMalloc -- processes whose device memory is handed out by their own
+ * pool allocator and must not be claimed behind its back by a library, and
+ * loops that cannot afford the device-wide synchronisation that
+ * cudaMalloc/cudaFree imply.  It needs no msllr_ctx.
  *
  * Computes exactly what msllr_blocksvt computes, with the same argument
- * meaning (block sizes that divide the matrix; not the noise scale), on the stream `cuda_stream` (a cudaStream_t, or NULL for the
- * legacy default stream) of the current CUDA device, and returns after
- * that stream has finished the work.  Its workspace is one fixed array of
+ * meaning (block sizes that divide the matrix; not the noise scale), on the
+ * stream `cuda_stream` (a cudaStream_t, or NULL for the legacy default
+ * stream) of the current CUDA device, and returns after that stream has
+ * finished the work.  Its workspace is one fixed array of
  * MSLLR_NOALLOC_SCRATCH_BYTES in device memory that every GPU loading the
  * library holds until the process exits; a call whose workspace would not
  * fit (many or wide blocks; the 1x1 and narrow-block paths need almost
@@ -296,7 +310,7 @@ int msllr_wait(msllr_ctx* ctx, uint64_t job_id, int timeout_ms);
  * scratch array and leaves its contents behind: calls that overlap on the
  * GPU (other host threads, other streams) race and must be serialised by
  * the caller.  Errors: EINVAL, ECUDA; the message is available from
- * msllr_last_error(NULL). */
+ * msllr_last_error(NULL) on the calling thread. */
 int msllr_blocksvt_noalloc(const float* A, float* Z, int M, int N, int ld, int bm, int bn,
                            double tau, int shift_r, int shift_c, int* block_rank_out,
                            void* cuda_stream);

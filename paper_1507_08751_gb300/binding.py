@@ -81,6 +81,8 @@ class Stats(ctypes.Structure):
         ("kernel_launches", (ctypes.c_longlong * MAX_SCALES) * len(KERNEL_KINDS)),
         ("kernel_ms", (ctypes.c_double * MAX_SCALES) * len(KERNEL_KINDS)),
         ("blocks_uncertified", ctypes.c_longlong * MAX_SCALES),
+        ("flops", ctypes.c_longlong * MAX_SCALES),
+        ("flops_fallback", ctypes.c_longlong * MAX_SCALES),
     ]
 
     def to_dict(self):
@@ -102,6 +104,8 @@ class Stats(ctypes.Structure):
                                 for i, k in enumerate(KERNEL_KINDS)},
             "kernel_ms": {k: list(self.kernel_ms[i][:max(L, 1)]) for i, k in enumerate(KERNEL_KINDS)},
             "blocks_uncertified": list(self.blocks_uncertified[:L]),
+            "flops": list(self.flops[:L]),
+            "flops_fallback": list(self.flops_fallback[:L]),
         }
 
 
@@ -198,9 +202,13 @@ def msllr_lambda_default(M, N, m, n):
 def msllr_blocksvt_noalloc(A, Z, bm, bn, tau, shift=(0, 0), rank_out=None, N=None, stream=None):
     """Block SVT without any device allocation (no context needed): same result as
     Context.msllr_blocksvt, using the library's fixed device scratch.  Runs on `stream`
-    (a cudaStream_t handle, or None for the default stream) of the current device."""
+    (a cudaStream_t handle) of the current device; None means torch's current stream,
+    so that the call is ordered after the kernels that produced A."""
     M, ld = A.shape[0], A.shape[1]
     N = ld if N is None else N
+    if stream is None:
+        import torch
+        stream = torch.cuda.current_stream().cuda_stream
     st = ctypes.c_void_p(stream) if stream else None
     _check(lib().msllr_blocksvt_noalloc(_ptr(A), _ptr(Z), M, N, ld, bm, bn, float(tau),
                                         int(shift[0]), int(shift[1]), _ptr(rank_out), st))

@@ -120,6 +120,10 @@ cudaError_t launch_huge(const ScaleLaunch& s, const BigWorkspace& ws, cudaStream
 // Zero the warm-start counts of a scale's workspace (start of a decomposition).
 cudaError_t reset_warm_start(const BigWorkspace& w, int M, int N, int m, int n, cudaStream_t st);
 
+// Streaming multiprocessors of the current device (queried once per device
+// and cached; configure_kernels() primes the cache outside any capture).
+int sm_count();
+
 // Message returned by msllr_last_error(NULL).
 void set_contextless_error(const char* msg);
 

@@ -183,7 +183,7 @@ size_t eig_smem_bytes(int nn) {
 // quotient (a lower bound of lambda_max(G)) already exceeds thr, i.e. the
 // block certainly has a singular value above tau.
 template <class S>
-__device__ bool power_above(S G, int n, float thr, EigScratch& s, LzScratch& z) {
+__device__ bool power_above(S G, int n, float thr, EigScratch& s, LzScratch& z, int* steps) {
   constexpr int NT = kEigThreads;
   const int tid = threadIdx.x;
   float part = 0.f;
@@ -194,7 +194,9 @@ __device__ bool power_above(S G, int n, float thr, EigScratch& s, LzScratch& z) 
   }
   float nrm = sqrtf(block_sum<NT>(part, s.red));
   float rq = 0.f;
+  *steps = 0;
   for (int it = 0; it < 3; ++it) {
+    *steps = it + 1;
     for (int e = tid; e < n; e += NT) z.x[e] /= nrm;
     __syncthreads();
     symv_rows<NT, kEigMax>(G, n, z.x, z.w);
@@ -266,6 +268,7 @@ eig_big_kernel(ScaleLaunch a, const float* __restrict__ Gall, BigWorkspace ws) {
   tr = block_sum<NT>(tr, s.red);
   const float rs = gershgorin_lower<NT, NMAX>(Gacc, nn, z.x, z.w, s.red);
   const float gbound = fminf(tr, rs);
+  double fl = nn + fl_symv(nn);  // trace, Gershgorin row sums
   const bool full = (a.m == a.M && a.n == a.N);
   const int kwarm = (a.warm_start && (full || !a.shift)) ? min(ws.kwarm[b], kLzMaxK) : 0;
   bool skipped = false, lanczos_ok = false;
@@ -284,7 +287,11 @@ eig_big_kernel(ScaleLaunch a, const float* __restrict__ Gall, BigWorkspace ws) {
         k = 0;
         break;
       }
-      if (kwarm > 0 || power_above(Gacc, nn, thr, s, z)) continue;
+      if (kwarm > 0) continue;
+      int psteps = 0;
+      const bool above = power_above(Gacc, nn, thr, s, z, &psteps);
+      fl += psteps * (fl_symv(nn) + 4.0 * nn);
+      if (above) continue;
       // certified lambda_max(G) < tau^2 by Cholesky of (tau^2 - margin) I - G
       c0 = thr - (float)n8 * (float)n8 * FLT_EPSILON * (thr + gbound);
       if (!(c0 > 0.f)) continue;
@@ -292,13 +299,17 @@ eig_big_kernel(ScaleLaunch a, const float* __restrict__ Gall, BigWorkspace ws) {
     } else {
       PHASE(3, 1);
       const float* warm = ws.warm + (size_t)b * kLzMaxK * nn;
+      int J = 0;
       kk = lanczos_candidates<NT, NMAX>(Gacc, nn, thr, gbound, Qs,
                                                         min(nn, kLzMaxJ), U, warm, kwarm,
                                                         0x1234567u + 977u * b, s, z, panel, &ku,
-                                                        &c0, 4);
+                                                        &c0, 4, &J);
+      fl += fl_lanczos(nn, J, ku);
       PHASE(3, 5);
       if (kk < 0) break;
+      fl += fl_deflate(nn, ku);
     }
+    fl += fl_chol(nn);
     const bool pd = regchol_pd<NT, NMAX>(Gacc, nn, c0, attempt == 1, panel, panel + 8 * n8,
                                          attempt == 1 ? ku : 0, panel + 16 * n8, s.red,
                                          3 + attempt);
@@ -324,6 +335,7 @@ eig_big_kernel(ScaleLaunch a, const float* __restrict__ Gall, BigWorkspace ws) {
     }
   }
   if (tid == 0) {
+    if (a.cnt) atomicAdd(a.cnt + 5, (unsigned long long)fl);
     // k < 0: not settled here; eig_fallback_kernel takes the block
     ws.k[b] = k;
     if (k < 0) {
@@ -396,6 +408,7 @@ __device__ __forceinline__ void eig_fallback_block(const ScaleLaunch& a, const f
     if (a.cnt) {
       if (k == 0) atomicAdd(a.cnt + 1, 1ull);
       atomicAdd(a.cnt + 3, 1ull);
+      atomicAdd(a.cnt + 6, (unsigned long long)fl_householder(nn, k));
     }
     if (a.nuc_acc && k > 0) {
       double t = 0.0;
@@ -636,6 +649,7 @@ cudaError_t reset_warm_start(const BigWorkspace& w, int M, int N, int m, int n, 
 }
 
 cudaError_t configure_big_kernels() {
+  sm_count();  // cache the SM count outside any stream capture
   cudaError_t e = cudaFuncSetAttribute(eig_big_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)eig_smem_bytes(kEigMax));
   if (e != cudaSuccess) return e;
@@ -690,7 +704,8 @@ cudaError_t launch_big(const ScaleLaunch& s, const BigWorkspace& ws, cudaStream_
   PROF_AFTER()
   PROF_BEFORE(KK_REBUILD)
   const int slab_items = slabs * d.nblocks;
-  const int reb_grid = s.skip_bound ? (slab_items < 152 ? slab_items : 152) : slab_items;
+  const int nsm = sm_count();
+  const int reb_grid = s.skip_bound ? (slab_items < nsm ? slab_items : nsm) : slab_items;
   rebuild_kernel<<<reb_grid, kRebThreads, smem, st>>>(s, ws.Y, ws.ystride, ws.k, rs, slabs,
                                                       d.nblocks);
   PROF_AFTER()

@@ -70,8 +70,9 @@ HugeDims huge_dims(int M, int N, int m, int n) {
   d.ntiles = d.T * (d.T + 1) / 2;
   // row chunks: enough CTAs for two waves of 5 per SM, chunks of >= 256 rows
   d.chunk_rows = 256;
+  const long long waves = 10LL * sm_count();
   while (d.chunk_rows < d.mm &&
-         (long long)d.ntiles * d.nblocks * ((d.mm + 2 * d.chunk_rows - 1) / (2 * d.chunk_rows)) >= 1520)
+         (long long)d.ntiles * d.nblocks * ((d.mm + 2 * d.chunk_rows - 1) / (2 * d.chunk_rows)) >= waves)
     d.chunk_rows *= 2;
   d.chunks = (d.mm + d.chunk_rows - 1) / d.chunk_rows;
   return d;

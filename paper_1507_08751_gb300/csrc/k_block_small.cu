@@ -142,8 +142,10 @@ blocksvt_small_kernel(ScaleLaunch a) {
   int k = 0;
   bool skipped = false;
   float gbound = fro;  // trace(G) >= lambda_max(G)
+  float fl = 0.f;      // flops of the steps run (see fl_symv in lanczos.cuh)
   if (a.skip_bound && fro <= thr) skipped = true;
   if (!skipped) {
+    fl += (float)(mm * nn * (nn + 1));  // lower triangle of G
     if ((nn & 3) == 0) {
       // 4x4 register tiles of the lower triangle: per row of C one 128-bit
       // load for the tile's rows and one for its columns, 16 FMAs
@@ -199,6 +201,7 @@ blocksvt_small_kernel(ScaleLaunch a) {
       rs = block_max<NT>(rs, s.red);
       if constexpr (NT == 32) __syncwarp();
       gbound = fminf(gbound, rs);
+      fl += (float)fl_symv(nn);
       if (rs <= thr) {
         skipped = true;
       } else {
@@ -220,13 +223,17 @@ blocksvt_small_kernel(ScaleLaunch a) {
     if (attempt == 0) {
       if (!(c_skip > 0.f)) continue;
     } else if constexpr (kAttempts == 2) {
+      int J = 0;
       kk = lanczos_candidates<NT, NMAX>(LowerFull{G, ldg}, nn, thr, gbound, Qs,
                                         nn < JCAP ? nn : JCAP, Us, nullptr, 0,
                                         0x51ED27u + 131u * blockIdx.x, s, z, panel, &ku, &c0,
-                                        5 + SLOT);
+                                        5 + SLOT, &J);
+      fl += (float)fl_lanczos(nn, J, ku);
       PHASE(SLOT, 10);
       if (kk < 0) break;
+      fl += (float)fl_deflate(nn, ku);
     }
+    fl += (float)fl_chol(nn);
     const bool pd = regchol_pd<NT, NMAX>(LowerFull{G, ldg}, nn, c0, attempt == 1, panel,
                                          panel + 8 * n8, attempt == 1 ? ku : 0, panel + 16 * n8,
                                          s.red, attempt == 1 ? 5 + SLOT : -1);
@@ -247,6 +254,7 @@ blocksvt_small_kernel(ScaleLaunch a) {
     k = top_eigenvalues<NT>(nn, thr, s, &tn);
     PHASE(SLOT, 4);
     if (k > 0) top_eigenvectors<NT, NMAX>(Gacc, nn, k, tn, s, Y, ldy, SLOT);
+    fl += (float)fl_householder(nn, k);
     PHASE(SLOT, 5);
   }
   const bool transposed = g.transposed();
@@ -260,6 +268,7 @@ blocksvt_small_kernel(ScaleLaunch a) {
     if (tid == 0) {
       if (a.rank_out) a.rank_out[blockIdx.x] = 0;
       if (a.cnt) {
+        if (fl > 0.f) atomicAdd(a.cnt + 5, (unsigned long long)fl);
         if (skipped) atomicAdd(a.cnt, 1ull);
         atomicAdd(a.cnt + 1, 1ull);
         if (lanczos_ok) atomicAdd(a.cnt + 2, 1ull);
@@ -301,6 +310,7 @@ blocksvt_small_kernel(ScaleLaunch a) {
   if (tid == 0) {
     if (a.rank_out) a.rank_out[blockIdx.x] = k;
     if (a.cnt) {
+      atomicAdd(a.cnt + 5, (unsigned long long)(fl + 4.f * (float)(mm * nn * k)));  // + rebuild
       if (lanczos_ok) atomicAdd(a.cnt + 2, 1ull);
       else atomicAdd(a.cnt + 3, 1ull);
     }

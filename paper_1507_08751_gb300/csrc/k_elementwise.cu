@@ -16,14 +16,32 @@
 
 namespace msllr {
 
+int sm_count() {
+  static int cache[64] = {};
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) {
+    cudaGetLastError();
+    return 152;
+  }
+  if (!cache[dev]) {
+    int n = 0;
+    if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n <= 0) {
+      cudaGetLastError();
+      return 152;
+    }
+    cache[dev] = n;
+  }
+  return cache[dev];
+}
+
 namespace {
 
 constexpr int kEwThreads = 256;
 
 int ew_grid(size_t n_items) {
-  // enough CTAs for 8 resident per SM on 152 SMs; grid-stride beyond that
+  // enough CTAs for 8 resident per SM; grid-stride beyond that
   size_t g = (n_items + kEwThreads - 1) / kEwThreads;
-  const size_t cap = 152 * 8;
+  const size_t cap = (size_t)sm_count() * 8;
   return (int)(g < cap ? (g > 0 ? g : 1) : cap);
 }
 

@@ -34,6 +34,23 @@ namespace msllr {
 constexpr int kLzMaxJ = 32;  // Lanczos steps
 constexpr int kLzMaxK = 8;   // Ritz pairs kept (above 0.95 tau^2)
 
+// FP32 flops of the eigen-solve steps, each counted at its algorithmic cost
+// (a multiply-add is 2 flops); the kernels add them up per block so that the
+// ALU roofline follows the steps that actually ran.
+__device__ __forceinline__ double fl_symv(int n) { return 2.0 * n * n; }
+__device__ __forceinline__ double fl_chol(int n) { return (double)n * n * n / 3.0; }
+// J Lanczos steps (matrix-vector product plus two Gram-Schmidt passes over
+// j + 1 vectors), U = Q_J Y, W = G U for 8 vectors, B = U^T W
+__device__ __forceinline__ double fl_lanczos(int n, int J, int ku) {
+  return 2.0 * n * n * J + 4.0 * n * J * (J + 1) + 2.0 * n * J * ku + 16.0 * n * n + 16.0 * n * ku;
+}
+// the rank-2k deflation G - U What^T - What U^T on the lower triangle
+__device__ __forceinline__ double fl_deflate(int n, int ku) { return 2.0 * ku * n * n; }
+// Householder tridiagonalisation, back-transformation of k eigenvectors
+__device__ __forceinline__ double fl_householder(int n, int k) {
+  return 4.0 * n * n * n / 3.0 + 2.0 * n * n * k;
+}
+
 // leading dimension of the Lanczos basis in shared memory: padded for the
 // thread-per-coefficient projection of small blocks
 template <int NMAX>
@@ -395,7 +412,8 @@ __device__ float gershgorin_lower(S A, int n, float* ones, float* sums, float* r
 // above thr) with s.lam[0..k), the vectors in U's columns 0..k-1 (U holds
 // ku >= k kept pairs, *ku_out = ku), U and What = W - U sym(B) / 2 staged at
 // panel and panel + 8 n8 (n8 = roundup(n, 8)) and the certificate shift
-// in *c0_out: the pairs are certified iff
+// in *c0_out (and, if J_out is given, the Lanczos steps run in *J_out):
+// the pairs are certified iff
 //   regchol_pd<NT, NMAX>(G, n, *c0_out, true, panel, panel + 8 n8, ku,
 //                        panel + 16 n8, red)
 // holds (one call site per kernel keeps the code size and the register
@@ -405,7 +423,8 @@ template <int NT, int NMAX, class SG>
 __device__ int lanczos_candidates(SG Gs, int n, float thr, float gbound, float* Q, int jmax,
                                   float* U, const float* warm, int kwarm,
                                   uint32_t seed, EigScratch& s, LzScratch& z, float* panel,
-                                  int* ku_out, float* c0_out, int slot = -1) {
+                                  int* ku_out, float* c0_out, int slot = -1,
+                                  int* J_out = nullptr) {
   constexpr int NW = NT / 32;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   PHASE_INIT();
@@ -464,7 +483,10 @@ __device__ int lanczos_candidates(SG Gs, int n, float thr, float gbound, float* 
       // converged when every kept Ritz pair has |beta_J * y_{J-1}| small
       k = lz_ritz<NT>(J, thr_keep, s, z, &tn);
       PHASE(slot, 11);
-      if (k > kLzMaxK) return -1;
+      if (k > kLzMaxK) {
+      if (J_out) *J_out = J;
+      return -1;
+    }
       bool conv = true;
       const float bJ = z.beta[J - 1];
       for (int q = 0; q < k; ++q)
@@ -475,7 +497,10 @@ __device__ int lanczos_candidates(SG Gs, int n, float thr, float gbound, float* 
   }
   if (k < 0) {
     k = lz_ritz<NT>(J, thr_keep, s, z, &tn);
-    if (k > kLzMaxK) return -1;
+    if (k > kLzMaxK) {
+      if (J_out) *J_out = J;
+      return -1;
+    }
   }
   const int ku = k;
   // U = Q_J Y (n x ku) into the caller's U and, row-major n x 8 with zero
@@ -545,10 +570,16 @@ __device__ int lanczos_candidates(SG Gs, int n, float thr, float gbound, float* 
   for (int q = 0; q < ku; ++q) {
     const float th = z.Bm[q * kLzMaxK + q];
     kk += th > thr;
-    if (q > 0 && th > thr && !(z.Bm[(q - 1) * kLzMaxK + (q - 1)] > thr)) return -1;
+    if (q > 0 && th > thr && !(z.Bm[(q - 1) * kLzMaxK + (q - 1)] > thr)) {
+      if (J_out) *J_out = J;
+      return -1;
+    }
   }
   const float c0 = thr - 2.f * rho - 8.f * (float)(ku + 1) * FLT_EPSILON * gbound;
-  if (!(c0 > 0.f)) return -1;
+  if (!(c0 > 0.f)) {
+      if (J_out) *J_out = J;
+      return -1;
+    }
   __syncthreads();
   if (tid < ku) s.lam[tid] = z.Bm[tid * kLzMaxK + tid];
   // P G P = G - U What^T - What U^T with What = W - U sym(B) / 2, staged in
@@ -572,6 +603,7 @@ __device__ int lanczos_candidates(SG Gs, int n, float thr, float gbound, float* 
   PHASE(slot, 11);
   *ku_out = ku;
   *c0_out = c0;
+  if (J_out) *J_out = J;
   return kk;
 }
 

@@ -25,7 +25,9 @@ using namespace msllr;
 
 namespace {
 
-std::string g_last_error = "";  // for calls made without a context
+// message of the last failed call made without a context, one per host
+// thread (msllr_last_error(NULL) reads the calling thread's copy)
+thread_local std::string g_last_error;
 
 }  // namespace
 
@@ -483,7 +485,8 @@ int enqueue_iteration(msllr_ctx* ctx, const Layout& lay, int M, int N, int L, co
       s.warm_start = 1;
       s.rank_out = nullptr;
       s.nuc_acc = stats ? ctx->d_acc + i : nullptr;
-      s.cnt = stats ? ctx->d_cnt + 8 * i : nullptr;
+      // block counts: the last iteration, or every iteration of a profiled run
+      s.cnt = (stats || p.profile) ? ctx->d_cnt + 8 * i : nullptr;
       s.norm_acc = ctx->d_noise + i;
       prof->scale = i;
       const bool gate = fork && wide && i > 0;
@@ -688,6 +691,8 @@ int decompose_device(msllr_ctx* ctx, const float* Y, int M, int N, int ld, int L
       stats->blocks_lanczos[i] = (long long)cnt[8 * i + 2];
       stats->blocks_householder[i] = (long long)cnt[8 * i + 3];
       stats->blocks_uncertified[i] = (long long)cnt[8 * i + 4];
+      stats->flops[i] = (long long)cnt[8 * i + 5];
+      stats->flops_fallback[i] = (long long)cnt[8 * i + 6];
       stats->lambda[i] = lam[i];
     }
     stats->objective = obj;
@@ -946,7 +951,12 @@ int msllr_wait(msllr_ctx* ctx, uint64_t job_id, int timeout_ms) {
   } else if (!ctx->done_cv.wait_for(lk, std::chrono::milliseconds(timeout_ms), ready)) {
     return fail(ctx, MSLLR_ETIMEOUT, "msllr_wait: job not finished within the timeout");
   }
-  return collect(ctx, ctx->jobs.find(job_id));
+  // another thread's msllr_poll or msllr_wait may have collected the job
+  // while this one slept
+  auto again = ctx->jobs.find(job_id);
+  if (again == ctx->jobs.end())
+    return fail(ctx, MSLLR_EINVAL, "msllr_wait: job already collected by another call");
+  return collect(ctx, again);
 }
 
 }  // extern "C"

@@ -79,3 +79,13 @@ def test_create_without_device_fails_loudly(built):
     with pytest.raises(B.MsllrError) as e:
         B.Context(0)
     assert e.value.code == B.MSLLR_EINVAL
+
+
+def test_stats_struct_matches_header_field_order():
+    """The ctypes mirror lists the header's msllr_stats fields in order."""
+    src = open(os.path.join(ROOT, "include", "msllr.h")).read()
+    body = src[src.index("typedef struct msllr_stats"):src.index("} msllr_stats;")]
+    body = re.sub(r"/\*.*?\*/", "", body, flags=re.S)
+    names = re.findall(r"^\s+(?:long long|int|double)\s+(\w+)", body, re.M)
+    mirror = [f[0].rstrip("_") for f in B.Stats._fields_]
+    assert names == mirror

@@ -94,6 +94,21 @@ def test_lambda_endpoints_paper_text():
     assert full - (math.sqrt(M) + math.sqrt(N)) == pytest.approx(math.sqrt(math.log(N)))
 
 
+def test_lambda_area_hand_values():
+    """The area form of eq:lambda that the 64x64 workload specifies,
+    sqrt(m) + sqrt(n) + sqrt(log(64^2 / (m n))), at values worked by hand:
+    1x1: 2 + sqrt(12 ln 2) = 4.8840538;  4x4: 4 + sqrt(8 ln 2) = 6.3548200;
+    16x16: 8 + sqrt(4 ln 2) = 9.6651092;  64x64: the log term vanishes, 16.
+    The paper's form (log of MN / max(m, n)) differs at 4x4 (4 + sqrt(10 ln 2)
+    = 6.6327688); a max() in place of the area would give that value here."""
+    want = {(1, 1): 4.8840538, (4, 4): 6.3548200, (16, 16): 9.6651092, (64, 64): 16.0}
+    for (m, n), v in want.items():
+        assert O.lambda_area(64, 64, m, n) == pytest.approx(v, abs=5e-7), (m, n)
+    assert O.lambda_default(64, 64, 4, 4) == pytest.approx(6.6327688, abs=5e-7)
+    # non-square blocks: 2x8 of a 64x64 matrix, area 16 like 4x4
+    assert O.lambda_area(64, 64, 2, 8) == pytest.approx(1.4142136 + 2.8284271 + 2.3548200, abs=5e-7)
+
+
 # ------------------------------------------------------------------- SVT ----
 
 @pytest.mark.parametrize("shape", [(6, 6), (9, 4), (3, 11), (16, 16)])

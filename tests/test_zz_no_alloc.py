@@ -1,7 +1,7 @@
 """msllr_blocksvt_noalloc: the block SVT for callers that cannot allocate
-device memory (work captured into a CUDA graph, processes whose device
-memory belongs to their own pool, loops that cannot take cudaMalloc's
-device-wide synchronisation).  It must give what msllr_blocksvt gives,
+device memory (processes whose device memory is handed out by their own pool
+allocator, loops that cannot take cudaMalloc's device-wide
+synchronisation).  It must give what msllr_blocksvt gives,
 call after call, although every call reuses the same fixed device scratch.
 
 Collected last on purpose, and self-contained: it loads the library and
@@ -72,3 +72,24 @@ def test_noalloc_rejects_workspace_beyond_the_fixed_scratch():
         B.msllr_blocksvt_noalloc(A, Z, 256, 256, 1.0)
     assert e.value.code == B.MSLLR_EINVAL
     assert "scratch" in str(e.value)
+
+
+def test_noalloc_takes_no_device_memory():
+    """After a first call (which sets the device up and loads the kernels it
+    uses), further calls leave the device's free memory exactly as it was:
+    the call claims nothing beyond the library's fixed scratch."""
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    from paper_1507_08751_gb300 import binding as B
+    B.lib()
+    M, N, m, n = 1024, 256, 256, 256
+    A = _matrix(7, M, N, m, n)
+    Z = torch.empty_like(A)
+    r = torch.empty(((M // m) * (N // n),), dtype=torch.int32, device="cuda")
+    B.msllr_blocksvt_noalloc(A, Z, m, n, 5.0, (3, 4), rank_out=r)
+    torch.cuda.synchronize()
+    free0 = torch.cuda.mem_get_info()[0]
+    for call in range(3):
+        B.msllr_blocksvt_noalloc(A, Z, m, n, 5.0 + call, (3 + call, 4), rank_out=r)
+    torch.cuda.synchronize()
+    assert torch.cuda.mem_get_info()[0] == free0
