@@ -45,6 +45,8 @@ def parse():
     ap.add_argument("--iters", type=int, default=ITERS_DEF)
     ap.add_argument("--M", type=int, default=M_DEF)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-plain", action="store_true",
+                    help="skip timing the plain one-launch-per-block comparator")
     ap.add_argument("--spin-grid", type=int, default=0,
                     help="averaged cycle spinning (Sec. 9) over a g x g shift lattice per scale")
     ap.add_argument("--serve-jobs", type=int, default=24)
@@ -301,6 +303,7 @@ def run_oracle_iters(M, n_it, threads, save=""):
 
 
 PARITY_ITERS = 5
+PLAIN_ITERS = 2
 
 
 def cpu_baseline(M, save):
@@ -459,6 +462,26 @@ def ours(a):
     seg = {f"{m}x{n}": round(max(cstats["kernel_ms"]["eig_big"][i], cstats["kernel_ms"]["fused_small"][i])
                              / a.iters * 1e3, 1) for i, (m, n) in enumerate(scales)}
 
+    # the plain FP32 comparator on the same job: one launch per block (Gram,
+    # cyclic Jacobi, threshold, rebuild), no bound, no graph; one warm-up
+    # iteration, then PLAIN_ITERS timed iterations
+    plain = None
+    if a.workload == "video" and a.spin_grid <= 1 and not a.no_plain:
+        pp = B.msllr_params_default()
+        pp.plain = 1
+        ctx.msllr_decompose(Yd, scales, X, iters=1, seed=SEED, params=pp)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        pst = ctx.msllr_decompose(Yd, scales, X, iters=PLAIN_ITERS, seed=SEED, params=pp)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        t_plain = e0.elapsed_time(e1) / 1e3
+        plain = {"value": round(PLAIN_ITERS / t_plain, 4), "unit": "iter/s",
+                 "iters": PLAIN_ITERS, "launches_per_iter": pst["launches"] // PLAIN_ITERS,
+                 "speedup": round(value / world / (PLAIN_ITERS / t_plain), 1),
+                 "form": "plain FP32, one launch per block: Gram, cyclic Jacobi, threshold, "
+                         "rebuild; no bound, no certificate, no CUDA graph"}
+
     # end to end through the host API: pinned host Y in, X out, copies timed
     Yh = torch.from_numpy(Y32).pin_memory()
     Xh = torch.empty((L, M, N), dtype=torch.float32).pin_memory()
@@ -528,6 +551,7 @@ def ours(a):
             "clocks": ck,
             "cpu_baseline": cpu,
             "parity": parity,
+            "plain": plain,
         }
         print(json.dumps(line), flush=True)
     ctx.close()

@@ -102,6 +102,14 @@ typedef struct msllr_params {
                           g_r g_c block SVTs per scale and iteration; block
                           counts in msllr_stats add up over the shifts and
                           scale_nuclear is their mean.                      */
+  int plain;           /* 1: the plain FP32 comparator path, for measurement:
+                          every block of every scale is solved by its own
+                          kernel launch (one CTA: Gram matrix, cyclic Jacobi
+                          eigen-decomposition, threshold, rebuild), with no
+                          skip bound, no certificate, no CUDA graph and no
+                          concurrent scales; the 1x1 and noise scales are one
+                          element-wise launch each.  Blocks up to 256 wide;
+                          not with spin_grid > 1 (EINVAL).  Default 0.      */
 } msllr_params;
 
 /* Per-run diagnostics, taken at the last iteration; when params->profile is

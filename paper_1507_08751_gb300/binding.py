@@ -61,6 +61,7 @@ class Params(ctypes.Structure):
         ("U_out", ctypes.c_void_p),
         ("profile", ctypes.c_int),
         ("spin_grid", ctypes.c_int),
+        ("plain", ctypes.c_int),
     ]
 
 

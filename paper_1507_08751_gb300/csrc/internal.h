@@ -124,6 +124,13 @@ cudaError_t reset_warm_start(const BigWorkspace& w, int M, int N, int m, int n, 
 // and cached; configure_kernels() primes the cache outside any capture).
 int sm_count();
 
+// The plain one-block-per-launch comparator (k_plain.cu): global scratch a
+// scale needs (0 when the block fits shared memory), kernel attributes, and
+// the per-scale launcher (one launch per block).
+size_t plain_scratch_bytes(int m, int n);
+cudaError_t configure_plain_kernels();
+cudaError_t launch_plain(const ScaleLaunch& s, float* scratch, cudaStream_t st, Prof* prof);
+
 // Message returned by msllr_last_error(NULL).
 void set_contextless_error(const char* msg);
 

@@ -355,6 +355,8 @@ cudaError_t configure_kernels() {
   e = cudaFuncSetAttribute(blocksvt_small_kernel<128, 64>,
                            cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
   if (e != cudaSuccess) return e;
+  e = configure_plain_kernels();
+  if (e != cudaSuccess) return e;
   return configure_big_kernels();
 }
 

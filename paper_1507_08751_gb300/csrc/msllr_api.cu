@@ -395,13 +395,14 @@ struct Layout {
   float* R;
   float* Yd;
   uint8_t* mask;
+  float* plain;  // scratch of the plain comparator path, or null
   std::vector<BigWorkspace> big;
   size_t total;
 };
 
 // Offsets of every buffer inside the workspace (base may be null to size it).
 Layout plan(void* base, int M, int N, int L, const int* bm, const int* bn, bool masked,
-            bool spin) {
+            bool spin, bool plain = false) {
   Layout lay;
   lay.MN = (size_t)M * N;
   char* b = (char*)base;
@@ -417,6 +418,17 @@ Layout plan(void* base, int M, int N, int L, const int* bm, const int* bn, bool 
   lay.T = spin ? (float*)take(sizeof(float) * L * lay.MN) : nullptr;
   lay.Yd = (float*)take(sizeof(float) * lay.MN);
   lay.mask = masked ? (uint8_t*)take(lay.MN) : nullptr;
+  lay.plain = nullptr;
+  if (plain) {
+    size_t need = 0;
+    for (int i = 0; i < L; ++i) {
+      const size_t b = plain_scratch_bytes(bm[i], bn[i]);
+      need = b > need ? b : need;
+    }
+    if (need) lay.plain = (float*)take(need);
+    lay.total = off + 256;
+    return lay;  // the plain path holds no wide-block workspace
+  }
   for (int i = 0; i < L; ++i) {
     const size_t bytes = big_workspace_bytes(M, N, bm[i], bn[i]);
     char* p = take(bytes);
@@ -448,6 +460,30 @@ int enqueue_iteration(msllr_ctx* ctx, const Layout& lay, int M, int N, int L, co
                       Prof* prof) {
   CK(launch_advance(ctx->d_table, ctx->d_small, ctx->d_small + 1, ctx->stream, prof));
   CK(launch_consensus(lay.Yd, lay.W, lay.R, lay.mask, L, lay.MN, ctx->stream, prof));
+  if (p.plain) {
+    // the comparator: scales one after the other on the context stream, one
+    // launch per block
+    for (int i = 0; i < L; ++i) {
+      ScaleLaunch s{};
+      s.A1 = lay.Z + (size_t)i * lay.MN;
+      s.A2 = lay.R;
+      s.Zout = lay.Z + (size_t)i * lay.MN;
+      s.Wout = lay.W + (size_t)i * lay.MN;
+      s.M = M;
+      s.N = N;
+      s.ld = N;
+      s.m = bm[i];
+      s.n = bn[i];
+      s.shift = p.cycle_spin ? ctx->d_small + 1 : nullptr;
+      s.tau = taus[i];
+      s.nuc_acc = stats ? ctx->d_acc + i : nullptr;
+      s.cnt = (stats || p.profile) ? ctx->d_cnt + 8 * i : nullptr;
+      s.norm_acc = ctx->d_noise + i;
+      prof->scale = i;
+      CK(launch_plain(s, lay.plain, ctx->stream, prof));
+    }
+    return MSLLR_OK;
+  }
   // fork: scale i > 0 runs on its own stream, scale 0 on the context stream.
   // When kernels are timed one by one (profile), everything stays on the
   // context stream so that each event pair brackets one kernel running alone.
@@ -547,6 +583,11 @@ int decompose_device(msllr_ctx* ctx, const float* Y, int M, int N, int ld, int L
   if (params) p = *params;
   if (p.iter_offset < 0) return fail(ctx, MSLLR_EINVAL, "iter_offset must be >= 0");
   if (p.spin_grid < 0) return fail(ctx, MSLLR_EINVAL, "spin_grid must be >= 0");
+  if (p.plain && p.spin_grid > 1)
+    return fail(ctx, MSLLR_EINVAL, "the plain comparator path takes no spin_grid");
+  for (int i = 0; i < L && p.plain; ++i)
+    if (choose_path(bm[i], bn[i]) == ScalePath::Huge)
+      return fail(ctx, MSLLR_EINVAL, "the plain comparator path takes blocks up to 256 wide");
   for (int i = 0; i < L && p.spin_grid > 1; ++i) {
     const int m = bm[i], n = bn[i];
     if (m <= 0 || n <= 0) continue;
@@ -556,8 +597,8 @@ int decompose_device(msllr_ctx* ctx, const float* Y, int M, int N, int ld, int L
   }
   Prof prof;
   prof.timing = p.profile != 0;
-  prof.per_scale = p.profile == 2;
-  if (p.profile) p.use_graph = 0;
+  prof.per_scale = p.profile == 2 && !p.plain;
+  if (p.profile || p.plain) p.use_graph = 0;
   struct EventPool {
     Prof* pr;
     ~EventPool() {
@@ -575,9 +616,9 @@ int decompose_device(msllr_ctx* ctx, const float* Y, int M, int N, int ld, int L
   }
   CK(cudaSetDevice(ctx->device));
   const bool spin = p.spin_grid > 1;
-  const Layout sizing = plan(nullptr, M, N, L, bm, bn, mask != nullptr, spin);
+  const Layout sizing = plan(nullptr, M, N, L, bm, bn, mask != nullptr, spin, p.plain != 0);
   if (int r = ensure_ws(ctx, sizing.total)) return r;
-  const Layout lay = plan(ctx->ws, M, N, L, bm, bn, mask != nullptr, spin);
+  const Layout lay = plan(ctx->ws, M, N, L, bm, bn, mask != nullptr, spin, p.plain != 0);
   cudaStream_t st = ctx->stream;
 
   // inputs: finiteness check, dense copies
@@ -610,7 +651,7 @@ int decompose_device(msllr_ctx* ctx, const float* Y, int M, int N, int ld, int L
   CK(cudaMemcpyAsync(ctx->d_table, h_table.data(), tab * sizeof(int), cudaMemcpyHostToDevice, st));
   CK(cudaMemsetAsync(ctx->d_small, 0, sizeof(int), st));
   CK(launch_init_state(p.Z_init, p.U_init, lay.Z, lay.W, L, lay.MN, st, &prof));
-  for (int i = 0; i < L; ++i) CK(reset_warm_start(lay.big[i], M, N, bm[i], bn[i], st));
+  for (int i = 0; i < L && !p.plain; ++i) CK(reset_warm_start(lay.big[i], M, N, bm[i], bn[i], st));
   CK(cudaMemsetAsync(ctx->d_acc, 0, (MSLLR_MAX_SCALES + 8) * sizeof(double), st));
   CK(cudaMemsetAsync(ctx->d_cnt, 0, 8 * MSLLR_MAX_SCALES * sizeof(unsigned long long), st));
 
@@ -884,7 +925,9 @@ int msllr_submit(msllr_ctx* ctx, const msllr_job* job, uint64_t* job_id) {
   // the context's HBM budget
   const size_t MN = (size_t)M * N;
   const bool spin = job->params && job->params->spin_grid > 1;
-  const size_t need = plan(nullptr, M, N, L, job->block_m, job->block_n, job->mask != nullptr, spin).total +
+  const bool plain = job->params && job->params->plain;
+  const size_t need = plan(nullptr, M, N, L, job->block_m, job->block_n, job->mask != nullptr, spin,
+                           plain).total +
                       sizeof(float) * MN * (1 + (size_t)L * (job->Z_out ? 2 : 1)) +
                       (job->mask ? MN : 0);
   if (ctx->budget && need > ctx->budget)

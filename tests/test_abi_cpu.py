@@ -60,7 +60,7 @@ def test_params_default(built):
     p = B.msllr_params_default()
     assert (p.skip_bound, p.cycle_spin, p.use_graph, p.iter_offset) == (1, 1, 1, 0)
     assert not p.Z_init and not p.U_init and not p.U_out
-    assert p.profile == 0 and p.spin_grid == 0
+    assert p.profile == 0 and p.spin_grid == 0 and p.plain == 0
 
 
 def test_params_struct_matches_header_field_order():

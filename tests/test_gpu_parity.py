@@ -387,6 +387,42 @@ def test_full_size_video_matches_oracle_over_30_iterations(ctx):
     np.testing.assert_allclose(X.sum(0), Y32, atol=2e-4 * np.abs(Y32).max())
 
 
+def test_plain_comparator_matches_oracle_and_the_optimised_path(ctx):
+    """The plain FP32 comparator (msllr_params.plain: one launch per block,
+    Gram + cyclic Jacobi, no bound, no certificate) on the 64x64 workload
+    (500 iterations) and on a 1024 x 256 video input with the video scales
+    (its 256-wide blocks keep their Jacobi state in global scratch), against
+    the FP64 oracle and against the optimised path."""
+    from paper_1507_08751_gb300 import binding as B
+    p = B.msllr_params_default()
+    p.plain = 1
+    Y, comps, scales = synth.tiny_64()
+    Y32 = Y.astype(np.float32)
+    M, N = Y32.shape
+    lam = [O.lambda_area(M, N, m, n) for m, n in scales]
+    X, Z, stats = _run_decompose(ctx, Y32, scales, lam, 500, 1507087510, params=p)
+    ref = O.admm(Y32.astype(np.float64), scales, lam, 1.0, 500,
+                 shifts=O.shift_table(1507087510, 500, M, N))
+    assert np.all(O.relerr(X, ref["X"], Y32) <= TOL)
+    assert np.all(O.relerr(Z, ref["Z"], Y32) <= TOL)
+    nblocks = sum((M // m) * (N // n) for m, n in scales[1:])
+    assert stats["launches"] >= 500 * nblocks  # one launch per block and iteration
+    Y32, comps, scales = synth.video(M=1024, N=256)
+    M, N = Y32.shape
+    lam = [O.lambda_default(M, N, m, n) for m, n in scales]
+    iters, seed = 6, 99
+    Xp, _, _ = _run_decompose(ctx, Y32, scales, lam, iters, seed, params=p)
+    Xo, _, _ = _run_decompose(ctx, Y32, scales, lam, iters, seed)
+    ref = O.admm(Y32.astype(np.float64), scales, lam, 1.0, iters,
+                 shifts=O.shift_table(seed, iters, M, N))
+    assert np.all(O.relerr(Xp, ref["X"], Y32) <= TOL)
+    assert np.all(O.relerr(Xp, Xo, Y32) <= 2 * TOL)
+    p.spin_grid = 2
+    with pytest.raises(B.MsllrError) as e:
+        _run_decompose(ctx, Y32, scales, lam, 1, 0, params=p)
+    assert e.value.code == B.MSLLR_EINVAL
+
+
 def test_error_paths(ctx):
     from paper_1507_08751_gb300 import binding as B
     Y = torch.zeros((64, 64), dtype=torch.float32, device="cuda")
