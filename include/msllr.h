@@ -110,13 +110,25 @@ typedef struct msllr_params {
                           concurrent scales; the 1x1 and noise scales are one
                           element-wise launch each.  Blocks up to 256 wide;
                           not with spin_grid > 1 (EINVAL).  Default 0.      */
+  double stop_tol;     /* > 0: stopping test of the ADMM (Boyd et al. 2011,
+                          Sec. 3.3; the paper fixes none): every stop_every
+                          iterations, FP64 sums give the primal residual
+                          r = ||X - Z||_F and the dual residual
+                          s = rho ||Z - Z_prev||_F of that iteration; once
+                          r <= stop_tol ||Z||_F and s <= stop_tol rho ||U||_F
+                          the run ends after one more iteration (the one
+                          that collects msllr_stats), which may be before
+                          `iters`.  0 (default): exactly `iters`.           */
+  int stop_every;      /* iterations between stopping tests; 0 means 10.   */
 } msllr_params;
 
 /* Per-run diagnostics, taken at the last iteration; when params->profile is
  * set, the block counts (blocks_skipped .. blocks_householder,
  * blocks_uncertified) and flops are summed over all iterations instead. */
 typedef struct msllr_stats {
-  int iters;                                  /* iterations run               */
+  int iters;                                  /* iterations run (fewer than
+                                                 asked when the stopping
+                                                 test ended the run)          */
   int L;                                      /* scales                       */
   double objective;                           /* sum_i lambda_i ||Z_i||_(i),
                                                  blocks taken on the grid of
@@ -152,6 +164,12 @@ typedef struct msllr_stats {
    * to 256 wide; 0 for the other paths. */
   long long flops[MSLLR_MAX_SCALES];
   long long flops_fallback[MSLLR_MAX_SCALES];
+  /* rho ||Z - Z_prev||_F over all scales at the last iteration (FP64), the
+   * dual residual of the ADMM; with primal_residual it is what the
+   * stopping test reads. */
+  double dual_residual;
+  int stopped;                                /* 1: params->stop_tol ended the
+                                                 run before `iters`          */
 } msllr_stats;
 
 /* Fill *p with the defaults.  Returns MSLLR_EINVAL if p is NULL. */

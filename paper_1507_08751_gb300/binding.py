@@ -62,6 +62,8 @@ class Params(ctypes.Structure):
         ("profile", ctypes.c_int),
         ("spin_grid", ctypes.c_int),
         ("plain", ctypes.c_int),
+        ("stop_tol", ctypes.c_double),
+        ("stop_every", ctypes.c_int),
     ]
 
 
@@ -84,6 +86,8 @@ class Stats(ctypes.Structure):
         ("blocks_uncertified", ctypes.c_longlong * MAX_SCALES),
         ("flops", ctypes.c_longlong * MAX_SCALES),
         ("flops_fallback", ctypes.c_longlong * MAX_SCALES),
+        ("dual_residual", ctypes.c_double),
+        ("stopped", ctypes.c_int),
     ]
 
     def to_dict(self):
@@ -107,6 +111,8 @@ class Stats(ctypes.Structure):
             "blocks_uncertified": list(self.blocks_uncertified[:L]),
             "flops": list(self.flops[:L]),
             "flops_fallback": list(self.flops_fallback[:L]),
+            "dual_residual": self.dual_residual,
+            "stopped": self.stopped,
         }
 
 

@@ -124,6 +124,11 @@ cudaError_t reset_warm_start(const BigWorkspace& w, int M, int N, int m, int n, 
 // and cached; configure_kernels() primes the cache outside any capture).
 int sm_count();
 
+// Narrow blocks with one warp per block (k_block_warp.cu): the block shapes
+// it takes (min(m, n) <= 16, max(m, n) <= 32) and its launcher.
+bool warp_path(int m, int n);
+cudaError_t launch_warp(const ScaleLaunch& s, cudaStream_t st, Prof* prof);
+
 // The plain one-block-per-launch comparator (k_plain.cu): global scratch a
 // scale needs (0 when the block fits shared memory), kernel attributes, and
 // the per-scale launcher (one launch per block).
@@ -147,9 +152,16 @@ cudaError_t launch_scale(const ScaleLaunch& s, const BigWorkspace& ws, cudaStrea
 
 cudaError_t launch_consensus(const float* Y, const float* W, float* R, const uint8_t* mask,
                              int L, size_t MN, cudaStream_t st, Prof* prof = nullptr);
+// X_out = W + R, U_out = Z - W; FP64 ||X - Z||^2 into pres_acc[0] and, with
+// `dual` (X_out holding the previous Z on entry), ||Z - Z_prev||^2 into
+// pres_acc[1].
 cudaError_t launch_finalize(const float* W, const float* Z, const float* R, float* X_out,
-                            float* U_out, double* pres_acc, int L, size_t MN, cudaStream_t st,
-                            Prof* prof = nullptr);
+                            float* U_out, double* pres_acc, bool dual, int L, size_t MN,
+                            cudaStream_t st, Prof* prof = nullptr);
+// Stopping-test sums against the state (Zs, Ws) of one iteration earlier:
+// acc4 += (||U - Us||^2, ||Z - Zs||^2, ||Z||^2, ||U||^2), U = Z - W.
+cudaError_t launch_residual(const float* Z, const float* W, const float* Zs, const float* Ws,
+                            double* acc4, size_t n, cudaStream_t st, Prof* prof = nullptr);
 cudaError_t launch_init_state(const float* Z0, const float* U0, float* Z, float* W, int L,
                               size_t MN, cudaStream_t st, Prof* prof = nullptr);
 cudaError_t launch_advance(const int* table, int* iter, int* cur_shift, cudaStream_t st,

@@ -379,6 +379,7 @@ cudaError_t launch_scale(const ScaleLaunch& s, const BigWorkspace& ws, cudaStrea
       return launch_noise(s, st, prof);
     case ScalePath::Small: {
       const int nn = s.m < s.n ? s.m : s.n;
+      if (warp_path(s.m, s.n)) return launch_warp(s, st, prof);
       if (nn <= 16) return launch_small_t<32, 16>(s, st, prof);
       if (nn <= 32) return launch_small_t<64, 32>(s, st, prof);
       return launch_small_t<128, 64>(s, st, prof);

@@ -1,0 +1,207 @@
+// Block SVT of narrow blocks (min(m, n) <= 16, max(m, n) <= 32) with one
+// warp per block and the whole block in registers -- eq:bsvt under the
+// Sec. 9 shift:
+//   gather R_b(Shift_s(A)), A = A1 + A2, as C (mm x nn, the block or its
+//   transpose: SVT(B^T) = SVT(B)^T); lane (h, c) holds column c of C at the
+//   rows of parity h, so that one load instruction reads two 64-byte row
+//   segments;
+//   skip when ||C||_F <= tau (Sec. 8: ||C||_F bounds sigma_max);
+//   otherwise the SVD by one-sided Jacobi (Hestenes): columns p, q of C V
+//   are rotated until every pair is orthogonal to working precision, with
+//   the round-robin pair order of 16 columns (15 rounds of 8 disjoint pairs
+//   per sweep); the singular values are the column norms of C V (no Gram
+//   matrix, so no squared condition number) and the right singular vectors
+//   are the columns of V;
+//   Z' = (C V) diag(f) V^T with f_j = max(1 - tau / sigma_j, 0) (eq:svt),
+//   scattered through Shift_{-s}, and the fused dual update W' = 2 Z' - A
+//   of eq:admm.
+// Nothing but the inputs and outputs touches global memory.
+#include <math.h>
+
+#include "common.cuh"
+#include "internal.h"
+
+namespace msllr {
+
+namespace {
+
+constexpr int kWT = 256;            // threads per CTA: 8 warps, 8 blocks
+constexpr int kWarps = kWT / 32;
+constexpr float kRotTol = 2e-6f;    // rotate columns p, q while |c_p . c_q| > tol ||c_p|| ||c_q||
+constexpr int kMaxSweeps = 12;
+constexpr unsigned kFull = 0xffffffffu;
+
+// RPL: rows of C per lane (mm <= 2 RPL)
+template <int RPL>
+__global__ void __launch_bounds__(kWT, RPL <= 8 ? 4 : 2)
+blocksvt_warp_kernel(ScaleLaunch a, int nblocks) {
+  __shared__ float vsh[kWarps][16][17];  // V of each warp, for the rebuild
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const int b = blockIdx.x * kWarps + wid;
+  if (b >= nblocks) return;  // the whole warp leaves together
+  const int h = lane >> 4, c = lane & 15;
+  BlockGeom g;
+  g.M = a.M;
+  g.N = a.N;
+  g.ld = a.ld;
+  g.m = a.m;
+  g.n = a.n;
+  const int nbn = a.N / a.n;
+  g.p = b / nbn;
+  g.q = b - g.p * nbn;
+  const bool full = (a.m == a.M && a.n == a.N);  // SVT commutes with permutations
+  g.sr = (a.shift && !full) ? (a.shift[0] + a.shift_add_r) % a.M : 0;
+  g.sc = (a.shift && !full) ? (a.shift[1] + a.shift_add_c) % a.N : 0;
+  const int mm = g.mm(), nn = g.nn();
+  const bool tr = g.transposed();
+  const bool col = c < nn;
+
+  // gather (all loads in flight at once); ||C||_F^2
+  float x[RPL];
+  float fro = 0.f;
+#pragma unroll
+  for (int i = 0; i < RPL; ++i) {
+    const int r = h + 2 * i;
+    float v = 0.f;
+    if (col && r < mm) {
+      const size_t off = tr ? g.offset(c, r) : g.offset(r, c);
+      v = a.A1[off];
+      if (a.A2) v += a.A2[off];
+    }
+    x[i] = v;
+    fro = fmaf(v, v, fro);
+  }
+  fro = warp_sum(fro);
+  const bool skipped = a.skip_bound && fro <= a.tau * a.tau;
+
+  float z[RPL];
+#pragma unroll
+  for (int i = 0; i < RPL; ++i) z[i] = 0.f;
+  int k = 0;
+  int sweeps = 0;
+  if (!skipped) {
+    // one-sided Jacobi: y = C V, V = I at the start
+    float y[RPL], v[8];
+#pragma unroll
+    for (int i = 0; i < RPL; ++i) y[i] = x[i];
+#pragma unroll
+    for (int i = 0; i < 8; ++i) v[i] = (h + 2 * i == c) ? 1.f : 0.f;
+    for (; sweeps < kMaxSweeps;) {
+      ++sweeps;
+      bool rotated = false;
+#pragma unroll 1
+      for (int rd = 0; rd < 15; ++rd) {
+        // round-robin partner: column 15 stays, the others turn (p + q = 2 rd mod 15)
+        const int o = c == 15 ? rd : (c == rd ? 15 : (2 * rd - c + 15) % 15);
+        const int src = (h << 4) | o;
+        float yo[RPL];
+        float al = 0.f, ga = 0.f;
+#pragma unroll
+        for (int i = 0; i < RPL; ++i) {
+          yo[i] = __shfl_sync(kFull, y[i], src);
+          al = fmaf(y[i], y[i], al);
+          ga = fmaf(y[i], yo[i], ga);
+        }
+        al += __shfl_xor_sync(kFull, al, 16);
+        ga += __shfl_xor_sync(kFull, ga, 16);
+        const float be = __shfl_sync(kFull, al, src);
+        // the rotation that zeroes the off-diagonal of the 2 x 2 Gram matrix
+        // [[al, ga], [ga, be]] of columns (me, o) (Golub & Van Loan,
+        // Alg. 8.5.1); partner lanes compute the same c and opposite s
+        float cr = 1.f, sr = 0.f;
+        if (fabsf(ga) > kRotTol * (sqrtf(al) * sqrtf(be))) {
+          const float zeta = (be - al) / (2.f * ga);
+          const float t = copysignf(1.f, zeta) / (fabsf(zeta) + sqrtf(1.f + zeta * zeta));
+          cr = 1.f / sqrtf(1.f + t * t);
+          sr = t * cr;
+          rotated = true;
+        }
+#pragma unroll
+        for (int i = 0; i < RPL; ++i) y[i] = cr * y[i] - sr * yo[i];
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+          const float vo = __shfl_sync(kFull, v[i], src);
+          v[i] = cr * v[i] - sr * vo;
+        }
+      }
+      if (!__any_sync(kFull, rotated)) break;
+    }
+    // singular values: the column norms of C V
+    float al = 0.f;
+#pragma unroll
+    for (int i = 0; i < RPL; ++i) al = fmaf(y[i], y[i], al);
+    al += __shfl_xor_sync(kFull, al, 16);
+    const float sig = sqrtf(al);
+    const float f = (col && sig > a.tau) ? 1.f - a.tau / sig : 0.f;
+    const unsigned act = __ballot_sync(kFull, f > 0.f) & 0xffffu;
+    k = __popc(act);
+    if (k > 0) {
+      if (a.nuc_acc) {
+        double t = (lane < 16 && f > 0.f) ? (double)(sig - a.tau) : 0.0;
+        t = warp_sum_d(t);
+        if (lane == 0) atomicAdd(a.nuc_acc, t);
+      }
+      // Z' = sum over kept j of f_j (C V)_j V_j^T; lane (h, c) needs V(c, j),
+      // which another lane holds: V goes through shared memory
+#pragma unroll
+      for (int i = 0; i < 8; ++i) vsh[wid][h + 2 * i][c] = v[i];
+      __syncwarp();
+      unsigned rest = act;
+      while (rest) {
+        const int j = __ffs(rest) - 1;
+        rest &= rest - 1;
+        const float w = __shfl_sync(kFull, f, j) * vsh[wid][c][j];
+        const int sj = (h << 4) | j;
+#pragma unroll
+        for (int i = 0; i < RPL; ++i) z[i] = fmaf(__shfl_sync(kFull, y[i], sj), w, z[i]);
+      }
+    }
+  }
+  // scatter Z' and W' = 2 Z' - A through Shift_{-s}
+#pragma unroll
+  for (int i = 0; i < RPL; ++i) {
+    const int r = h + 2 * i;
+    if (col && r < mm) {
+      const size_t off = tr ? g.offset(c, r) : g.offset(r, c);
+      a.Zout[off] = z[i];
+      if (a.Wout) a.Wout[off] = 2.f * z[i] - x[i];
+    }
+  }
+  if (lane == 0) {
+    if (a.rank_out) a.rank_out[b] = k;
+    if (a.cnt) {
+      if (skipped) atomicAdd(a.cnt, 1ull);
+      if (k == 0) atomicAdd(a.cnt + 1, 1ull);
+      if (!skipped) {
+        atomicAdd(a.cnt + 3, 1ull);
+        // per sweep 15 rounds of 8 column pairs: norms and inner product
+        // (6 mm), the two columns of C V and of V rotated (6 mm + 96); the
+        // rebuild 2 mm nn per kept pair
+        const double fl = (double)sweeps * 15.0 * 8.0 * (12.0 * mm + 96.0) + 2.0 * mm * nn * k;
+        atomicAdd(a.cnt + 5, (unsigned long long)fl);
+      }
+    }
+  }
+}
+
+}  // namespace
+
+bool warp_path(int m, int n) {
+  const int nn = m < n ? m : n, mm = m < n ? n : m;
+  return nn >= 1 && nn <= 16 && mm <= 32;
+}
+
+cudaError_t launch_warp(const ScaleLaunch& s, cudaStream_t st, Prof* prof) {
+  const int mm = s.m >= s.n ? s.m : s.n;
+  const int nblocks = (s.M / s.m) * (s.N / s.n);
+  const int grid = (nblocks + kWarps - 1) / kWarps;
+  if (prof)
+    if (cudaError_t e = prof->before(st, KK_FUSED)) return e;
+  if (mm <= 16) blocksvt_warp_kernel<8><<<grid, kWT, 0, st>>>(s, nblocks);
+  else blocksvt_warp_kernel<16><<<grid, kWT, 0, st>>>(s, nblocks);
+  if (prof)
+    if (cudaError_t e = prof->after(st)) return e;
+  return cudaGetLastError();
+}
+
+}  // namespace msllr

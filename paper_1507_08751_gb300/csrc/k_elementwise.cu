@@ -179,21 +179,41 @@ soft1x1_kernel(const float* A1, const float* __restrict__ A2, float* Zout, float
   }
 }
 
+// Sums of a CTA's per-thread FP64 values, added to *acc by thread 0.
+__device__ __forceinline__ void cta_add_d(double v, double* acc, double* sred) {
+  v = warp_sum_d(v);
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  if (lane == 0) sred[w] = v;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int i = 0; i < kEwThreads / 32; ++i) t += sred[i];
+    atomicAdd(acc, t);
+  }
+  __syncthreads();
+}
+
 // X_i = W_i + R (the X-update of eq:admm on the final state), U_i = Z_i - W_i,
-// and sum over i of ||X_i - Z_i||^2 in FP64.
+// and in FP64 sum over i of ||X_i - Z_i||^2 (primal residual) into
+// pres_acc[0] and, with `dual`, sum of ||Z_i - Z_i^prev||^2 into
+// pres_acc[1], where X_out holds the previous iteration's Z on entry.
 __global__ void __launch_bounds__(kEwThreads)
 finalize_kernel(const float* __restrict__ W, const float* __restrict__ Z,
-                const float* __restrict__ R, float* __restrict__ X_out, float* __restrict__ U_out,
-                double* pres_acc, int L, size_t MN) {
+                const float* __restrict__ R, float* X_out, float* __restrict__ U_out,
+                double* pres_acc, int dual, int L, size_t MN) {
   __shared__ double sred[kEwThreads / 32];
   const size_t stride = (size_t)gridDim.x * blockDim.x;
-  double acc = 0.0;
+  double acc = 0.0, accd = 0.0;
   for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < MN; i += stride) {
     const float r = R[i];
     for (int j = 0; j < L; ++j) {
       const size_t o = (size_t)j * MN + i;
       const float w = W[o], z = Z[o];
       const float x = w + r;
+      if (dual) {
+        const double dz = (double)z - (double)X_out[o];
+        accd += dz * dz;
+      }
       X_out[o] = x;
       if (U_out) U_out[o] = z - w;
       const double dxz = (double)x - (double)z;
@@ -201,16 +221,35 @@ finalize_kernel(const float* __restrict__ W, const float* __restrict__ Z,
     }
   }
   if (pres_acc) {
-    acc = warp_sum_d(acc);
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    if (lane == 0) sred[w] = acc;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-      double t = 0.0;
-      for (int i = 0; i < kEwThreads / 32; ++i) t += sred[i];
-      atomicAdd(pres_acc, t);
-    }
+    cta_add_d(acc, pres_acc, sred);
+    if (dual) cta_add_d(accd, pres_acc + 1, sred);
   }
+}
+
+// Stopping test of the ADMM (Boyd et al. 2011, Sec. 3.3): with (Zs, Ws) the
+// state one iteration earlier, sums in FP64 of ||U - Us||^2 (the primal
+// residual ||X - Z||^2 of that iteration, since U' - U = X - Z'), of
+// ||Z - Zs||^2 (the dual residual / rho), of ||Z||^2 and of ||U||^2, with
+// U = Z - W.
+__global__ void __launch_bounds__(kEwThreads)
+residual_kernel(const float* __restrict__ Z, const float* __restrict__ W,
+                const float* __restrict__ Zs, const float* __restrict__ Ws, double* acc4,
+                size_t n) {
+  __shared__ double sred[kEwThreads / 32];
+  const size_t stride = (size_t)gridDim.x * blockDim.x;
+  double du = 0.0, dz = 0.0, zz = 0.0, uu = 0.0;
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+    const double z = Z[i], w = W[i], zs = Zs[i], ws = Ws[i];
+    const double u = z - w, us = zs - ws;
+    du += (u - us) * (u - us);
+    dz += (z - zs) * (z - zs);
+    zz += z * z;
+    uu += u * u;
+  }
+  cta_add_d(du, acc4, sred);
+  cta_add_d(dz, acc4 + 1, sred);
+  cta_add_d(zz, acc4 + 2, sred);
+  cta_add_d(uu, acc4 + 3, sred);
 }
 
 __global__ void __launch_bounds__(kEwThreads)
@@ -369,10 +408,19 @@ cudaError_t launch_soft1x1(const ScaleLaunch& s, cudaStream_t st, Prof* prof) {
     if (cudaError_t e_ = prof->after(st)) return e_;
 
 cudaError_t launch_finalize(const float* W, const float* Z, const float* R, float* X_out,
-                            float* U_out, double* pres_acc, int L, size_t MN, cudaStream_t st,
-                            Prof* prof) {
+                            float* U_out, double* pres_acc, bool dual, int L, size_t MN,
+                            cudaStream_t st, Prof* prof) {
   MISC_BEFORE()
-  finalize_kernel<<<ew_grid(MN), kEwThreads, 0, st>>>(W, Z, R, X_out, U_out, pres_acc, L, MN);
+  finalize_kernel<<<ew_grid(MN), kEwThreads, 0, st>>>(W, Z, R, X_out, U_out, pres_acc, dual ? 1 : 0,
+                                                      L, MN);
+  MISC_AFTER()
+  return cudaGetLastError();
+}
+
+cudaError_t launch_residual(const float* Z, const float* W, const float* Zs, const float* Ws,
+                            double* acc4, size_t n, cudaStream_t st, Prof* prof) {
+  MISC_BEFORE()
+  residual_kernel<<<ew_grid(n), kEwThreads, 0, st>>>(Z, W, Zs, Ws, acc4, n);
   MISC_AFTER()
   return cudaGetLastError();
 }

@@ -1,6 +1,6 @@
 // The plain FP32 comparator of the block SVT (eq:bsvt under the Sec. 9
-// shift): one kernel launch per block, one CTA, textbook steps and nothing
-// skipped --
+// shift): the blocks one after another, each by its own launches, with
+// textbook steps and nothing skipped --
 //   G = C^T C of the gathered block (C = R_b(Shift_s(A)), or its transpose
 //   for wide blocks, since SVT(B^T) = SVT(B)^T),
 //   eigen-decomposition of G by the cyclic Jacobi method with the
@@ -8,10 +8,11 @@
 //   sigma_j = sqrt(lambda_j), f_j = max(1 - tau / sigma_j, 0) (eq:svt),
 //   Z' = C V diag(f) V^T scattered through Shift_{-s}, W' = 2 Z' - A.
 // It exists to be timed beside the optimised path (msllr_params.plain): no
-// skip bound, no certificate, no batching of blocks into one launch.  Blocks
-// up to 64 wide keep G, V and Q = V diag(f) V^T in shared memory; wider ones
-// (up to 256) keep them in a global scratch that consecutive launches on the
-// one stream reuse.
+// skip bound, no certificate, no batching of blocks into one launch.  Per
+// block three launches: the Gram matrix (a grid of 16 x 16 tiles), the
+// Jacobi eigen-solve (one CTA; G and V in shared memory up to 64 wide, else
+// in a global scratch that the launches on the one stream reuse) and the
+// rebuild (a grid of row slabs).
 #include <math.h>
 
 #include "common.cuh"
@@ -21,7 +22,6 @@ namespace msllr {
 
 namespace {
 
-constexpr int kPT = 256;          // threads of the one CTA
 constexpr int kPlainSmemN = 64;   // widest block with G, V, Q in shared memory
 constexpr int kStageFloats = 8192;  // rows of C staged for the rebuild
 constexpr int kMaxSweeps = 24;
@@ -63,44 +63,62 @@ __device__ __forceinline__ void rr_pair(int np, int k, int t, int* p, int* q) {
   }
 }
 
+// sum over the CTA (NT threads; red holds NT / 32 floats)
+template <int NT>
 __device__ __forceinline__ float cta_sum(float v, float* red) {
   v = warp_sum(v);
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   if (lane == 0) red[w] = v;
   __syncthreads();
   float t = 0.f;
-  for (int i = 0; i < kPT / 32; ++i) t += red[i];
+  for (int i = 0; i < NT / 32; ++i) t += red[i];
   __syncthreads();
   return t;
 }
 
-template <bool SMEM>
-__global__ void __launch_bounds__(kPT) plain_block_kernel(ScaleLaunch a, int b, float* gscr) {
-  extern __shared__ float sm[];
-  const int tid = threadIdx.x;
+// Launch 1 of a block: G = C^T C, one 16 x 16 tile of G per CTA, the rows
+// of C streamed through shared memory 16 at a time.
+__global__ void __launch_bounds__(256) plain_gram_kernel(ScaleLaunch a, int b, float* G) {
+  __shared__ float ci[16][17], cj[16][17];
   const BlockGeom g = plain_geom(a, b);
   const int mm = g.mm(), nn = g.nn();
+  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+  const int i0 = 16 * blockIdx.y, j0 = 16 * blockIdx.x;
+  float acc = 0.f;
+  for (int r0 = 0; r0 < mm; r0 += 16) {
+    const int r = r0 + ty;
+    ci[ty][tx] = (r < mm && i0 + tx < nn) ? plain_c(a, g, r, i0 + tx) : 0.f;
+    cj[ty][tx] = (r < mm && j0 + tx < nn) ? plain_c(a, g, r, j0 + tx) : 0.f;
+    __syncthreads();
+#pragma unroll
+    for (int t = 0; t < 16; ++t) acc = fmaf(ci[t][ty], cj[t][tx], acc);
+    __syncthreads();
+  }
+  if (i0 + ty < nn && j0 + tx < nn) G[(i0 + ty) * nn + j0 + tx] = acc;
+}
+
+// Launch 2 of a block, one CTA: the eigen-decomposition G = V diag(lambda)
+// V^T by the cyclic Jacobi method, then Q = V diag(f) V^T with
+// f_j = max(1 - tau / sqrt(lambda_j), 0).  G, V in shared memory for blocks
+// up to 64 wide (NT = 256 threads), else in the global scratch (NT = 1024).
+template <bool SMEM, int NT>
+__global__ void __launch_bounds__(NT) plain_jacobi_kernel(ScaleLaunch a, int b, float* gscr) {
+  extern __shared__ float sm[];
+  const int tid = threadIdx.x;
+  const int nn = a.m < a.n ? a.m : a.n;
   const int nn2 = nn * nn;
   float* G = SMEM ? sm : gscr;
   float* V = G + nn2;
-  float* Q = V + nn2;
-  float* red = SMEM ? Q + nn2 : sm;  // 8 floats
-  float* cs = red + 8;               // rotation (c, s) per pair, then f_j
-  float* stage = cs + 2 * (nn + 2);  // staged rows of C
-
-  // 1. G = C^T C (both triangles), V = I
-  for (int e = tid; e < nn2; e += kPT) {
-    const int i = e / nn, j = e - i * nn;
-    V[e] = i == j ? 1.f : 0.f;
-    if (j > i) continue;
-    float acc = 0.f;
-    for (int r = 0; r < mm; ++r) acc = fmaf(plain_c(a, g, r, i), plain_c(a, g, r, j), acc);
-    G[i * nn + j] = acc;
-    G[j * nn + i] = acc;
+  float* Q = gscr + 2 * nn2;
+  float* red = SMEM ? V + nn2 : sm;  // 32 floats
+  float* cs = red + 32;              // rotation (c, s) per pair, then f_j
+  for (int e = tid; e < nn2; e += NT) {
+    if (SMEM) G[e] = gscr[e];
+    V[e] = (e / nn == e % nn) ? 1.f : 0.f;
   }
   __syncthreads();
 
-  // 2. cyclic Jacobi: sweeps of np - 1 rounds of disjoint rotations (an odd
+  // cyclic Jacobi: sweeps of np - 1 rounds of disjoint rotations (an odd
   // width pairs the last index with a dummy that no rotation touches) until
   // the off-diagonal part is below 1e-6 of ||G||_F, or a sweep has stopped
   // reducing it (rounding level reached)
@@ -108,19 +126,19 @@ __global__ void __launch_bounds__(kPT) plain_block_kernel(ScaleLaunch a, int b, 
   float off_prev = 0.f;
   for (int sweep = 0; sweep < kMaxSweeps; ++sweep) {
     float off = 0.f, tot = 0.f;
-    for (int e = tid; e < nn2; e += kPT) {
+    for (int e = tid; e < nn2; e += NT) {
       const float v = G[e];
       tot = fmaf(v, v, tot);
       if (e / nn != e % nn) off = fmaf(v, v, off);
     }
-    off = cta_sum(off, red);
-    tot = cta_sum(tot, red);
+    off = cta_sum<NT>(off, red);
+    tot = cta_sum<NT>(tot, red);
     if (!(off > 1e-12f * tot)) break;
     if (sweep > 0 && !(off < 0.9f * off_prev)) break;
     off_prev = off;
     for (int k = 0; k < np - 1; ++k) {
       // rotation of each pair (Golub & Van Loan, Alg. 8.5.1, sym.schur2)
-      for (int t = tid; t < npairs; t += kPT) {
+      for (int t = tid; t < npairs; t += NT) {
         int p, q;
         rr_pair(np, k, t, &p, &q);
         float c = 1.f, s = 0.f;
@@ -138,7 +156,7 @@ __global__ void __launch_bounds__(kPT) plain_block_kernel(ScaleLaunch a, int b, 
       }
       __syncthreads();
       // rows p, q  <-  J^T G
-      for (int e = tid; e < npairs * nn; e += kPT) {
+      for (int e = tid; e < npairs * nn; e += NT) {
         const int t = e / nn, j = e - t * nn;
         int p, q;
         rr_pair(np, k, t, &p, &q);
@@ -150,7 +168,7 @@ __global__ void __launch_bounds__(kPT) plain_block_kernel(ScaleLaunch a, int b, 
       }
       __syncthreads();
       // columns p, q  <-  G J, and V J
-      for (int e = tid; e < npairs * nn; e += kPT) {
+      for (int e = tid; e < npairs * nn; e += NT) {
         const int t = e / nn, i = e - t * nn;
         int p, q;
         rr_pair(np, k, t, &p, &q);
@@ -167,9 +185,9 @@ __global__ void __launch_bounds__(kPT) plain_block_kernel(ScaleLaunch a, int b, 
     }
   }
 
-  // 3. soft threshold of the singular values sigma_j = sqrt(lambda_j)
+  // soft threshold of the singular values sigma_j = sqrt(lambda_j)
   float* f = cs;
-  for (int j = tid; j < nn; j += kPT) {
+  for (int j = tid; j < nn; j += NT) {
     const float sig = sqrtf(fmaxf(G[j * nn + j], 0.f));
     f[j] = sig > a.tau ? 1.f - a.tau / sig : 0.f;
   }
@@ -186,8 +204,8 @@ __global__ void __launch_bounds__(kPT) plain_block_kernel(ScaleLaunch a, int b, 
     if (a.nuc_acc && k > 0) atomicAdd(a.nuc_acc, nuc);
     if (a.cnt && k == 0) atomicAdd(a.cnt + 1, 1ull);
   }
-  // 4. Q = V diag(f) V^T
-  for (int e = tid; e < nn2; e += kPT) {
+  // Q = V diag(f) V^T
+  for (int e = tid; e < nn2; e += NT) {
     const int c = e / nn, d = e - c * nn;
     float acc = 0.f;
     for (int j = 0; j < nn; ++j)
@@ -195,47 +213,51 @@ __global__ void __launch_bounds__(kPT) plain_block_kernel(ScaleLaunch a, int b, 
     Q[e] = acc;
   }
   __syncthreads();
+}
 
-  // 5. Z' = C Q row slab by row slab (C staged, so that the in-place write of
-  // Z' never overtakes a read of A), W' = 2 Z' - A
+// Launch 3 of a block: Z' = C Q for a slab of rows per CTA (C staged, so that
+// the in-place write of Z' never overtakes a read of A), W' = 2 Z' - A.
+__global__ void __launch_bounds__(256) plain_rebuild_kernel(ScaleLaunch a, int b,
+                                                            const float* __restrict__ Q) {
+  __shared__ float stage[kStageFloats];
+  const BlockGeom g = plain_geom(a, b);
+  const int mm = g.mm(), nn = g.nn();
   const int rs = kStageFloats / nn;
-  for (int r0 = 0; r0 < mm; r0 += rs) {
-    const int rows = min(rs, mm - r0);
-    for (int e = tid; e < rows * nn; e += kPT) {
-      const int i = e / nn, c = e - i * nn;
-      stage[e] = plain_c(a, g, r0 + i, c);
-    }
-    __syncthreads();
-    for (int e = tid; e < rows * nn; e += kPT) {
-      const int i = e / nn, c = e - i * nn;
-      float z = 0.f;
-      for (int d = 0; d < nn; ++d) z = fmaf(stage[i * nn + d], Q[d * nn + c], z);
-      const size_t off = g.transposed() ? g.offset(c, r0 + i) : g.offset(r0 + i, c);
-      a.Zout[off] = z;
-      if (a.Wout) a.Wout[off] = 2.f * z - stage[e];
-    }
-    __syncthreads();
+  const int r0 = blockIdx.x * rs;
+  const int rows = min(rs, mm - r0);
+  for (int e = threadIdx.x; e < rows * nn; e += 256) {
+    const int i = e / nn, c = e - i * nn;
+    stage[e] = plain_c(a, g, r0 + i, c);
+  }
+  __syncthreads();
+  for (int e = threadIdx.x; e < rows * nn; e += 256) {
+    const int i = e / nn, c = e - i * nn;
+    float z = 0.f;
+    for (int d = 0; d < nn; ++d) z = fmaf(stage[i * nn + d], Q[d * nn + c], z);
+    const size_t off = g.transposed() ? g.offset(c, r0 + i) : g.offset(r0 + i, c);
+    a.Zout[off] = z;
+    if (a.Wout) a.Wout[off] = 2.f * z - stage[e];
   }
 }
 
 size_t plain_smem_bytes(int nn) {
-  const size_t small = nn <= kPlainSmemN ? 3 * (size_t)nn * nn : 0;
-  return sizeof(float) * (small + 8 + 2 * ((size_t)nn + 2) + kStageFloats);
+  const size_t small = nn <= kPlainSmemN ? 2 * (size_t)nn * nn : 0;
+  return sizeof(float) * (small + 32 + 2 * ((size_t)nn + 2));
 }
 
 }  // namespace
 
 size_t plain_scratch_bytes(int m, int n) {
   const int nn = m < n ? m : n;
-  return nn > kPlainSmemN ? sizeof(float) * 3 * (size_t)nn * nn : 0;
+  return sizeof(float) * 3 * (size_t)nn * nn;
 }
 
 cudaError_t configure_plain_kernels() {
-  cudaError_t e = cudaFuncSetAttribute(plain_block_kernel<true>,
+  cudaError_t e = cudaFuncSetAttribute(plain_jacobi_kernel<true, 256>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)plain_smem_bytes(kPlainSmemN));
   if (e != cudaSuccess) return e;
-  return cudaFuncSetAttribute(plain_block_kernel<false>,
+  return cudaFuncSetAttribute(plain_jacobi_kernel<false, 1024>,
                               cudaFuncAttributeMaxDynamicSharedMemorySize,
                               (int)plain_smem_bytes(256));
 }
@@ -254,16 +276,27 @@ cudaError_t launch_plain(const ScaleLaunch& s, float* scratch, cudaStream_t st, 
     default:
       break;
   }
-  const int nn = s.m < s.n ? s.m : s.n;
+  if (!scratch) return cudaErrorInvalidValue;
+  const int nn = s.m < s.n ? s.m : s.n, mm = s.m < s.n ? s.n : s.m;
   const int nblocks = (s.M / s.m) * (s.N / s.n);
-  const bool in_smem = nn <= kPlainSmemN;
-  if (!in_smem && !scratch) return cudaErrorInvalidValue;
+  const int T = (nn + 15) / 16;
+  const int slabs = (mm + kStageFloats / nn - 1) / (kStageFloats / nn);
   const size_t smem = plain_smem_bytes(nn);
   for (int b = 0; b < nblocks; ++b) {
     if (prof)
-      if (cudaError_t e = prof->before(st, KK_FUSED)) return e;
-    if (in_smem) plain_block_kernel<true><<<1, kPT, smem, st>>>(s, b, nullptr);
-    else plain_block_kernel<false><<<1, kPT, smem, st>>>(s, b, scratch);
+      if (cudaError_t e = prof->before(st, KK_GRAM)) return e;
+    plain_gram_kernel<<<dim3(T, T), 256, 0, st>>>(s, b, scratch);
+    if (prof)
+      if (cudaError_t e = prof->after(st)) return e;
+    if (prof)
+      if (cudaError_t e = prof->before(st, KK_EIG)) return e;
+    if (nn <= kPlainSmemN) plain_jacobi_kernel<true, 256><<<1, 256, smem, st>>>(s, b, scratch);
+    else plain_jacobi_kernel<false, 1024><<<1, 1024, smem, st>>>(s, b, scratch);
+    if (prof)
+      if (cudaError_t e = prof->after(st)) return e;
+    if (prof)
+      if (cudaError_t e = prof->before(st, KK_REBUILD)) return e;
+    plain_rebuild_kernel<<<slabs, 256, 0, st>>>(s, b, scratch + 2 * (size_t)nn * nn);
     if (prof)
       if (cudaError_t e = prof->after(st)) return e;
   }

@@ -396,13 +396,15 @@ struct Layout {
   float* Yd;
   uint8_t* mask;
   float* plain;  // scratch of the plain comparator path, or null
+  float* Zs;     // stopping test: Z and W one iteration earlier, or null
+  float* Ws;
   std::vector<BigWorkspace> big;
   size_t total;
 };
 
 // Offsets of every buffer inside the workspace (base may be null to size it).
 Layout plan(void* base, int M, int N, int L, const int* bm, const int* bn, bool masked,
-            bool spin, bool plain = false) {
+            bool spin, bool plain = false, bool snap = false) {
   Layout lay;
   lay.MN = (size_t)M * N;
   char* b = (char*)base;
@@ -418,6 +420,8 @@ Layout plan(void* base, int M, int N, int L, const int* bm, const int* bn, bool 
   lay.T = spin ? (float*)take(sizeof(float) * L * lay.MN) : nullptr;
   lay.Yd = (float*)take(sizeof(float) * lay.MN);
   lay.mask = masked ? (uint8_t*)take(lay.MN) : nullptr;
+  lay.Zs = snap ? (float*)take(sizeof(float) * L * lay.MN) : nullptr;
+  lay.Ws = snap ? (float*)take(sizeof(float) * L * lay.MN) : nullptr;
   lay.plain = nullptr;
   if (plain) {
     size_t need = 0;
@@ -616,9 +620,15 @@ int decompose_device(msllr_ctx* ctx, const float* Y, int M, int N, int ld, int L
   }
   CK(cudaSetDevice(ctx->device));
   const bool spin = p.spin_grid > 1;
-  const Layout sizing = plan(nullptr, M, N, L, bm, bn, mask != nullptr, spin, p.plain != 0);
+  if (!(p.stop_tol >= 0.0) || !isfinite(p.stop_tol) || p.stop_every < 0)
+    return fail(ctx, MSLLR_EINVAL, "stop_tol must be finite and >= 0, stop_every >= 0");
+  const bool stop_test = p.stop_tol > 0.0;
+  const int every = p.stop_every > 0 ? p.stop_every : 10;
+  const Layout sizing = plan(nullptr, M, N, L, bm, bn, mask != nullptr, spin, p.plain != 0,
+                             stop_test);
   if (int r = ensure_ws(ctx, sizing.total)) return r;
-  const Layout lay = plan(ctx->ws, M, N, L, bm, bn, mask != nullptr, spin, p.plain != 0);
+  const Layout lay = plan(ctx->ws, M, N, L, bm, bn, mask != nullptr, spin, p.plain != 0,
+                          stop_test);
   cudaStream_t st = ctx->stream;
 
   // inputs: finiteness check, dense copies
@@ -695,20 +705,50 @@ int decompose_device(msllr_ctx* ctx, const float* Y, int M, int N, int ld, int L
         return fail(ctx, MSLLR_ECUDA, std::string("graph instantiate: ") + cudaGetErrorString(e));
       ctx->graph_key = key;
     }
-    for (int k = 0; k < plain_iters; ++k) CK(cudaGraphLaunch(ctx->graph, st));
-    for (int a = 0; a < KK_COUNT; ++a)
-      for (int b = 0; b < 8; ++b) prof.launches[a][b] += ctx->graph_launches[a][b] * plain_iters;
-  } else {
-    for (int k = 0; k < plain_iters; ++k)
-      if (int r = enqueue_iteration(ctx, lay, M, N, L, bm, bn, taus, p, false, &prof)) return r;
   }
-  if (iters > 0)
+  // iterations 0 .. plain_iters-1: graph replays or plain launches, with the
+  // stopping test every `every` iterations when asked for
+  const size_t LMN = (size_t)L * lay.MN;
+  int ran = 0;
+  bool stopped = false;
+  double* acc4 = ctx->d_acc + MSLLR_MAX_SCALES + 2;
+  for (int k = 0; k < plain_iters && !stopped; ++k) {
+    const bool check = stop_test && (k + 1) % every == 0;
+    if (check) {
+      CK(cudaMemcpyAsync(lay.Zs, lay.Z, sizeof(float) * LMN, cudaMemcpyDeviceToDevice, st));
+      CK(cudaMemcpyAsync(lay.Ws, lay.W, sizeof(float) * LMN, cudaMemcpyDeviceToDevice, st));
+    }
+    if (p.use_graph) {
+      CK(cudaGraphLaunch(ctx->graph, st));
+      for (int a = 0; a < KK_COUNT; ++a)
+        for (int b = 0; b < 8; ++b) prof.launches[a][b] += ctx->graph_launches[a][b];
+    } else if (int r = enqueue_iteration(ctx, lay, M, N, L, bm, bn, taus, p, false, &prof)) {
+      return r;
+    }
+    ++ran;
+    if (check) {
+      double h4[4];
+      CK(cudaMemsetAsync(acc4, 0, 4 * sizeof(double), st));
+      CK(launch_residual(lay.Z, lay.W, lay.Zs, lay.Ws, acc4, LMN, st, &prof));
+      CK(cudaMemcpyAsync(h4, acc4, sizeof h4, cudaMemcpyDeviceToHost, st));
+      CK(cudaStreamSynchronize(st));
+      // r = ||X - Z|| = ||U - U_prev||, s / rho = ||Z - Z_prev||
+      stopped = sqrt(h4[0]) <= p.stop_tol * sqrt(h4[2]) &&
+                sqrt(h4[1]) <= p.stop_tol * sqrt(h4[3]);
+    }
+  }
+  // the last iteration collects the statistics; the output pass then reads
+  // the Z it started from (copied into X_out) for the dual residual
+  if (iters > 0) {
+    CK(cudaMemcpyAsync(X_out, lay.Z, sizeof(float) * LMN, cudaMemcpyDeviceToDevice, st));
     if (int r = enqueue_iteration(ctx, lay, M, N, L, bm, bn, taus, p, true, &prof)) return r;
+    ++ran;
+  }
 
   // output X-update on the final state
   CK(launch_consensus(lay.Yd, lay.W, lay.R, lay.mask, L, lay.MN, st, &prof));
-  CK(launch_finalize(lay.W, lay.Z, lay.R, X_out, p.U_out, ctx->d_acc + MSLLR_MAX_SCALES, L,
-                     lay.MN, st, &prof));
+  CK(launch_finalize(lay.W, lay.Z, lay.R, X_out, p.U_out, ctx->d_acc + MSLLR_MAX_SCALES,
+                     iters > 0, L, lay.MN, st, &prof));
   if (Z_out)
     CK(cudaMemcpyAsync(Z_out, lay.Z, sizeof(float) * L * lay.MN, cudaMemcpyDeviceToDevice, st));
   double acc[MSLLR_MAX_SCALES + 8];
@@ -737,7 +777,10 @@ int decompose_device(msllr_ctx* ctx, const float* Y, int M, int N, int ld, int L
       stats->lambda[i] = lam[i];
     }
     stats->objective = obj;
+    stats->iters = ran;
+    stats->stopped = stopped ? 1 : 0;
     stats->primal_residual = sqrt(acc[MSLLR_MAX_SCALES]);
+    stats->dual_residual = rho * sqrt(acc[MSLLR_MAX_SCALES + 1]);
     long long total = 0;
     for (int a = 0; a < KK_COUNT && a < MSLLR_KERNEL_KINDS; ++a)
       for (int b = 0; b < MSLLR_MAX_SCALES; ++b) {

@@ -61,6 +61,7 @@ def test_params_default(built):
     assert (p.skip_bound, p.cycle_spin, p.use_graph, p.iter_offset) == (1, 1, 1, 0)
     assert not p.Z_init and not p.U_init and not p.U_out
     assert p.profile == 0 and p.spin_grid == 0 and p.plain == 0
+    assert p.stop_tol == 0.0 and p.stop_every == 0
 
 
 def test_params_struct_matches_header_field_order():
@@ -86,6 +87,6 @@ def test_stats_struct_matches_header_field_order():
     src = open(os.path.join(ROOT, "include", "msllr.h")).read()
     body = src[src.index("typedef struct msllr_stats"):src.index("} msllr_stats;")]
     body = re.sub(r"/\*.*?\*/", "", body, flags=re.S)
-    names = re.findall(r"^\s+(?:long long|int|double)\s+(\w+)", body, re.M)
+    names = re.findall(r"^\s*(?:long long|int|double)\s+(\w+)", body, re.M)
     mirror = [f[0].rstrip("_") for f in B.Stats._fields_]
     assert names == mirror

@@ -423,6 +423,56 @@ def test_plain_comparator_matches_oracle_and_the_optimised_path(ctx):
     assert e.value.code == B.MSLLR_EINVAL
 
 
+def test_dual_residual_against_consecutive_states_and_the_oracle(ctx):
+    """The FP64 dual residual rho ||Z_K - Z_{K-1}||_F the library reports
+    (stopping-test quantity of the ADMM): against the GPU's own states after
+    K - 1 and K iterations (same shifts, deterministic runs), and against the
+    oracle's, which it may miss by at most the two states' distances to the
+    oracle (triangle inequality)."""
+    Y, comps, scales = synth.tiny_64()
+    Y32 = Y.astype(np.float32)
+    M, N = Y32.shape
+    lam = [O.lambda_area(M, N, m, n) for m, n in scales]
+    K, seed = 40, 21
+    _, Z1, _ = _run_decompose(ctx, Y32, scales, lam, K - 1, seed)
+    _, Z2, s2 = _run_decompose(ctx, Y32, scales, lam, K, seed)
+    own = np.linalg.norm(Z2.astype(np.float64) - Z1.astype(np.float64))
+    assert s2["dual_residual"] == pytest.approx(own, rel=1e-7)
+    sh = O.shift_table(seed, K, M, N)
+    Y64 = Y32.astype(np.float64)
+    r1 = O.admm(Y64, scales, lam, 1.0, K - 1, shifts=sh[:K - 1])
+    r2 = O.admm(Y64, scales, lam, 1.0, K, shifts=sh)
+    ref = np.linalg.norm(r2["Z"] - r1["Z"])
+    slack = np.linalg.norm(Z2 - r2["Z"]) + np.linalg.norm(Z1 - r1["Z"])
+    assert abs(s2["dual_residual"] - ref) <= slack + 1e-12
+    assert ref > 0.0
+
+
+def test_stopping_test_ends_the_run_and_matches_the_oracle(ctx):
+    """stop_tol > 0: with shifts off the ADMM converges, the FP64 stopping
+    test (every 10 iterations) ends the run before the iteration cap, and the
+    result is the oracle's after the same number of iterations."""
+    from paper_1507_08751_gb300 import binding as B
+    Y, comps, scales = synth.hanning_blobs()
+    Y32 = Y.astype(np.float32)
+    M, N = Y32.shape
+    lam = [O.lambda_default(M, N, m, n) for m, n in scales]
+    p = B.msllr_params_default()
+    p.cycle_spin = 0
+    p.stop_tol = 1e-4
+    p.stop_every = 10
+    X, Z, st = _run_decompose(ctx, Y32, scales, lam, 5000, 0, params=p)
+    assert st["stopped"] == 1
+    assert 10 < st["iters"] < 5000 and st["iters"] % 10 == 1
+    ref = O.admm(Y32.astype(np.float64), scales, lam, 1.0, st["iters"])
+    assert np.all(O.relerr(X, ref["X"], Y32) <= TOL)
+    # the stopping rule held at the test: relative residuals near stop_tol
+    assert st["primal_residual"] <= 2e-4 * np.linalg.norm(Z)
+    p.stop_tol = 0.0
+    _, _, full = _run_decompose(ctx, Y32, scales, lam, 50, 0, params=p)
+    assert full["stopped"] == 0 and full["iters"] == 50
+
+
 def test_error_paths(ctx):
     from paper_1507_08751_gb300 import binding as B
     Y = torch.zeros((64, 64), dtype=torch.float32, device="cuda")
