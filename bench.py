@@ -631,7 +631,7 @@ def serve(a):
         "data": "synthetic",
         "config": {"workload": "serve-mix", "sizes": [f"{m}x{n_}" for m, n_ in SERVE_SIZES],
                    "scales": "3-6 dyadic", "rating_like": 0.3, "arrival_rate": a.serve_rate,
-                   "jobs": n, "iters_per_job": iters, "queue": "msllr_submit, one worker"},
+                   "jobs": n, "iters_per_job": iters, "queue": "msllr_submit, 4 concurrent slots"},
         "p50_s": round(p50, 4), "p99_s": round(p99, 4),
         "aggregate_iter_s": round(n * iters / t_total, 2),
         "makespan_s": round(t_total, 3), "clocks": ck,

@@ -120,6 +120,19 @@ typedef struct msllr_params {
                           that collects msllr_stats), which may be before
                           `iters`.  0 (default): exactly `iters`.           */
   int stop_every;      /* iterations between stopping tests; 0 means 10.   */
+  int frame_w;         /* spatio-temporal blocks (Sec. 10.2): Y is a video
+                          of M = H x frame_w pixels (row y frame_w + x for
+                          pixel (y, x)) by N frames.  0 (default): none.    */
+  const int* st_patch_w; /* host, L values, or NULL.  st_patch_w[i] = bw > 0
+                          makes scale i the bh x bw x bt partition of the
+                          video cube with bh = block_m[i] / bw and
+                          bt = block_n[i]: each block is the (bh bw) x bt
+                          matrix of a pixel patch (pixels in row-major
+                          order) over bt frames, and the iteration's shift
+                          (s_r, s_c) moves the cube by (s_r div frame_w,
+                          s_r mod frame_w) pixels and s_c frames.  Needs
+                          frame_w > 0 with bh | H, bw | frame_w, bt | N;
+                          not with spin_grid > 1.  0 or NULL: 2-D blocks.  */
 } msllr_params;
 
 /* Per-run diagnostics, taken at the last iteration; when params->profile is
@@ -170,6 +183,10 @@ typedef struct msllr_stats {
   double dual_residual;
   int stopped;                                /* 1: params->stop_tol ended the
                                                  run before `iters`          */
+  int serve_jobs_running;                     /* serving queue: jobs running
+                                                 on the device, this one
+                                                 included, when it was
+                                                 admitted; 0 for direct calls */
 } msllr_stats;
 
 /* Fill *p with the defaults.  Returns MSLLR_EINVAL if p is NULL. */
@@ -260,19 +277,27 @@ int msllr_decompose_host(msllr_ctx* ctx, const float* Y, int M, int N, int ld,
                          float* X_out, float* Z_out, msllr_stats* stats);
 
 /* ---- serving queue ------------------------------------------------------
- * Independent decompositions of one context run in submission order on a
- * worker thread of the library, so that a caller can keep submitting while
- * earlier jobs run (the jobs and their sizes are those of msllr_decompose,
+ * Independent decompositions submitted to one context run concurrently on
+ * its device (the jobs and their sizes are those of msllr_decompose,
  * eq:admm with the Sec. 9 cycle spin; the queue itself is plumbing around
- * it).  A job's inputs (Y, mask, block sizes, lambda, params) are copied at
- * submission; its outputs go to the caller's HOST buffers, which must stay
- * valid until msllr_poll reports the job done or msllr_wait returns.  While
- * jobs are queued or running, msllr_decompose, msllr_decompose_host and
- * msllr_blocksvt on the same context return MSLLR_EBUSY.  Destroying the
- * context lets the running job finish and drops the queued ones. */
+ * it).  MSLLR_SERVE_SLOTS worker threads of the library, each with a stream
+ * and workspace of its own, take the queued jobs in submission order: the
+ * job at the head of the queue starts as soon as a slot is free and the
+ * device memory held by the running jobs plus its own footprint fits the
+ * context's HBM budget (no budget: as soon as a slot is free).  A job holds
+ * device memory only while it runs.  Its inputs (Y, mask, block sizes,
+ * lambda, params and the arrays they point to) are copied at submission;
+ * its outputs go to the caller's HOST buffers, which must stay valid until
+ * msllr_poll reports the job done or msllr_wait returns.  A job's result
+ * does not depend on the jobs that run beside it.  While jobs are queued
+ * or running, msllr_decompose, msllr_decompose_host and msllr_blocksvt on
+ * the same context return MSLLR_EBUSY.  Destroying the context lets the
+ * running jobs finish and drops the queued ones. */
 
 /* Jobs that may wait in the queue of one context. */
 #define MSLLR_SERVE_QUEUE 64
+/* Jobs of one context that run on the device at the same time. */
+#define MSLLR_SERVE_SLOTS 4
 
 typedef struct msllr_job {
   const float* Y;          /* host, M x N row-major with row stride ld       */
@@ -292,9 +317,9 @@ typedef struct msllr_job {
 } msllr_job;
 
 /* Queue a job; *job_id identifies it for msllr_poll / msllr_wait.  Checks
- * the arguments (EINVAL) and admits the job only if its device footprint
- * (workspace plus input and output copies) fits the context's HBM budget
- * (ENOMEM); EBUSY when MSLLR_SERVE_QUEUE jobs are already waiting. */
+ * the arguments (EINVAL) and accepts the job only if its device footprint
+ * (workspace plus input and output copies) alone fits the context's HBM
+ * budget (ENOMEM); EBUSY when MSLLR_SERVE_QUEUE jobs are already waiting. */
 int msllr_submit(msllr_ctx* ctx, const msllr_job* job, uint64_t* job_id);
 
 /* *done = 1 once the job has finished, 0 before.  When it reports done the

@@ -41,6 +41,7 @@ EXPORTS = (
     "msllr_wait",
 )
 SERVE_QUEUE = 64
+SERVE_SLOTS = 4
 NOALLOC_SCRATCH_BYTES = 32 * 1024 * 1024
 
 
@@ -64,6 +65,8 @@ class Params(ctypes.Structure):
         ("plain", ctypes.c_int),
         ("stop_tol", ctypes.c_double),
         ("stop_every", ctypes.c_int),
+        ("frame_w", ctypes.c_int),
+        ("st_patch_w", ctypes.c_void_p),
     ]
 
 
@@ -88,6 +91,7 @@ class Stats(ctypes.Structure):
         ("flops_fallback", ctypes.c_longlong * MAX_SCALES),
         ("dual_residual", ctypes.c_double),
         ("stopped", ctypes.c_int),
+        ("serve_jobs_running", ctypes.c_int),
     ]
 
     def to_dict(self):
@@ -113,6 +117,7 @@ class Stats(ctypes.Structure):
             "flops_fallback": list(self.flops_fallback[:L]),
             "dual_residual": self.dual_residual,
             "stopped": self.stopped,
+            "serve_jobs_running": self.serve_jobs_running,
         }
 
 
@@ -189,6 +194,16 @@ def _int_array(v):
     return (ctypes.c_int * len(v))(*[int(x) for x in v])
 
 
+def _scale_arrays(scales):
+    """block_m, block_n and (for spatio-temporal scales, given as 3-tuples
+    (bh, bw, bt) as in Sec. 10.2) the patch widths; None when all are 2-D."""
+    bm = _int_array([s[0] * s[1] if len(s) == 3 else s[0] for s in scales])
+    bn = _int_array([s[-1] for s in scales])
+    if all(len(s) == 2 for s in scales):
+        return bm, bn, None
+    return bm, bn, _int_array([s[1] if len(s) == 3 else 0 for s in scales])
+
+
 def _double_array(v):
     return None if v is None else (ctypes.c_double * len(v))(*[float(x) for x in v])
 
@@ -262,12 +277,14 @@ class Context:
                                     int(shift[0]), int(shift[1]), _ptr(rank_out)), self._ctx)
 
     def _decompose(self, fn, Yp, M, N, ld, scales, lambdas, rho, iters, seed, maskp, params, Xp,
-                   Zp):
+                   Zp, frame=None):
         L = len(scales)
-        bm = _int_array([s[0] for s in scales])
-        bn = _int_array([s[1] for s in scales])
+        bm, bn, pw = _scale_arrays(scales)
         lam = _double_array(lambdas)
         p = params if params is not None else msllr_params_default()
+        if pw is not None:
+            p.frame_w = int(frame[1])
+            p.st_patch_w = ctypes.cast(pw, ctypes.c_void_p)
         st = Stats()
         _check(fn(self._ctx, Yp, M, N, ld, L, bm, bn, lam, float(rho), int(iters),
                   ctypes.c_uint64(seed), maskp, ctypes.byref(p), Xp, Zp, ctypes.byref(st)),
@@ -275,15 +292,18 @@ class Context:
         return st.to_dict()
 
     def msllr_decompose(self, Y, scales, X_out, lambdas=None, rho=1.0, iters=100, seed=0,
-                        mask=None, params=None, Z_out=None):
+                        mask=None, params=None, Z_out=None, frame=None):
         """Device-pointer decomposition: Y (M x N), X_out / Z_out (L x M x N) torch CUDA
-        float32 tensors, mask a torch CUDA uint8 tensor or None.  Returns the stats dict."""
+        float32 tensors, mask a torch CUDA uint8 tensor or None.  A scale is (m, n), or
+        (bh, bw, bt) for spatio-temporal blocks of the video whose frame is
+        frame = (H, W).  Returns the stats dict."""
         M, N = Y.shape
         return self._decompose(lib().msllr_decompose, _ptr(Y), M, N, N, scales, lambdas, rho,
-                               iters, seed, _ptr(mask), params, _ptr(X_out), _ptr(Z_out))
+                               iters, seed, _ptr(mask), params, _ptr(X_out), _ptr(Z_out),
+                               frame)
 
     def msllr_decompose_host(self, Y, scales, X_out, lambdas=None, rho=1.0, iters=100, seed=0,
-                             mask=None, params=None, Z_out=None):
+                             mask=None, params=None, Z_out=None, frame=None):
         """Host-buffer decomposition: NumPy (or pinned torch CPU) arrays; copies happen
         inside the call."""
         def hp(a, dt):
@@ -297,11 +317,11 @@ class Context:
         M, N = Y.shape
         return self._decompose(lib().msllr_decompose_host, hp(Y, np.float32), M, N, N, scales,
                                lambdas, rho, iters, seed, hp(mask, np.uint8), params,
-                               hp(X_out, np.float32), hp(Z_out, np.float32))
+                               hp(X_out, np.float32), hp(Z_out, np.float32), frame)
 
     # -- serving queue ---------------------------------------------------------
     def msllr_submit(self, Y, scales, X_out, lambdas=None, rho=1.0, iters=100, seed=0,
-                     mask=None, params=None, Z_out=None):
+                     mask=None, params=None, Z_out=None, frame=None):
         """Queue a decomposition of the host array Y (NumPy float32); X_out (and Z_out)
         are host arrays filled when the job completes.  Returns the job id."""
         def hp(a, dt):
@@ -312,10 +332,12 @@ class Context:
             return a.ctypes.data
         M, N = Y.shape
         L = len(scales)
-        bm = _int_array([s[0] for s in scales])
-        bn = _int_array([s[1] for s in scales])
+        bm, bn, pw = _scale_arrays(scales)
         lam = _double_array(lambdas)
         p = params if params is not None else msllr_params_default()
+        if pw is not None:
+            p.frame_w = int(frame[1])
+            p.st_patch_w = ctypes.cast(pw, ctypes.c_void_p)
         st = Stats()
         job = Job(Y=hp(Y, np.float32), M=M, N=N, ld=N, L=L,
                   block_m=ctypes.cast(bm, ctypes.c_void_p),

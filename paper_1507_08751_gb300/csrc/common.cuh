@@ -66,18 +66,36 @@ __device__ __forceinline__ float block_max(float v, float* red) {
 // (q*n + c + sc) mod N].  `C` is the block as the eigen-solver sees it:
 // mm x nn with nn = min(m, n); for a wide block (m < n) C is its transpose,
 // since SVT(B^T) = SVT(B)^T.
+// Spatio-temporal blocks (Sec. 10.2, fw > 0): the rows of the matrix are the
+// pixels of an fh x fw frame (row y fw + x for pixel (y, x)) and its columns
+// the frames; block (p, q) is the bh x bw pixel patch p (patches in
+// row-major order) over the frames q n .. q n + n - 1, its row r the patch
+// pixel (r / bw, r mod bw), so m = bh bw.  The shift moves the video cube
+// circularly by (sy, sx) = divmod(sr, fw) pixels and sc frames.
 struct BlockGeom {
   int M, N, ld;     // matrix shape and row stride (elements)
   int m, n;         // block shape
   int p, q;         // block coordinates on the shifted grid
   int sr, sc;       // shift
+  int fw, fh, bh, bw, sy, sx;  // spatio-temporal blocks (fw = 0: none)
   __device__ __forceinline__ int mm() const { return m >= n ? m : n; }
   __device__ __forceinline__ int nn() const { return m >= n ? n : m; }
   __device__ __forceinline__ bool transposed() const { return m < n; }
   // global element offset of block element (r, c), natural orientation
   __device__ __forceinline__ size_t offset(int r, int c) const {
-    int gr = p * m + r + sr;
-    if (gr >= M) gr -= M;
+    int gr;
+    if (fw) {
+      const int pw = fw / bw, py = p / pw, px = p - py * pw;
+      const int iy = r / bw, ix = r - iy * bw;
+      int y = py * bh + iy + sy;
+      if (y >= fh) y -= fh;
+      int x = px * bw + ix + sx;
+      if (x >= fw) x -= fw;
+      gr = y * fw + x;
+    } else {
+      gr = p * m + r + sr;
+      if (gr >= M) gr -= M;
+    }
     int gc = q * n + c + sc;
     if (gc >= N) gc -= N;
     return (size_t)gr * ld + gc;
@@ -87,6 +105,32 @@ struct BlockGeom {
     return m >= n ? r * ldc + c : c * ldc + r;
   }
 };
+
+// Block b of the scale described by a launch (row-major block order on the
+// shifted grid).  The full-matrix scale ignores the shift: SVT commutes with
+// row and column permutations.
+template <class SL>
+__device__ __forceinline__ BlockGeom block_geom(const SL& a, int b) {
+  BlockGeom g;
+  g.M = a.M;
+  g.N = a.N;
+  g.ld = a.ld;
+  g.m = a.m;
+  g.n = a.n;
+  const int nbn = a.N / a.n;
+  g.p = b / nbn;
+  g.q = b - g.p * nbn;
+  const bool full = (a.m == a.M && a.n == a.N && !a.fw);
+  g.sr = (a.shift && !full) ? (a.shift[0] + a.shift_add_r) % a.M : 0;
+  g.sc = (a.shift && !full) ? (a.shift[1] + a.shift_add_c) % a.N : 0;
+  g.fw = a.fw;
+  g.fh = a.fw ? a.M / a.fw : 0;
+  g.bw = a.fw ? a.bw : 0;
+  g.bh = a.fw ? a.m / a.bw : 0;
+  g.sy = a.fw ? g.sr / a.fw : 0;
+  g.sx = a.fw ? g.sr - g.sy * a.fw : 0;
+  return g;
+}
 
 // Optional per-phase timing (debug aid, enabled by the MSLLR_PHASE_TIMING
 // environment variable): thread 0 of every CTA adds clock64() deltas between

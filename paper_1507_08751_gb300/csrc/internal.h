@@ -33,6 +33,9 @@ struct ScaleLaunch {
   unsigned long long* cnt; // device [4]: blocks skipped by a bound, blocks of rank 0,
                            // blocks solved by certified Lanczos, by Householder; or null
   double* norm_acc;        // device scratch double (noise scale: ||A||_F^2)
+  int fw;                  // spatio-temporal blocks (Sec. 10.2): frame width of the
+                           // video whose pixels are the rows (0: 2-D blocks)
+  int bw;                  // their patch width (patch height m / bw, n frames)
 };
 
 // Device workspace needed by the wide-block path for one scale.

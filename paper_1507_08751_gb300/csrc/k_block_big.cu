@@ -52,19 +52,7 @@ BigDims big_dims(int M, int N, int m, int n) {
 }
 
 __device__ __forceinline__ BlockGeom make_geom(const ScaleLaunch& a, int b) {
-  BlockGeom g;
-  g.M = a.M;
-  g.N = a.N;
-  g.ld = a.ld;
-  g.m = a.m;
-  g.n = a.n;
-  const int nbn = a.N / a.n;
-  g.p = b / nbn;
-  g.q = b - g.p * nbn;
-  const bool full = (a.m == a.M && a.n == a.N);
-  g.sr = (a.shift && !full) ? (a.shift[0] + a.shift_add_r) % a.M : 0;
-  g.sc = (a.shift && !full) ? (a.shift[1] + a.shift_add_c) % a.N : 0;
-  return g;
+  return block_geom(a, b);
 }
 
 // element (i, c) of C (mm x nn) -> global offset
@@ -440,6 +428,9 @@ size_t fallback_smem_bytes(int nn) {
 // per CTA.  Every load of C and store of Z', W' is a warp-wide row segment.
 constexpr int kRowK = 8;
 constexpr int kRowsPerCta = 32;  // 8 warps x 4 rows: one wave at 4 CTAs per SM
+// ST: spatio-temporal blocks; the 2-D instantiation knows fw = 0 at compile
+// time, which keeps its index arithmetic in registers.
+template <bool ST>
 __global__ void __launch_bounds__(kRebThreads, 4)
 rebuild_rows_kernel(ScaleLaunch a, const float* __restrict__ Yall, size_t ystride,
                     const int* __restrict__ kin) {
@@ -447,7 +438,8 @@ rebuild_rows_kernel(ScaleLaunch a, const float* __restrict__ Yall, size_t ystrid
   const int b = blockIdx.y;
   const int k = kin[b];
   if (k > kRowK) return;  // rebuild_kernel takes the block
-  const BlockGeom g = make_geom(a, b);
+  BlockGeom g = make_geom(a, b);
+  if (!ST) g.fw = 0;
   const int mm = g.mm(), nn = g.nn();
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const float* Yb = Yall + (size_t)b * ystride;
@@ -699,8 +691,9 @@ cudaError_t launch_big(const ScaleLaunch& s, const BigWorkspace& ws, cudaStream_
   const int slabs = (d.mm + rs - 1) / rs;
   const size_t smem = sizeof(float) * ((size_t)rs * d.nn + (size_t)(d.nn + 1) * kKC + (size_t)rs * kKC);
   PROF_BEFORE(KK_REBUILD)
-  rebuild_rows_kernel<<<dim3((d.mm + kRowsPerCta - 1) / kRowsPerCta, d.nblocks), kRebThreads, 0,
-                        st>>>(s, ws.Y, ws.ystride, ws.k);
+  const dim3 rgrid((d.mm + kRowsPerCta - 1) / kRowsPerCta, d.nblocks);
+  if (s.fw) rebuild_rows_kernel<true><<<rgrid, kRebThreads, 0, st>>>(s, ws.Y, ws.ystride, ws.k);
+  else rebuild_rows_kernel<false><<<rgrid, kRebThreads, 0, st>>>(s, ws.Y, ws.ystride, ws.k);
   PROF_AFTER()
   PROF_BEFORE(KK_REBUILD)
   const int slab_items = slabs * d.nblocks;

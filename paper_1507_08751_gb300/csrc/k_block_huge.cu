@@ -79,19 +79,7 @@ HugeDims huge_dims(int M, int N, int m, int n) {
 }
 
 __device__ __forceinline__ BlockGeom huge_geom(const ScaleLaunch& a, int b) {
-  BlockGeom g;
-  g.M = a.M;
-  g.N = a.N;
-  g.ld = a.ld;
-  g.m = a.m;
-  g.n = a.n;
-  const int nbn = a.N / a.n;
-  g.p = b / nbn;
-  g.q = b - g.p * nbn;
-  const bool full = (a.m == a.M && a.n == a.N);
-  g.sr = (a.shift && !full) ? (a.shift[0] + a.shift_add_r) % a.M : 0;
-  g.sc = (a.shift && !full) ? (a.shift[1] + a.shift_add_c) % a.N : 0;
-  return g;
+  return block_geom(a, b);
 }
 
 __device__ __forceinline__ size_t huge_off(const BlockGeom& g, int i, int c) {

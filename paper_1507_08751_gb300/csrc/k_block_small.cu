@@ -75,18 +75,7 @@ blocksvt_small_kernel(ScaleLaunch a) {
   const int tid = threadIdx.x;
   constexpr int SLOT = NT == 32 ? 0 : (NT == 64 ? 1 : 2);
   PHASE_INIT();
-  const int nbn = a.N / a.n;
-  BlockGeom g;
-  g.M = a.M;
-  g.N = a.N;
-  g.ld = a.ld;
-  g.m = a.m;
-  g.n = a.n;
-  g.p = blockIdx.x / nbn;
-  g.q = blockIdx.x - g.p * nbn;
-  const bool full = (a.m == a.M && a.n == a.N);  // SVT commutes with permutations
-  g.sr = (a.shift && !full) ? (a.shift[0] + a.shift_add_r) % a.M : 0;
-  g.sc = (a.shift && !full) ? (a.shift[1] + a.shift_add_c) % a.N : 0;
+  const BlockGeom g = block_geom(a, (int)blockIdx.x);
   const int mm = g.mm(), nn = g.nn();
   const int ldc = nn, ldg = nn + 1, ldy = nn;
 

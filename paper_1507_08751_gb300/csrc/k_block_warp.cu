@@ -5,7 +5,10 @@
 //   transpose: SVT(B^T) = SVT(B)^T); lane (h, c) holds column c of C at the
 //   rows of parity h, so that one load instruction reads two 64-byte row
 //   segments;
-//   skip when ||C||_F <= tau (Sec. 8: ||C||_F bounds sigma_max);
+//   skip when an upper bound of sigma_max^2 is <= tau^2 (Sec. 8): ||C||_F^2,
+//   then Gershgorin on G = C^T C (formed by shuffles), then a certificate
+//   that c0 I - G is positive definite (Cholesky in registers, lane c holding
+//   row c) with c0 below tau^2 by the factorisation's rounding margin;
 //   otherwise the SVD by one-sided Jacobi (Hestenes): columns p, q of C V
 //   are rotated until every pair is orthogonal to working precision, with
 //   the round-robin pair order of 16 columns (15 rounds of 8 disjoint pairs
@@ -16,6 +19,7 @@
 //   scattered through Shift_{-s}, and the fused dual update W' = 2 Z' - A
 //   of eq:admm.
 // Nothing but the inputs and outputs touches global memory.
+#include <float.h>
 #include <math.h>
 
 #include "common.cuh"
@@ -28,6 +32,7 @@ namespace {
 constexpr int kWT = 256;            // threads per CTA: 8 warps, 8 blocks
 constexpr int kWarps = kWT / 32;
 constexpr float kRotTol = 2e-6f;    // rotate columns p, q while |c_p . c_q| > tol ||c_p|| ||c_q||
+constexpr float kTinyCol = 1e-13f;  // squared norm of a numerically zero column, relative to ||C||_F^2
 constexpr int kMaxSweeps = 12;
 constexpr unsigned kFull = 0xffffffffu;
 
@@ -40,18 +45,7 @@ blocksvt_warp_kernel(ScaleLaunch a, int nblocks) {
   const int b = blockIdx.x * kWarps + wid;
   if (b >= nblocks) return;  // the whole warp leaves together
   const int h = lane >> 4, c = lane & 15;
-  BlockGeom g;
-  g.M = a.M;
-  g.N = a.N;
-  g.ld = a.ld;
-  g.m = a.m;
-  g.n = a.n;
-  const int nbn = a.N / a.n;
-  g.p = b / nbn;
-  g.q = b - g.p * nbn;
-  const bool full = (a.m == a.M && a.n == a.N);  // SVT commutes with permutations
-  g.sr = (a.shift && !full) ? (a.shift[0] + a.shift_add_r) % a.M : 0;
-  g.sc = (a.shift && !full) ? (a.shift[1] + a.shift_add_c) % a.N : 0;
+  const BlockGeom g = block_geom(a, b);
   const int mm = g.mm(), nn = g.nn();
   const bool tr = g.transposed();
   const bool col = c < nn;
@@ -72,7 +66,55 @@ blocksvt_warp_kernel(ScaleLaunch a, int nblocks) {
     fro = fmaf(v, v, fro);
   }
   fro = warp_sum(fro);
-  const bool skipped = a.skip_bound && fro <= a.tau * a.tau;
+  const float thr = a.tau * a.tau;
+  bool skipped = a.skip_bound && fro <= thr;
+  float fl = 0.f;  // flops of the steps run
+  if (a.skip_bound && !skipped) {
+    // G = C^T C: lane (h, c) forms row c of G from its rows of C and the
+    // other columns' values at the same rows (shuffles), then adds the other
+    // half's partial sums
+    float gr[16];
+#pragma unroll
+    for (int j = 0; j < 16; ++j) gr[j] = 0.f;
+#pragma unroll
+    for (int i = 0; i < RPL; ++i)
+#pragma unroll
+      for (int j = 0; j < 16; ++j) gr[j] = fmaf(x[i], __shfl_sync(kFull, x[i], (h << 4) | j), gr[j]);
+    float rs = 0.f;
+#pragma unroll
+    for (int j = 0; j < 16; ++j) {
+      gr[j] += __shfl_xor_sync(kFull, gr[j], 16);
+      rs += fabsf(gr[j]);
+    }
+    // Gershgorin: lambda_max(G) <= max_c sum_j |G_cj| (Sec. 8)
+    const float gbound = fminf(fro, warp_max(rs));
+    fl += (float)(2 * mm * nn * nn + 2 * nn * nn);
+    if (gbound <= thr) {
+      skipped = true;
+    } else {
+      // certified lambda_max(G) < tau^2 by the Cholesky factorisation of
+      // c0 I - G, c0 below tau^2 by the backward-error margin of the
+      // factorisation (Golub & Van Loan, Sec. 4.2.7); lane c holds row c
+      const int n8 = (nn + 7) & ~7;
+      const float c0 = thr - (float)(n8 * n8) * FLT_EPSILON * (thr + gbound);
+      bool pd = c0 > 0.f;
+#pragma unroll
+      for (int j = 0; j < 16; ++j) gr[j] = (j == c ? c0 : 0.f) - gr[j];
+#pragma unroll
+      for (int kk = 0; kk < 16; ++kk) {
+        if (kk < nn && pd) {
+          const float d = __shfl_sync(kFull, gr[kk], kk);
+          pd = d > 0.f;
+          const float l = gr[kk] * rsqrtf(d > 0.f ? d : 1.f);  // L(c, kk) for c > kk
+#pragma unroll
+          for (int j = kk + 1; j < 16; ++j)
+            if (j < nn) gr[j] = fmaf(-l, __shfl_sync(kFull, l, j), gr[j]);
+        }
+      }
+      fl += (float)(nn * nn * nn) / 3.f;
+      skipped = pd;
+    }
+  }
 
   float z[RPL];
 #pragma unroll
@@ -106,22 +148,29 @@ blocksvt_warp_kernel(ScaleLaunch a, int nblocks) {
         ga += __shfl_xor_sync(kFull, ga, 16);
         const float be = __shfl_sync(kFull, al, src);
         // the rotation that zeroes the off-diagonal of the 2 x 2 Gram matrix
-        // [[al, ga], [ga, be]] of columns (me, o) (Golub & Van Loan,
-        // Alg. 8.5.1); partner lanes compute the same c and opposite s
+        // [[a_lo, ga], [ga, a_hi]] of columns lo < hi (Golub & Van Loan,
+        // Alg. 8.5.1): both lanes of the pair evaluate it in that order, so
+        // they get the same (c, s), and apply
+        //   c_lo' = c c_lo - s c_hi,   c_hi' = s c_lo + c c_hi
+        const bool lo = c < o;
+        const float a_lo = lo ? al : be, a_hi = lo ? be : al;
         float cr = 1.f, sr = 0.f;
-        if (fabsf(ga) > kRotTol * (sqrtf(al) * sqrtf(be))) {
-          const float zeta = (be - al) / (2.f * ga);
+        // (a column at the rounding level of ||C||_F is numerically zero:
+        // no rotation, else an exactly rank-deficient block never settles)
+        if (fminf(a_lo, a_hi) > kTinyCol * fro && fabsf(ga) > kRotTol * (sqrtf(a_lo) * sqrtf(a_hi))) {
+          const float zeta = (a_hi - a_lo) / (2.f * ga);
           const float t = copysignf(1.f, zeta) / (fabsf(zeta) + sqrtf(1.f + zeta * zeta));
           cr = 1.f / sqrtf(1.f + t * t);
           sr = t * cr;
           rotated = true;
         }
+        const float so = lo ? -sr : sr;  // weight of the partner column
 #pragma unroll
-        for (int i = 0; i < RPL; ++i) y[i] = cr * y[i] - sr * yo[i];
+        for (int i = 0; i < RPL; ++i) y[i] = fmaf(so, yo[i], cr * y[i]);
 #pragma unroll
         for (int i = 0; i < 8; ++i) {
           const float vo = __shfl_sync(kFull, v[i], src);
-          v[i] = cr * v[i] - sr * vo;
+          v[i] = fmaf(so, vo, cr * v[i]);
         }
       }
       if (!__any_sync(kFull, rotated)) break;
@@ -172,14 +221,12 @@ blocksvt_warp_kernel(ScaleLaunch a, int nblocks) {
     if (a.cnt) {
       if (skipped) atomicAdd(a.cnt, 1ull);
       if (k == 0) atomicAdd(a.cnt + 1, 1ull);
-      if (!skipped) {
-        atomicAdd(a.cnt + 3, 1ull);
-        // per sweep 15 rounds of 8 column pairs: norms and inner product
-        // (6 mm), the two columns of C V and of V rotated (6 mm + 96); the
-        // rebuild 2 mm nn per kept pair
-        const double fl = (double)sweeps * 15.0 * 8.0 * (12.0 * mm + 96.0) + 2.0 * mm * nn * k;
-        atomicAdd(a.cnt + 5, (unsigned long long)fl);
-      }
+      if (!skipped) atomicAdd(a.cnt + 3, 1ull);
+      // per sweep 15 rounds of 8 column pairs: norms and inner product
+      // (6 mm), the two columns of C V and of V rotated (6 mm + 96); the
+      // rebuild 2 mm nn per kept pair
+      const double fj = (double)sweeps * 15.0 * 8.0 * (12.0 * mm + 96.0) + 2.0 * mm * nn * k;
+      if (fl > 0.f || fj > 0.0) atomicAdd(a.cnt + 5, (unsigned long long)(fj + fl));
     }
   }
 }

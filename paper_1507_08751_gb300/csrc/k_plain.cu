@@ -10,9 +10,9 @@
 // It exists to be timed beside the optimised path (msllr_params.plain): no
 // skip bound, no certificate, no batching of blocks into one launch.  Per
 // block three launches: the Gram matrix (a grid of 16 x 16 tiles), the
-// Jacobi eigen-solve (one CTA; G and V in shared memory up to 64 wide, else
-// in a global scratch that the launches on the one stream reuse) and the
-// rebuild (a grid of row slabs).
+// Jacobi eigen-solve (one CTA, G packed in shared memory, V and Q in a
+// global scratch that the launches on the one stream reuse) and the rebuild
+// (a grid of row slabs).
 #include <math.h>
 
 #include "common.cuh"
@@ -22,23 +22,12 @@ namespace msllr {
 
 namespace {
 
-constexpr int kPlainSmemN = 64;   // widest block with G, V, Q in shared memory
+constexpr int kPlainSmemN = 64;   // widest block solved by a 256-thread CTA (1024 above)
 constexpr int kStageFloats = 8192;  // rows of C staged for the rebuild
 constexpr int kMaxSweeps = 24;
 
 __device__ __forceinline__ BlockGeom plain_geom(const ScaleLaunch& a, int b) {
-  BlockGeom g;
-  g.M = a.M;
-  g.N = a.N;
-  g.ld = a.ld;
-  g.m = a.m;
-  g.n = a.n;
-  const int nbn = a.N / a.n;
-  g.p = b / nbn;
-  g.q = b - g.p * nbn;
-  g.sr = a.shift ? a.shift[0] % a.M : 0;
-  g.sc = a.shift ? a.shift[1] % a.N : 0;
-  return g;
+  return block_geom(a, b);
 }
 
 // element (i, c) of C = the block (m >= n) or its transpose
@@ -97,39 +86,57 @@ __global__ void __launch_bounds__(256) plain_gram_kernel(ScaleLaunch a, int b, f
   if (i0 + ty < nn && j0 + tx < nn) G[(i0 + ty) * nn + j0 + tx] = acc;
 }
 
+// packed lower-triangle index of symmetric G(i, j)
+__device__ __forceinline__ int tri(int i, int j) {
+  return i >= j ? i * (i + 1) / 2 + j : j * (j + 1) / 2 + i;
+}
+
 // Launch 2 of a block, one CTA: the eigen-decomposition G = V diag(lambda)
-// V^T by the cyclic Jacobi method, then Q = V diag(f) V^T with
-// f_j = max(1 - tau / sqrt(lambda_j), 0).  G, V in shared memory for blocks
-// up to 64 wide (NT = 256 threads), else in the global scratch (NT = 1024).
-template <bool SMEM, int NT>
+// V^T by the parallel cyclic Jacobi method (Golub & Van Loan, Sec. 8.5.4):
+// each round rotates np / 2 disjoint pairs at once, so the new G is
+// J^T G J with J their product, applied 2 x 2 block by 2 x 2 block (block
+// (P1, P2) holds rows {p1, q1} and columns {p2, q2}: B' = R1^T B R2).  G is
+// kept packed (lower triangle) in shared memory, V^T row by row in the
+// global scratch.  Then Q = V diag(f) V^T with f_j = max(1 - tau /
+// sqrt(lambda_j), 0).
+template <int NT>
 __global__ void __launch_bounds__(NT) plain_jacobi_kernel(ScaleLaunch a, int b, float* gscr) {
   extern __shared__ float sm[];
   const int tid = threadIdx.x;
   const int nn = a.m < a.n ? a.m : a.n;
   const int nn2 = nn * nn;
-  float* G = SMEM ? sm : gscr;
-  float* V = G + nn2;
+  const float* Gin = gscr;  // full G from the Gram launch
+  float* Vt = gscr + nn2;   // V^T: row j is eigenvector j
   float* Q = gscr + 2 * nn2;
-  float* red = SMEM ? V + nn2 : sm;  // 32 floats
-  float* cs = red + 32;              // rotation (c, s) per pair, then f_j
-  for (int e = tid; e < nn2; e += NT) {
-    if (SMEM) G[e] = gscr[e];
-    V[e] = (e / nn == e % nn) ? 1.f : 0.f;
+  const int ntri = nn * (nn + 1) / 2;
+  float* G = sm;                              // packed lower triangle
+  float* red = sm + ((ntri + 3) & ~3);        // NT / 32 floats
+  float* cs = red + NT / 32;                  // (c, s) per pair, then f_j
+  for (int e = tid; e < ntri; e += NT) {
+    int i = (int)((sqrtf(8.f * (float)e + 1.f) - 1.f) * 0.5f);
+    while ((i + 1) * (i + 2) / 2 <= e) ++i;
+    while (i * (i + 1) / 2 > e) --i;
+    G[e] = Gin[i * nn + (e - i * (i + 1) / 2)];
   }
+  for (int e = tid; e < nn2; e += NT) Vt[e] = (e / nn == e % nn) ? 1.f : 0.f;
   __syncthreads();
 
-  // cyclic Jacobi: sweeps of np - 1 rounds of disjoint rotations (an odd
-  // width pairs the last index with a dummy that no rotation touches) until
-  // the off-diagonal part is below 1e-6 of ||G||_F, or a sweep has stopped
-  // reducing it (rounding level reached)
+  // sweeps of np - 1 rounds (an odd width pairs the last index with a dummy
+  // that no rotation touches) until the off-diagonal part is below 1e-6 of
+  // ||G||_F, or a sweep has stopped reducing it (rounding level reached)
   const int np = (nn + 1) & ~1, npairs = np / 2;
+  const int nblk = npairs * (npairs + 1) / 2;
   float off_prev = 0.f;
   for (int sweep = 0; sweep < kMaxSweeps; ++sweep) {
     float off = 0.f, tot = 0.f;
-    for (int e = tid; e < nn2; e += NT) {
+    for (int e = tid; e < ntri; e += NT) {
       const float v = G[e];
-      tot = fmaf(v, v, tot);
-      if (e / nn != e % nn) off = fmaf(v, v, off);
+      int i = (int)((sqrtf(8.f * (float)e + 1.f) - 1.f) * 0.5f);
+      while ((i + 1) * (i + 2) / 2 <= e) ++i;
+      while (i * (i + 1) / 2 > e) --i;
+      const bool diag = e == i * (i + 1) / 2 + i;
+      tot = fmaf(diag ? v : 2.f * v, v, tot);
+      if (!diag) off = fmaf(2.f * v, v, off);
     }
     off = cta_sum<NT>(off, red);
     tot = cta_sum<NT>(tot, red);
@@ -143,9 +150,9 @@ __global__ void __launch_bounds__(NT) plain_jacobi_kernel(ScaleLaunch a, int b, 
         rr_pair(np, k, t, &p, &q);
         float c = 1.f, s = 0.f;
         if (p < nn && q < nn) {
-          const float apq = G[p * nn + q];
+          const float apq = G[tri(p, q)];
           if (apq != 0.f) {
-            const float theta = (G[q * nn + q] - G[p * nn + p]) / (2.f * apq);
+            const float theta = (G[tri(q, q)] - G[tri(p, p)]) / (2.f * apq);
             const float tt = copysignf(1.f, theta) / (fabsf(theta) + sqrtf(1.f + theta * theta));
             c = 1.f / sqrtf(1.f + tt * tt);
             s = tt * c;
@@ -155,31 +162,52 @@ __global__ void __launch_bounds__(NT) plain_jacobi_kernel(ScaleLaunch a, int b, 
         cs[2 * t + 1] = s;
       }
       __syncthreads();
-      // rows p, q  <-  J^T G
-      for (int e = tid; e < npairs * nn; e += NT) {
-        const int t = e / nn, j = e - t * nn;
-        int p, q;
-        rr_pair(np, k, t, &p, &q);
-        if (p >= nn || q >= nn) continue;
-        const float c = cs[2 * t], s = cs[2 * t + 1];
-        const float gp = G[p * nn + j], gq = G[q * nn + j];
-        G[p * nn + j] = c * gp - s * gq;
-        G[q * nn + j] = s * gp + c * gq;
+      // G <- J^T G J, one 2 x 2 block (P1 >= P2) per item
+      for (int e = tid; e < nblk; e += NT) {
+        int P1 = (int)((sqrtf(8.f * (float)e + 1.f) - 1.f) * 0.5f);
+        while ((P1 + 1) * (P1 + 2) / 2 <= e) ++P1;
+        while (P1 * (P1 + 1) / 2 > e) --P1;
+        const int P2 = e - P1 * (P1 + 1) / 2;
+        int p1, q1, p2, q2;
+        rr_pair(np, k, P1, &p1, &q1);
+        rr_pair(np, k, P2, &p2, &q2);
+        const float c1 = cs[2 * P1], s1 = cs[2 * P1 + 1];
+        const float c2 = cs[2 * P2], s2 = cs[2 * P2 + 1];
+        if (P1 == P2) {
+          if (p1 >= nn || q1 >= nn) continue;
+          const float gpp = G[tri(p1, p1)], gqq = G[tri(q1, q1)], gpq = G[tri(p1, q1)];
+          // [c -s; s c] [gpp gpq; gpq gqq] [c s; -s c]; the off-diagonal is zeroed
+          G[tri(p1, p1)] = c1 * (c1 * gpp - s1 * gpq) - s1 * (c1 * gpq - s1 * gqq);
+          G[tri(q1, q1)] = s1 * (s1 * gpp + c1 * gpq) + c1 * (s1 * gpq + c1 * gqq);
+          G[tri(p1, q1)] = 0.f;
+        } else {
+          // rows {p1, q1} x columns {p2, q2}; an index past nn (the dummy)
+          // has no entries
+          const bool r0 = p1 < nn, r1 = q1 < nn, k0 = p2 < nn, k1 = q2 < nn;
+          const float b00 = (r0 && k0) ? G[tri(p1, p2)] : 0.f;
+          const float b01 = (r0 && k1) ? G[tri(p1, q2)] : 0.f;
+          const float b10 = (r1 && k0) ? G[tri(q1, p2)] : 0.f;
+          const float b11 = (r1 && k1) ? G[tri(q1, q2)] : 0.f;
+          // left: rows p1, q1 by R1^T
+          const float t00 = c1 * b00 - s1 * b10, t01 = c1 * b01 - s1 * b11;
+          const float t10 = s1 * b00 + c1 * b10, t11 = s1 * b01 + c1 * b11;
+          // right: columns p2, q2 by R2
+          if (r0 && k0) G[tri(p1, p2)] = c2 * t00 - s2 * t01;
+          if (r0 && k1) G[tri(p1, q2)] = s2 * t00 + c2 * t01;
+          if (r1 && k0) G[tri(q1, p2)] = c2 * t10 - s2 * t11;
+          if (r1 && k1) G[tri(q1, q2)] = s2 * t10 + c2 * t11;
+        }
       }
-      __syncthreads();
-      // columns p, q  <-  G J, and V J
+      // V <- V J: rows p, q of V^T
       for (int e = tid; e < npairs * nn; e += NT) {
         const int t = e / nn, i = e - t * nn;
         int p, q;
         rr_pair(np, k, t, &p, &q);
         if (p >= nn || q >= nn) continue;
         const float c = cs[2 * t], s = cs[2 * t + 1];
-        const float gp = G[i * nn + p], gq = G[i * nn + q];
-        G[i * nn + p] = c * gp - s * gq;
-        G[i * nn + q] = s * gp + c * gq;
-        const float vp = V[i * nn + p], vq = V[i * nn + q];
-        V[i * nn + p] = c * vp - s * vq;
-        V[i * nn + q] = s * vp + c * vq;
+        const float vp = Vt[p * nn + i], vq = Vt[q * nn + i];
+        Vt[p * nn + i] = c * vp - s * vq;
+        Vt[q * nn + i] = s * vp + c * vq;
       }
       __syncthreads();
     }
@@ -188,7 +216,7 @@ __global__ void __launch_bounds__(NT) plain_jacobi_kernel(ScaleLaunch a, int b, 
   // soft threshold of the singular values sigma_j = sqrt(lambda_j)
   float* f = cs;
   for (int j = tid; j < nn; j += NT) {
-    const float sig = sqrtf(fmaxf(G[j * nn + j], 0.f));
+    const float sig = sqrtf(fmaxf(G[tri(j, j)], 0.f));
     f[j] = sig > a.tau ? 1.f - a.tau / sig : 0.f;
   }
   __syncthreads();
@@ -198,7 +226,7 @@ __global__ void __launch_bounds__(NT) plain_jacobi_kernel(ScaleLaunch a, int b, 
     for (int j = 0; j < nn; ++j)
       if (f[j] > 0.f) {
         ++k;
-        nuc += (double)(sqrtf(fmaxf(G[j * nn + j], 0.f)) - a.tau);
+        nuc += (double)(sqrtf(fmaxf(G[tri(j, j)], 0.f)) - a.tau);
       }
     if (a.rank_out) a.rank_out[b] = k;
     if (a.nuc_acc && k > 0) atomicAdd(a.nuc_acc, nuc);
@@ -209,10 +237,9 @@ __global__ void __launch_bounds__(NT) plain_jacobi_kernel(ScaleLaunch a, int b, 
     const int c = e / nn, d = e - c * nn;
     float acc = 0.f;
     for (int j = 0; j < nn; ++j)
-      if (f[j] > 0.f) acc = fmaf(V[c * nn + j] * f[j], V[d * nn + j], acc);
+      if (f[j] > 0.f) acc = fmaf(Vt[j * nn + c] * f[j], Vt[j * nn + d], acc);
     Q[e] = acc;
   }
-  __syncthreads();
 }
 
 // Launch 3 of a block: Z' = C Q for a slab of rows per CTA (C staged, so that
@@ -241,8 +268,8 @@ __global__ void __launch_bounds__(256) plain_rebuild_kernel(ScaleLaunch a, int b
 }
 
 size_t plain_smem_bytes(int nn) {
-  const size_t small = nn <= kPlainSmemN ? 2 * (size_t)nn * nn : 0;
-  return sizeof(float) * (small + 32 + 2 * ((size_t)nn + 2));
+  const size_t ntri = ((size_t)nn * (nn + 1) / 2 + 3) & ~(size_t)3;
+  return sizeof(float) * (ntri + 1024 / 32 + 2 * ((size_t)nn + 2));
 }
 
 }  // namespace
@@ -253,11 +280,11 @@ size_t plain_scratch_bytes(int m, int n) {
 }
 
 cudaError_t configure_plain_kernels() {
-  cudaError_t e = cudaFuncSetAttribute(plain_jacobi_kernel<true, 256>,
+  cudaError_t e = cudaFuncSetAttribute(plain_jacobi_kernel<256>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)plain_smem_bytes(kPlainSmemN));
   if (e != cudaSuccess) return e;
-  return cudaFuncSetAttribute(plain_jacobi_kernel<false, 1024>,
+  return cudaFuncSetAttribute(plain_jacobi_kernel<1024>,
                               cudaFuncAttributeMaxDynamicSharedMemorySize,
                               (int)plain_smem_bytes(256));
 }
@@ -290,8 +317,8 @@ cudaError_t launch_plain(const ScaleLaunch& s, float* scratch, cudaStream_t st, 
       if (cudaError_t e = prof->after(st)) return e;
     if (prof)
       if (cudaError_t e = prof->before(st, KK_EIG)) return e;
-    if (nn <= kPlainSmemN) plain_jacobi_kernel<true, 256><<<1, 256, smem, st>>>(s, b, scratch);
-    else plain_jacobi_kernel<false, 1024><<<1, 1024, smem, st>>>(s, b, scratch);
+    if (nn <= kPlainSmemN) plain_jacobi_kernel<256><<<1, 256, smem, st>>>(s, b, scratch);
+    else plain_jacobi_kernel<1024><<<1, 1024, smem, st>>>(s, b, scratch);
     if (prof)
       if (cudaError_t e = prof->after(st)) return e;
     if (prof)

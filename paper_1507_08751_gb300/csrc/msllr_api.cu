@@ -50,9 +50,12 @@ struct ServeJob {
   uint64_t seed = 0;
   msllr_params p{};
   bool has_p = false;
+  std::vector<int> patch_w;  // copy of p.st_patch_w
   float* X_out = nullptr;
   float* Z_out = nullptr;
   msllr_stats* stats = nullptr;
+  size_t need = 0;       // device bytes the job holds while it runs
+  int running_with = 0;  // jobs running (this one included) when it was admitted
   int status = MSLLR_OK;
   bool done = false;
   std::string err;
@@ -68,6 +71,9 @@ struct msllr_ctx {
   // grow-only device workspace
   void* ws = nullptr;
   size_t ws_bytes = 0;
+  // grow-only device copies of the host API's inputs and outputs
+  void* io = nullptr;
+  size_t io_bytes = 0;
   // small device scalars
   int* d_small = nullptr;          // [0] iter, [1..2] cur shift, [3] nonfinite flag, [4..5] tmp shift
   double* d_acc = nullptr;         // [0..MAX) nuc per scale, [MAX] primal residual^2
@@ -88,17 +94,26 @@ struct msllr_ctx {
   // error message; written under err_mu (the serving worker runs concurrently)
   std::mutex err_mu;
 
-  // serving queue: one worker thread runs the submitted jobs in order
+  // serving queue: MSLLR_SERVE_SLOTS worker threads, each with a slot
+  // context of its own (stream, workspace, graph), take the queued jobs in
+  // submission order as device memory allows, so that admitted jobs run
+  // concurrently on the device
   std::mutex q_mu;
-  std::condition_variable q_cv;     // wakes the worker
+  std::condition_variable q_cv;     // wakes the workers
   std::condition_variable done_cv;  // a job finished
   std::deque<std::shared_ptr<ServeJob>> queue;
   std::unordered_map<uint64_t, std::shared_ptr<ServeJob>> jobs;
   uint64_t next_job = 1;
-  std::thread worker;
-  bool worker_started = false;
+  std::vector<msllr_ctx*> slots;
+  std::vector<std::thread> workers;
+  size_t serve_bytes = 0;   // device bytes held by the running jobs
+  int serve_running = 0;    // running jobs
   bool stop = false;
   std::atomic<int> in_flight{0};
+  // a serving slot's context: its workspace and slabs are allocated and
+  // freed in stream order (cudaMallocAsync / cudaFreeAsync), so that one
+  // slot's allocations never wait for the other slots' work
+  bool serve_child = false;
 
   // cached graph of one iteration
   cudaGraphExec_t graph = nullptr;
@@ -162,13 +177,17 @@ size_t align_up(size_t x) { return (x + 255) & ~(size_t)255; }
 // Make sure the context workspace holds at least `bytes`.
 int ensure_ws(msllr_ctx* ctx, size_t bytes) {
   if (bytes <= ctx->ws_bytes) return MSLLR_OK;
-  if (ctx->budget && bytes > ctx->budget)
+  if (ctx->budget && bytes + ctx->io_bytes > ctx->budget)
     return fail(ctx, MSLLR_ENOMEM,
                 "workspace of " + std::to_string(bytes) + " bytes exceeds the HBM budget of " +
                     std::to_string(ctx->budget));
   if (ctx->ws) {
-    cudaStreamSynchronize(ctx->stream);
-    cudaFree(ctx->ws);
+    if (ctx->serve_child) {
+      cudaFreeAsync(ctx->ws, ctx->stream);
+    } else {
+      cudaStreamSynchronize(ctx->stream);
+      cudaFree(ctx->ws);
+    }
     ctx->ws = nullptr;
     ctx->ws_bytes = 0;
   }
@@ -177,7 +196,8 @@ int ensure_ws(msllr_ctx* ctx, size_t bytes) {
     ctx->graph = nullptr;
     ctx->graph_key.clear();
   }
-  cudaError_t e = cudaMalloc(&ctx->ws, bytes);
+  cudaError_t e = ctx->serve_child ? cudaMallocAsync(&ctx->ws, bytes, ctx->stream)
+                                   : cudaMalloc(&ctx->ws, bytes);
   if (e != cudaSuccess) {
     cudaGetLastError();
     ctx->ws = nullptr;
@@ -274,18 +294,20 @@ int msllr_create(msllr_ctx** out, int device, size_t hbm_budget_bytes, void* cud
 
 int msllr_destroy(msllr_ctx* ctx) {
   if (!ctx) return MSLLR_OK;
-  if (ctx->worker_started) {
+  if (!ctx->workers.empty()) {
     {
       std::lock_guard<std::mutex> lk(ctx->q_mu);
-      ctx->stop = true;  // the running job completes, queued ones are dropped
+      ctx->stop = true;  // the running jobs complete, queued ones are dropped
     }
     ctx->q_cv.notify_all();
-    ctx->worker.join();
+    for (auto& w : ctx->workers) w.join();
   }
+  for (msllr_ctx* child : ctx->slots) msllr_destroy(child);
   cudaSetDevice(ctx->device);
   if (ctx->stream) cudaStreamSynchronize(ctx->stream);
   if (ctx->graph) cudaGraphExecDestroy(ctx->graph);
   if (ctx->ws) cudaFree(ctx->ws);
+  if (ctx->io) cudaFree(ctx->io);
   if (ctx->d_phase) {
     unsigned long long h[8 * 16 * 2];
     if (cudaMemcpy(h, ctx->d_phase, sizeof h, cudaMemcpyDeviceToHost) == cudaSuccess) {
@@ -483,6 +505,8 @@ int enqueue_iteration(msllr_ctx* ctx, const Layout& lay, int M, int N, int L, co
       s.nuc_acc = stats ? ctx->d_acc + i : nullptr;
       s.cnt = (stats || p.profile) ? ctx->d_cnt + 8 * i : nullptr;
       s.norm_acc = ctx->d_noise + i;
+      s.bw = p.st_patch_w ? p.st_patch_w[i] : 0;
+      s.fw = s.bw > 0 ? p.frame_w : 0;
       prof->scale = i;
       CK(launch_plain(s, lay.plain, ctx->stream, prof));
     }
@@ -528,6 +552,8 @@ int enqueue_iteration(msllr_ctx* ctx, const Layout& lay, int M, int N, int L, co
       // block counts: the last iteration, or every iteration of a profiled run
       s.cnt = (stats || p.profile) ? ctx->d_cnt + 8 * i : nullptr;
       s.norm_acc = ctx->d_noise + i;
+      s.bw = p.st_patch_w ? p.st_patch_w[i] : 0;
+      s.fw = s.bw > 0 ? p.frame_w : 0;
       prof->scale = i;
       const bool gate = fork && wide && i > 0;
       // one block SVT, or the average over the scale's shift set
@@ -589,6 +615,19 @@ int decompose_device(msllr_ctx* ctx, const float* Y, int M, int N, int ld, int L
   if (p.spin_grid < 0) return fail(ctx, MSLLR_EINVAL, "spin_grid must be >= 0");
   if (p.plain && p.spin_grid > 1)
     return fail(ctx, MSLLR_EINVAL, "the plain comparator path takes no spin_grid");
+  for (int i = 0; i < L && p.st_patch_w; ++i) {
+    const int bw = p.st_patch_w[i];
+    if (bw == 0) continue;
+    const int fw = p.frame_w;
+    if (bw < 0 || fw <= 0 || M % fw || fw % bw || bm[i] <= 0 || bn[i] <= 0 || bm[i] % bw ||
+        (M / fw) % (bm[i] / bw) || N % bn[i])
+      return fail(ctx, MSLLR_EINVAL,
+                  "spatio-temporal scale " + std::to_string(i) +
+                      ": needs frame_w > 0 dividing M, bw | frame_w, bh = block_m / bw | M / frame_w, "
+                      "block_n | N");
+    if (p.spin_grid > 1)
+      return fail(ctx, MSLLR_EINVAL, "spin_grid does not combine with spatio-temporal scales");
+  }
   for (int i = 0; i < L && p.plain; ++i)
     if (choose_path(bm[i], bn[i]) == ScalePath::Huge)
       return fail(ctx, MSLLR_EINVAL, "the plain comparator path takes blocks up to 256 wide");
@@ -645,7 +684,10 @@ int decompose_device(msllr_ctx* ctx, const float* Y, int M, int N, int ld, int L
   // shift table for iterations iter_offset .. iter_offset + iters - 1
   const size_t tab = 2 * (size_t)(iters > 0 ? iters : 1);
   if (tab > ctx->table_cap) {
-    if (ctx->d_table) cudaFree(ctx->d_table);
+    if (ctx->d_table) {
+      if (ctx->serve_child) cudaFreeAsync(ctx->d_table, st);
+      else cudaFree(ctx->d_table);
+    }
     ctx->d_table = nullptr;
     ctx->table_cap = 0;
     if (ctx->graph) {
@@ -653,7 +695,8 @@ int decompose_device(msllr_ctx* ctx, const float* Y, int M, int N, int ld, int L
       ctx->graph = nullptr;
       ctx->graph_key.clear();
     }
-    CK(cudaMalloc(&ctx->d_table, tab * sizeof(int)));
+    if (ctx->serve_child) CK(cudaMallocAsync((void**)&ctx->d_table, tab * sizeof(int), st));
+    else CK(cudaMalloc(&ctx->d_table, tab * sizeof(int)));
     ctx->table_cap = tab;
   }
   std::vector<int32_t> h_table(tab, 0);
@@ -678,8 +721,12 @@ int decompose_device(msllr_ctx* ctx, const float* Y, int M, int N, int ld, int L
     put(bm, sizeof(int) * L);
     put(bn, sizeof(int) * L);
     put(taus, sizeof(float) * L);
-    const int flags[4] = {p.skip_bound, p.cycle_spin, mask != nullptr, p.spin_grid};
+    const int flags[5] = {p.skip_bound, p.cycle_spin, mask != nullptr, p.spin_grid, p.frame_w};
     put(flags, sizeof flags);
+    for (int i = 0; i < L; ++i) {
+      const int bw = p.st_patch_w ? p.st_patch_w[i] : 0;
+      put(&bw, sizeof bw);
+    }
     void* wsp = ctx->ws;
     put(&wsp, sizeof wsp);
     if (!ctx->graph || key != ctx->graph_key) {
@@ -809,17 +856,18 @@ int run_job(msllr_ctx* ctx, ServeJob& j) {
   float* dX = nullptr;
   float* dZ = nullptr;
   uint8_t* dmask = nullptr;
+  cudaStream_t s = ctx->stream;
   auto cleanup = [&]() {
-    if (dY) cudaFree(dY);
-    if (dX) cudaFree(dX);
-    if (dZ) cudaFree(dZ);
-    if (dmask) cudaFree(dmask);
+    if (dY) cudaFreeAsync(dY, s);
+    if (dX) cudaFreeAsync(dX, s);
+    if (dZ) cudaFreeAsync(dZ, s);
+    if (dmask) cudaFreeAsync(dmask, s);
   };
   CK(cudaSetDevice(ctx->device));
-  if (cudaMalloc(&dY, sizeof(float) * MN) != cudaSuccess ||
-      cudaMalloc(&dX, sizeof(float) * j.L * MN) != cudaSuccess ||
-      (j.Z_out && cudaMalloc(&dZ, sizeof(float) * j.L * MN) != cudaSuccess) ||
-      (!j.mask.empty() && cudaMalloc(&dmask, MN) != cudaSuccess)) {
+  if (cudaMallocAsync((void**)&dY, sizeof(float) * MN, s) != cudaSuccess ||
+      cudaMallocAsync((void**)&dX, sizeof(float) * j.L * MN, s) != cudaSuccess ||
+      (j.Z_out && cudaMallocAsync((void**)&dZ, sizeof(float) * j.L * MN, s) != cudaSuccess) ||
+      (!j.mask.empty() && cudaMallocAsync((void**)&dmask, MN, s) != cudaSuccess)) {
     cudaGetLastError();
     cleanup();
     return fail(ctx, MSLLR_ENOMEM, "serving job: device buffers");
@@ -848,36 +896,83 @@ int run_job(msllr_ctx* ctx, ServeJob& j) {
                                      cudaGetErrorString(e));
   }
   cleanup();
+  // the slot keeps no memory between jobs: the admission of the next jobs
+  // counts only what the running ones hold
+  if (ctx->graph) {
+    cudaGraphExecDestroy(ctx->graph);
+    ctx->graph = nullptr;
+    ctx->graph_key.clear();
+  }
+  if (ctx->ws) cudaFreeAsync(ctx->ws, s);
+  ctx->ws = nullptr;
+  ctx->ws_bytes = 0;
+  if (ctx->d_table) cudaFreeAsync(ctx->d_table, s);
+  ctx->d_table = nullptr;
+  ctx->table_cap = 0;
+  cudaStreamSynchronize(s);
   return r;
 }
 
-// The serving worker: takes the queued jobs in submission order until the
-// context is destroyed.
-void serve_loop(msllr_ctx* ctx) {
+// A serving worker: takes the job at the head of the queue once the device
+// memory held by the running jobs leaves room for it (submission order, no
+// overtaking), runs it on its slot context, and repeats until the context is
+// destroyed.
+void serve_loop(msllr_ctx* ctx, int slot) {
+  msllr_ctx* child = ctx->slots[slot];
   for (;;) {
     std::shared_ptr<ServeJob> job;
     {
       std::unique_lock<std::mutex> lk(ctx->q_mu);
-      ctx->q_cv.wait(lk, [&] { return ctx->stop || !ctx->queue.empty(); });
+      ctx->q_cv.wait(lk, [&] {
+        if (ctx->stop) return true;
+        if (ctx->queue.empty()) return false;
+        return !ctx->budget || ctx->serve_bytes + ctx->queue.front()->need <= ctx->budget;
+      });
       if (ctx->stop) return;
       job = ctx->queue.front();
       ctx->queue.pop_front();
+      ctx->serve_bytes += job->need;
+      job->running_with = ++ctx->serve_running;
     }
-    const int r = run_job(ctx, *job);
+    const int r = run_job(child, *job);
     std::string msg;
     if (r != MSLLR_OK) {
-      std::lock_guard<std::mutex> lk(ctx->err_mu);
-      msg = ctx->err;
+      std::lock_guard<std::mutex> lk(child->err_mu);
+      msg = child->err;
+    } else if (job->stats) {
+      job->stats->serve_jobs_running = job->running_with;
     }
     {
       std::lock_guard<std::mutex> lk(ctx->q_mu);
       job->status = r;
       job->err = msg;
       job->done = true;
+      ctx->serve_bytes -= job->need;
+      --ctx->serve_running;
       ctx->in_flight.fetch_sub(1);
     }
     ctx->done_cv.notify_all();
+    ctx->q_cv.notify_all();  // memory came free: the head job may fit now
   }
+}
+
+// Creates the serving slots and their workers (first submission).
+int start_serving(msllr_ctx* ctx) {
+  for (int i = 0; i < MSLLR_SERVE_SLOTS; ++i) {
+    cudaStream_t st = nullptr;
+    CK(cudaSetDevice(ctx->device));
+    CK(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking));
+    msllr_ctx* child = nullptr;
+    if (int r = msllr_create(&child, ctx->device, 0, st)) {
+      cudaStreamDestroy(st);
+      return fail(ctx, r, std::string("serving slot: ") + msllr_last_error(nullptr));
+    }
+    child->own_stream = true;
+    child->serve_child = true;
+    ctx->slots.push_back(child);
+  }
+  for (int i = 0; i < MSLLR_SERVE_SLOTS; ++i) ctx->workers.emplace_back(serve_loop, ctx, i);
+  return MSLLR_OK;
 }
 
 // a finished job leaves the table and hands its status (and message) back
@@ -912,24 +1007,32 @@ int msllr_decompose_host(msllr_ctx* ctx, const float* Y, int M, int N, int ld, i
     return fail(ctx, MSLLR_EINVAL, "msllr_decompose_host takes no device state pointers");
   CK(cudaSetDevice(ctx->device));
   const size_t MN = (size_t)M * N;
-  float* dY = nullptr;
-  float* dX = nullptr;
-  float* dZ = nullptr;
-  uint8_t* dmask = nullptr;
-  auto cleanup = [&]() {
-    if (dY) cudaFree(dY);
-    if (dX) cudaFree(dX);
-    if (dZ) cudaFree(dZ);
-    if (dmask) cudaFree(dmask);
-  };
-  if (cudaMalloc(&dY, sizeof(float) * MN) != cudaSuccess ||
-      cudaMalloc(&dX, sizeof(float) * L * MN) != cudaSuccess ||
-      (Z_out && cudaMalloc(&dZ, sizeof(float) * L * MN) != cudaSuccess) ||
-      (mask && cudaMalloc(&dmask, MN) != cudaSuccess)) {
-    cudaGetLastError();
-    cleanup();
-    return fail(ctx, MSLLR_ENOMEM, "msllr_decompose_host: device buffers");
+  // device copies of Y, X, Z and the mask in the context's grow-only I/O
+  // slab: after the first call of a size, no allocation per call
+  const size_t bY = align_up(sizeof(float) * MN), bX = align_up(sizeof(float) * L * MN);
+  const size_t need = bY + bX + (Z_out ? bX : 0) + (mask ? align_up(MN) : 0);
+  if (need > ctx->io_bytes) {
+    if (ctx->budget && need + ctx->ws_bytes > ctx->budget)
+      return fail(ctx, MSLLR_ENOMEM, "msllr_decompose_host: device copies exceed the HBM budget");
+    if (ctx->io) {
+      cudaStreamSynchronize(ctx->stream);
+      cudaFree(ctx->io);
+      ctx->io = nullptr;
+      ctx->io_bytes = 0;
+    }
+    if (cudaMalloc(&ctx->io, need) != cudaSuccess) {
+      cudaGetLastError();
+      ctx->io = nullptr;
+      return fail(ctx, MSLLR_ENOMEM, "msllr_decompose_host: device buffers");
+    }
+    ctx->io_bytes = need;
   }
+  char* io = (char*)ctx->io;
+  float* dY = (float*)io;
+  float* dX = (float*)(io + bY);
+  float* dZ = Z_out ? (float*)(io + bY + bX) : nullptr;
+  uint8_t* dmask = mask ? (uint8_t*)(io + bY + bX + (Z_out ? bX : 0)) : nullptr;
+  auto cleanup = [&]() {};
   cudaError_t e = cudaMemcpy2DAsync(dY, sizeof(float) * N, Y, sizeof(float) * ld,
                                     sizeof(float) * N, M, cudaMemcpyHostToDevice, ctx->stream);
   if (e == cudaSuccess && mask)
@@ -973,8 +1076,9 @@ int msllr_submit(msllr_ctx* ctx, const msllr_job* job, uint64_t* job_id) {
                            plain).total +
                       sizeof(float) * MN * (1 + (size_t)L * (job->Z_out ? 2 : 1)) +
                       (job->mask ? MN : 0);
-  if (ctx->budget && need > ctx->budget)
-    return fail(ctx, MSLLR_ENOMEM, "msllr_submit: job needs " + std::to_string(need) +
+  const size_t need_all = need + 2 * sizeof(int) * (size_t)(job->iters > 0 ? job->iters : 1);
+  if (ctx->budget && need_all > ctx->budget)
+    return fail(ctx, MSLLR_ENOMEM, "msllr_submit: job needs " + std::to_string(need_all) +
                                        " bytes, above the HBM budget");
   auto j = std::make_shared<ServeJob>();
   j->M = M;
@@ -993,22 +1097,25 @@ int msllr_submit(msllr_ctx* ctx, const msllr_job* job, uint64_t* job_id) {
   if (job->params) {
     j->p = *job->params;
     j->has_p = true;
+    if (j->p.st_patch_w) {
+      j->patch_w.assign(j->p.st_patch_w, j->p.st_patch_w + L);
+      j->p.st_patch_w = j->patch_w.data();
+    }
   }
   j->X_out = job->X_out;
   j->Z_out = job->Z_out;
   j->stats = job->stats;
+  j->need = need_all;
   {
     std::lock_guard<std::mutex> lk(ctx->q_mu);
     if ((int)ctx->queue.size() >= MSLLR_SERVE_QUEUE)
       return fail(ctx, MSLLR_EBUSY, "msllr_submit: the serving queue is full");
+    if (ctx->slots.empty())
+      if (int r = start_serving(ctx)) return r;
     j->id = ctx->next_job++;
     ctx->jobs[j->id] = j;
     ctx->queue.push_back(j);
     ctx->in_flight.fetch_add(1);
-    if (!ctx->worker_started) {
-      ctx->worker = std::thread(serve_loop, ctx);
-      ctx->worker_started = true;
-    }
   }
   ctx->q_cv.notify_one();
   *job_id = j->id;

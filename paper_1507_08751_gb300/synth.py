@@ -66,6 +66,32 @@ def video(seed=BASE_SEED + 1, M=16384, N=256, mid=(16, 64, 256), p_mid=0.02,
     return comps.sum(axis=0).astype(np.float32), comps, scales
 
 
+def video3d(seed=BASE_SEED + 3, H=64, W=64, T=64, blocks=((4, 4, 4), (16, 16, 16)), p_active=0.05,
+            p_sparse=0.01):
+    """Video matrix of H x W-pixel frames by T frames (row y W + x for pixel
+    (y, x)) with spatio-temporal structure at the given bh x bw x bt block
+    sizes (the Sec. 10.2 partitions): each block of the video cube is active
+    with probability p_active and then holds a rank-1 term (a Gaussian patch
+    image times a Gaussian time course), plus a rank-1 Gaussian background
+    and a p_sparse foreground of uniform(0, 1) values.
+    Returns (Y float32, scales with the full matrix last, frame (H, W))."""
+    rng = np.random.default_rng(seed)
+    V = np.zeros((H, W, T))
+    for bh, bw, bt in blocks:
+        for y0 in range(0, H, bh):
+            for x0 in range(0, W, bw):
+                for t0 in range(0, T, bt):
+                    if rng.random() < p_active:
+                        patch = rng.standard_normal((bh, bw))
+                        course = rng.standard_normal(bt)
+                        V[y0:y0 + bh, x0:x0 + bw, t0:t0 + bt] += patch[:, :, None] * course
+    Y = V.reshape(H * W, T)
+    Y += np.outer(rng.standard_normal(H * W), rng.standard_normal(T))
+    Y += (rng.random((H * W, T)) < p_sparse) * rng.random((H * W, T))
+    scales = [(1, 1)] + [tuple(b) for b in blocks] + [(H * W, T)]
+    return Y.astype(np.float32), scales, (H, W)
+
+
 def dyadic_scales(M, N, L, base=4):
     """Two-sided dyadic partition of the batching/serving workloads:
     1x1, then base^k x base^k for k = 1..L-2 (clamped so that blocks divide

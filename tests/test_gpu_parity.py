@@ -473,6 +473,34 @@ def test_stopping_test_ends_the_run_and_matches_the_oracle(ctx):
     assert full["stopped"] == 0 and full["iters"] == 50
 
 
+def test_decompose_spatio_temporal_blocks_matches_oracle(ctx):
+    """The video partitions of Sec. 10.2: 4x4x4 and 16x16x16 spatio-temporal
+    blocks (pixel patches over runs of frames, reshaped to 16 x 4 and 256 x 16
+    matrices) next to the 1x1 and full-matrix scales of a 64x64-pixel,
+    64-frame video, with the random shift moving the video cube, against the
+    oracle's spatio-temporal ADMM on the same shift table."""
+    from paper_1507_08751_gb300 import binding as B
+    Y32, scales, frame = synth.video3d()
+    M, N = Y32.shape
+    lam = [O.lambda_default(M, N, sc[0] * sc[1], sc[2]) if len(sc) == 3
+           else O.lambda_default(M, N, *sc) for sc in scales]
+    iters, seed = 30, 77
+    Xd = torch.empty((len(scales), M, N), dtype=torch.float32, device="cuda")
+    Zd = torch.empty_like(Xd)
+    ctx.msllr_decompose(dev(Y32), scales, Xd, lambdas=lam, iters=iters, seed=seed, Z_out=Zd,
+                        frame=frame)
+    torch.cuda.synchronize()
+    ref = O.admm(Y32.astype(np.float64), scales, lam, 1.0, iters,
+                 shifts=O.shift_table(seed, iters, M, N), frame=frame)
+    assert np.all(O.relerr(Xd.cpu().numpy(), ref["X"], Y32) <= TOL)
+    assert np.all(O.relerr(Zd.cpu().numpy(), ref["Z"], Y32) <= TOL)
+    # a patch width that does not divide the frame is refused
+    p = B.msllr_params_default()
+    with pytest.raises(B.MsllrError) as e:
+        ctx.msllr_decompose(dev(Y32), [(1, 1), (4, 3, 4)], Xd[:2], iters=1, frame=frame, params=p)
+    assert e.value.code == B.MSLLR_EINVAL
+
+
 def test_error_paths(ctx):
     from paper_1507_08751_gb300 import binding as B
     Y = torch.zeros((64, 64), dtype=torch.float32, device="cuda")

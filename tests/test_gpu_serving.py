@@ -113,3 +113,91 @@ def test_submit_rejects_bad_jobs(B):
         with pytest.raises(B.MsllrError) as e:
             ctx.msllr_wait(12345)
         assert e.value.code == B.MSLLR_EINVAL
+
+
+def _need_bytes(B, Y, scales, iters):
+    """The device footprint msllr_submit charges for a job (read from its
+    ENOMEM message under a one-byte budget)."""
+    import re
+    M, N = Y.shape
+    with B.Context(0, hbm_budget_bytes=1) as ctx:
+        with pytest.raises(B.MsllrError) as e:
+            ctx.msllr_submit(Y, scales, np.empty((len(scales), M, N), np.float32), iters=iters)
+    return int(re.search(r"needs (\d+) bytes", str(e.value)).group(1))
+
+
+def test_concurrent_jobs_overlap_and_match_solo_runs(B):
+    """Continuous batching: four jobs of different shapes (a masked one among
+    them) submitted together run at the same time on the device -- at least
+    three of them see others running when they start -- and each result is
+    bit for bit the result of the same job run alone."""
+    Y0, _, s0 = synth.video(M=1024, N=256)
+    Y1, s1 = synth.job(11, 512, 512, 5)
+    Y2, m2 = synth.ratings(7, 256, 256, density=0.05)
+    Y3, _, s3 = synth.tiny_64()
+    jobs = [
+        dict(Y=Y0.astype(np.float32), scales=s0, iters=200, seed=21, mask=None),
+        dict(Y=Y1, scales=s1, iters=200, seed=22, mask=None),
+        dict(Y=Y2, scales=synth.dyadic_scales(256, 256, 5), iters=200, seed=23, mask=m2),
+        dict(Y=Y3.astype(np.float32), scales=s3, iters=200, seed=24, mask=None),
+    ]
+    with B.Context(0) as ctx:
+        outs, ids = [], []
+        for j in jobs:
+            M, N = j["Y"].shape
+            X = np.full((len(j["scales"]), M, N), np.nan, np.float32)
+            outs.append(X)
+            ids.append(ctx.msllr_submit(j["Y"], j["scales"], X, iters=j["iters"], seed=j["seed"],
+                                        mask=j["mask"]))
+        stats = [ctx.msllr_wait(i) for i in ids]
+        running = [st["serve_jobs_running"] for st in stats]
+        assert max(running) >= 3, running
+        for j, X in zip(jobs, outs):
+            ref = np.empty_like(X)
+            ctx.msllr_decompose_host(j["Y"], j["scales"], ref, iters=j["iters"], seed=j["seed"],
+                                     mask=j["mask"])
+            np.testing.assert_array_equal(X, ref)
+
+
+def test_admission_holds_jobs_to_the_hbm_budget(B):
+    """With a budget that holds one job but not two, the queued jobs run one
+    at a time (each sees only itself running) and still all complete with
+    the solo result."""
+    Y, _, scales = synth.video(M=1024, N=256)
+    Y = Y.astype(np.float32)
+    need = _need_bytes(B, Y, scales, 40)
+    M, N = Y.shape
+    with B.Context(0, hbm_budget_bytes=int(1.5 * need)) as ctx:
+        outs = [np.empty((len(scales), M, N), np.float32) for _ in range(3)]
+        ids = [ctx.msllr_submit(Y, scales, X, iters=40, seed=9) for X in outs]
+        stats = [ctx.msllr_wait(i) for i in ids]
+        assert [st["serve_jobs_running"] for st in stats] == [1, 1, 1]
+        ref = np.empty_like(outs[0])
+        ctx.msllr_decompose_host(Y, scales, ref, iters=40, seed=9)
+        for X in outs:
+            np.testing.assert_array_equal(X, ref)
+
+
+def test_two_threads_waiting_on_one_job(B):
+    """Two host threads wait for the same job: one collects its status, the
+    other is told that the job was already collected (EINVAL), and neither
+    crashes."""
+    import threading
+    Y, _, scales = synth.video(M=1024, N=256)
+    Y = Y.astype(np.float32)
+    M, N = Y.shape
+    with B.Context(0) as ctx:
+        X = np.empty((len(scales), M, N), np.float32)
+        jid = ctx.msllr_submit(Y, scales, X, iters=100, seed=3)
+        codes = []
+
+        def waiter():
+            code = B.lib().msllr_wait(ctx._ctx, jid, -1)
+            codes.append(code)
+
+        ts = [threading.Thread(target=waiter) for _ in range(2)]
+        for t in ts:
+            t.start()
+        for t in ts:
+            t.join()
+        assert sorted(codes) == [B.MSLLR_OK, B.MSLLR_EINVAL]
