@@ -132,6 +132,16 @@ __device__ __forceinline__ BlockGeom block_geom(const SL& a, int b) {
   return g;
 }
 
+// block_geom for kernels instantiated per partition kind: with ST false the
+// launch is a 2-D scale (fw = 0) and the compiler drops the spatio-temporal
+// index arithmetic from the instantiation.
+template <bool ST, class SL>
+__device__ __forceinline__ BlockGeom block_geom_t(const SL& a, int b) {
+  BlockGeom g = block_geom(a, b);
+  if (!ST) g.fw = 0;
+  return g;
+}
+
 // Optional per-phase timing (debug aid, enabled by the MSLLR_PHASE_TIMING
 // environment variable): thread 0 of every CTA adds clock64() deltas between
 // phase marks to acc[(slot * 16 + phase) * 2] and counts to the next entry.

@@ -66,6 +66,7 @@ __device__ __forceinline__ float load_a(const ScaleLaunch& a, size_t off) {
   return v;
 }
 
+template <bool ST>
 __global__ void __launch_bounds__(kGramThreads, 5)
 gram_tiles_kernel(ScaleLaunch a, float* __restrict__ G, float* __restrict__ part, int chunks) {
   __shared__ __align__(16) float As[32][kTile + 4];
@@ -75,7 +76,7 @@ gram_tiles_kernel(ScaleLaunch a, float* __restrict__ G, float* __restrict__ part
   while (((ta + 1) * (ta + 2)) / 2 <= t) ++ta;
   while ((ta * (ta + 1)) / 2 > t) --ta;
   const int tc = t - (ta * (ta + 1)) / 2;
-  const BlockGeom g = make_geom(a, b);
+  const BlockGeom g = block_geom_t<ST>(a, b);
   const int mm = g.mm(), nn = g.nn();
   const int a0 = ta * kTile, c0 = tc * kTile;
   const int r_begin = chunk * kChunk;
@@ -438,8 +439,7 @@ rebuild_rows_kernel(ScaleLaunch a, const float* __restrict__ Yall, size_t ystrid
   const int b = blockIdx.y;
   const int k = kin[b];
   if (k > kRowK) return;  // rebuild_kernel takes the block
-  BlockGeom g = make_geom(a, b);
-  if (!ST) g.fw = 0;
+  const BlockGeom g = block_geom_t<ST>(a, b);
   const int mm = g.mm(), nn = g.nn();
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const float* Yb = Yall + (size_t)b * ystride;
@@ -499,12 +499,13 @@ rebuild_rows_kernel(ScaleLaunch a, const float* __restrict__ Yall, size_t ystrid
 // rank above kRowK (only the Householder path produces them).  The CTAs
 // stride over the (slab, block) items, so that a launch with nothing to do
 // holds few SMs.
+template <bool ST>
 __device__ __forceinline__ void rebuild_slab(const ScaleLaunch& a, const float* __restrict__ Yall,
                                              size_t ystride, const int* __restrict__ kin, int rs,
                                              int slab, int b) {
   extern __shared__ float sm[];
   const int tid = threadIdx.x;
-  const BlockGeom g = make_geom(a, b);
+  const BlockGeom g = block_geom_t<ST>(a, b);
   const int mm = g.mm(), nn = g.nn();
   const int r0 = slab * rs;
   const int rows = min(rs, mm - r0);
@@ -573,13 +574,14 @@ __device__ __forceinline__ void rebuild_slab(const ScaleLaunch& a, const float* 
   }
 }
 
+template <bool ST>
 __global__ void __launch_bounds__(kRebThreads)
 rebuild_kernel(ScaleLaunch a, const float* __restrict__ Yall, size_t ystride,
                const int* __restrict__ kin, int rs, int slabs, int nblocks) {
   for (int w = blockIdx.x; w < slabs * nblocks; w += gridDim.x) {
     const int b = w / slabs;
     if (kin[b] <= kRowK) continue;  // rebuild_rows_kernel took the block
-    rebuild_slab(a, Yall, ystride, kin, rs, w - b * slabs, b);
+    rebuild_slab<ST>(a, Yall, ystride, kin, rs, w - b * slabs, b);
     __syncthreads();
   }
 }
@@ -648,7 +650,10 @@ cudaError_t configure_big_kernels() {
   e = cudaFuncSetAttribute(eig_fallback_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            (int)fallback_smem_bytes(kEigMax));
   if (e != cudaSuccess) return e;
-  return cudaFuncSetAttribute(rebuild_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  e = cudaFuncSetAttribute(rebuild_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           100 * 1024);
+  if (e != cudaSuccess) return e;
+  return cudaFuncSetAttribute(rebuild_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                               100 * 1024);
 }
 
@@ -665,8 +670,9 @@ cudaError_t launch_big(const ScaleLaunch& s, const BigWorkspace& ws, cudaStream_
   if (prof)          \
     if (cudaError_t e_ = prof->after(st)) return e_;
   PROF_BEFORE(KK_GRAM)
-  gram_tiles_kernel<<<dim3(d.ntiles, d.chunks, d.nblocks), kGramThreads, 0, st>>>(s, ws.G, ws.part,
-                                                                                  d.chunks);
+  const dim3 ggrid(d.ntiles, d.chunks, d.nblocks);
+  if (s.fw) gram_tiles_kernel<true><<<ggrid, kGramThreads, 0, st>>>(s, ws.G, ws.part, d.chunks);
+  else gram_tiles_kernel<false><<<ggrid, kGramThreads, 0, st>>>(s, ws.G, ws.part, d.chunks);
   PROF_AFTER()
   if (d.chunks > 1) {
     PROF_BEFORE(KK_GRAM_REDUCE)
@@ -699,7 +705,11 @@ cudaError_t launch_big(const ScaleLaunch& s, const BigWorkspace& ws, cudaStream_
   const int slab_items = slabs * d.nblocks;
   const int nsm = sm_count();
   const int reb_grid = s.skip_bound ? (slab_items < nsm ? slab_items : nsm) : slab_items;
-  rebuild_kernel<<<reb_grid, kRebThreads, smem, st>>>(s, ws.Y, ws.ystride, ws.k, rs, slabs,
+  if (s.fw)
+    rebuild_kernel<true><<<reb_grid, kRebThreads, smem, st>>>(s, ws.Y, ws.ystride, ws.k, rs, slabs,
+                                                             d.nblocks);
+  else
+    rebuild_kernel<false><<<reb_grid, kRebThreads, smem, st>>>(s, ws.Y, ws.ystride, ws.k, rs, slabs,
                                                       d.nblocks);
   PROF_AFTER()
 #undef PROF_BEFORE

@@ -114,6 +114,7 @@ __device__ __forceinline__ float huge_hash(uint32_t a, uint32_t b) {
 // ---------------------------------------------------------------------------
 // 1. Gram partial sums: tile t of the lower triangle over one row chunk.
 // ---------------------------------------------------------------------------
+template <bool ST>
 __global__ void __launch_bounds__(kHThreads, 4)
 huge_gram_kernel(ScaleLaunch a, float* __restrict__ part, int chunk_rows, int chunks,
                  const HugeBlock* __restrict__ hb) {
@@ -123,7 +124,7 @@ huge_gram_kernel(ScaleLaunch a, float* __restrict__ part, int chunk_rows, int ch
   (void)hb;
   int ta, tc;
   tile_of(t, &ta, &tc);
-  const BlockGeom g = huge_geom(a, b);
+  const BlockGeom g = block_geom_t<ST>(a, b);
   const int mm = g.mm(), nn = g.nn();
   const int a0 = ta * kHT, c0 = tc * kHT;
   const int r_begin = chunk * chunk_rows;
@@ -922,11 +923,12 @@ huge_final_kernel(ScaleLaunch a, const float* __restrict__ U, float* __restrict_
 // warp.  Rows of rank-0 blocks get Z' = 0, W' = -A.
 // ---------------------------------------------------------------------------
 constexpr int kHRebRows = 32;
+template <bool ST>
 __global__ void __launch_bounds__(kHThreads)
 huge_rebuild_kernel(ScaleLaunch a, const float* __restrict__ Y, const int* __restrict__ kin) {
   const int b = blockIdx.y;
   const int k = kin[b];
-  const BlockGeom g = huge_geom(a, b);
+  const BlockGeom g = block_geom_t<ST>(a, b);
   const int mm = g.mm(), nn = g.nn();
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   constexpr int RPW = kHRebRows / (kHThreads / 32);
@@ -1043,7 +1045,11 @@ cudaError_t launch_huge(const ScaleLaunch& s, const BigWorkspace& ws, cudaStream
   const float thr = s.tau * s.tau;
   const int B = d.nblocks, nn = d.nn;
   PROF_BEFORE(KK_GRAM)
-  huge_gram_kernel<<<dim3(d.ntiles, d.chunks, B), kHThreads, 0, st>>>(s, ws.part, d.chunk_rows,
+  if (s.fw)
+    huge_gram_kernel<true><<<dim3(d.ntiles, d.chunks, B), kHThreads, 0, st>>>(s, ws.part, d.chunk_rows,
+                                                                      d.chunks, hb);
+  else
+    huge_gram_kernel<false><<<dim3(d.ntiles, d.chunks, B), kHThreads, 0, st>>>(s, ws.part, d.chunk_rows,
                                                                       d.chunks, hb);
   PROF_AFTER()
   PROF_BEFORE(KK_GRAM_REDUCE)
@@ -1105,7 +1111,11 @@ cudaError_t launch_huge(const ScaleLaunch& s, const BigWorkspace& ws, cudaStream
   huge_final_kernel<<<B, kHThreads, 0, st>>>(s, ws.U, ws.Y, ws.k, nn, hb);
   PROF_AFTER()
   PROF_BEFORE(KK_REBUILD)
-  huge_rebuild_kernel<<<dim3((d.mm + kHRebRows - 1) / kHRebRows, B), kHThreads, 0, st>>>(s, ws.Y,
+  if (s.fw)
+    huge_rebuild_kernel<true><<<dim3((d.mm + kHRebRows - 1) / kHRebRows, B), kHThreads, 0, st>>>(s, ws.Y,
+                                                                                         ws.k);
+  else
+    huge_rebuild_kernel<false><<<dim3((d.mm + kHRebRows - 1) / kHRebRows, B), kHThreads, 0, st>>>(s, ws.Y,
                                                                                          ws.k);
   PROF_AFTER()
 #undef PROF_BEFORE

@@ -68,14 +68,14 @@ static_assert(16 * 16 <= lz_cert_floats(16, 32), "Y alias (16)");
 static_assert(32 * 32 <= lz_cert_floats(32, 64), "Y alias (32)");
 static_assert(64 * 64 <= lz_cert_floats(64, 128) + 65 * 32 + 64 * kLzMaxK, "Y alias (64)");
 
-template <int NT, int NMAX>
+template <int NT, int NMAX, bool ST>
 __global__ void __launch_bounds__(NT, NT == 32 ? 24 : (NT == 128 ? 3 : 1))
 blocksvt_small_kernel(ScaleLaunch a) {
   extern __shared__ float sm[];
   const int tid = threadIdx.x;
   constexpr int SLOT = NT == 32 ? 0 : (NT == 64 ? 1 : 2);
   PHASE_INIT();
-  const BlockGeom g = block_geom(a, (int)blockIdx.x);
+  const BlockGeom g = block_geom_t<ST>(a, (int)blockIdx.x);
   const int mm = g.mm(), nn = g.nn();
   const int ldc = nn, ldg = nn + 1, ldy = nn;
 
@@ -322,7 +322,8 @@ cudaError_t launch_small_t(const ScaleLaunch& s, cudaStream_t st, Prof* prof) {
   const size_t smem = small_smem_bytes<NT, NMAX>(mm, nn);
   const int nblocks = (s.M / s.m) * (s.N / s.n);
   if (prof) if (cudaError_t e = prof->before(st, KK_FUSED)) return e;
-  blocksvt_small_kernel<NT, NMAX><<<nblocks, NT, smem, st>>>(s);
+  if (s.fw) blocksvt_small_kernel<NT, NMAX, true><<<nblocks, NT, smem, st>>>(s);
+  else blocksvt_small_kernel<NT, NMAX, false><<<nblocks, NT, smem, st>>>(s);
   if (prof) if (cudaError_t e = prof->after(st)) return e;
   return cudaGetLastError();
 }
@@ -335,13 +336,22 @@ cudaError_t configure_big_kernels();
 // per device from msllr_create, outside any stream capture.
 cudaError_t configure_kernels() {
   cudaError_t e;
-  e = cudaFuncSetAttribute(blocksvt_small_kernel<32, 16>,
+  e = cudaFuncSetAttribute(blocksvt_small_kernel<32, 16, false>,
                            cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
   if (e != cudaSuccess) return e;
-  e = cudaFuncSetAttribute(blocksvt_small_kernel<64, 32>,
+  e = cudaFuncSetAttribute(blocksvt_small_kernel<64, 32, false>,
                            cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
   if (e != cudaSuccess) return e;
-  e = cudaFuncSetAttribute(blocksvt_small_kernel<128, 64>,
+  e = cudaFuncSetAttribute(blocksvt_small_kernel<128, 64, false>,
+                           cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+  if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(blocksvt_small_kernel<32, 16, true>,
+                           cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+  if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(blocksvt_small_kernel<64, 32, true>,
+                           cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+  if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(blocksvt_small_kernel<128, 64, true>,
                            cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
   if (e != cudaSuccess) return e;
   e = configure_plain_kernels();

@@ -37,7 +37,7 @@ constexpr int kMaxSweeps = 12;
 constexpr unsigned kFull = 0xffffffffu;
 
 // RPL: rows of C per lane (mm <= 2 RPL)
-template <int RPL>
+template <int RPL, bool ST>
 __global__ void __launch_bounds__(kWT, RPL <= 8 ? 4 : 2)
 blocksvt_warp_kernel(ScaleLaunch a, int nblocks) {
   __shared__ float vsh[kWarps][16][17];  // V of each warp, for the rebuild
@@ -45,7 +45,7 @@ blocksvt_warp_kernel(ScaleLaunch a, int nblocks) {
   const int b = blockIdx.x * kWarps + wid;
   if (b >= nblocks) return;  // the whole warp leaves together
   const int h = lane >> 4, c = lane & 15;
-  const BlockGeom g = block_geom(a, b);
+  const BlockGeom g = block_geom_t<ST>(a, b);
   const int mm = g.mm(), nn = g.nn();
   const bool tr = g.transposed();
   const bool col = c < nn;
@@ -244,8 +244,13 @@ cudaError_t launch_warp(const ScaleLaunch& s, cudaStream_t st, Prof* prof) {
   const int grid = (nblocks + kWarps - 1) / kWarps;
   if (prof)
     if (cudaError_t e = prof->before(st, KK_FUSED)) return e;
-  if (mm <= 16) blocksvt_warp_kernel<8><<<grid, kWT, 0, st>>>(s, nblocks);
-  else blocksvt_warp_kernel<16><<<grid, kWT, 0, st>>>(s, nblocks);
+  if (mm <= 16) {
+    if (s.fw) blocksvt_warp_kernel<8, true><<<grid, kWT, 0, st>>>(s, nblocks);
+    else blocksvt_warp_kernel<8, false><<<grid, kWT, 0, st>>>(s, nblocks);
+  } else {
+    if (s.fw) blocksvt_warp_kernel<16, true><<<grid, kWT, 0, st>>>(s, nblocks);
+    else blocksvt_warp_kernel<16, false><<<grid, kWT, 0, st>>>(s, nblocks);
+  }
   if (prof)
     if (cudaError_t e = prof->after(st)) return e;
   return cudaGetLastError();
