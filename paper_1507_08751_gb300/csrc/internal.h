@@ -145,6 +145,7 @@ void set_contextless_error(const char* msg);
 // Debug phase timing buffers (see PHASE in common.cuh).
 cudaError_t set_phase_buffer_small(unsigned long long* p);
 cudaError_t set_phase_buffer_big(unsigned long long* p);
+cudaError_t set_phase_buffer_warp(unsigned long long* p);
 
 // Set kernel attributes (dynamic shared memory opt-in) on the current device.
 cudaError_t configure_kernels();

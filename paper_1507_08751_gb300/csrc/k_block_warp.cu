@@ -27,6 +27,10 @@
 
 namespace msllr {
 
+cudaError_t set_phase_buffer_warp(unsigned long long* p) {
+  return cudaMemcpyToSymbol(g_phase_acc, &p, sizeof(p));
+}
+
 namespace {
 
 constexpr int kWT = 256;            // threads per CTA: 8 warps, 8 blocks
@@ -45,6 +49,7 @@ blocksvt_warp_kernel(ScaleLaunch a, int nblocks) {
   const int b = blockIdx.x * kWarps + wid;
   if (b >= nblocks) return;  // the whole warp leaves together
   const int h = lane >> 4, c = lane & 15;
+  PHASE_INIT();
   const BlockGeom g = block_geom_t<ST>(a, b);
   const int mm = g.mm(), nn = g.nn();
   const bool tr = g.transposed();
@@ -66,6 +71,7 @@ blocksvt_warp_kernel(ScaleLaunch a, int nblocks) {
     fro = fmaf(v, v, fro);
   }
   fro = warp_sum(fro);
+  PHASE(0, 0);
   const float thr = a.tau * a.tau;
   bool skipped = a.skip_bound && fro <= thr;
   float fl = 0.f;  // flops of the steps run
@@ -116,6 +122,7 @@ blocksvt_warp_kernel(ScaleLaunch a, int nblocks) {
     }
   }
 
+  PHASE(0, 1);
   float z[RPL];
 #pragma unroll
   for (int i = 0; i < RPL; ++i) z[i] = 0.f;
@@ -128,43 +135,60 @@ blocksvt_warp_kernel(ScaleLaunch a, int nblocks) {
     for (int i = 0; i < RPL; ++i) y[i] = x[i];
 #pragma unroll
     for (int i = 0; i < 8; ++i) v[i] = (h + 2 * i == c) ? 1.f : 0.f;
+    const float inv_fro = 1.f / fro;
     for (; sweeps < kMaxSweeps;) {
       ++sweeps;
+      // squared norm of this lane's column of C V: recomputed every sweep,
+      // carried through the sweep's rotations by a' = a -/+ t ga
+      float al = 0.f;
+#pragma unroll
+      for (int i = 0; i < RPL; ++i) al = fmaf(y[i], y[i], al);
+      al += __shfl_xor_sync(kFull, al, 16);
       bool rotated = false;
 #pragma unroll 1
       for (int rd = 0; rd < 15; ++rd) {
         // round-robin partner: column 15 stays, the others turn (p + q = 2 rd mod 15)
         const int o = c == 15 ? rd : (c == rd ? 15 : (2 * rd - c + 15) % 15);
         const int src = (h << 4) | o;
+        const float be = __shfl_sync(kFull, al, src);
         float yo[RPL];
-        float al = 0.f, ga = 0.f;
+        float g0 = 0.f, g1 = 0.f;
 #pragma unroll
         for (int i = 0; i < RPL; ++i) {
           yo[i] = __shfl_sync(kFull, y[i], src);
-          al = fmaf(y[i], y[i], al);
-          ga = fmaf(y[i], yo[i], ga);
+          if (i & 1) g1 = fmaf(y[i], yo[i], g1);
+          else g0 = fmaf(y[i], yo[i], g0);
         }
-        al += __shfl_xor_sync(kFull, al, 16);
+        float ga = g0 + g1;
         ga += __shfl_xor_sync(kFull, ga, 16);
-        const float be = __shfl_sync(kFull, al, src);
         // the rotation that zeroes the off-diagonal of the 2 x 2 Gram matrix
         // [[a_lo, ga], [ga, a_hi]] of columns lo < hi (Golub & Van Loan,
         // Alg. 8.5.1): both lanes of the pair evaluate it in that order, so
         // they get the same (c, s), and apply
         //   c_lo' = c c_lo - s c_hi,   c_hi' = s c_lo + c c_hi
+        // (t needs no full accuracy: any (c, s) with c^2 + s^2 = 1 is a
+        // rotation; c comes from rsqrt with one Newton step)
         const bool lo = c < o;
         const float a_lo = lo ? al : be, a_hi = lo ? be : al;
-        float cr = 1.f, sr = 0.f;
+        const float gn = ga * inv_fro;
+        float cr = 1.f, sr = 0.f, t = 0.f;
         // (a column at the rounding level of ||C||_F is numerically zero:
         // no rotation, else an exactly rank-deficient block never settles)
-        if (fminf(a_lo, a_hi) > kTinyCol * fro && fabsf(ga) > kRotTol * (sqrtf(a_lo) * sqrtf(a_hi))) {
-          const float zeta = (a_hi - a_lo) / (2.f * ga);
-          const float t = copysignf(1.f, zeta) / (fabsf(zeta) + sqrtf(1.f + zeta * zeta));
-          cr = 1.f / sqrtf(1.f + t * t);
+        if (fminf(a_lo, a_hi) > kTinyCol * fro &&
+            gn * gn > (kRotTol * kRotTol) * ((a_lo * inv_fro) * (a_hi * inv_fro))) {
+          const float zeta = __fdividef(a_hi - a_lo, 2.f * ga);
+          const float az = fabsf(zeta);
+          const float r = fmaf(az, az, 1.f);
+          const float den = az < 1e18f ? fmaf(r, rsqrtf(r), az) : 2.f * az;
+          t = copysignf(__fdividef(1.f, den), zeta);
+          const float u = fmaf(t, t, 1.f);
+          cr = rsqrtf(u);
+          cr = cr * fmaf(-0.5f * u * cr, cr, 1.5f);
           sr = t * cr;
           rotated = true;
         }
         const float so = lo ? -sr : sr;  // weight of the partner column
+        al = lo ? fmaf(-t, ga, al) : fmaf(t, ga, al);
 #pragma unroll
         for (int i = 0; i < RPL; ++i) y[i] = fmaf(so, yo[i], cr * y[i]);
 #pragma unroll
@@ -175,6 +199,8 @@ blocksvt_warp_kernel(ScaleLaunch a, int nblocks) {
       }
       if (!__any_sync(kFull, rotated)) break;
     }
+    PHASE(0, 2);
+    if (threadIdx.x == 0) PHASE_ADD(0, 5, sweeps);
     // singular values: the column norms of C V
     float al = 0.f;
 #pragma unroll
@@ -216,6 +242,7 @@ blocksvt_warp_kernel(ScaleLaunch a, int nblocks) {
       if (a.Wout) a.Wout[off] = 2.f * z[i] - x[i];
     }
   }
+  PHASE(0, 3);
   if (lane == 0) {
     if (a.rank_out) a.rank_out[b] = k;
     if (a.cnt) {

@@ -280,7 +280,8 @@ int msllr_create(msllr_ctx** out, int device, size_t hbm_budget_bytes, void* cud
     if (cudaMalloc(&ctx->d_phase, 8 * 16 * 2 * sizeof(unsigned long long)) != cudaSuccess ||
         cudaMemset(ctx->d_phase, 0, 8 * 16 * 2 * sizeof(unsigned long long)) != cudaSuccess ||
         set_phase_buffer_small(ctx->d_phase) != cudaSuccess ||
-        set_phase_buffer_big(ctx->d_phase) != cudaSuccess)
+        set_phase_buffer_big(ctx->d_phase) != cudaSuccess ||
+        set_phase_buffer_warp(ctx->d_phase) != cudaSuccess)
       return bail(fail(ctx, MSLLR_ECUDA, "phase timing buffer"));
   }
   if (cudaMalloc(&ctx->d_small, 64 * sizeof(int)) != cudaSuccess ||
@@ -311,7 +312,7 @@ int msllr_destroy(msllr_ctx* ctx) {
   if (ctx->d_phase) {
     unsigned long long h[8 * 16 * 2];
     if (cudaMemcpy(h, ctx->d_phase, sizeof h, cudaMemcpyDeviceToHost) == cudaSuccess) {
-      static const char* names[8] = {"small32", "small64", "small128", "eig_big", "eig_lanczos",
+      static const char* names[8] = {"small32/warp", "small64", "small128", "eig_big", "eig_lanczos",
                                      "lz32", "lz64", "lz128"};
       for (int k = 0; k < 8; ++k) {
         fprintf(stderr, "[msllr phase] %s:", names[k]);
@@ -325,6 +326,7 @@ int msllr_destroy(msllr_ctx* ctx) {
     }
     set_phase_buffer_small(nullptr);
     set_phase_buffer_big(nullptr);
+    set_phase_buffer_warp(nullptr);
     cudaFree(ctx->d_phase);
   }
   if (ctx->d_small) cudaFree(ctx->d_small);

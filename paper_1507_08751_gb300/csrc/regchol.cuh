@@ -153,24 +153,59 @@ __device__ bool regchol_pd(SX src, int n, float c0, bool frob, const float* U, c
       v[s][15] += c;
     }
 
-  if constexpr (NT >= 256) {
-    // Lookahead: warps 0..kFW-1 factor the diagonal block of panel p + 1 and
-    // solve its rows while the other warps apply panel p's update to the
-    // rest of the trailing matrix.  Per panel: the owners of panel p + 1's
-    // tiles update them first and write them to the other strip; barrier;
-    // factor group on panel p + 1, everyone on the remaining tiles; barrier.
-    constexpr int kFW = 4;
-    int* fail = reinterpret_cast<int*>(red);  // free after the norm above
-    const bool fgrp = warp < kFW;
-    auto factor_panel = [&](int q) {
-      // diagonal block and rows below of panel q (strip q & 1), factor group
-      const int j0 = 8 * q;
-      float* Sb = S + (q & 1) * 8 * n8;
+  for (int p = 0; 8 * p < n8; ++p) {
+    const int j0 = 8 * p;
+    float* Sb = S + (p & 1) * 8 * n8;
+    if (p > 0) {
+#pragma unroll
+      for (int s = 0; s < SL; ++s)
+        if (tb[s] == 2 * p || tb[s] == 2 * p + 1) {
+#pragma unroll
+          for (int j = 0; j < 4; ++j)
+            *reinterpret_cast<float4*>(Sb + (4 * tb[s] + j - j0) * n8 + 4 * ta[s]) =
+                make_float4(v[s][j], v[s][4 + j], v[s][8 + j], v[s][12 + j]);
+        }
+    }
+    __syncthreads();
+    // 8x8 diagonal block into this warp's packed copy Lw (lower triangle,
+    // the diagonal replaced by the reciprocal pivots).  Every warp factors
+    // it; rsqrt (a few ulp) instead of sqrt and a division keeps the chain
+    // of 8 dependent pivots short, and its error stays far inside the
+    // backward-error margin.
+    bool ok = true;
+    if constexpr (REGF) {
+      // every thread holds the whole block (broadcast loads): no shuffles
+      float L[36];
+#pragma unroll
+      for (int t = 0; t < 8; ++t)
+#pragma unroll
+        for (int u = 0; u <= t; ++u) L[t * (t + 1) / 2 + u] = Sb[u * n8 + j0 + t];
+#pragma unroll
+      for (int j = 0; j < 8; ++j) {
+        const float dj = L[j * (j + 1) / 2 + j];
+        ok = ok && (dj > 0.f);
+        const float inv = rsqrtf(dj > 0.f ? dj : 1.f);
+        L[j * (j + 1) / 2 + j] = inv;
+#pragma unroll
+        for (int i = j + 1; i < 8; ++i) L[i * (i + 1) / 2 + j] *= inv;
+#pragma unroll
+        for (int i = j + 1; i < 8; ++i)
+#pragma unroll
+          for (int t = j + 1; t <= i; ++t)
+            L[i * (i + 1) / 2 + t] = fmaf(-L[i * (i + 1) / 2 + j], L[t * (t + 1) / 2 + j],
+                                          L[i * (i + 1) / 2 + t]);
+      }
+      if (!ok) return false;
+      if (lane == 0) {
+#pragma unroll
+        for (int e = 0; e < 36; ++e) Lw[e] = L[e];
+      }
+    } else {
+      // lane l < 8 holds row l (fewer registers, shuffles on the chain)
       float row[8];
 #pragma unroll
       for (int t = 0; t < 8; ++t) row[t] = (lane < 8 && t <= lane) ? Sb[t * n8 + j0 + lane] : 0.f;
       float myinv = 1.f;
-      bool ok = true;
 #pragma unroll
       for (int j = 0; j < 8; ++j) {
         const float dj = __shfl_sync(0xffffffffu, row[j], j);
@@ -184,10 +219,7 @@ __device__ bool regchol_pd(SX src, int n, float c0, bool frob, const float* U, c
           if (lane >= t) row[t] = fmaf(-row[j], ltj, row[t]);
         }
       }
-      if (!ok) {
-        if (lane == 0) *fail = 1;
-        return;
-      }
+      if (!ok) return false;
       if (lane < 8) {
         const int base = lane * (lane + 1) / 2;
 #pragma unroll
@@ -195,174 +227,38 @@ __device__ bool regchol_pd(SX src, int n, float c0, bool frob, const float* U, c
           if (t < lane) Lw[base + t] = row[t];
         Lw[base + lane] = myinv;
       }
-      __syncwarp();
-      // rows below the block: L21 = A21 L11^{-T}
-      for (int r = j0 + 8 + tid; r < n8; r += 32 * kFW) {
-        float x[8];
-#pragma unroll
-        for (int t = 0; t < 8; ++t) {
-          float acc = Sb[t * n8 + r];
-#pragma unroll
-          for (int u = 0; u < t; ++u) acc = fmaf(-x[u], Lw[t * (t + 1) / 2 + u], acc);
-          x[t] = acc * Lw[t * (t + 1) / 2 + t];
-        }
-#pragma unroll
-        for (int t = 0; t < 8; ++t) Sb[t * n8 + r] = x[t];
-      }
-    };
-    // rank-8 update from panel p's strip of the tiles with column in [lo, hi)
-    auto update = [&](int p, int lo, int hi) {
-      const float* Sb = S + (p & 1) * 8 * n8;
-#pragma unroll
-      for (int s = 0; s < SL; ++s) {
-        if (tb[s] < lo || tb[s] >= hi) continue;
-        const float* pr = Sb + 4 * ta[s];
-        const float* pc = Sb + 4 * tb[s];
-#pragma unroll
-        for (int u = 0; u < 8; ++u) {
-          const float4 a4 = *reinterpret_cast<const float4*>(pr + u * n8);
-          const float4 b4 = *reinterpret_cast<const float4*>(pc + u * n8);
-          const float av[4] = {a4.x, a4.y, a4.z, a4.w}, bv[4] = {b4.x, b4.y, b4.z, b4.w};
-#pragma unroll
-          for (int i = 0; i < 4; ++i)
-#pragma unroll
-            for (int j = 0; j < 4; ++j) v[s][i * 4 + j] = fmaf(-av[i], bv[j], v[s][i * 4 + j]);
-        }
-      }
-    };
-    if (tid == 0) *fail = 0;
-    __syncthreads();
-    if (fgrp) factor_panel(0);
-    __syncthreads();
-    if (*fail) return false;
-    const int np8 = n8 / 8;
-    for (int p = 0; p + 1 < np8; ++p) {
-      // panel p + 1's tiles: update, then into the other strip
-      update(p, 2 * p + 2, 2 * p + 4);
-      float* Sn = S + ((p + 1) & 1) * 8 * n8;
-      const int j1 = 8 * (p + 1);
-#pragma unroll
-      for (int s = 0; s < SL; ++s)
-        if (tb[s] == 2 * p + 2 || tb[s] == 2 * p + 3) {
-#pragma unroll
-          for (int j = 0; j < 4; ++j)
-            *reinterpret_cast<float4*>(Sn + (4 * tb[s] + j - j1) * n8 + 4 * ta[s]) =
-                make_float4(v[s][j], v[s][4 + j], v[s][8 + j], v[s][12 + j]);
-        }
-      __syncthreads();
-      if (fgrp) factor_panel(p + 1);
-      update(p, 2 * p + 4, 1 << 30);
-      __syncthreads();
-      if (*fail) return false;
     }
-  } else {
-    for (int p = 0; 8 * p < n8; ++p) {
-      const int j0 = 8 * p;
-      float* Sb = S + (p & 1) * 8 * n8;
-      if (p > 0) {
+    __syncwarp();
+    // rows below the block: L21 = A21 L11^{-T}
+    for (int r = j0 + 8 + tid; r < n8; r += NT) {
+      float x[8];
 #pragma unroll
-        for (int s = 0; s < SL; ++s)
-          if (tb[s] == 2 * p || tb[s] == 2 * p + 1) {
+      for (int t = 0; t < 8; ++t) {
+        float acc = Sb[t * n8 + r];
 #pragma unroll
-            for (int j = 0; j < 4; ++j)
-              *reinterpret_cast<float4*>(Sb + (4 * tb[s] + j - j0) * n8 + 4 * ta[s]) =
-                  make_float4(v[s][j], v[s][4 + j], v[s][8 + j], v[s][12 + j]);
-          }
+        for (int u = 0; u < t; ++u) acc = fmaf(-x[u], Lw[t * (t + 1) / 2 + u], acc);
+        x[t] = acc * Lw[t * (t + 1) / 2 + t];
       }
-      __syncthreads();
-      // 8x8 diagonal block into this warp's packed copy Lw (lower triangle,
-      // the diagonal replaced by the reciprocal pivots).  Every warp factors
-      // it; rsqrt (a few ulp) instead of sqrt and a division keeps the chain
-      // of 8 dependent pivots short, and its error stays far inside the
-      // backward-error margin.
-      bool ok = true;
-      if constexpr (REGF) {
-        // every thread holds the whole block (broadcast loads): no shuffles
-        float L[36];
 #pragma unroll
-        for (int t = 0; t < 8; ++t)
+      for (int t = 0; t < 8; ++t) Sb[t * n8 + r] = x[t];
+    }
+    __syncthreads();
+    // trailing rank-8 update of the active tiles (column >= j0 + 8)
+    const int bmin = 2 * p + 2;
 #pragma unroll
-          for (int u = 0; u <= t; ++u) L[t * (t + 1) / 2 + u] = Sb[u * n8 + j0 + t];
+    for (int s = 0; s < SL; ++s) {
+      if (tb[s] < bmin) continue;
+      const float* pr = Sb + 4 * ta[s];
+      const float* pc = Sb + 4 * tb[s];
 #pragma unroll
-        for (int j = 0; j < 8; ++j) {
-          const float dj = L[j * (j + 1) / 2 + j];
-          ok = ok && (dj > 0.f);
-          const float inv = rsqrtf(dj > 0.f ? dj : 1.f);
-          L[j * (j + 1) / 2 + j] = inv;
+      for (int u = 0; u < 8; ++u) {
+        const float4 a4 = *reinterpret_cast<const float4*>(pr + u * n8);
+        const float4 b4 = *reinterpret_cast<const float4*>(pc + u * n8);
+        const float av[4] = {a4.x, a4.y, a4.z, a4.w}, bv[4] = {b4.x, b4.y, b4.z, b4.w};
 #pragma unroll
-          for (int i = j + 1; i < 8; ++i) L[i * (i + 1) / 2 + j] *= inv;
+        for (int i = 0; i < 4; ++i)
 #pragma unroll
-          for (int i = j + 1; i < 8; ++i)
-#pragma unroll
-            for (int t = j + 1; t <= i; ++t)
-              L[i * (i + 1) / 2 + t] = fmaf(-L[i * (i + 1) / 2 + j], L[t * (t + 1) / 2 + j],
-                                            L[i * (i + 1) / 2 + t]);
-        }
-        if (!ok) return false;
-        if (lane == 0) {
-#pragma unroll
-          for (int e = 0; e < 36; ++e) Lw[e] = L[e];
-        }
-      } else {
-        // lane l < 8 holds row l (fewer registers, shuffles on the chain)
-        float row[8];
-#pragma unroll
-        for (int t = 0; t < 8; ++t) row[t] = (lane < 8 && t <= lane) ? Sb[t * n8 + j0 + lane] : 0.f;
-        float myinv = 1.f;
-#pragma unroll
-        for (int j = 0; j < 8; ++j) {
-          const float dj = __shfl_sync(0xffffffffu, row[j], j);
-          ok = ok && (dj > 0.f);
-          const float inv = rsqrtf(dj > 0.f ? dj : 1.f);
-          if (lane == j) myinv = inv;
-          if (lane > j) row[j] *= inv;
-#pragma unroll
-          for (int t = j + 1; t < 8; ++t) {
-            const float ltj = __shfl_sync(0xffffffffu, row[j], t);
-            if (lane >= t) row[t] = fmaf(-row[j], ltj, row[t]);
-          }
-        }
-        if (!ok) return false;
-        if (lane < 8) {
-          const int base = lane * (lane + 1) / 2;
-#pragma unroll
-          for (int t = 0; t < 8; ++t)
-            if (t < lane) Lw[base + t] = row[t];
-          Lw[base + lane] = myinv;
-        }
-      }
-      __syncwarp();
-      // rows below the block: L21 = A21 L11^{-T}
-      for (int r = j0 + 8 + tid; r < n8; r += NT) {
-        float x[8];
-#pragma unroll
-        for (int t = 0; t < 8; ++t) {
-          float acc = Sb[t * n8 + r];
-#pragma unroll
-          for (int u = 0; u < t; ++u) acc = fmaf(-x[u], Lw[t * (t + 1) / 2 + u], acc);
-          x[t] = acc * Lw[t * (t + 1) / 2 + t];
-        }
-#pragma unroll
-        for (int t = 0; t < 8; ++t) Sb[t * n8 + r] = x[t];
-      }
-      __syncthreads();
-      // trailing rank-8 update of the active tiles (column >= j0 + 8)
-      const int bmin = 2 * p + 2;
-#pragma unroll
-      for (int s = 0; s < SL; ++s) {
-        if (tb[s] < bmin) continue;
-        const float* pr = Sb + 4 * ta[s];
-        const float* pc = Sb + 4 * tb[s];
-#pragma unroll
-        for (int u = 0; u < 8; ++u) {
-          const float4 a4 = *reinterpret_cast<const float4*>(pr + u * n8);
-          const float4 b4 = *reinterpret_cast<const float4*>(pc + u * n8);
-          const float av[4] = {a4.x, a4.y, a4.z, a4.w}, bv[4] = {b4.x, b4.y, b4.z, b4.w};
-#pragma unroll
-          for (int i = 0; i < 4; ++i)
-#pragma unroll
-            for (int j = 0; j < 4; ++j) v[s][i * 4 + j] = fmaf(-av[i], bv[j], v[s][i * 4 + j]);
-        }
+          for (int j = 0; j < 4; ++j) v[s][i * 4 + j] = fmaf(-av[i], bv[j], v[s][i * 4 + j]);
       }
     }
   }
