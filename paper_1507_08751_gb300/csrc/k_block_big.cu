@@ -168,9 +168,14 @@ size_t eig_smem_bytes(int nn) {
                           9 * kEigMax + 4 * kEigThreads + 64 + lz_scratch_floats(kEigMax, kLzMaxJ));
 }
 
-// Three power steps from a pseudo-random vector: true when the Rayleigh
-// quotient (a lower bound of lambda_max(G)) already exceeds thr, i.e. the
-// block certainly has a singular value above tau.
+// Up to three power steps from a pseudo-random vector: true when the
+// Rayleigh quotient (a lower bound of lambda_max(G)) exceeds `thr`.  Called
+// with thr = kZeroTry tau^2: a block whose quotient comes that close to
+// tau^2 goes straight to the Lanczos path, because its zero-rank
+// certificate would most likely fail, and a failed Cholesky costs as much
+// as a successful one (the decision only routes work; the certificates
+// decide the result).
+constexpr float kZeroTry = 0.85f;
 template <class S>
 __device__ bool power_above(S G, int n, float thr, EigScratch& s, LzScratch& z, int* steps) {
   constexpr int NT = kEigThreads;
@@ -278,7 +283,7 @@ eig_big_kernel(ScaleLaunch a, const float* __restrict__ Gall, BigWorkspace ws) {
       }
       if (kwarm > 0) continue;
       int psteps = 0;
-      const bool above = power_above(Gacc, nn, thr, s, z, &psteps);
+      const bool above = power_above(Gacc, nn, kZeroTry * thr, s, z, &psteps);
       fl += psteps * (fl_symv(nn) + 4.0 * nn);
       if (above) continue;
       // certified lambda_max(G) < tau^2 by Cholesky of (tau^2 - margin) I - G

@@ -133,31 +133,38 @@ __device__ void symv_rows(S G, int n, const float* x, float* y) {
     if (b0 < n) {
       const int rr = r < n ? r : n - 1;  // lanes past n compute a dummy row
       const int tr = (rr * (rr + 1)) / 2;
-      float a0 = 0.f, a1 = 0.f;
+      // four accumulators, so that four loads and FMAs are in flight
+      float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f;
       int c = c_lo;
       const int e1 = min(c_hi, b0);
-      for (; c + 1 < e1; c += 2) {
+      for (; c + 3 < e1; c += 4) {
         a0 = fmaf(ABS ? fabsf(g[tr + c]) : g[tr + c], x[c], a0);
         a1 = fmaf(ABS ? fabsf(g[tr + c + 1]) : g[tr + c + 1], x[c + 1], a1);
+        a2 = fmaf(ABS ? fabsf(g[tr + c + 2]) : g[tr + c + 2], x[c + 2], a2);
+        a3 = fmaf(ABS ? fabsf(g[tr + c + 3]) : g[tr + c + 3], x[c + 3], a3);
       }
-      if (c < e1) {
-        a0 = fmaf(ABS ? fabsf(g[tr + c]) : g[tr + c], x[c], a0);
-        ++c;
-      }
+      for (; c < e1; ++c) a0 = fmaf(ABS ? fabsf(g[tr + c]) : g[tr + c], x[c], a0);
       const int e2 = min(c_hi, b0 + 32);
       for (; c < e2; ++c) {
         const int idx = c <= rr ? tr + c : (c * (c + 1)) / 2 + rr;
-        a0 = fmaf(ABS ? fabsf(g[idx]) : g[idx], x[c], a0);
+        a1 = fmaf(ABS ? fabsf(g[idx]) : g[idx], x[c], a1);
       }
       int idx = (c * (c + 1)) / 2 + rr;
-      for (; c + 1 < c_hi; c += 2) {
+      for (; c + 3 < c_hi; c += 4) {
         const int i1 = idx + c + 1;
+        const int i2 = i1 + c + 2;
+        const int i3 = i2 + c + 3;
         a0 = fmaf(ABS ? fabsf(g[idx]) : g[idx], x[c], a0);
         a1 = fmaf(ABS ? fabsf(g[i1]) : g[i1], x[c + 1], a1);
-        idx = i1 + c + 2;
+        a2 = fmaf(ABS ? fabsf(g[i2]) : g[i2], x[c + 2], a2);
+        a3 = fmaf(ABS ? fabsf(g[i3]) : g[i3], x[c + 3], a3);
+        idx = i3 + c + 4;
       }
-      if (c < c_hi) a0 = fmaf(ABS ? fabsf(g[idx]) : g[idx], x[c], a0);
-      acc = a0 + a1;
+      for (; c < c_hi; ++c) {
+        a0 = fmaf(ABS ? fabsf(g[idx]) : g[idx], x[c], a0);
+        idx += c + 1;
+      }
+      acc = (a0 + a1) + (a2 + a3);
     }
     if (half && r < n) y[r] = acc;
     __syncthreads();
