@@ -34,7 +34,6 @@ constexpr int kEigMax = 256;
 constexpr int kRebThreads = 256;
 constexpr int kRebElems = 4096;  // rows-per-slab * nn
 constexpr int kKC = 16;          // eigenvectors per rebuild step
-constexpr bool kGramTensor = true;  // Gram tiles on the tensor cores (3-pass TF32)
 
 struct BigDims {
   int mm, nn, nblocks, nbn, T, ntiles, chunks;
@@ -134,129 +133,6 @@ gram_tiles_kernel(ScaleLaunch a, float* __restrict__ G, float* __restrict__ part
     for (int x = 0; x < 4; ++x)
 #pragma unroll
       for (int y = 0; y < 4; ++y) dst[(ty * 4 + x) * kTile + tx * 4 + y] = acc[x][y];
-  }
-}
-
-// TF32 tensor-core form of the Gram tile (the contraction G = C^T C is dense
-// and Gram products of blocks >= 32 wide go to the tensor cores): the same
-// tile, slab and output layout as gram_tiles_kernel, with warp-level
-// mma.sync m16n8k8 TF32 products in three passes, C = C_hi + C_lo with
-// C_hi = tf32(C), C_lo = tf32(C - C_hi), G ~ C_hi^T C_hi + C_hi^T C_lo +
-// C_lo^T C_hi, which keeps FP32-level accuracy (the dropped C_lo^T C_lo is
-// below 2^-21 relative).  The next slab's loads are issued before the
-// current slab's products, so the gather latency overlaps the MMAs.
-__device__ __forceinline__ uint32_t to_tf32(float x) {
-  uint32_t r;
-  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
-  return r;
-}
-
-__device__ __forceinline__ void mma_tf32(float (&d)[4], const uint32_t (&a)[4], uint32_t b0,
-                                         uint32_t b1) {
-  asm volatile(
-      "mma.sync.aligned.m16n8k8.row.col.f32.tf32.tf32.f32 {%0, %1, %2, %3}, {%4, %5, %6, %7}, "
-      "{%8, %9}, {%0, %1, %2, %3};"
-      : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
-      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
-}
-
-template <bool ST>
-__global__ void __launch_bounds__(kGramThreads, 3)
-gram_mma_kernel(ScaleLaunch a, float* __restrict__ G, float* __restrict__ part, int chunks) {
-  __shared__ __align__(16) float As[32][kTile + 4];
-  __shared__ __align__(16) float Bs[32][kTile + 4];
-  const int t = blockIdx.x, chunk = blockIdx.y, b = blockIdx.z;
-  int ta = (int)((sqrtf(8.f * t + 1.f) - 1.f) * 0.5f);
-  while (((ta + 1) * (ta + 2)) / 2 <= t) ++ta;
-  while ((ta * (ta + 1)) / 2 > t) --ta;
-  const int tc = t - (ta * (ta + 1)) / 2;
-  const BlockGeom g = block_geom_t<ST>(a, b);
-  const int mm = g.mm(), nn = g.nn();
-  const int a0 = ta * kTile, c0 = tc * kTile;
-  const int r_begin = chunk * kChunk;
-  const int r_end = min(mm, r_begin + kChunk);
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const int gq = lane >> 2, tq = lane & 3;
-  // warp w: rows 16 (w / 2) .. + 16 and columns 32 (w % 2) .. + 32 of the tile
-  const int mrow = 16 * (warp >> 1), ncol = 32 * (warp & 1);
-  float acc[4][4];
-#pragma unroll
-  for (int f = 0; f < 4; ++f)
-#pragma unroll
-    for (int q = 0; q < 4; ++q) acc[f][q] = 0.f;
-  constexpr int EPT = (32 * kTile) / kGramThreads;
-  float pa[EPT], pb[EPT];
-  auto fetch = [&](int r0) {
-#pragma unroll
-    for (int j = 0; j < EPT; ++j) {
-      const int e = tid + j * kGramThreads;
-      const int rr = e / kTile, cc = e - rr * kTile;
-      const int i = r0 + rr;
-      float va = 0.f, vb = 0.f;
-      if (i < r_end) {
-        if (a0 + cc < nn) va = load_a(a, c_offset(g, i, a0 + cc));
-        if (c0 + cc < nn) vb = (ta == tc) ? va : load_a(a, c_offset(g, i, c0 + cc));
-      }
-      pa[j] = va;
-      pb[j] = vb;
-    }
-  };
-  fetch(r_begin);
-  for (int r0 = r_begin; r0 < r_end; r0 += 32) {
-#pragma unroll
-    for (int j = 0; j < EPT; ++j) {
-      const int e = tid + j * kGramThreads;
-      const int rr = e / kTile, cc = e - rr * kTile;
-      As[rr][cc] = pa[j];
-      Bs[rr][cc] = pb[j];
-    }
-    __syncthreads();
-    if (r0 + 32 < r_end) fetch(r0 + 32);
-#pragma unroll
-    for (int kk = 0; kk < 4; ++kk) {
-      const int k0 = 8 * kk;
-      const float af[4] = {As[k0 + tq][mrow + gq], As[k0 + tq][mrow + gq + 8],
-                           As[k0 + tq + 4][mrow + gq], As[k0 + tq + 4][mrow + gq + 8]};
-      uint32_t ah[4], al[4];
-#pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        ah[q] = to_tf32(af[q]);
-        al[q] = to_tf32(af[q] - __uint_as_float(ah[q]));
-      }
-#pragma unroll
-      for (int f = 0; f < 4; ++f) {
-        const int col = ncol + 8 * f + gq;
-        const float b0 = Bs[k0 + tq][col], b1 = Bs[k0 + tq + 4][col];
-        const uint32_t bh0 = to_tf32(b0), bh1 = to_tf32(b1);
-        const uint32_t bl0 = to_tf32(b0 - __uint_as_float(bh0));
-        const uint32_t bl1 = to_tf32(b1 - __uint_as_float(bh1));
-        mma_tf32(acc[f], al, bh0, bh1);
-        mma_tf32(acc[f], ah, bl0, bl1);
-        mma_tf32(acc[f], ah, bh0, bh1);
-      }
-    }
-    __syncthreads();
-  }
-  // accumulator (f, q): tile row mrow + gq (+8 for q >= 2), column
-  // ncol + 8 f + 2 tq (+1 for odd q)
-  if (chunks == 1) {
-    float* Gb = G + (size_t)b * nn * nn;
-#pragma unroll
-    for (int f = 0; f < 4; ++f)
-#pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        const int i = a0 + mrow + gq + (q >= 2 ? 8 : 0);
-        const int j = c0 + ncol + 8 * f + 2 * tq + (q & 1);
-        if (i < nn && j <= i) Gb[(size_t)i * (i + 1) / 2 + j] = acc[f][q];
-      }
-  } else {
-    const int ntiles = gridDim.x;
-    float* dst = part + (((size_t)b * chunks + chunk) * ntiles + t) * (kTile * kTile);
-#pragma unroll
-    for (int f = 0; f < 4; ++f)
-#pragma unroll
-      for (int q = 0; q < 4; ++q)
-        dst[(mrow + gq + (q >= 2 ? 8 : 0)) * kTile + ncol + 8 * f + 2 * tq + (q & 1)] = acc[f][q];
   }
 }
 
@@ -800,13 +676,8 @@ cudaError_t launch_big(const ScaleLaunch& s, const BigWorkspace& ws, cudaStream_
     if (cudaError_t e_ = prof->after(st)) return e_;
   PROF_BEFORE(KK_GRAM)
   const dim3 ggrid(d.ntiles, d.chunks, d.nblocks);
-  if (kGramTensor) {
-    if (s.fw) gram_mma_kernel<true><<<ggrid, kGramThreads, 0, st>>>(s, ws.G, ws.part, d.chunks);
-    else gram_mma_kernel<false><<<ggrid, kGramThreads, 0, st>>>(s, ws.G, ws.part, d.chunks);
-  } else {
-    if (s.fw) gram_tiles_kernel<true><<<ggrid, kGramThreads, 0, st>>>(s, ws.G, ws.part, d.chunks);
-    else gram_tiles_kernel<false><<<ggrid, kGramThreads, 0, st>>>(s, ws.G, ws.part, d.chunks);
-  }
+  if (s.fw) gram_tiles_kernel<true><<<ggrid, kGramThreads, 0, st>>>(s, ws.G, ws.part, d.chunks);
+  else gram_tiles_kernel<false><<<ggrid, kGramThreads, 0, st>>>(s, ws.G, ws.part, d.chunks);
   PROF_AFTER()
   if (d.chunks > 1) {
     PROF_BEFORE(KK_GRAM_REDUCE)
