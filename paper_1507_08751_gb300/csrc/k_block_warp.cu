@@ -33,7 +33,10 @@ cudaError_t set_phase_buffer_warp(unsigned long long* p) {
 
 namespace {
 
-constexpr int kWT = 256;            // threads per CTA: 8 warps, 8 blocks
+// one warp (one block) per CTA: a CTA's resources return to the SM as soon
+// as its block is done, so a warp busy with a Jacobi block holds no idle
+// warp slots beside it
+constexpr int kWT = 32;
 constexpr int kWarps = kWT / 32;
 constexpr float kRotTol = 2e-6f;    // rotate columns p, q while |c_p . c_q| > tol ||c_p|| ||c_q||
 constexpr float kTinyCol = 1e-13f;  // squared norm of a numerically zero column, relative to ||C||_F^2
@@ -42,7 +45,7 @@ constexpr unsigned kFull = 0xffffffffu;
 
 // RPL: rows of C per lane (mm <= 2 RPL)
 template <int RPL, bool ST>
-__global__ void __launch_bounds__(kWT, RPL <= 8 ? 4 : 2)
+__global__ void __launch_bounds__(kWT, RPL <= 8 ? 32 : 16)
 blocksvt_warp_kernel(ScaleLaunch a, int nblocks) {
   __shared__ float vsh[kWarps][16][17];  // V of each warp, for the rebuild
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
