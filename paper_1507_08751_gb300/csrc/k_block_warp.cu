@@ -179,15 +179,20 @@ blocksvt_warp_kernel(ScaleLaunch a, int nblocks) {
         // no rotation, else an exactly rank-deficient block never settles)
         if (fminf(a_lo, a_hi) > kTinyCol * fro &&
             gn * gn > (kRotTol * kRotTol) * ((a_lo * inv_fro) * (a_hi * inv_fro))) {
-          const float zeta = __fdividef(a_hi - a_lo, 2.f * ga);
-          const float az = fabsf(zeta);
-          const float r = fmaf(az, az, 1.f);
-          const float den = az < 1e18f ? fmaf(r, rsqrtf(r), az) : 2.f * az;
-          t = copysignf(__fdividef(1.f, den), zeta);
-          const float u = fmaf(t, t, 1.f);
-          cr = rsqrtf(u);
-          cr = cr * fmaf(-0.5f * u * cr, cr, 1.5f);
-          sr = t * cr;
+          // the angle with tan 2 phi = 2 ga / (a_hi - a_lo), |phi| <= pi / 4,
+          // by half angles: cos 2 phi = |D| / q, sin 2 phi = 2 ga sign(D) / q,
+          // q = sqrt(D^2 + 4 ga^2); c = sqrt((1 + cos 2 phi) / 2) >= 1 / sqrt(2),
+          // s = sin 2 phi / (2 c); two rsqrt, each with one Newton step
+          const float dn = (a_hi - a_lo) * inv_fro;
+          const float q2 = fmaf(dn, dn, 4.f * gn * gn);
+          float rq = rsqrtf(q2);
+          rq = rq * fmaf(-0.5f * q2 * rq, rq, 1.5f);
+          const float hh = fmaf(0.5f * fabsf(dn), rq, 0.5f);
+          float rh = rsqrtf(hh);
+          rh = rh * fmaf(-0.5f * hh * rh, rh, 1.5f);
+          cr = hh * rh;
+          sr = copysignf(1.f, dn) * gn * rq * rh;
+          t = sr * rh;  // tan phi = s / c
           rotated = true;
         }
         const float so = lo ? -sr : sr;  // weight of the partner column
