@@ -51,7 +51,8 @@ def parse():
                     help="averaged cycle spinning (Sec. 9) over a g x g shift lattice per scale")
     ap.add_argument("--serve-jobs", type=int, default=24)
     ap.add_argument("--serve-rate", type=float, default=50.0)
-    ap.add_argument("--workload", default="video", choices=["video", "serve"] + sorted(JOBS),
+    ap.add_argument("--batch-jobs", type=int, default=64)
+    ap.add_argument("--workload", default="video", choices=["video", "serve", "batch"] + sorted(JOBS),
                     help="video (default, the headline line), a batching-shaped job whose "
                          "full-matrix scale is wider than 256, or serve (p50/p99 latency of "
                          "queued jobs under Poisson arrivals)")
@@ -639,12 +640,109 @@ def serve(a):
     print(json.dumps(line), flush=True)
 
 
+# ---------------------------------------------------------------- batching ----
+
+BATCH_SIZES = [(512, 512), (1024, 256), (2048, 1024), (4096, 512)]
+
+
+def batch_jobs(n):
+    """The batching workload: n jobs, sizes uniform from BATCH_SIZES, 4-6
+    dyadic scales (1x1 .. full), rank-1/2 blocks with p in [0.02, 0.1], 2 %
+    sparse entries (synth.job); job j seeded SEED + 200 + j."""
+    import numpy as np
+
+    from paper_1507_08751_gb300 import synth
+
+    rng = np.random.default_rng(SEED + 33)
+    jobs = []
+    for j in range(n):
+        M, N = BATCH_SIZES[int(rng.integers(len(BATCH_SIZES)))]
+        Y, scales = synth.job(SEED + 200 + j, M, N, int(rng.integers(4, 7)))
+        jobs.append((Y, scales))
+    return jobs
+
+
+def batch(a):
+    """Batching: the jobs of one shape and scale list run as one batched
+    decomposition (msllr_decompose_batch: every kernel launch of an iteration
+    covers all of them); value = job-iterations per second over the whole set,
+    the groups one after another on one context, inputs resident in HBM.  The
+    same jobs one at a time (msllr_decompose) are timed beside it."""
+    import numpy as np
+    import torch
+
+    from paper_1507_08751_gb300 import binding as B
+
+    if int(os.environ.get("RANK", "0")) != 0:
+        return
+    iters = a.iters if a.iters != ITERS_DEF else 200
+    jobs = batch_jobs(a.batch_jobs)
+    groups = {}
+    for j, (Y, scales) in enumerate(jobs):
+        groups.setdefault((Y.shape, tuple(scales)), []).append(j)
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(0)
+    stream = torch.cuda.Stream(device=dev)
+    ctx = B.Context(0, stream=stream.cuda_stream)
+    staged = []
+    for (shape, scales), idx in groups.items():
+        M, N = shape
+        Yb = torch.from_numpy(np.stack([jobs[j][0] for j in idx])).to(dev)
+        Xb = torch.empty((len(scales), len(idx), M, N), dtype=torch.float32, device=dev)
+        staged.append((list(scales), idx, Yb, Xb))
+
+    def run_batched(n_it):
+        for scales, idx, Yb, Xb in staged:
+            ctx.msllr_decompose_batch(Yb, scales, Xb, [SEED + j for j in idx], iters=n_it)
+
+    def run_single(n_it):
+        for scales, idx, Yb, Xb in staged:
+            for t, j in enumerate(idx):
+                ctx.msllr_decompose(Yb[t], scales, Xb[:, t], iters=n_it, seed=SEED + j)
+
+    run_batched(3)  # warm-up: kernels loaded, workspace grown
+    run_single(3)
+    torch.cuda.synchronize()
+    clocks = ClockSampler(0)
+    clocks.start()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    run_batched(iters)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    t_b = e0.elapsed_time(e1) / 1e3
+    e0.record(stream)
+    run_single(iters)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    t_s = e0.elapsed_time(e1) / 1e3
+    ck = clocks.stop()
+    ctx.close()
+    n = len(jobs)
+    line = {
+        "metric": f"batched job-iterations/s ({n} jobs, {iters} iters/job)",
+        "value": round(n * iters / t_b, 2), "unit": "job-iter/s", "n_gpus": 1, "steps": 1,
+        "warmup": 1, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32", "data": "synthetic",
+        "config": {"workload": "batch-mix", "sizes": [f"{m}x{n_}" for m, n_ in BATCH_SIZES],
+                   "scales": "4-6 dyadic", "jobs": n, "iters_per_job": iters,
+                   "groups": len(staged), "group_sizes": sorted(len(g[1]) for g in staged)},
+        "one_at_a_time": round(n * iters / t_s, 2),
+        "speedup": round(t_s / t_b, 3),
+        "clocks": ck,
+    }
+    print(json.dumps(line), flush=True)
+
+
 def main():
     a = parse()
     if a.impl == "reference":
         reference_arm(a)
     elif a.workload == "serve":
         serve(a)
+    elif a.workload == "batch":
+        batch(a)
     else:
         ours(a)
 

@@ -266,6 +266,27 @@ int msllr_decompose(msllr_ctx* ctx, const float* Y, int M, int N, int ld,
                     const uint8_t* mask, const msllr_params* params,
                     float* X_out, float* Z_out, msllr_stats* stats);
 
+/* Batched decompositions: `batch` independent jobs of one shape (M x N, the
+ * same scales, lambda and rho), each the eq:admm iteration of
+ * msllr_decompose with its own cycle-spin shift sequence (seeds[j], as
+ * msllr_shift_table), run together so that every kernel launch of an
+ * iteration covers the blocks of all jobs (one CUDA graph per iteration for
+ * the whole batch).  Job j's result equals msllr_decompose of that job alone.
+ *  Y        device, the jobs stacked row-wise: batch x M rows of N, row
+ *           stride ld (job j at Y + j M ld).
+ *  seeds    host array of batch shift seeds.
+ *  mask     device uint8 batch x M x N, or NULL.
+ *  X_out    device, L x batch x M x N: for scale i the stacked jobs at
+ *           X_out + i batch M N (job j at + j M N).  Z_out likewise or NULL.
+ *  stats    host or NULL: block counts and the objective summed over jobs.
+ * Not with the noise scale, spin_grid > 1, spatio-temporal scales or an
+ * initial state (EINVAL).  Errors as msllr_decompose. */
+int msllr_decompose_batch(msllr_ctx* ctx, int batch, const float* Y, int M, int N, int ld, int L,
+                          const int* block_m, const int* block_n, const double* lambda, double rho,
+                          int iters, const uint64_t* seeds, const uint8_t* mask,
+                          const msllr_params* params, float* X_out, float* Z_out,
+                          msllr_stats* stats);
+
 /* Same as msllr_decompose, but Y, mask, X_out and Z_out are HOST pointers:
  * the library copies Y (and mask) to the device, runs, and copies the
  * results back before returning.  params->Z_init / U_init / U_out must be

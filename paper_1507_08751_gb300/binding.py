@@ -37,8 +37,8 @@ STATUS_NAMES = {0: "MSLLR_OK", 1: "MSLLR_EINVAL", 2: "MSLLR_ENOMEM", 3: "MSLLR_E
 EXPORTS = (
     "msllr_params_default", "msllr_create", "msllr_destroy", "msllr_last_error",
     "msllr_shift_table", "msllr_lambda_default", "msllr_blocksvt", "msllr_decompose",
-    "msllr_decompose_host", "msllr_blocksvt_noalloc", "msllr_submit", "msllr_poll",
-    "msllr_wait",
+    "msllr_decompose_host", "msllr_decompose_batch", "msllr_blocksvt_noalloc", "msllr_submit",
+    "msllr_poll", "msllr_wait",
 )
 SERVE_QUEUE = 64
 SERVE_SLOTS = 4
@@ -165,6 +165,8 @@ def lib():
                ctypes.POINTER(Stats)]
         L.msllr_decompose.argtypes = dec
         L.msllr_decompose_host.argtypes = dec
+        L.msllr_decompose_batch.argtypes = [vp, ci, vp, ci, ci, ci, ci, vp, vp, vp, cd, ci, vp, vp,
+                                            ctypes.POINTER(Params), vp, vp, ctypes.POINTER(Stats)]
         L.msllr_blocksvt_noalloc.argtypes = [vp, vp, ci, ci, ci, ci, ci, cd, ci, ci, vp, vp]
         L.msllr_submit.argtypes = [vp, ctypes.POINTER(Job), ctypes.POINTER(cu64)]
         L.msllr_poll.argtypes = [vp, cu64, ctypes.POINTER(ci)]
@@ -301,6 +303,29 @@ class Context:
         return self._decompose(lib().msllr_decompose, _ptr(Y), M, N, N, scales, lambdas, rho,
                                iters, seed, _ptr(mask), params, _ptr(X_out), _ptr(Z_out),
                                frame)
+
+    def msllr_decompose_batch(self, Y, scales, X_out, seeds, lambdas=None, rho=1.0, iters=100,
+                              mask=None, params=None, Z_out=None):
+        """Batched jobs of one shape: Y a torch CUDA float32 tensor (batch, M, N), X_out
+        (and Z_out) (L, batch, M, N), seeds one shift seed per job, mask (batch, M, N)
+        uint8 or None.  Every kernel launch covers all jobs; job j's result is that of
+        msllr_decompose of job j alone.  Returns the stats dict (summed over jobs)."""
+        batch, M, N = Y.shape
+        if len(seeds) != batch:
+            raise MsllrError(MSLLR_EINVAL, "one seed per job")
+        L = len(scales)
+        bm, bn, pw = _scale_arrays(scales)
+        if pw is not None:
+            raise MsllrError(MSLLR_EINVAL, "batched jobs take no spatio-temporal scales")
+        lam = _double_array(lambdas)
+        sd = (ctypes.c_uint64 * batch)(*[int(x) for x in seeds])
+        p = params if params is not None else msllr_params_default()
+        st = Stats()
+        _check(lib().msllr_decompose_batch(self._ctx, batch, _ptr(Y), M, N, N, L, bm, bn, lam,
+                                           float(rho), int(iters), sd, _ptr(mask),
+                                           ctypes.byref(p), _ptr(X_out), _ptr(Z_out),
+                                           ctypes.byref(st)), self._ctx)
+        return st.to_dict()
 
     def msllr_decompose_host(self, Y, scales, X_out, lambdas=None, rho=1.0, iters=100, seed=0,
                              mask=None, params=None, Z_out=None, frame=None):

@@ -78,6 +78,7 @@ struct BlockGeom {
   int p, q;         // block coordinates on the shifted grid
   int sr, sc;       // shift
   int fw, fh, bh, bw, sy, sx;  // spatio-temporal blocks (fw = 0: none)
+  int rbase;                    // batched jobs: first row of the block's job
   __device__ __forceinline__ int mm() const { return m >= n ? m : n; }
   __device__ __forceinline__ int nn() const { return m >= n ? n : m; }
   __device__ __forceinline__ bool transposed() const { return m < n; }
@@ -98,7 +99,7 @@ struct BlockGeom {
     }
     int gc = q * n + c + sc;
     if (gc >= N) gc -= N;
-    return (size_t)gr * ld + gc;
+    return (size_t)(rbase + gr) * ld + gc;
   }
   // index into the row-major mm x nn matrix C of block element (r, c)
   __device__ __forceinline__ int cidx(int r, int c, int ldc) const {
@@ -107,12 +108,15 @@ struct BlockGeom {
 };
 
 // Block b of the scale described by a launch (row-major block order on the
-// shifted grid).  The full-matrix scale ignores the shift: SVT commutes with
-// row and column permutations.
+// shifted grid; with batched jobs, the jobs' block grids one above the other,
+// each job shifted by its own pair and wrapped within its own rows).  The
+// full-matrix scale ignores the shift: SVT commutes with row and column
+// permutations.
 template <class SL>
 __device__ __forceinline__ BlockGeom block_geom(const SL& a, int b) {
   BlockGeom g;
-  g.M = a.M;
+  const int rows = a.rows ? a.rows : a.M;
+  g.M = rows;
   g.N = a.N;
   g.ld = a.ld;
   g.m = a.m;
@@ -120,11 +124,19 @@ __device__ __forceinline__ BlockGeom block_geom(const SL& a, int b) {
   const int nbn = a.N / a.n;
   g.p = b / nbn;
   g.q = b - g.p * nbn;
-  const bool full = (a.m == a.M && a.n == a.N && !a.fw);
-  g.sr = (a.shift && !full) ? (a.shift[0] + a.shift_add_r) % a.M : 0;
-  g.sc = (a.shift && !full) ? (a.shift[1] + a.shift_add_c) % a.N : 0;
+  int job = 0;
+  if (a.rows) {
+    const int pj = rows / a.m;
+    job = g.p / pj;
+    g.p -= job * pj;
+  }
+  g.rbase = job * rows;
+  const int* sh = a.shift ? a.shift + 2 * job : nullptr;
+  const bool full = (a.m == rows && a.n == a.N && !a.fw);
+  g.sr = (sh && !full) ? (sh[0] + a.shift_add_r) % rows : 0;
+  g.sc = (sh && !full) ? (sh[1] + a.shift_add_c) % a.N : 0;
   g.fw = a.fw;
-  g.fh = a.fw ? a.M / a.fw : 0;
+  g.fh = a.fw ? rows / a.fw : 0;
   g.bw = a.fw ? a.bw : 0;
   g.bh = a.fw ? a.m / a.bw : 0;
   g.sy = a.fw ? g.sr / a.fw : 0;

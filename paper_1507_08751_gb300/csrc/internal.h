@@ -36,7 +36,14 @@ struct ScaleLaunch {
   int fw;                  // spatio-temporal blocks (Sec. 10.2): frame width of the
                            // video whose pixels are the rows (0: 2-D blocks)
   int bw;                  // their patch width (patch height m / bw, n frames)
+  int rows;                // batched jobs: rows of one job (M = jobs x rows, job j
+                           // at rows j rows ..; its shift at shift[2 j]); 0: one job
 };
+
+// rows of one job of a launch (the whole M unless jobs are batched)
+__host__ __device__ __forceinline__ int launch_rows(const ScaleLaunch& s) {
+  return s.rows ? s.rows : s.M;
+}
 
 // Device workspace needed by the wide-block path for one scale.
 struct BigWorkspace {
@@ -168,7 +175,9 @@ cudaError_t launch_residual(const float* Z, const float* W, const float* Zs, con
                             double* acc4, size_t n, cudaStream_t st, Prof* prof = nullptr);
 cudaError_t launch_init_state(const float* Z0, const float* U0, float* Z, float* W, int L,
                               size_t MN, cudaStream_t st, Prof* prof = nullptr);
-cudaError_t launch_advance(const int* table, int* iter, int* cur_shift, cudaStream_t st,
+// the shifts of iteration *iter (one pair per job, table iters x jobs x 2)
+// into cur_shift, then ++*iter
+cudaError_t launch_advance(const int* table, int* iter, int* cur_shift, int jobs, cudaStream_t st,
                            Prof* prof = nullptr);
 cudaError_t launch_nonfinite(const float* Y, int M, int N, int ld, int* flag, cudaStream_t st,
                              Prof* prof = nullptr);

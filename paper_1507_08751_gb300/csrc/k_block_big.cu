@@ -263,7 +263,7 @@ eig_big_kernel(ScaleLaunch a, const float* __restrict__ Gall, BigWorkspace ws) {
   const float rs = gershgorin_lower<NT, NMAX>(Gacc, nn, z.x, z.w, s.red);
   const float gbound = fminf(tr, rs);
   double fl = nn + fl_symv(nn);  // trace, Gershgorin row sums
-  const bool full = (a.m == a.M && a.n == a.N);
+  const bool full = (a.m == launch_rows(a) && a.n == a.N);
   const int kwarm = (a.warm_start && (full || !a.shift)) ? min(ws.kwarm[b], kLzMaxK) : 0;
   bool skipped = false, lanczos_ok = false;
   int k = -1, ku = 0;

@@ -1064,7 +1064,7 @@ cudaError_t launch_huge(const ScaleLaunch& s, const BigWorkspace& ws, cudaStream
   // subspace iteration: a first round (short when the grid does not move and
   // the basis carries over from the previous call), a second round for the
   // blocks whose Ritz residuals are still large
-  const bool full = (s.m == s.M && s.n == s.N);
+  const bool full = (s.m == launch_rows(s) && s.n == s.N);
   const bool warm = s.warm_start && (full || !s.shift);
   const int rounds[3] = {warm ? 2 : 6, 6, 12};
   const dim3 gv_grid((nn + kHGvRows - 1) / kHGvRows, B);

@@ -265,10 +265,12 @@ init_state_kernel(const float* __restrict__ Z0, const float* __restrict__ U0, fl
 }
 
 // Start of an iteration: publish this iteration's shift and advance.
-__global__ void advance_kernel(const int* __restrict__ table, int* iter, int* cur_shift) {
+__global__ void advance_kernel(const int* __restrict__ table, int* iter, int* cur_shift, int jobs) {
   const int k = *iter;
-  cur_shift[0] = table[2 * k];
-  cur_shift[1] = table[2 * k + 1];
+  for (int j = 0; j < jobs; ++j) {
+    cur_shift[2 * j] = table[2 * (k * jobs + j)];
+    cur_shift[2 * j + 1] = table[2 * (k * jobs + j) + 1];
+  }
   *iter = k + 1;
 }
 
@@ -434,11 +436,11 @@ cudaError_t launch_init_state(const float* Z0, const float* U0, float* Z, float*
   return cudaGetLastError();
 }
 
-cudaError_t launch_advance(const int* table, int* iter, int* cur_shift, cudaStream_t st,
+cudaError_t launch_advance(const int* table, int* iter, int* cur_shift, int jobs, cudaStream_t st,
                            Prof* prof) {
   if (prof) prof->scale = 0;
   if (prof) if (cudaError_t e = prof->before(st, KK_ADVANCE)) return e;
-  advance_kernel<<<1, 1, 0, st>>>(table, iter, cur_shift);
+  advance_kernel<<<1, 1, 0, st>>>(table, iter, cur_shift, jobs);
   if (prof) if (cudaError_t e = prof->after(st)) return e;
   return cudaGetLastError();
 }

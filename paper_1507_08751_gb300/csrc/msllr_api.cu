@@ -81,6 +81,8 @@ struct msllr_ctx {
   unsigned long long* d_cnt = nullptr;  // [2*MAX]
   int* d_table = nullptr;
   size_t table_cap = 0;
+  int* d_shift = nullptr;          // current shift, one (s_r, s_c) pair per batched job
+  int shift_cap = 0;               // pairs d_shift holds
 
   // one stream per scale: the scales of an iteration are independent given R.
   // Wide-block scales (the longest dependency chain) get high-priority
@@ -287,8 +289,10 @@ int msllr_create(msllr_ctx** out, int device, size_t hbm_budget_bytes, void* cud
   if (cudaMalloc(&ctx->d_small, 64 * sizeof(int)) != cudaSuccess ||
       cudaMalloc(&ctx->d_acc, (MSLLR_MAX_SCALES + 8) * sizeof(double)) != cudaSuccess ||
       cudaMalloc(&ctx->d_noise, MSLLR_MAX_SCALES * sizeof(double)) != cudaSuccess ||
-      cudaMalloc(&ctx->d_cnt, 8 * MSLLR_MAX_SCALES * sizeof(unsigned long long)) != cudaSuccess)
+      cudaMalloc(&ctx->d_cnt, 8 * MSLLR_MAX_SCALES * sizeof(unsigned long long)) != cudaSuccess ||
+      cudaMalloc(&ctx->d_shift, 2 * sizeof(int)) != cudaSuccess)
     return bail(fail(ctx, MSLLR_ENOMEM, "cudaMalloc of context scalars"));
+  ctx->shift_cap = 1;
   *out = ctx;
   return MSLLR_OK;
 }
@@ -334,6 +338,7 @@ int msllr_destroy(msllr_ctx* ctx) {
   if (ctx->d_noise) cudaFree(ctx->d_noise);
   if (ctx->d_cnt) cudaFree(ctx->d_cnt);
   if (ctx->d_table) cudaFree(ctx->d_table);
+  if (ctx->d_shift) cudaFree(ctx->d_shift);
   for (int i = 0; i < MSLLR_MAX_SCALES; ++i) {
     if (ctx->side[i]) cudaStreamDestroy(ctx->side[i]);
     if (ctx->side_hi[i]) cudaStreamDestroy(ctx->side_hi[i]);
@@ -483,10 +488,13 @@ std::vector<std::pair<int, int>> spin_offsets(int M, int N, int m, int n, int g)
   return out;
 }
 
+// One ADMM iteration.  M counts the rows of all batched jobs; `rows` is the
+// rows of one job (0: a single job).
 int enqueue_iteration(msllr_ctx* ctx, const Layout& lay, int M, int N, int L, const int* bm,
                       const int* bn, const float* taus, const msllr_params& p, bool stats,
-                      Prof* prof) {
-  CK(launch_advance(ctx->d_table, ctx->d_small, ctx->d_small + 1, ctx->stream, prof));
+                      Prof* prof, int rows = 0) {
+  const int jobs = rows ? M / rows : 1;
+  CK(launch_advance(ctx->d_table, ctx->d_small, ctx->d_shift, jobs, ctx->stream, prof));
   CK(launch_consensus(lay.Yd, lay.W, lay.R, lay.mask, L, lay.MN, ctx->stream, prof));
   if (p.plain) {
     // the comparator: scales one after the other on the context stream, one
@@ -502,7 +510,8 @@ int enqueue_iteration(msllr_ctx* ctx, const Layout& lay, int M, int N, int L, co
       s.ld = N;
       s.m = bm[i];
       s.n = bn[i];
-      s.shift = p.cycle_spin ? ctx->d_small + 1 : nullptr;
+      s.shift = p.cycle_spin ? ctx->d_shift : nullptr;
+      s.rows = rows;
       s.tau = taus[i];
       s.nuc_acc = stats ? ctx->d_acc + i : nullptr;
       s.cnt = (stats || p.profile) ? ctx->d_cnt + 8 * i : nullptr;
@@ -534,7 +543,7 @@ int enqueue_iteration(msllr_ctx* ctx, const Layout& lay, int M, int N, int L, co
       if (pass == 1 && fork)
         for (int j = 0; j < L; ++j)
           if (gated[j]) CK(cudaStreamWaitEvent(st, ctx->ev_gate[j], 0));
-      const auto offs = spin_offsets(M, N, bm[i], bn[i], p.spin_grid);
+      const auto offs = spin_offsets(rows ? rows : M, N, bm[i], bn[i], p.spin_grid);
       ScaleLaunch s{};
       s.A1 = lay.Z + (size_t)i * lay.MN;
       s.A2 = lay.R;
@@ -545,7 +554,8 @@ int enqueue_iteration(msllr_ctx* ctx, const Layout& lay, int M, int N, int L, co
       s.ld = N;
       s.m = bm[i];
       s.n = bn[i];
-      s.shift = (p.cycle_spin || offs.size() > 1) ? ctx->d_small + 1 : nullptr;
+      s.shift = (p.cycle_spin || offs.size() > 1) ? ctx->d_shift : nullptr;
+      s.rows = rows;
       s.tau = taus[i];
       s.skip_bound = p.skip_bound;
       s.warm_start = 1;
@@ -599,13 +609,20 @@ int enqueue_iteration(msllr_ctx* ctx, const Layout& lay, int M, int N, int L, co
   return MSLLR_OK;
 }
 
+// `batch` jobs of one shape M x N stacked row-wise in Y (job j at rows
+// j M ..), each with its own shift sequence from seeds[j]; X_out and Z_out
+// hold per scale the batch x M x N stack.
 int decompose_device(msllr_ctx* ctx, const float* Y, int M, int N, int ld, int L, const int* bm,
-                     const int* bn, const double* lambda, double rho, int iters, uint64_t seed,
-                     const uint8_t* mask, const msllr_params* params, float* X_out, float* Z_out,
-                     msllr_stats* stats) {
+                     const int* bn, const double* lambda, double rho, int iters,
+                     const uint64_t* seeds, int batch, const uint8_t* mask,
+                     const msllr_params* params, float* X_out, float* Z_out, msllr_stats* stats) {
   if (!ctx) return fail(nullptr, MSLLR_EINVAL, "ctx is NULL");
   if (!Y || !X_out || M <= 0 || N <= 0 || ld < N)
     return fail(ctx, MSLLR_EINVAL, "msllr_decompose: bad matrix arguments");
+  if (batch < 1 || !seeds || (long long)M * batch > 0x7fffffffLL)
+    return fail(ctx, MSLLR_EINVAL, "batch must be >= 1 with one seed per job");
+  const int MT = M * batch;           // rows of the stacked jobs
+  const int rows = batch > 1 ? M : 0;  // rows of one job for the kernels
   if (L <= 0 || L > MSLLR_MAX_SCALES || !bm || !bn)
     return fail(ctx, MSLLR_EINVAL, "L must be in 1..MSLLR_MAX_SCALES with block sizes given");
   if (!(rho > 0.0) || !isfinite(rho)) return fail(ctx, MSLLR_EINVAL, "rho must be > 0");
@@ -633,6 +650,19 @@ int decompose_device(msllr_ctx* ctx, const float* Y, int M, int N, int ld, int L
   for (int i = 0; i < L && p.plain; ++i)
     if (choose_path(bm[i], bn[i]) == ScalePath::Huge)
       return fail(ctx, MSLLR_EINVAL, "the plain comparator path takes blocks up to 256 wide");
+  if (batch > 1) {
+    if (p.spin_grid > 1 || p.frame_w || p.Z_init || p.U_init)
+      return fail(ctx, MSLLR_EINVAL,
+                  "batched jobs take no spin_grid, spatio-temporal scales or initial state");
+    for (int i = 0; i < L; ++i) {
+      if (bm[i] == 0 && bn[i] == 0)
+        return fail(ctx, MSLLR_EINVAL, "batched jobs take no noise scale");
+      const ScalePath path = choose_path(bm[i], bn[i]);
+      if ((path == ScalePath::Big || path == ScalePath::Huge) && bm[i] > 0 && bn[i] > 0 &&
+          (long long)(MT / bm[i]) * (N / bn[i]) > 65535)
+        return fail(ctx, MSLLR_EINVAL, "too many wide blocks over the batch (max 65535)");
+    }
+  }
   for (int i = 0; i < L && p.spin_grid > 1; ++i) {
     const int m = bm[i], n = bn[i];
     if (m <= 0 || n <= 0) continue;
@@ -665,26 +695,43 @@ int decompose_device(msllr_ctx* ctx, const float* Y, int M, int N, int ld, int L
     return fail(ctx, MSLLR_EINVAL, "stop_tol must be finite and >= 0, stop_every >= 0");
   const bool stop_test = p.stop_tol > 0.0;
   const int every = p.stop_every > 0 ? p.stop_every : 10;
-  const Layout sizing = plan(nullptr, M, N, L, bm, bn, mask != nullptr, spin, p.plain != 0,
+  const Layout sizing = plan(nullptr, MT, N, L, bm, bn, mask != nullptr, spin, p.plain != 0,
                              stop_test);
   if (int r = ensure_ws(ctx, sizing.total)) return r;
-  const Layout lay = plan(ctx->ws, M, N, L, bm, bn, mask != nullptr, spin, p.plain != 0,
+  const Layout lay = plan(ctx->ws, MT, N, L, bm, bn, mask != nullptr, spin, p.plain != 0,
                           stop_test);
   cudaStream_t st = ctx->stream;
+  if (batch > ctx->shift_cap) {
+    if (ctx->graph) {
+      cudaGraphExecDestroy(ctx->graph);
+      ctx->graph = nullptr;
+      ctx->graph_key.clear();
+    }
+    if (ctx->d_shift) {
+      if (ctx->serve_child) cudaFreeAsync(ctx->d_shift, st);
+      else cudaFree(ctx->d_shift);
+    }
+    ctx->d_shift = nullptr;
+    ctx->shift_cap = 0;
+    if (ctx->serve_child) CK(cudaMallocAsync((void**)&ctx->d_shift, 2 * sizeof(int) * batch, st));
+    else CK(cudaMalloc(&ctx->d_shift, 2 * sizeof(int) * batch));
+    ctx->shift_cap = batch;
+  }
 
   // inputs: finiteness check, dense copies
   CK(cudaMemsetAsync(ctx->d_small + 3, 0, sizeof(int), st));
-  CK(launch_nonfinite(Y, M, N, ld, ctx->d_small + 3, st, &prof));
+  CK(launch_nonfinite(Y, MT, N, ld, ctx->d_small + 3, st, &prof));
   int bad = 0;
   CK(cudaMemcpyAsync(&bad, ctx->d_small + 3, sizeof(int), cudaMemcpyDeviceToHost, st));
   CK(cudaStreamSynchronize(st));
   if (bad) return fail(ctx, MSLLR_ENONFINITE, "Y contains NaN or Inf");
   if (ld == N) CK(cudaMemcpyAsync(lay.Yd, Y, sizeof(float) * lay.MN, cudaMemcpyDeviceToDevice, st));
-  else CK(launch_copy_dense(Y, M, N, ld, lay.Yd, st, &prof));
+  else CK(launch_copy_dense(Y, MT, N, ld, lay.Yd, st, &prof));
   if (mask) CK(cudaMemcpyAsync(lay.mask, mask, lay.MN, cudaMemcpyDeviceToDevice, st));
 
-  // shift table for iterations iter_offset .. iter_offset + iters - 1
-  const size_t tab = 2 * (size_t)(iters > 0 ? iters : 1);
+  // shift table for iterations iter_offset .. iter_offset + iters - 1, one
+  // pair per job (iters x batch x 2)
+  const size_t tab = 2 * (size_t)(iters > 0 ? iters : 1) * batch;
   if (tab > ctx->table_cap) {
     if (ctx->d_table) {
       if (ctx->serve_child) cudaFreeAsync(ctx->d_table, st);
@@ -702,11 +749,20 @@ int decompose_device(msllr_ctx* ctx, const float* Y, int M, int N, int ld, int L
     ctx->table_cap = tab;
   }
   std::vector<int32_t> h_table(tab, 0);
-  if (p.cycle_spin) fill_shift_table(seed, p.iter_offset, iters, M, N, h_table.data());
+  if (p.cycle_spin) {
+    std::vector<int32_t> one(2 * (size_t)(iters > 0 ? iters : 1));
+    for (int j = 0; j < batch; ++j) {
+      fill_shift_table(seeds[j], p.iter_offset, iters, M, N, one.data());
+      for (int k = 0; k < iters; ++k) {
+        h_table[2 * ((size_t)k * batch + j)] = one[2 * k];
+        h_table[2 * ((size_t)k * batch + j) + 1] = one[2 * k + 1];
+      }
+    }
+  }
   CK(cudaMemcpyAsync(ctx->d_table, h_table.data(), tab * sizeof(int), cudaMemcpyHostToDevice, st));
   CK(cudaMemsetAsync(ctx->d_small, 0, sizeof(int), st));
   CK(launch_init_state(p.Z_init, p.U_init, lay.Z, lay.W, L, lay.MN, st, &prof));
-  for (int i = 0; i < L && !p.plain; ++i) CK(reset_warm_start(lay.big[i], M, N, bm[i], bn[i], st));
+  for (int i = 0; i < L && !p.plain; ++i) CK(reset_warm_start(lay.big[i], MT, N, bm[i], bn[i], st));
   CK(cudaMemsetAsync(ctx->d_acc, 0, (MSLLR_MAX_SCALES + 8) * sizeof(double), st));
   CK(cudaMemsetAsync(ctx->d_cnt, 0, 8 * MSLLR_MAX_SCALES * sizeof(unsigned long long), st));
 
@@ -717,7 +773,8 @@ int decompose_device(msllr_ctx* ctx, const float* Y, int M, int N, int ld, int L
     auto put = [&](const void* v, size_t n) {
       key.insert(key.end(), (const char*)v, (const char*)v + n);
     };
-    put(&M, sizeof M);
+    put(&MT, sizeof MT);
+    put(&rows, sizeof rows);
     put(&N, sizeof N);
     put(&L, sizeof L);
     put(bm, sizeof(int) * L);
@@ -739,7 +796,7 @@ int decompose_device(msllr_ctx* ctx, const float* Y, int M, int N, int ld, int L
       cudaGraph_t g = nullptr;
       CK(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
       Prof counter;
-      int r = enqueue_iteration(ctx, lay, M, N, L, bm, bn, taus, p, false, &counter);
+      int r = enqueue_iteration(ctx, lay, MT, N, L, bm, bn, taus, p, false, &counter, rows);
       memcpy(ctx->graph_launches, counter.launches, sizeof counter.launches);
       cudaError_t e = cudaStreamEndCapture(st, &g);
       if (r) {
@@ -771,7 +828,7 @@ int decompose_device(msllr_ctx* ctx, const float* Y, int M, int N, int ld, int L
       CK(cudaGraphLaunch(ctx->graph, st));
       for (int a = 0; a < KK_COUNT; ++a)
         for (int b = 0; b < 8; ++b) prof.launches[a][b] += ctx->graph_launches[a][b];
-    } else if (int r = enqueue_iteration(ctx, lay, M, N, L, bm, bn, taus, p, false, &prof)) {
+    } else if (int r = enqueue_iteration(ctx, lay, MT, N, L, bm, bn, taus, p, false, &prof, rows)) {
       return r;
     }
     ++ran;
@@ -790,7 +847,7 @@ int decompose_device(msllr_ctx* ctx, const float* Y, int M, int N, int ld, int L
   // the Z it started from (copied into X_out) for the dual residual
   if (iters > 0) {
     CK(cudaMemcpyAsync(X_out, lay.Z, sizeof(float) * LMN, cudaMemcpyDeviceToDevice, st));
-    if (int r = enqueue_iteration(ctx, lay, M, N, L, bm, bn, taus, p, true, &prof)) return r;
+    if (int r = enqueue_iteration(ctx, lay, MT, N, L, bm, bn, taus, p, true, &prof, rows)) return r;
     ++ran;
   }
 
@@ -812,10 +869,10 @@ int decompose_device(msllr_ctx* ctx, const float* Y, int M, int N, int ld, int L
     double obj = 0.0;
     for (int i = 0; i < L; ++i) {
       // averaged cycle spinning sums the nuclear norms of all the shifts
-      const double nspin = (double)spin_offsets(M, N, bm[i], bn[i], p.spin_grid).size();
+      const double nspin = (double)spin_offsets(M, N, bm[i], bn[i], p.spin_grid).size();  // one job
       stats->scale_nuclear[i] = acc[i] / nspin;
       obj += lam[i] * acc[i] / nspin;
-      stats->blocks[i] = (bm[i] == 0 && bn[i] == 0) ? 1 : (long long)(M / bm[i]) * (N / bn[i]);
+      stats->blocks[i] = (bm[i] == 0 && bn[i] == 0) ? 1 : (long long)(MT / bm[i]) * (N / bn[i]);
       stats->blocks_skipped[i] = (long long)cnt[8 * i];
       stats->blocks_zero[i] = (long long)cnt[8 * i + 1];
       stats->blocks_lanczos[i] = (long long)cnt[8 * i + 2];
@@ -884,7 +941,7 @@ int run_job(msllr_ctx* ctx, ServeJob& j) {
                                       cudaGetErrorString(e));
   }
   int r = decompose_device(ctx, dY, j.M, j.N, j.N, j.L, j.bm.data(), j.bn.data(),
-                           j.lam.empty() ? nullptr : j.lam.data(), j.rho, j.iters, j.seed, dmask,
+                           j.lam.empty() ? nullptr : j.lam.data(), j.rho, j.iters, &j.seed, 1, dmask,
                            j.has_p ? &j.p : nullptr, dX, dZ, j.stats);
   if (r == MSLLR_OK) {
     e = cudaMemcpyAsync(j.X_out, dX, sizeof(float) * j.L * MN, cudaMemcpyDeviceToHost,
@@ -993,8 +1050,19 @@ int msllr_decompose(msllr_ctx* ctx, const float* Y, int M, int N, int ld, int L,
                     float* X_out, float* Z_out, msllr_stats* stats) {
   if (ctx)
     if (int r = busy(ctx)) return r;
-  return decompose_device(ctx, Y, M, N, ld, L, block_m, block_n, lambda, rho, iters, seed, mask,
+  return decompose_device(ctx, Y, M, N, ld, L, block_m, block_n, lambda, rho, iters, &seed, 1, mask,
                           params, X_out, Z_out, stats);
+}
+
+int msllr_decompose_batch(msllr_ctx* ctx, int batch, const float* Y, int M, int N, int ld, int L,
+                          const int* block_m, const int* block_n, const double* lambda, double rho,
+                          int iters, const uint64_t* seeds, const uint8_t* mask,
+                          const msllr_params* params, float* X_out, float* Z_out,
+                          msllr_stats* stats) {
+  if (ctx)
+    if (int r = busy(ctx)) return r;
+  return decompose_device(ctx, Y, M, N, ld, L, block_m, block_n, lambda, rho, iters, seeds, batch,
+                          mask, params, X_out, Z_out, stats);
 }
 
 int msllr_decompose_host(msllr_ctx* ctx, const float* Y, int M, int N, int ld, int L,
@@ -1043,7 +1111,7 @@ int msllr_decompose_host(msllr_ctx* ctx, const float* Y, int M, int N, int ld, i
     cleanup();
     return fail(ctx, MSLLR_ECUDA, std::string("host to device copy: ") + cudaGetErrorString(e));
   }
-  int r = decompose_device(ctx, dY, M, N, N, L, block_m, block_n, lambda, rho, iters, seed, dmask,
+  int r = decompose_device(ctx, dY, M, N, N, L, block_m, block_n, lambda, rho, iters, &seed, 1, dmask,
                            params, dX, dZ, stats);
   if (r == MSLLR_OK) {
     e = cudaMemcpyAsync(X_out, dX, sizeof(float) * L * MN, cudaMemcpyDeviceToHost, ctx->stream);

@@ -524,3 +524,56 @@ def test_error_paths(ctx):
     # the context still works after errors
     ctx.msllr_decompose(Y, [(1, 1), (64, 64)], X, iters=2)
     assert torch.all(X == 0)
+
+
+def _batch_case(ctx, jobs, scales, iters, seeds, masks=None, tol_solo=0.0):
+    """Runs the jobs (a list of M x N float32 arrays of one shape) as one
+    batch and one by one; returns the batch result (L, batch, M, N) after
+    checking every job against its solo run (bit for bit when tol_solo is 0)."""
+    B = len(jobs)
+    M, N = jobs[0].shape
+    L = len(scales)
+    Yb = torch.from_numpy(np.stack(jobs)).cuda()
+    Xb = torch.empty((L, B, M, N), dtype=torch.float32, device="cuda")
+    mb = None if masks is None else torch.from_numpy(np.stack(masks)).cuda()
+    st = ctx.msllr_decompose_batch(Yb, scales, Xb, seeds, iters=iters, mask=mb)
+    torch.cuda.synchronize()
+    Xb = Xb.cpu().numpy()
+    for j in range(B):
+        Xs, _, _ = _run_decompose(ctx, jobs[j], scales, None, iters, seeds[j],
+                                  mask=None if masks is None else masks[j])
+        if tol_solo == 0.0:
+            np.testing.assert_array_equal(Xb[:, j], Xs)
+        else:
+            assert np.all(O.relerr(Xb[:, j], Xs, jobs[j]) <= tol_solo)
+    assert st["blocks"][1] == B * (M // scales[1][0]) * (N // scales[1][1])
+    return Xb
+
+
+def test_batched_jobs_equal_their_solo_runs_and_the_oracle(ctx):
+    """Batched decompositions (every launch covers all jobs of a shape, each
+    job with its own shift sequence): three 1024 x 256 video-shaped jobs give
+    bit for bit their solo results, and job 0 matches the oracle; a batch of
+    three masked ratings-like jobs likewise; a batch of two 512 x 512 jobs
+    whose full-matrix scale takes the path for blocks wider than 256 (whose
+    row chunking of the Gram sums depends on the block count) within 1e-5 of
+    the solo runs."""
+    vids = [synth.video(seed=500 + j, M=1024, N=256)[0] for j in range(3)]
+    scales = synth.video(M=1024, N=256)[2]
+    Xb = _batch_case(ctx, vids, scales, 30, [5, 6, 7])
+    M, N = vids[0].shape
+    lam = [O.lambda_default(M, N, m, n) for m, n in scales]
+    ref = O.admm(vids[0].astype(np.float64), scales, lam, 1.0, 30,
+                 shifts=O.shift_table(5, 30, M, N))
+    assert np.all(O.relerr(Xb[:, 0], ref["X"], vids[0]) <= TOL)
+    rat = [synth.ratings(40 + j, 128, 96, density=0.3) for j in range(3)]
+    _batch_case(ctx, [r[0] for r in rat], [(1, 1), (4, 4), (16, 16), (128, 96)], 40, [1, 2, 3],
+                masks=[r[1] for r in rat])
+    wide = [synth.job(60 + j, 512, 512, 5)[0] for j in range(2)]
+    _batch_case(ctx, wide, synth.dyadic_scales(512, 512, 5), 20, [8, 9], tol_solo=1e-5)
+    from paper_1507_08751_gb300 import binding as B
+    with pytest.raises(B.MsllrError) as e:  # no noise scale in a batch
+        Yb = torch.zeros((2, 64, 64), dtype=torch.float32, device="cuda")
+        ctx.msllr_decompose_batch(Yb, [(1, 1), (0, 0)], torch.empty((2, 2, 64, 64), device="cuda"),
+                                  [1, 2], iters=1)
+    assert e.value.code == B.MSLLR_EINVAL
