@@ -45,6 +45,12 @@ __host__ __device__ __forceinline__ int launch_rows(const ScaleLaunch& s) {
   return s.rows ? s.rows : s.M;
 }
 
+// index of block b within its own job (seeds that depend on it then do not
+// depend on the batch the job runs in)
+__host__ __device__ __forceinline__ int job_block(const ScaleLaunch& s, int b) {
+  return s.rows ? b % ((s.rows / s.m) * (s.N / s.n)) : b;
+}
+
 // Device workspace needed by the wide-block path for one scale.
 struct BigWorkspace {
   float* G;      // nblocks * nn * nn; block b at b * nn * nn, lower triangle packed row by row

@@ -296,7 +296,7 @@ eig_big_kernel(ScaleLaunch a, const float* __restrict__ Gall, BigWorkspace ws) {
       int J = 0;
       kk = lanczos_candidates<NT, NMAX>(Gacc, nn, thr, gbound, Qs,
                                                         min(nn, kLzMaxJ), U, warm, kwarm,
-                                                        0x1234567u + 977u * b, s, z, panel, &ku,
+                                                        0x1234567u + 977u * job_block(a, b), s, z, panel, &ku,
                                                         &c0, 4, &J);
       fl += fl_lanczos(nn, J, ku);
       PHASE(3, 5);

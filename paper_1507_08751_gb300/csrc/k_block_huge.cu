@@ -262,11 +262,13 @@ huge_prep_kernel(const float* __restrict__ tstat, int ntiles, HugeBlock* __restr
 }
 
 // Start basis: deterministic pseudo-random columns (any full-rank start
-// serves subspace iteration).
-__global__ void huge_init_basis_kernel(float* __restrict__ V, size_t total) {
+// serves subspace iteration), the same for every block (rows r of a block
+// at V + (b nn + r) kHP), so that a block's start does not depend on its
+// index.
+__global__ void huge_init_basis_kernel(float* __restrict__ V, size_t total, int nn) {
   for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total;
        e += (size_t)gridDim.x * blockDim.x)
-    V[e] = huge_hash((uint32_t)(e / kHP), (uint32_t)(e % kHP) + 0x51EDu);
+    V[e] = huge_hash((uint32_t)((e / kHP) % nn), (uint32_t)(e % kHP) + 0x51EDu);
 }
 
 __device__ __forceinline__ bool huge_active(const HugeBlock& h) {
@@ -1027,7 +1029,7 @@ cudaError_t reset_huge_basis(const BigWorkspace& w, int M, int N, int m, int n, 
   const HugeDims d = huge_dims(M, N, m, n);
   const size_t total = (size_t)d.nblocks * d.nn * kHP;
   const int grid = (int)((total + 255) / 256 < 4096 ? (total + 255) / 256 : 4096);
-  huge_init_basis_kernel<<<grid, 256, 0, st>>>(w.V, total);
+  huge_init_basis_kernel<<<grid, 256, 0, st>>>(w.V, total, d.nn);
   return cudaGetLastError();
 }
 

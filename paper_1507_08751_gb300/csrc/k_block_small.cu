@@ -215,7 +215,7 @@ blocksvt_small_kernel(ScaleLaunch a) {
       int J = 0;
       kk = lanczos_candidates<NT, NMAX>(LowerFull{G, ldg}, nn, thr, gbound, Qs,
                                         nn < JCAP ? nn : JCAP, Us, nullptr, 0,
-                                        0x51ED27u + 131u * blockIdx.x, s, z, panel, &ku, &c0,
+                                        0x51ED27u + 131u * job_block(a, (int)blockIdx.x), s, z, panel, &ku, &c0,
                                         5 + SLOT, &J);
       fl += (float)fl_lanczos(nn, J, ku);
       PHASE(SLOT, 10);
