@@ -233,13 +233,20 @@ def scale_rooflines(stats, scales, M, N, iters, pk):
     hbm, fp32 = pk["hbm_gbs"], pk["fp32_tflops"]
     ms, nl = stats["kernel_ms"], stats["kernel_launches"]
     rows = []
+    # the 1x1 scale runs inside the consensus pass (outside the last,
+    # statistics iteration): that pass reads Y, L W_j and Z_1 and writes R,
+    # Z_1 and W_1
+    fused = (1, 1) in [tuple(sc) for sc in scales]
     if nl["consensus"][0]:
         t = ms["consensus"][0] / nl["consensus"][0] / 1e3
-        byt = (L + 2) * 4 * MN
-        rows.append({"step": "consensus", "us": round(t * 1e6, 2), "bytes": byt,
+        byt = (L + 5 if fused else L + 2) * 4 * MN
+        rows.append({"step": "consensus + 1x1 scale" if fused else "consensus",
+                     "us": round(t * 1e6, 2), "bytes": byt,
                      "bound": "hbm", "frac": round(byt / t / 1e9 / hbm, 4)})
     skip = ("advance", "consensus", "misc")
     for i, (m, n) in enumerate(scales):
+        if fused and (m, n) == (1, 1):
+            continue
         kinds = [k for k in ms if k not in skip and ms[k][i] > 0]
         t = sum(ms[k][i] for k in kinds) / iters / 1e3
         if t <= 0:

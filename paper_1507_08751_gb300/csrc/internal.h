@@ -167,8 +167,11 @@ cudaError_t configure_kernels();
 cudaError_t launch_scale(const ScaleLaunch& s, const BigWorkspace& ws, cudaStream_t st,
                          Prof* prof, cudaEvent_t after_gram = nullptr);
 
+// R = (1/L)(Y - sum_j W_j); with Z11 (and W11, tau11) given, the 1x1
+// scale's soft threshold and dual update in the same pass.
 cudaError_t launch_consensus(const float* Y, const float* W, float* R, const uint8_t* mask,
-                             int L, size_t MN, cudaStream_t st, Prof* prof = nullptr);
+                             int L, size_t MN, cudaStream_t st, Prof* prof = nullptr,
+                             float* Z11 = nullptr, float* W11 = nullptr, float tau11 = 0.f);
 // X_out = W + R, U_out = Z - W; FP64 ||X - Z||^2 into pres_acc[0] and, with
 // `dual` (X_out holding the previous Z on entry), ||Z - Z_prev||^2 into
 // pres_acc[1].

@@ -11,8 +11,9 @@
 //   row c) with c0 below tau^2 by the factorisation's rounding margin;
 //   otherwise the SVD by one-sided Jacobi (Hestenes): columns p, q of C V
 //   are rotated until every pair is orthogonal to working precision, with
-//   the round-robin pair order of 16 columns (15 rounds of 8 disjoint pairs
-//   per sweep); the singular values are the column norms of C V (no Gram
+//   the round-robin pair order of the block's columns (nn rounded up to
+//   even: nn - 1 rounds of nn / 2 disjoint pairs per sweep); the singular
+//   values are the column norms of C V (no Gram
 //   matrix, so no squared condition number) and the right singular vectors
 //   are the columns of V;
 //   Z' = (C V) diag(f) V^T with f_j = max(1 - tau / sigma_j, 0) (eq:svt),
@@ -139,6 +140,7 @@ blocksvt_warp_kernel(ScaleLaunch a, int nblocks) {
 #pragma unroll
     for (int i = 0; i < 8; ++i) v[i] = (h + 2 * i == c) ? 1.f : 0.f;
     const float inv_fro = 1.f / fro;
+    const int np = (nn + 1) & ~1;  // columns in the rotation order (nn rounded up to even)
     for (; sweeps < kMaxSweeps;) {
       ++sweeps;
       // squared norm of this lane's column of C V: recomputed every sweep,
@@ -149,9 +151,12 @@ blocksvt_warp_kernel(ScaleLaunch a, int nblocks) {
       al += __shfl_xor_sync(kFull, al, 16);
       bool rotated = false;
 #pragma unroll 1
-      for (int rd = 0; rd < 15; ++rd) {
-        // round-robin partner: column 15 stays, the others turn (p + q = 2 rd mod 15)
-        const int o = c == 15 ? rd : (c == rd ? 15 : (2 * rd - c + 15) % 15);
+      for (int rd = 0; rd < np - 1; ++rd) {
+        // round-robin partner among the np (even) columns: column np - 1
+        // stays, the others turn (p + q = 2 rd mod (np - 1)); lanes past np
+        // are their own partners and never rotate
+        const int o = c >= np ? c
+                      : (c == np - 1 ? rd : (c == rd ? np - 1 : (2 * rd - c + np - 1) % (np - 1)));
         const int src = (h << 4) | o;
         const float be = __shfl_sync(kFull, al, src);
         float yo[RPL];
@@ -177,7 +182,7 @@ blocksvt_warp_kernel(ScaleLaunch a, int nblocks) {
         float cr = 1.f, sr = 0.f, t = 0.f;
         // (a column at the rounding level of ||C||_F is numerically zero:
         // no rotation, else an exactly rank-deficient block never settles)
-        if (fminf(a_lo, a_hi) > kTinyCol * fro &&
+        if (o != c && fminf(a_lo, a_hi) > kTinyCol * fro &&
             gn * gn > (kRotTol * kRotTol) * ((a_lo * inv_fro) * (a_hi * inv_fro))) {
           // the angle with tan 2 phi = 2 ga / (a_hi - a_lo), |phi| <= pi / 4,
           // by half angles: cos 2 phi = |D| / q, sin 2 phi = 2 ga sign(D) / q,
@@ -257,10 +262,11 @@ blocksvt_warp_kernel(ScaleLaunch a, int nblocks) {
       if (skipped) atomicAdd(a.cnt, 1ull);
       if (k == 0) atomicAdd(a.cnt + 1, 1ull);
       if (!skipped) atomicAdd(a.cnt + 3, 1ull);
-      // per sweep 15 rounds of 8 column pairs: norms and inner product
-      // (6 mm), the two columns of C V and of V rotated (6 mm + 96); the
-      // rebuild 2 mm nn per kept pair
-      const double fj = (double)sweeps * 15.0 * 8.0 * (12.0 * mm + 96.0) + 2.0 * mm * nn * k;
+      // per sweep np - 1 rounds of np / 2 column pairs: norms and inner
+      // product (6 mm), the two columns of C V and of V rotated (6 mm + 96);
+      // the rebuild 2 mm nn per kept pair
+      const int npr = (nn + 1) & ~1;
+      const double fj = (double)sweeps * (npr - 1) * (npr / 2) * (12.0 * mm + 96.0) + 2.0 * mm * nn * k;
       if (fl > 0.f || fj > 0.0) atomicAdd(a.cnt + 5, (unsigned long long)(fj + fl));
     }
   }

@@ -47,10 +47,22 @@ int ew_grid(size_t n_items) {
 
 static_assert(MSLLR_MAX_SCALES == 8, "consensus dispatch covers 1..8 scales");
 
-template <int LC>  // the scale count, a compile-time constant so that all loads are in flight
+// Soft threshold of eq:bsvt for a 1x1 block and the fused dual update.
+__device__ __forceinline__ void soft_update(float a, float tau, float& z, float& w) {
+  z = copysignf(fmaxf(fabsf(a) - tau, 0.f), a);
+  w = 2.f * z - a;
+}
+
+// R = (1/L)(Y - sum_j W_j), zero at unobserved entries.  With FUSE the
+// 1x1 scale's block SVT runs in the same pass (the scale is element-wise,
+// so the thread that forms R(i) can finish it): A = Z11(i) + R(i),
+// Z11(i) = soft(A), W11(i) = 2 Z11(i) - A.  W11 is one of the W_j summed
+// here; each element is read before the same thread overwrites it.
+template <int LC, bool FUSE>  // the scale count, a compile-time constant so that all loads are in flight
 __global__ void __launch_bounds__(kEwThreads)
-consensus_kernel(const float* __restrict__ Y, const float* __restrict__ W, float* __restrict__ R,
-                 const uint8_t* __restrict__ mask, size_t MN) {
+consensus_kernel(const float* __restrict__ Y, const float* W, float* __restrict__ R,
+                 const uint8_t* __restrict__ mask, size_t MN, float* Z11, float* W11,
+                 float tau11) {
   constexpr int L = LC;
   const float invL = 1.f / (float)L;
   const size_t stride = (size_t)gridDim.x * blockDim.x;
@@ -62,6 +74,8 @@ consensus_kernel(const float* __restrict__ Y, const float* __restrict__ W, float
       float4 w[L];
 #pragma unroll
       for (int j = 0; j < L; ++j) w[j] = reinterpret_cast<const float4*>(W + (size_t)j * MN)[i];
+      float4 z11;
+      if (FUSE) z11 = reinterpret_cast<const float4*>(Z11)[i];
 #pragma unroll
       for (int j = 0; j < L; ++j) {
         acc.x -= w[j].x;
@@ -81,6 +95,15 @@ consensus_kernel(const float* __restrict__ Y, const float* __restrict__ W, float
         if (!mk.w) acc.w = 0.f;
       }
       reinterpret_cast<float4*>(R)[i] = acc;
+      if (FUSE) {
+        float4 zo, wo;
+        soft_update(z11.x + acc.x, tau11, zo.x, wo.x);
+        soft_update(z11.y + acc.y, tau11, zo.y, wo.y);
+        soft_update(z11.z + acc.z, tau11, zo.z, wo.z);
+        soft_update(z11.w + acc.w, tau11, zo.w, wo.w);
+        reinterpret_cast<float4*>(Z11)[i] = zo;
+        reinterpret_cast<float4*>(W11)[i] = wo;
+      }
     }
   } else {
     for (size_t i = i0; i < MN; i += stride) {
@@ -89,6 +112,12 @@ consensus_kernel(const float* __restrict__ Y, const float* __restrict__ W, float
       acc *= invL;
       if (mask && !mask[i]) acc = 0.f;
       R[i] = acc;
+      if (FUSE) {
+        float zo, wo;
+        soft_update(Z11[i] + acc, tau11, zo, wo);
+        Z11[i] = zo;
+        W11[i] = wo;
+      }
     }
   }
 }
@@ -351,14 +380,19 @@ noise_shrink_kernel(const float* A1, const float* __restrict__ A2, float* Zout, 
 }  // namespace
 
 cudaError_t launch_consensus(const float* Y, const float* W, float* R, const uint8_t* mask, int L,
-                             size_t MN, cudaStream_t st, Prof* prof) {
+                             size_t MN, cudaStream_t st, Prof* prof, float* Z11, float* W11,
+                             float tau11) {
   if (prof) prof->scale = 0;
   if (prof) if (cudaError_t e = prof->before(st, KK_CONSENSUS)) return e;
   const int grid = ew_grid((MN + 3) / 4);
+  const bool fuse = Z11 != nullptr;
   switch (L) {
-#define MSLLR_CONSENSUS_CASE(n) \
-  case n:                      \
-    consensus_kernel<n><<<grid, kEwThreads, 0, st>>>(Y, W, R, mask, MN); \
+#define MSLLR_CONSENSUS_CASE(n)                                                                 \
+  case n:                                                                                       \
+    if (fuse)                                                                                   \
+      consensus_kernel<n, true><<<grid, kEwThreads, 0, st>>>(Y, W, R, mask, MN, Z11, W11, tau11); \
+    else                                                                                        \
+      consensus_kernel<n, false><<<grid, kEwThreads, 0, st>>>(Y, W, R, mask, MN, nullptr, nullptr, 0.f); \
     break;
     MSLLR_CONSENSUS_CASE(1)
     MSLLR_CONSENSUS_CASE(2)

@@ -495,7 +495,19 @@ int enqueue_iteration(msllr_ctx* ctx, const Layout& lay, int M, int N, int L, co
                       Prof* prof, int rows = 0) {
   const int jobs = rows ? M / rows : 1;
   CK(launch_advance(ctx->d_table, ctx->d_small, ctx->d_shift, jobs, ctx->stream, prof));
-  CK(launch_consensus(lay.Yd, lay.W, lay.R, lay.mask, L, lay.MN, ctx->stream, prof));
+  // the 1x1 scale is element-wise: outside the statistics iteration it runs
+  // inside the consensus pass (its soft threshold needs nothing but R(i))
+  int e11 = -1;
+  for (int i = 0; i < L && !stats && !p.plain; ++i)
+    if (bm[i] == 1 && bn[i] == 1) {
+      e11 = i;
+      break;
+    }
+  if (e11 >= 0)
+    CK(launch_consensus(lay.Yd, lay.W, lay.R, lay.mask, L, lay.MN, ctx->stream, prof,
+                        lay.Z + (size_t)e11 * lay.MN, lay.W + (size_t)e11 * lay.MN, taus[e11]));
+  else
+    CK(launch_consensus(lay.Yd, lay.W, lay.R, lay.mask, L, lay.MN, ctx->stream, prof));
   if (p.plain) {
     // the comparator: scales one after the other on the context stream, one
     // launch per block
@@ -537,7 +549,7 @@ int enqueue_iteration(msllr_ctx* ctx, const Layout& lay, int M, int N, int L, co
     for (int i = 0; i < L; ++i) {
       const ScalePath path = choose_path(bm[i], bn[i]);
       const bool wide = path == ScalePath::Big || path == ScalePath::Huge;
-      if ((pass == 0) != wide) continue;
+      if ((pass == 0) != wide || i == e11) continue;
       cudaStream_t st = (i == 0 || !fork) ? ctx->stream : (wide ? ctx->side_hi[i] : ctx->side[i]);
       if (i > 0 && fork) CK(cudaStreamWaitEvent(st, ctx->ev_fork, 0));
       if (pass == 1 && fork)
@@ -605,7 +617,8 @@ int enqueue_iteration(msllr_ctx* ctx, const Layout& lay, int M, int N, int L, co
   }
   // join
   if (fork)
-    for (int i = 1; i < L; ++i) CK(cudaStreamWaitEvent(ctx->stream, ctx->ev_join[i], 0));
+    for (int i = 1; i < L; ++i)
+      if (i != e11) CK(cudaStreamWaitEvent(ctx->stream, ctx->ev_join[i], 0));
   return MSLLR_OK;
 }
 
