@@ -111,11 +111,13 @@ struct BlockGeom {
 // shifted grid; with batched jobs, the jobs' block grids one above the other,
 // each job shifted by its own pair and wrapped within its own rows).  The
 // full-matrix scale ignores the shift: SVT commutes with row and column
-// permutations.
-template <class SL>
-__device__ __forceinline__ BlockGeom block_geom(const SL& a, int b) {
+// permutations.  GEN false: the caller promises a single job of 2-D blocks
+// (a.fw == 0, a.rows == 0), and the compiler drops the spatio-temporal and
+// batch index arithmetic from that instantiation.
+template <bool GEN, class SL>
+__device__ __forceinline__ BlockGeom block_geom_t(const SL& a, int b) {
   BlockGeom g;
-  const int rows = a.rows ? a.rows : a.M;
+  const int rows = (GEN && a.rows) ? a.rows : a.M;
   g.M = rows;
   g.N = a.N;
   g.ld = a.ld;
@@ -125,33 +127,29 @@ __device__ __forceinline__ BlockGeom block_geom(const SL& a, int b) {
   g.p = b / nbn;
   g.q = b - g.p * nbn;
   int job = 0;
-  if (a.rows) {
+  if (GEN && a.rows) {
     const int pj = rows / a.m;
     job = g.p / pj;
     g.p -= job * pj;
   }
   g.rbase = job * rows;
+  const int fw = GEN ? a.fw : 0;
   const int* sh = a.shift ? a.shift + 2 * job : nullptr;
-  const bool full = (a.m == rows && a.n == a.N && !a.fw);
+  const bool full = (a.m == rows && a.n == a.N && !fw);
   g.sr = (sh && !full) ? (sh[0] + a.shift_add_r) % rows : 0;
   g.sc = (sh && !full) ? (sh[1] + a.shift_add_c) % a.N : 0;
-  g.fw = a.fw;
-  g.fh = a.fw ? rows / a.fw : 0;
-  g.bw = a.fw ? a.bw : 0;
-  g.bh = a.fw ? a.m / a.bw : 0;
-  g.sy = a.fw ? g.sr / a.fw : 0;
-  g.sx = a.fw ? g.sr - g.sy * a.fw : 0;
+  g.fw = fw;
+  g.fh = fw ? rows / fw : 0;
+  g.bw = fw ? a.bw : 0;
+  g.bh = fw ? a.m / a.bw : 0;
+  g.sy = fw ? g.sr / fw : 0;
+  g.sx = fw ? g.sr - g.sy * fw : 0;
   return g;
 }
 
-// block_geom for kernels instantiated per partition kind: with ST false the
-// launch is a 2-D scale (fw = 0) and the compiler drops the spatio-temporal
-// index arithmetic from the instantiation.
-template <bool ST, class SL>
-__device__ __forceinline__ BlockGeom block_geom_t(const SL& a, int b) {
-  BlockGeom g = block_geom(a, b);
-  if (!ST) g.fw = 0;
-  return g;
+template <class SL>
+__device__ __forceinline__ BlockGeom block_geom(const SL& a, int b) {
+  return block_geom_t<true>(a, b);
 }
 
 // Optional per-phase timing (debug aid, enabled by the MSLLR_PHASE_TIMING

@@ -51,9 +51,6 @@ BigDims big_dims(int M, int N, int m, int n) {
   return d;
 }
 
-__device__ __forceinline__ BlockGeom make_geom(const ScaleLaunch& a, int b) {
-  return block_geom(a, b);
-}
 
 // element (i, c) of C (mm x nn) -> global offset
 __device__ __forceinline__ size_t c_offset(const BlockGeom& g, int i, int c) {
@@ -676,7 +673,7 @@ cudaError_t launch_big(const ScaleLaunch& s, const BigWorkspace& ws, cudaStream_
     if (cudaError_t e_ = prof->after(st)) return e_;
   PROF_BEFORE(KK_GRAM)
   const dim3 ggrid(d.ntiles, d.chunks, d.nblocks);
-  if (s.fw) gram_tiles_kernel<true><<<ggrid, kGramThreads, 0, st>>>(s, ws.G, ws.part, d.chunks);
+  if (s.fw || s.rows) gram_tiles_kernel<true><<<ggrid, kGramThreads, 0, st>>>(s, ws.G, ws.part, d.chunks);
   else gram_tiles_kernel<false><<<ggrid, kGramThreads, 0, st>>>(s, ws.G, ws.part, d.chunks);
   PROF_AFTER()
   if (d.chunks > 1) {
@@ -703,14 +700,14 @@ cudaError_t launch_big(const ScaleLaunch& s, const BigWorkspace& ws, cudaStream_
   const size_t smem = sizeof(float) * ((size_t)rs * d.nn + (size_t)(d.nn + 1) * kKC + (size_t)rs * kKC);
   PROF_BEFORE(KK_REBUILD)
   const dim3 rgrid((d.mm + kRowsPerCta - 1) / kRowsPerCta, d.nblocks);
-  if (s.fw) rebuild_rows_kernel<true><<<rgrid, kRebThreads, 0, st>>>(s, ws.Y, ws.ystride, ws.k);
+  if (s.fw || s.rows) rebuild_rows_kernel<true><<<rgrid, kRebThreads, 0, st>>>(s, ws.Y, ws.ystride, ws.k);
   else rebuild_rows_kernel<false><<<rgrid, kRebThreads, 0, st>>>(s, ws.Y, ws.ystride, ws.k);
   PROF_AFTER()
   PROF_BEFORE(KK_REBUILD)
   const int slab_items = slabs * d.nblocks;
   const int nsm = sm_count();
   const int reb_grid = s.skip_bound ? (slab_items < nsm ? slab_items : nsm) : slab_items;
-  if (s.fw)
+  if (s.fw || s.rows)
     rebuild_kernel<true><<<reb_grid, kRebThreads, smem, st>>>(s, ws.Y, ws.ystride, ws.k, rs, slabs,
                                                              d.nblocks);
   else

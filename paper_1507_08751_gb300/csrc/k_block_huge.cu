@@ -78,9 +78,6 @@ HugeDims huge_dims(int M, int N, int m, int n) {
   return d;
 }
 
-__device__ __forceinline__ BlockGeom huge_geom(const ScaleLaunch& a, int b) {
-  return block_geom(a, b);
-}
 
 __device__ __forceinline__ size_t huge_off(const BlockGeom& g, int i, int c) {
   return g.transposed() ? g.offset(c, i) : g.offset(i, c);
@@ -1047,7 +1044,7 @@ cudaError_t launch_huge(const ScaleLaunch& s, const BigWorkspace& ws, cudaStream
   const float thr = s.tau * s.tau;
   const int B = d.nblocks, nn = d.nn;
   PROF_BEFORE(KK_GRAM)
-  if (s.fw)
+  if (s.fw || s.rows)
     huge_gram_kernel<true><<<dim3(d.ntiles, d.chunks, B), kHThreads, 0, st>>>(s, ws.part, d.chunk_rows,
                                                                       d.chunks, hb);
   else
@@ -1113,7 +1110,7 @@ cudaError_t launch_huge(const ScaleLaunch& s, const BigWorkspace& ws, cudaStream
   huge_final_kernel<<<B, kHThreads, 0, st>>>(s, ws.U, ws.Y, ws.k, nn, hb);
   PROF_AFTER()
   PROF_BEFORE(KK_REBUILD)
-  if (s.fw)
+  if (s.fw || s.rows)
     huge_rebuild_kernel<true><<<dim3((d.mm + kHRebRows - 1) / kHRebRows, B), kHThreads, 0, st>>>(s, ws.Y,
                                                                                          ws.k);
   else

@@ -322,7 +322,7 @@ cudaError_t launch_small_t(const ScaleLaunch& s, cudaStream_t st, Prof* prof) {
   const size_t smem = small_smem_bytes<NT, NMAX>(mm, nn);
   const int nblocks = (s.M / s.m) * (s.N / s.n);
   if (prof) if (cudaError_t e = prof->before(st, KK_FUSED)) return e;
-  if (s.fw) blocksvt_small_kernel<NT, NMAX, true><<<nblocks, NT, smem, st>>>(s);
+  if (s.fw || s.rows) blocksvt_small_kernel<NT, NMAX, true><<<nblocks, NT, smem, st>>>(s);
   else blocksvt_small_kernel<NT, NMAX, false><<<nblocks, NT, smem, st>>>(s);
   if (prof) if (cudaError_t e = prof->after(st)) return e;
   return cudaGetLastError();

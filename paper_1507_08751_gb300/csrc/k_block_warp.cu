@@ -44,8 +44,10 @@ constexpr float kTinyCol = 1e-13f;  // squared norm of a numerically zero column
 constexpr int kMaxSweeps = 12;
 constexpr unsigned kFull = 0xffffffffu;
 
-// RPL: rows of C per lane (mm <= 2 RPL)
-template <int RPL, bool ST>
+// RPL: rows of C per lane (mm <= 2 RPL); NP: columns in the rotation order
+// when fixed at compile time (16 for blocks 15 or 16 wide), 0 to take it
+// from the block
+template <int RPL, bool ST, int NP>
 __global__ void __launch_bounds__(kWT, RPL <= 8 ? 32 : 16)
 blocksvt_warp_kernel(ScaleLaunch a, int nblocks) {
   __shared__ float vsh[kWarps][16][17];  // V of each warp, for the rebuild
@@ -140,7 +142,7 @@ blocksvt_warp_kernel(ScaleLaunch a, int nblocks) {
 #pragma unroll
     for (int i = 0; i < 8; ++i) v[i] = (h + 2 * i == c) ? 1.f : 0.f;
     const float inv_fro = 1.f / fro;
-    const int np = (nn + 1) & ~1;  // columns in the rotation order (nn rounded up to even)
+    const int np = NP ? NP : (nn + 1) & ~1;  // columns in the rotation order (nn rounded up to even)
     for (; sweeps < kMaxSweeps;) {
       ++sweeps;
       // squared norm of this lane's column of C V: recomputed every sweep,
@@ -155,8 +157,12 @@ blocksvt_warp_kernel(ScaleLaunch a, int nblocks) {
         // round-robin partner among the np (even) columns: column np - 1
         // stays, the others turn (p + q = 2 rd mod (np - 1)); lanes past np
         // are their own partners and never rotate
-        const int o = c >= np ? c
-                      : (c == np - 1 ? rd : (c == rd ? np - 1 : (2 * rd - c + np - 1) % (np - 1)));
+        int o = 2 * rd - c;  // in (-(np - 1), 2 (np - 1)): one correction reduces it
+        if (o < 0) o += np - 1;
+        else if (o >= np - 1) o -= np - 1;
+        if (c == rd) o = np - 1;
+        if (c == np - 1) o = rd;
+        if (c >= np) o = c;
         const int src = (h << 4) | o;
         const float be = __shfl_sync(kFull, al, src);
         float yo[RPL];
@@ -285,12 +291,24 @@ cudaError_t launch_warp(const ScaleLaunch& s, cudaStream_t st, Prof* prof) {
   const int grid = (nblocks + kWarps - 1) / kWarps;
   if (prof)
     if (cudaError_t e = prof->before(st, KK_FUSED)) return e;
+  const int nn = s.m < s.n ? s.m : s.n;
+  const bool gen = s.fw || s.rows, w16 = nn >= 15;
   if (mm <= 16) {
-    if (s.fw) blocksvt_warp_kernel<8, true><<<grid, kWT, 0, st>>>(s, nblocks);
-    else blocksvt_warp_kernel<8, false><<<grid, kWT, 0, st>>>(s, nblocks);
+    if (w16) {
+      if (gen) blocksvt_warp_kernel<8, true, 16><<<grid, kWT, 0, st>>>(s, nblocks);
+      else blocksvt_warp_kernel<8, false, 16><<<grid, kWT, 0, st>>>(s, nblocks);
+    } else {
+      if (gen) blocksvt_warp_kernel<8, true, 0><<<grid, kWT, 0, st>>>(s, nblocks);
+      else blocksvt_warp_kernel<8, false, 0><<<grid, kWT, 0, st>>>(s, nblocks);
+    }
   } else {
-    if (s.fw) blocksvt_warp_kernel<16, true><<<grid, kWT, 0, st>>>(s, nblocks);
-    else blocksvt_warp_kernel<16, false><<<grid, kWT, 0, st>>>(s, nblocks);
+    if (w16) {
+      if (gen) blocksvt_warp_kernel<16, true, 16><<<grid, kWT, 0, st>>>(s, nblocks);
+      else blocksvt_warp_kernel<16, false, 16><<<grid, kWT, 0, st>>>(s, nblocks);
+    } else {
+      if (gen) blocksvt_warp_kernel<16, true, 0><<<grid, kWT, 0, st>>>(s, nblocks);
+      else blocksvt_warp_kernel<16, false, 0><<<grid, kWT, 0, st>>>(s, nblocks);
+    }
   }
   if (prof)
     if (cudaError_t e = prof->after(st)) return e;
