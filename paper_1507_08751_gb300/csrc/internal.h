@@ -38,6 +38,8 @@ struct ScaleLaunch {
   int bw;                  // their patch width (patch height m / bw, n frames)
   int rows;                // batched jobs: rows of one job (M = jobs x rows, job j
                            // at rows j rows ..; its shift at shift[2 j]); 0: one job
+  int* err;                // device flag, or null: set non-zero by a kernel whose
+                           // bounded wait on the tensor cores ran out
 };
 
 // rows of one job of a launch (the whole M unless jobs are batched)
@@ -162,6 +164,15 @@ cudaError_t set_phase_buffer_warp(unsigned long long* p);
 
 // Set kernel attributes (dynamic shared memory opt-in) on the current device.
 cudaError_t configure_kernels();
+
+// Gram matrices of wide blocks on the tensor cores (k_gram_tc.cu): eligible
+// shapes (m >= n, 64 < n <= 256), kernel attributes, and the launch, which
+// writes G packed (chunks == 1) or the per-chunk partial sums in the 64 x 64
+// tile layout of the FP32 Gram path (ntiles64 tiles per chunk).
+bool gram_tc_eligible(int m, int n);
+cudaError_t configure_gram_tc();
+cudaError_t launch_gram_tc(const ScaleLaunch& s, float* G, float* part, int chunks, int nblocks,
+                           int ntiles64, cudaStream_t st);
 
 // Launchers (all asynchronous on `st`).  Return cudaGetLastError().
 cudaError_t launch_scale(const ScaleLaunch& s, const BigWorkspace& ws, cudaStream_t st,

@@ -12,6 +12,7 @@
 //      the fused dual update W' = 2 Z' - A of eq:admm (warp per row for
 //      ranks up to 8, row slabs above).
 #include <math.h>
+#include <stdlib.h>
 
 #include "common.cuh"
 #include "internal.h"
@@ -84,19 +85,31 @@ gram_tiles_kernel(ScaleLaunch a, float* __restrict__ G, float* __restrict__ part
   for (int x = 0; x < 4; ++x)
 #pragma unroll
     for (int y = 0; y < 4; ++y) acc[x][y] = 0.f;
+  const bool has2 = a.A2 != nullptr, dg = ta == tc;
+  constexpr int kPer = (32 * kTile) / kGramThreads;
   for (int r0 = r_begin; r0 < r_end; r0 += 32) {
+    // predicated loads, all in flight before the sums are formed
+    float xa[kPer], ya[kPer], xb[kPer], yb[kPer];
 #pragma unroll
-    for (int j = 0; j < (32 * kTile) / kGramThreads; ++j) {
+    for (int j = 0; j < kPer; ++j) {
       const int e = tid + j * kGramThreads;
       const int rr = e / kTile, cc = e - rr * kTile;
       const int i = r0 + rr;
-      float va = 0.f, vb = 0.f;
-      if (i < r_end) {
-        if (a0 + cc < nn) va = load_a(a, c_offset(g, i, a0 + cc));
-        if (c0 + cc < nn) vb = (ta == tc) ? va : load_a(a, c_offset(g, i, c0 + cc));
-      }
+      const bool in = i < r_end, ina = in && a0 + cc < nn, inb = in && !dg && c0 + cc < nn;
+      const size_t oa = c_offset(g, ina ? i : r_begin, ina ? a0 + cc : 0);
+      const size_t ob = c_offset(g, inb ? i : r_begin, inb ? c0 + cc : 0);
+      xa[j] = ina ? __ldg(a.A1 + oa) : 0.f;
+      ya[j] = (ina && has2) ? __ldg(a.A2 + oa) : 0.f;
+      xb[j] = inb ? __ldg(a.A1 + ob) : 0.f;
+      yb[j] = (inb && has2) ? __ldg(a.A2 + ob) : 0.f;
+    }
+#pragma unroll
+    for (int j = 0; j < kPer; ++j) {
+      const int e = tid + j * kGramThreads;
+      const int rr = e / kTile, cc = e - rr * kTile;
+      const float va = xa[j] + ya[j];
       As[rr][cc] = va;
-      Bs[rr][cc] = vb;
+      Bs[rr][cc] = dg ? va : xb[j] + yb[j];
     }
     __syncthreads();
 #pragma unroll 8
@@ -644,8 +657,20 @@ cudaError_t reset_warm_start(const BigWorkspace& w, int M, int N, int m, int n, 
   return cudaMemsetAsync(w.kwarm, 0, sizeof(int) * (size_t)d.nblocks, st);
 }
 
+// The FP32 CUDA-core Gram instead of the tensor-core one (MSLLR_GRAM_FP32=1;
+// for comparisons), read once.
+bool gram_fp32_forced() {
+  static const bool v = [] {
+    const char* e = getenv("MSLLR_GRAM_FP32");
+    return e && e[0] && e[0] != '0';
+  }();
+  return v;
+}
+
 cudaError_t configure_big_kernels() {
   sm_count();  // cache the SM count outside any stream capture
+  gram_fp32_forced();
+  if (cudaError_t e0 = configure_gram_tc()) return e0;
   cudaError_t e = cudaFuncSetAttribute(eig_big_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)eig_smem_bytes(kEigMax));
   if (e != cudaSuccess) return e;
@@ -673,8 +698,14 @@ cudaError_t launch_big(const ScaleLaunch& s, const BigWorkspace& ws, cudaStream_
     if (cudaError_t e_ = prof->after(st)) return e_;
   PROF_BEFORE(KK_GRAM)
   const dim3 ggrid(d.ntiles, d.chunks, d.nblocks);
-  if (s.fw || s.rows) gram_tiles_kernel<true><<<ggrid, kGramThreads, 0, st>>>(s, ws.G, ws.part, d.chunks);
-  else gram_tiles_kernel<false><<<ggrid, kGramThreads, 0, st>>>(s, ws.G, ws.part, d.chunks);
+  if (gram_tc_eligible(s.m, s.n) && !gram_fp32_forced()) {
+    if (cudaError_t e_ = launch_gram_tc(s, ws.G, ws.part, d.chunks, d.nblocks, d.ntiles, st))
+      return e_;
+  } else if (s.fw || s.rows) {
+    gram_tiles_kernel<true><<<ggrid, kGramThreads, 0, st>>>(s, ws.G, ws.part, d.chunks);
+  } else {
+    gram_tiles_kernel<false><<<ggrid, kGramThreads, 0, st>>>(s, ws.G, ws.part, d.chunks);
+  }
   PROF_AFTER()
   if (d.chunks > 1) {
     PROF_BEFORE(KK_GRAM_REDUCE)

@@ -75,7 +75,8 @@ struct msllr_ctx {
   void* io = nullptr;
   size_t io_bytes = 0;
   // small device scalars
-  int* d_small = nullptr;          // [0] iter, [1..2] cur shift, [3] nonfinite flag, [4..5] tmp shift
+  int* d_small = nullptr;          // [0] iter, [1..2] cur shift, [3] nonfinite flag, [4..5] tmp shift,
+                                   // [6] device wait timeout flag
   double* d_acc = nullptr;         // [0..MAX) nuc per scale, [MAX] primal residual^2
   double* d_noise = nullptr;       // [MAX] noise-scale ||A||_F^2 scratch
   unsigned long long* d_cnt = nullptr;  // [2*MAX]
@@ -407,10 +408,16 @@ int msllr_blocksvt(msllr_ctx* ctx, const float* A, float* Z, int M, int N, int l
   s.skip_bound = 1;
   s.rank_out = block_rank_out;
   s.norm_acc = ctx->d_noise;
+  s.err = ctx->d_small + 6;
   BigWorkspace w = carve_big_workspace(ctx->ws, M, N, bm, bn);
+  CK(cudaMemsetAsync(ctx->d_small + 6, 0, sizeof(int), ctx->stream));
   CK(reset_warm_start(w, M, N, bm, bn, ctx->stream));
   CK(launch_scale(s, w, ctx->stream, nullptr));
+  int timed_out = 0;
+  CK(cudaMemcpyAsync(&timed_out, ctx->d_small + 6, sizeof(int), cudaMemcpyDeviceToHost,
+                     ctx->stream));
   CK(cudaStreamSynchronize(ctx->stream));
+  if (timed_out) return fail(ctx, MSLLR_ECUDA, "a tensor-core wait timed out on the device");
   return MSLLR_OK;
 }
 
@@ -528,6 +535,7 @@ int enqueue_iteration(msllr_ctx* ctx, const Layout& lay, int M, int N, int L, co
       s.nuc_acc = stats ? ctx->d_acc + i : nullptr;
       s.cnt = (stats || p.profile) ? ctx->d_cnt + 8 * i : nullptr;
       s.norm_acc = ctx->d_noise + i;
+      s.err = ctx->d_small + 6;
       s.bw = p.st_patch_w ? p.st_patch_w[i] : 0;
       s.fw = s.bw > 0 ? p.frame_w : 0;
       prof->scale = i;
@@ -576,6 +584,7 @@ int enqueue_iteration(msllr_ctx* ctx, const Layout& lay, int M, int N, int L, co
       // block counts: the last iteration, or every iteration of a profiled run
       s.cnt = (stats || p.profile) ? ctx->d_cnt + 8 * i : nullptr;
       s.norm_acc = ctx->d_noise + i;
+      s.err = ctx->d_small + 6;
       s.bw = p.st_patch_w ? p.st_patch_w[i] : 0;
       s.fw = s.bw > 0 ? p.frame_w : 0;
       prof->scale = i;
@@ -732,7 +741,7 @@ int decompose_device(msllr_ctx* ctx, const float* Y, int M, int N, int ld, int L
   }
 
   // inputs: finiteness check, dense copies
-  CK(cudaMemsetAsync(ctx->d_small + 3, 0, sizeof(int), st));
+  CK(cudaMemsetAsync(ctx->d_small + 3, 0, 4 * sizeof(int), st));
   CK(launch_nonfinite(Y, MT, N, ld, ctx->d_small + 3, st, &prof));
   int bad = 0;
   CK(cudaMemcpyAsync(&bad, ctx->d_small + 3, sizeof(int), cudaMemcpyDeviceToHost, st));
@@ -874,7 +883,10 @@ int decompose_device(msllr_ctx* ctx, const float* Y, int M, int N, int ld, int L
   unsigned long long cnt[8 * MSLLR_MAX_SCALES];
   CK(cudaMemcpyAsync(acc, ctx->d_acc, sizeof acc, cudaMemcpyDeviceToHost, st));
   CK(cudaMemcpyAsync(cnt, ctx->d_cnt, sizeof cnt, cudaMemcpyDeviceToHost, st));
+  int timed_out = 0;
+  CK(cudaMemcpyAsync(&timed_out, ctx->d_small + 6, sizeof(int), cudaMemcpyDeviceToHost, st));
   CK(cudaStreamSynchronize(st));
+  if (timed_out) return fail(ctx, MSLLR_ECUDA, "a tensor-core wait timed out on the device");
   if (stats) {
     memset(stats, 0, sizeof(*stats));
     stats->iters = iters;

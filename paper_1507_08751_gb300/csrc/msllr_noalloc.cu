@@ -25,9 +25,11 @@ void* g_scratch_ptr[kMaxDevices] = {};  // device address of g_noalloc_scratch p
 
 // Publishes the shift into the first bytes of the scratch, so the block
 // kernels read it like the shift of any other call.
+// dst[0..1]: the shift; dst[2]: the device wait timeout flag, cleared
 __global__ void set_shift_kernel(int* dst, int sr, int sc) {
   dst[0] = sr;
   dst[1] = sc;
+  dst[2] = 0;
 }
 
 int err(int code, const char* msg) {
@@ -105,10 +107,14 @@ extern "C" int msllr_blocksvt_noalloc(const float* A, float* Z, int M, int N, in
   s.tau = (float)tau;
   s.skip_bound = 1;
   s.rank_out = block_rank_out;
+  s.err = shift + 2;
   const BigWorkspace w = carve_big_workspace((char*)base + 256, M, N, bm, bn);
   cudaError_t e = cudaGetLastError();
   if (e == cudaSuccess) e = launch_scale(s, w, st, nullptr);
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  int timed_out = 0;
+  if (e == cudaSuccess) e = cudaMemcpy(&timed_out, shift + 2, sizeof(int), cudaMemcpyDeviceToHost);
   if (e != cudaSuccess) return err(MSLLR_ECUDA, cudaGetErrorString(e));
+  if (timed_out) return err(MSLLR_ECUDA, "msllr_blocksvt_noalloc: a tensor-core wait timed out");
   return MSLLR_OK;
 }
