@@ -166,10 +166,10 @@ cudaError_t set_phase_buffer_warp(unsigned long long* p);
 cudaError_t configure_kernels();
 
 // Gram matrices of wide blocks on the tensor cores (k_gram_tc.cu): eligible
-// shapes (m >= n, 64 < n <= 256), kernel attributes, and the launch, which
+// launches (m >= n, 64 < n <= 256, fewer than 2^31 elements), kernel attributes, and the launch, which
 // writes G packed (chunks == 1) or the per-chunk partial sums in the 64 x 64
 // tile layout of the FP32 Gram path (ntiles64 tiles per chunk).
-bool gram_tc_eligible(int m, int n);
+bool gram_tc_eligible(const ScaleLaunch& s);
 cudaError_t configure_gram_tc();
 cudaError_t launch_gram_tc(const ScaleLaunch& s, float* G, float* part, int chunks, int nblocks,
                            int ntiles64, cudaStream_t st);

@@ -698,7 +698,7 @@ cudaError_t launch_big(const ScaleLaunch& s, const BigWorkspace& ws, cudaStream_
     if (cudaError_t e_ = prof->after(st)) return e_;
   PROF_BEFORE(KK_GRAM)
   const dim3 ggrid(d.ntiles, d.chunks, d.nblocks);
-  if (gram_tc_eligible(s.m, s.n) && !gram_fp32_forced()) {
+  if (gram_tc_eligible(s) && !gram_fp32_forced()) {
     if (cudaError_t e_ = launch_gram_tc(s, ws.G, ws.part, d.chunks, d.nblocks, d.ntiles, st))
       return e_;
   } else if (s.fw || s.rows) {

@@ -102,7 +102,10 @@ __device__ __forceinline__ size_t c_off(const BlockGeom& g, int i, int c) {
   return g.transposed() ? g.offset(c, i) : g.offset(i, c);
 }
 
-template <bool GEN>
+// GEN: batched jobs or spatio-temporal blocks (block_geom_t); ST:
+// spatio-temporal blocks (generic gather), else 2-D blocks, whose gather
+// needs one row offset per row and one column index per thread.
+template <bool GEN, bool ST>
 __global__ void __launch_bounds__(kGT, 3)
 gram_tc_kernel(ScaleLaunch a, float* __restrict__ G, float* __restrict__ part, int chunks,
                int ntiles64, int* err) {
@@ -147,14 +150,30 @@ gram_tc_kernel(ScaleLaunch a, float* __restrict__ G, float* __restrict__ part, i
   const bool va = ca < nn, vb = !diag && cb < nn;
   const bool has2 = a.A2 != nullptr;
   float xa[8], ya[8], xb[8], yb[8];
+  // 2-D blocks: global columns of the thread's two C columns (Sec. 9 shift,
+  // wrapped) and the unwrapped global row of C's row 0
+  int gca = g.q * g.n + (va ? ca : 0) + g.sc;
+  if (gca >= g.N) gca -= g.N;
+  int gcb = g.q * g.n + (vb ? cb : 0) + g.sc;
+  if (gcb >= g.N) gcb -= g.N;
+  const int grow0 = g.p * g.m + g.sr;
   auto load = [&](int step) {
     const int r0 = r_begin + step * kKS;
 #pragma unroll
     for (int u = 0; u < 8; ++u) {
       const int row = r0 + 4 * (q0 + 2 * (u >> 2)) + (u & 3);
       const bool in = row < r_end;
-      const size_t oa = c_off(g, in ? row : r_begin, va ? ca : 0);
-      const size_t ob = c_off(g, in ? row : r_begin, vb ? cb : 0);
+      uint32_t oa, ob;
+      if constexpr (ST) {
+        oa = (uint32_t)c_off(g, in ? row : r_begin, va ? ca : 0);
+        ob = (uint32_t)c_off(g, in ? row : r_begin, vb ? cb : 0);
+      } else {
+        int gr = grow0 + row;
+        if (gr >= g.M) gr -= g.M;
+        const uint32_t ro = (uint32_t)(g.rbase + gr) * (uint32_t)g.ld;
+        oa = ro + (uint32_t)gca;
+        ob = ro + (uint32_t)gcb;
+      }
       xa[u] = (in && va) ? __ldg(a.A1 + oa) : 0.f;
       ya[u] = (in && va && has2) ? __ldg(a.A2 + oa) : 0.f;
       xb[u] = (in && vb) ? __ldg(a.A1 + ob) : 0.f;
@@ -284,29 +303,37 @@ gram_tc_kernel(ScaleLaunch a, float* __restrict__ G, float* __restrict__ part, i
 
 }  // namespace
 
-bool gram_tc_eligible(int m, int n) {
-  const int nn = m < n ? m : n;
-  return m >= n && nn > 64 && nn <= 2 * kTT;
+bool gram_tc_eligible(const ScaleLaunch& s) {
+  const int nn = s.m < s.n ? s.m : s.n;
+  // element offsets are 32-bit in the kernel
+  return s.m >= s.n && nn > 64 && nn <= 2 * kTT && (size_t)s.M * s.ld < ((size_t)1 << 31);
 }
 
 cudaError_t configure_gram_tc() {
-  cudaError_t e = cudaFuncSetAttribute(gram_tc_kernel<false>,
+  cudaError_t e = cudaFuncSetAttribute(gram_tc_kernel<false, false>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes);
   if (e != cudaSuccess) return e;
-  return cudaFuncSetAttribute(gram_tc_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              kSmemBytes);
+  e = cudaFuncSetAttribute(gram_tc_kernel<true, false>,
+                           cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes);
+  if (e != cudaSuccess) return e;
+  return cudaFuncSetAttribute(gram_tc_kernel<true, true>,
+                              cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes);
 }
 
 cudaError_t launch_gram_tc(const ScaleLaunch& s, float* G, float* part, int chunks, int nblocks,
                            int ntiles64, cudaStream_t st) {
   const int nn = s.m < s.n ? s.m : s.n;
-  if (!gram_tc_eligible(s.m, s.n)) return cudaErrorInvalidValue;
+  if (!gram_tc_eligible(s)) return cudaErrorInvalidValue;
   const int T = (nn + kTT - 1) / kTT;
   const dim3 grid(T * (T + 1) / 2, chunks, nblocks);
-  if (s.fw || s.rows)
-    gram_tc_kernel<true><<<grid, kGT, kSmemBytes, st>>>(s, G, part, chunks, ntiles64, s.err);
+  if (s.fw)
+    gram_tc_kernel<true, true><<<grid, kGT, kSmemBytes, st>>>(s, G, part, chunks, ntiles64, s.err);
+  else if (s.rows)
+    gram_tc_kernel<true, false><<<grid, kGT, kSmemBytes, st>>>(s, G, part, chunks, ntiles64,
+                                                               s.err);
   else
-    gram_tc_kernel<false><<<grid, kGT, kSmemBytes, st>>>(s, G, part, chunks, ntiles64, s.err);
+    gram_tc_kernel<false, false><<<grid, kGT, kSmemBytes, st>>>(s, G, part, chunks, ntiles64,
+                                                                s.err);
   return cudaGetLastError();
 }
 

@@ -473,14 +473,21 @@ def test_stopping_test_ends_the_run_and_matches_the_oracle(ctx):
     assert full["stopped"] == 0 and full["iters"] == 50
 
 
-def test_decompose_spatio_temporal_blocks_matches_oracle(ctx):
+@pytest.mark.parametrize("cube", ["64x64x64", "32x32x128"])
+def test_decompose_spatio_temporal_blocks_matches_oracle(ctx, cube):
     """The video partitions of Sec. 10.2: 4x4x4 and 16x16x16 spatio-temporal
     blocks (pixel patches over runs of frames, reshaped to 16 x 4 and 256 x 16
     matrices) next to the 1x1 and full-matrix scales of a 64x64-pixel,
-    64-frame video, with the random shift moving the video cube, against the
-    oracle's spatio-temporal ADMM on the same shift table."""
+    64-frame video; and 16x16x128 blocks (256 x 128 matrices, the wide-block
+    path with its tensor-core Gram) of a 32x32-pixel, 128-frame video; with
+    the random shift moving the video cube, against the oracle's
+    spatio-temporal ADMM on the same shift table."""
     from paper_1507_08751_gb300 import binding as B
-    Y32, scales, frame = synth.video3d()
+    if cube == "64x64x64":
+        Y32, scales, frame = synth.video3d()
+    else:
+        Y32, scales, frame = synth.video3d(H=32, W=32, T=128, blocks=((4, 4, 4), (16, 16, 128)),
+                                           p_active=0.3)
     M, N = Y32.shape
     lam = [O.lambda_default(M, N, sc[0] * sc[1], sc[2]) if len(sc) == 3
            else O.lambda_default(M, N, *sc) for sc in scales]
