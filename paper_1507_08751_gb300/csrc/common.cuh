@@ -168,16 +168,6 @@ static __device__ unsigned long long* g_phase_acc = nullptr;
     }                                                                          \
   } while (0)
 
-// keeps the maximum of `v` in the accumulator of (slot, phase), count one
-// (debug aid)
-#define PHASE_MAX(slot, p, v)                                                    \
-  do {                                                                           \
-    if (g_phase_acc && (slot) >= 0) {                                            \
-      atomicMax(&g_phase_acc[((slot) * 16 + (p)) * 2], (unsigned long long)(v)); \
-      g_phase_acc[((slot) * 16 + (p)) * 2 + 1] = 1ull;                           \
-    }                                                                            \
-  } while (0)
-
 // adds `v` to the accumulator of (slot, phase) and counts one (debug aid)
 #define PHASE_ADD(slot, p, v)                                                    \
   do {                                                                           \

@@ -250,8 +250,6 @@ eig_big_kernel(ScaleLaunch a, const float* __restrict__ Gall, BigWorkspace ws) {
   float* Qs = panel;
   lz_bind<NT>(z, s.red + 64, NMAX, kLzMaxJ);
   PHASE_INIT();
-  const long long t_block0 = (g_phase_acc && tid == 0) ? clock64() : 0;
-  int J_run = 0;
   LowerPacked Gacc{Gp};
   // G arrives packed (lower triangle, row by row): a straight copy
   auto load_g = [&]() {
@@ -311,7 +309,6 @@ eig_big_kernel(ScaleLaunch a, const float* __restrict__ Gall, BigWorkspace ws) {
                                                         0x1234567u + 977u * job_block(a, b), s, z, panel, &ku,
                                                         &c0, 4, &J);
       fl += fl_lanczos(nn, J, ku);
-      J_run = J;
       PHASE(3, 5);
       if (kk < 0) break;
       fl += fl_deflate(nn, ku);
@@ -342,10 +339,6 @@ eig_big_kernel(ScaleLaunch a, const float* __restrict__ Gall, BigWorkspace ws) {
     }
   }
   if (tid == 0) {
-    // slowest block of the kernel (debug aid): its cycles, Lanczos steps, rank
-    PHASE_MAX(5, 14, clock64() - t_block0);
-    PHASE_MAX(5, 13, J_run);
-    PHASE_MAX(5, 12, k < 0 ? 99 : k);
     if (a.cnt) atomicAdd(a.cnt + 5, (unsigned long long)fl);
     // k < 0: not settled here; eig_fallback_kernel takes the block
     ws.k[b] = k;

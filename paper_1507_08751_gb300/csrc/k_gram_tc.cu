@@ -39,7 +39,9 @@ constexpr int kChunkRows = 256;               // rows of C per partial sum (FP32
 constexpr int kT64 = 64;                      // partial-sum tile of the FP32 path
 constexpr int kTileBytes = kTT * kKS * 4;     // one operand tile, h or l: 8 KB
 constexpr int kStageBytes = 4 * kTileBytes;   // A h, A l, B h, B l
-constexpr int kSmemBytes = 2 * kStageBytes + 64;
+constexpr int kDLd = kTT + 1;                 // row stride of the staged accumulator
+constexpr int kBodyBytes = (2 * kStageBytes > kTT * kDLd * 4) ? 2 * kStageBytes : kTT * kDLd * 4;
+constexpr int kSmemBytes = kBodyBytes + 64;
 constexpr uint32_t kTmemCols = 128;
 constexpr int kWaitPolls = 1 << 20;
 
@@ -119,8 +121,8 @@ gram_tc_kernel(ScaleLaunch a, float* __restrict__ G, float* __restrict__ part, i
   const int r_end = min(mm, r_begin + kChunkRows);
   const int nsteps = (r_end - r_begin + kKS - 1) / kKS;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  uint64_t* bar = reinterpret_cast<uint64_t*>(smem + 2 * kStageBytes);
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(smem + 2 * kStageBytes + 32);
+  uint64_t* bar = reinterpret_cast<uint64_t*>(smem + kBodyBytes);
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(smem + kBodyBytes + 32);
   const uint32_t sbase = smem_u32(smem);
   const uint32_t bar0 = smem_u32(bar);
 
@@ -243,21 +245,14 @@ gram_tc_kernel(ScaleLaunch a, float* __restrict__ G, float* __restrict__ part, i
   }
   ok = __syncthreads_and(ok);
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  // the accumulator goes through shared memory (the operand buffers are
+  // free now; row stride kTT + 1 keeps both passes free of bank conflicts),
+  // so that the global writes are warp-wide row segments
+  float* Ds = reinterpret_cast<float*>(smem);
   if (ok) {
     const int x = 32 * (warp & 3) + lane;  // row of the tile (TMEM lane)
     const int ycol = 64 * (warp >> 2);      // first column of this warp
-    const int i = ti * kTT + x;
     const uint32_t taddr = tmem + ((uint32_t)(32 * (warp & 3)) << 16) + (uint32_t)ycol;
-    float* dstp = nullptr;
-    if (chunks > 1) {
-      const int a64 = 2 * ti + (x >> 6), c64 = 2 * tj + (warp >> 2);
-      const int T64 = (nn + kT64 - 1) / kT64;
-      if (c64 <= a64 && a64 < T64)
-        dstp = part + (((size_t)b * chunks + chunk) * ntiles64 + (a64 * (a64 + 1)) / 2 + c64) *
-                          (kT64 * kT64) +
-               (size_t)(x & 63) * kT64;
-    }
-    float* Grow = G + (size_t)b * nn * nn + (size_t)i * (i + 1) / 2;
 #pragma unroll
     for (int c = 0; c < 64; c += 16) {
       uint32_t v[16];
@@ -274,24 +269,38 @@ gram_tc_kernel(ScaleLaunch a, float* __restrict__ G, float* __restrict__ part, i
                      "+r"(v[12]), "+r"(v[13]), "+r"(v[14]), "+r"(v[15])
                    :
                    : "memory");
-      if (chunks > 1) {
-        if (dstp) {
 #pragma unroll
-          for (int e = 0; e < 16; e += 4)
-            *reinterpret_cast<float4*>(dstp + c + e) =
-                make_float4(__uint_as_float(v[e]), __uint_as_float(v[e + 1]),
-                            __uint_as_float(v[e + 2]), __uint_as_float(v[e + 3]));
-        }
-      } else if (i < nn) {
-#pragma unroll
-        for (int e = 0; e < 16; ++e) {
-          const int j = tj * kTT + ycol + c + e;
-          if (j <= i) Grow[j] = __uint_as_float(v[e]);
-        }
-      }
+      for (int e = 0; e < 16; ++e) Ds[x * kDLd + ycol + c + e] = __uint_as_float(v[e]);
     }
   } else if (tid == 0 && err) {
     atomicOr(err, 1);
+  }
+  __syncthreads();
+  if (ok) {
+    if (chunks > 1) {
+      // partial sums: the valid 64 x 64 tiles of this 128 x 128 tile, row by row
+      const int T64 = (nn + kT64 - 1) / kT64;
+      for (int xr = warp; xr < 2 * kTT; xr += kGT / 32) {
+        const int x = xr >> 1, hc = xr & 1;
+        const int a64 = 2 * ti + (x >> 6), c64 = 2 * tj + hc;
+        if (c64 > a64 || a64 >= T64) continue;
+        float* dst = part +
+                     (((size_t)b * chunks + chunk) * ntiles64 + (a64 * (a64 + 1)) / 2 + c64) *
+                         (kT64 * kT64) +
+                     (size_t)(x & 63) * kT64;
+        dst[lane] = Ds[x * kDLd + hc * kT64 + lane];
+        dst[lane + 32] = Ds[x * kDLd + hc * kT64 + lane + 32];
+      }
+    } else {
+      // packed lower triangle: row i's columns tj 128 .. min(i, tj 128 + 127)
+      for (int x = warp; x < kTT; x += kGT / 32) {
+        const int i = ti * kTT + x;
+        if (i >= nn) break;
+        const int cnt = min(i - tj * kTT + 1, kTT);
+        float* Grow = G + (size_t)b * nn * nn + (size_t)i * (i + 1) / 2 + tj * kTT;
+        for (int y = lane; y < cnt; y += 32) Grow[y] = Ds[x * kDLd + y];
+      }
+    }
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();

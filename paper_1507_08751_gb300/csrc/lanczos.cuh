@@ -22,7 +22,6 @@
 #pragma once
 
 #include <float.h>
-#include <stdint.h>
 
 #include <type_traits>
 
@@ -121,17 +120,15 @@ __device__ void symv_rows(S G, int n, const float* x, float* y) {
     // packed storage: warp w takes rows 32 (w & 7) + lane and half (w >> 3)
     // of the columns.  All lanes of a warp walk the same column c, so the
     // loads T(r) + c (c <= r) and T(c) + r (c > r), T(i) = i (i + 1) / 2,
-    // hit distinct banks, and x[c .. c + 3] is one broadcast float4 (when x
-    // is 16-byte aligned).  Left of the warp's row band the row part is
-    // contiguous, right of it the column part advances by c + 1; only the 32
-    // columns of the band need both forms.
+    // hit distinct banks, and x[c] is a broadcast.  Left of the warp's row
+    // band the row part is contiguous, right of it the column part advances
+    // by c + 1; only the 32 columns of the band need both forms.
     const float* g = G.g;
     const int lane = tid & 31, warp = tid >> 5;
     const int b0 = 32 * (warp & 7), half = warp >> 3;
     const int r = b0 + lane;
     const int cs = (n + 1) >> 1;
     const int c_lo = half ? cs : 0, c_hi = half ? n : cs;
-    const bool xv4 = (reinterpret_cast<uintptr_t>(x) & 15) == 0;
     float acc = 0.f;
     if (b0 < n) {
       const int rr = r < n ? r : n - 1;  // lanes past n compute a dummy row
@@ -140,16 +137,6 @@ __device__ void symv_rows(S G, int n, const float* x, float* y) {
       float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f;
       int c = c_lo;
       const int e1 = min(c_hi, b0);
-      if (xv4) {
-        for (; c < e1 && (c & 3); ++c) a0 = fmaf(ABS ? fabsf(g[tr + c]) : g[tr + c], x[c], a0);
-        for (; c + 3 < e1; c += 4) {
-          const float4 xq = *reinterpret_cast<const float4*>(x + c);
-          a0 = fmaf(ABS ? fabsf(g[tr + c]) : g[tr + c], xq.x, a0);
-          a1 = fmaf(ABS ? fabsf(g[tr + c + 1]) : g[tr + c + 1], xq.y, a1);
-          a2 = fmaf(ABS ? fabsf(g[tr + c + 2]) : g[tr + c + 2], xq.z, a2);
-          a3 = fmaf(ABS ? fabsf(g[tr + c + 3]) : g[tr + c + 3], xq.w, a3);
-        }
-      }
       for (; c + 3 < e1; c += 4) {
         a0 = fmaf(ABS ? fabsf(g[tr + c]) : g[tr + c], x[c], a0);
         a1 = fmaf(ABS ? fabsf(g[tr + c + 1]) : g[tr + c + 1], x[c + 1], a1);
@@ -163,23 +150,6 @@ __device__ void symv_rows(S G, int n, const float* x, float* y) {
         a1 = fmaf(ABS ? fabsf(g[idx]) : g[idx], x[c], a1);
       }
       int idx = (c * (c + 1)) / 2 + rr;
-      if (xv4) {
-        for (; c < c_hi && (c & 3); ++c) {
-          a0 = fmaf(ABS ? fabsf(g[idx]) : g[idx], x[c], a0);
-          idx += c + 1;
-        }
-        for (; c + 3 < c_hi; c += 4) {
-          const float4 xq = *reinterpret_cast<const float4*>(x + c);
-          const int i1 = idx + c + 1;
-          const int i2 = i1 + c + 2;
-          const int i3 = i2 + c + 3;
-          a0 = fmaf(ABS ? fabsf(g[idx]) : g[idx], xq.x, a0);
-          a1 = fmaf(ABS ? fabsf(g[i1]) : g[i1], xq.y, a1);
-          a2 = fmaf(ABS ? fabsf(g[i2]) : g[i2], xq.z, a2);
-          a3 = fmaf(ABS ? fabsf(g[i3]) : g[i3], xq.w, a3);
-          idx = i3 + c + 4;
-        }
-      }
       for (; c + 3 < c_hi; c += 4) {
         const int i1 = idx + c + 1;
         const int i2 = i1 + c + 2;
@@ -240,66 +210,6 @@ __device__ void symv_rows(S G, int n, const float* x, float* y) {
 // products.  Same row split as symv_rows; ends with a CTA barrier.
 template <int NT, int NMAX, class S>
 __device__ void symm_rows8(S G, int n, const float* X, float* Yo) {
-  if constexpr (std::is_same<S, LowerPacked>::value && NT == 512) {
-    // packed storage: the column walk of symv_rows (rows 32 (w & 7) + lane,
-    // column half w >> 3), X's row c one broadcast pair of float4
-    const float* g = G.g;
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int b0 = 32 * (warp & 7), half = warp >> 3;
-    const int r = b0 + lane;
-    const int cs = (n + 1) >> 1;
-    const int c_lo = half ? cs : 0, c_hi = half ? n : cs;
-    float acc[8];
-#pragma unroll
-    for (int q = 0; q < 8; ++q) acc[q] = 0.f;
-    auto step = [&](float gv, int c) {
-      const float4 x0 = *reinterpret_cast<const float4*>(X + c * 8);
-      const float4 x1 = *reinterpret_cast<const float4*>(X + c * 8 + 4);
-      acc[0] = fmaf(gv, x0.x, acc[0]);
-      acc[1] = fmaf(gv, x0.y, acc[1]);
-      acc[2] = fmaf(gv, x0.z, acc[2]);
-      acc[3] = fmaf(gv, x0.w, acc[3]);
-      acc[4] = fmaf(gv, x1.x, acc[4]);
-      acc[5] = fmaf(gv, x1.y, acc[5]);
-      acc[6] = fmaf(gv, x1.z, acc[6]);
-      acc[7] = fmaf(gv, x1.w, acc[7]);
-    };
-    if (b0 < n) {
-      const int rr = r < n ? r : n - 1;
-      const int tr = (rr * (rr + 1)) / 2;
-      int c = c_lo;
-      const int e1 = min(c_hi, b0);
-      for (; c < e1; ++c) step(g[tr + c], c);
-      const int e2 = min(c_hi, b0 + 32);
-      for (; c < e2; ++c) step(g[c <= rr ? tr + c : (c * (c + 1)) / 2 + rr], c);
-      int idx = (c * (c + 1)) / 2 + rr;
-      for (; c < c_hi; ++c) {
-        step(g[idx], c);
-        idx += c + 1;
-      }
-    }
-    if (half && r < n) {
-      *reinterpret_cast<float4*>(Yo + r * 8) = make_float4(acc[0], acc[1], acc[2], acc[3]);
-      *reinterpret_cast<float4*>(Yo + r * 8 + 4) = make_float4(acc[4], acc[5], acc[6], acc[7]);
-    }
-    __syncthreads();
-    if (!half && r < n) {
-      float4 y0 = *reinterpret_cast<float4*>(Yo + r * 8);
-      float4 y1 = *reinterpret_cast<float4*>(Yo + r * 8 + 4);
-      y0.x += acc[0];
-      y0.y += acc[1];
-      y0.z += acc[2];
-      y0.w += acc[3];
-      y1.x += acc[4];
-      y1.y += acc[5];
-      y1.z += acc[6];
-      y1.w += acc[7];
-      *reinterpret_cast<float4*>(Yo + r * 8) = y0;
-      *reinterpret_cast<float4*>(Yo + r * 8 + 4) = y1;
-    }
-    __syncthreads();
-    return;
-  }
   constexpr int TPR = (NT / NMAX >= 2) ? 2 : 1;
   const int tid = threadIdx.x, p = tid % TPR;
   for (int r0 = 0; r0 < n; r0 += NT / TPR) {

@@ -141,16 +141,8 @@ __device__ bool regchol_pd(SX src, int n, float c0, bool frob, const float* U, c
     c = c0 - (float)n8 * (float)n8 * FLT_EPSILON * (c0 + fx);
   }
   if (!(c > 0.f)) return false;
-  // failure flag of the shuffle form of the diagonal factor (only the warps
-  // that solve rows factor the block there)
-  volatile int* fail = reinterpret_cast<volatile int*>(red);
-  if (tid == 0) *fail = 0;
   __syncthreads();
   PHASE_INIT();
-  // per-panel phases (debug aid): strip hand-off, diagonal factor, row
-  // solve, trailing update; the wide kernel's two calls (slots 3 and 4)
-  // record them under slots 5 and 6
-  const int pslot = (slot == 3 || slot == 4) ? slot + 2 : -1;
   if (tid < 8) S[tid * n8 + tid] += c;
 #pragma unroll
   for (int s = 0; s < SL; ++s)
@@ -175,7 +167,6 @@ __device__ bool regchol_pd(SX src, int n, float c0, bool frob, const float* U, c
         }
     }
     __syncthreads();
-    PHASE(pslot, 0);
     // 8x8 diagonal block into this warp's packed copy Lw (lower triangle,
     // the diagonal replaced by the reciprocal pivots).  Every warp factors
     // it; rsqrt (a few ulp) instead of sqrt and a division keeps the chain
@@ -209,10 +200,8 @@ __device__ bool regchol_pd(SX src, int n, float c0, bool frob, const float* U, c
 #pragma unroll
         for (int e = 0; e < 36; ++e) Lw[e] = L[e];
       }
-    } else if (warp == 0 || 32 * warp < n8 - j0 - 8) {
-      // lane l < 8 holds row l (fewer registers, shuffles on the chain);
-      // only the warps with rows to solve below the block (and warp 0, which
-      // reports a failure) factor it
+    } else {
+      // lane l < 8 holds row l (fewer registers, shuffles on the chain)
       float row[8];
 #pragma unroll
       for (int t = 0; t < 8; ++t) row[t] = (lane < 8 && t <= lane) ? Sb[t * n8 + j0 + lane] : 0.f;
@@ -230,7 +219,7 @@ __device__ bool regchol_pd(SX src, int n, float c0, bool frob, const float* U, c
           if (lane >= t) row[t] = fmaf(-row[j], ltj, row[t]);
         }
       }
-      if (!ok && warp == 0 && lane == 0) *fail = 1;
+      if (!ok) return false;
       if (lane < 8) {
         const int base = lane * (lane + 1) / 2;
 #pragma unroll
@@ -240,7 +229,6 @@ __device__ bool regchol_pd(SX src, int n, float c0, bool frob, const float* U, c
       }
     }
     __syncwarp();
-    PHASE(pslot, 1);
     // rows below the block: L21 = A21 L11^{-T}
     for (int r = j0 + 8 + tid; r < n8; r += NT) {
       float x[8];
@@ -255,9 +243,6 @@ __device__ bool regchol_pd(SX src, int n, float c0, bool frob, const float* U, c
       for (int t = 0; t < 8; ++t) Sb[t * n8 + r] = x[t];
     }
     __syncthreads();
-    if constexpr (!REGF)
-      if (*fail) return false;
-    PHASE(pslot, 2);
     // trailing rank-8 update of the active tiles (column >= j0 + 8)
     const int bmin = 2 * p + 2;
 #pragma unroll
@@ -276,7 +261,6 @@ __device__ bool regchol_pd(SX src, int n, float c0, bool frob, const float* U, c
           for (int j = 0; j < 4; ++j) v[s][i * 4 + j] = fmaf(-av[i], bv[j], v[s][i * 4 + j]);
       }
     }
-    PHASE(pslot, 3);
   }
   PHASE(slot, 15);
   return true;
