@@ -61,20 +61,27 @@ blocksvt_warp_kernel(ScaleLaunch a, int nblocks) {
   const bool tr = g.transposed();
   const bool col = c < nn;
 
-  // gather (all loads in flight at once); ||C||_F^2
+  // gather (all loads in flight at once: predicated, the two halves of A
+  // added after the last load); ||C||_F^2
   float x[RPL];
   float fro = 0.f;
+  {
+    const bool has2 = a.A2 != nullptr;
+    float y[RPL];
 #pragma unroll
-  for (int i = 0; i < RPL; ++i) {
-    const int r = h + 2 * i;
-    float v = 0.f;
-    if (col && r < mm) {
-      const size_t off = tr ? g.offset(c, r) : g.offset(r, c);
-      v = a.A1[off];
-      if (a.A2) v += a.A2[off];
+    for (int i = 0; i < RPL; ++i) {
+      const int r = h + 2 * i;
+      const bool in = col && r < mm;
+      const int rr = in ? r : 0, cc = in ? c : 0;
+      const size_t off = tr ? g.offset(cc, rr) : g.offset(rr, cc);
+      x[i] = in ? __ldg(a.A1 + off) : 0.f;
+      y[i] = (in && has2) ? __ldg(a.A2 + off) : 0.f;
     }
-    x[i] = v;
-    fro = fmaf(v, v, fro);
+#pragma unroll
+    for (int i = 0; i < RPL; ++i) {
+      x[i] += y[i];
+      fro = fmaf(x[i], x[i], fro);
+    }
   }
   fro = warp_sum(fro);
   PHASE(0, 0);
