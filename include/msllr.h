@@ -377,8 +377,8 @@ int msllr_wait(msllr_ctx* ctx, uint64_t job_id, int timeout_ms);
  * none) fails with MSLLR_EINVAL and a message giving the size.
  *
  * The first call on a device does a one-time set-up on that device (it
- * looks up the scratch's device address and sets kernel attributes); make
- * that first call before any stream capture.  Every call shares the one
+ * looks up the scratch's device address and sets kernel attributes).
+ * Every call shares the one
  * scratch array and leaves its contents behind: calls that overlap on the
  * GPU (other host threads, other streams) race and must be serialised by
  * the caller.  Errors: EINVAL, ECUDA; the message is available from

@@ -110,10 +110,11 @@ extern "C" int msllr_blocksvt_noalloc(const float* A, float* Z, int M, int N, in
   s.err = shift + 2;
   const BigWorkspace w = carve_big_workspace((char*)base + 256, M, N, bm, bn);
   cudaError_t e = cudaGetLastError();
-  if (e == cudaSuccess) e = launch_scale(s, w, st, nullptr);
-  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
   int timed_out = 0;
-  if (e == cudaSuccess) e = cudaMemcpy(&timed_out, shift + 2, sizeof(int), cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess) e = launch_scale(s, w, st, nullptr);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(&timed_out, shift + 2, sizeof(int), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
   if (e != cudaSuccess) return err(MSLLR_ECUDA, cudaGetErrorString(e));
   if (timed_out) return err(MSLLR_ECUDA, "msllr_blocksvt_noalloc: a tensor-core wait timed out");
   return MSLLR_OK;
