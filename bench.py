@@ -49,6 +49,9 @@ def parse():
                     help="skip timing the plain one-launch-per-block comparator")
     ap.add_argument("--spin-grid", type=int, default=0,
                     help="averaged cycle spinning (Sec. 9) over a g x g shift lattice per scale")
+    ap.add_argument("--nested", type=int, default=None, choices=[0, 1],
+                    help="cross-scale tile fusion of nested narrow scales (library default "
+                         "when not given)")
     ap.add_argument("--serve-jobs", type=int, default=24)
     ap.add_argument("--serve-rate", type=float, default=50.0)
     ap.add_argument("--batch-jobs", type=int, default=64)
@@ -416,12 +419,18 @@ def ours(a):
     X = torch.empty((L, M, N), dtype=torch.float32, device=dev)
     torch.cuda.synchronize()
 
-    def step(params=None):
-        if params is None and a.spin_grid > 1:
+    def with_opts(params):
+        if params is None and (a.spin_grid > 1 or a.nested is not None):
             params = B.msllr_params_default()
         if params is not None:
             params.spin_grid = a.spin_grid
-        return ctx.msllr_decompose(Yd, scales, X, iters=a.iters, seed=SEED, params=params)
+            if a.nested is not None:
+                params.nested = a.nested
+        return params
+
+    def step(params=None):
+        return ctx.msllr_decompose(Yd, scales, X, iters=a.iters, seed=SEED,
+                                   params=with_opts(params))
 
     for _ in range(a.warmup):
         stats = step()
@@ -493,10 +502,7 @@ def ours(a):
     # end to end through the host API: pinned host Y in, X out, copies timed
     Yh = torch.from_numpy(Y32).pin_memory()
     Xh = torch.empty((L, M, N), dtype=torch.float32).pin_memory()
-    hp = None
-    if a.spin_grid > 1:
-        hp = B.msllr_params_default()
-        hp.spin_grid = a.spin_grid
+    hp = with_opts(None)
     ctx.msllr_decompose_host(Yh, scales, Xh, iters=a.iters, seed=SEED, params=hp)
     e_steps = max(1, min(a.steps, 3))
     t0 = time.perf_counter()
@@ -543,7 +549,8 @@ def ours(a):
                        "scales": [f"{m}x{n}" for m, n in scales], "iters_per_job": a.iters,
                        "parallelism": f"replicas{world}", "step": "one decomposition job",
                        "l2": f"ADMM state {2 * L + 1} x {4 * M * N / 1e6:.1f} MB"
-                             f" = {(2 * L + 1) * 4 * M * N / 1e6:.0f} MB vs 126 MB L2"},
+                             f" = {(2 * L + 1) * 4 * M * N / 1e6:.0f} MB vs 126 MB L2",
+                       **({"nested": a.nested} if a.nested is not None else {})},
             "blocks_per_s": round(value * nblocks, 1),
             "e2e": e2e,
             "gpu_launches": int(launches_per_step * a.steps),

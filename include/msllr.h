@@ -133,6 +133,17 @@ typedef struct msllr_params {
                           s_r mod frame_w) pixels and s_c frames.  Needs
                           frame_w > 0 with bh | H, bw | frame_w, bt | N;
                           not with spin_grid > 1.  0 or NULL: 2-D blocks.  */
+  int nested;          /* cross-scale tile fusion.  1: a narrow scale whose
+                          blocks nest inside the blocks of a 33-64-wide
+                          square scale (e.g. 16 x 16 inside 64 x 64) is
+                          solved in the same kernel: one CTA per coarse
+                          block reads the residual R once into shared memory
+                          and solves the fine blocks inside it, then the
+                          coarse block (the shift is shared, Sec. 9).  The
+                          results equal the separate kernels' bit for bit.
+                          Applies to 2-D blocks of single jobs with
+                          spin_grid <= 1; other scales run as usual.
+                          Default 0.                                       */
 } msllr_params;
 
 /* Per-run diagnostics, taken at the last iteration; when params->profile is

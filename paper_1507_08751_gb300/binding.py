@@ -67,6 +67,7 @@ class Params(ctypes.Structure):
         ("stop_every", ctypes.c_int),
         ("frame_w", ctypes.c_int),
         ("st_patch_w", ctypes.c_void_p),
+        ("nested", ctypes.c_int),
     ]
 
 

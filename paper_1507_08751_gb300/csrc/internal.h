@@ -170,6 +170,16 @@ cudaError_t configure_kernels();
 // writes G packed (chunks == 1) or the per-chunk partial sums in the 64 x 64
 // tile layout of the FP32 Gram path (ntiles64 tiles per chunk).
 bool gram_tc_eligible(const ScaleLaunch& s);
+
+// Cross-scale tile fusion (k_nested.cu): whether fine blocks fm x fn (warp
+// path) nest in coarse blocks cm x cn (64-wide CTA path) for one kernel, its
+// attributes, and the launch of both scales' block SVTs (same shift, 2-D
+// blocks, one job, the same A2 = R).
+bool nested_pair(int fm, int fn, int cm, int cn);
+cudaError_t configure_nested();
+struct Prof;
+cudaError_t launch_nested(const ScaleLaunch& fine, const ScaleLaunch& coarse, cudaStream_t st,
+                          Prof* prof);
 cudaError_t configure_gram_tc();
 cudaError_t launch_gram_tc(const ScaleLaunch& s, float* G, float* part, int chunks, int nblocks,
                            int ntiles64, cudaStream_t st);

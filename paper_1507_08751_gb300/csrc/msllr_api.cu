@@ -553,6 +553,45 @@ int enqueue_iteration(msllr_ctx* ctx, const Layout& lay, int M, int N, int L, co
   // scales' Gram phase is over; the eigen CTAs then claim SMs first and the
   // narrow-block kernels fill the rest.
   bool gated[MSLLR_MAX_SCALES] = {};
+  // cross-scale tile fusion (params.nested): coarse scale i solves the
+  // blocks of fine scale nest_of[i] in the same kernel (one read of R)
+  int nest_of[MSLLR_MAX_SCALES], absorbed[MSLLR_MAX_SCALES] = {};
+  for (int i = 0; i < L; ++i) nest_of[i] = -1;
+  if (p.nested && !rows && p.spin_grid <= 1 && !p.st_patch_w)
+    for (int i = 0; i < L; ++i)
+      for (int j = 0; j < L && nest_of[i] < 0; ++j)
+        if (j != i && j != e11 && i != e11 && !absorbed[j] && nest_of[j] < 0 &&
+            !absorbed[i] && !(bm[i] == M && bn[i] == N) &&
+            nested_pair(bm[j], bn[j], bm[i], bn[i])) {
+          nest_of[i] = j;
+          absorbed[j] = 1;
+        }
+  auto scale_launch = [&](int i, const std::vector<std::pair<int, int>>& offs) {
+    ScaleLaunch s{};
+    s.A1 = lay.Z + (size_t)i * lay.MN;
+    s.A2 = lay.R;
+    s.Zout = lay.Z + (size_t)i * lay.MN;
+    s.Wout = lay.W + (size_t)i * lay.MN;
+    s.M = M;
+    s.N = N;
+    s.ld = N;
+    s.m = bm[i];
+    s.n = bn[i];
+    s.shift = (p.cycle_spin || offs.size() > 1) ? ctx->d_shift : nullptr;
+    s.rows = rows;
+    s.tau = taus[i];
+    s.skip_bound = p.skip_bound;
+    s.warm_start = 1;
+    s.rank_out = nullptr;
+    s.nuc_acc = stats ? ctx->d_acc + i : nullptr;
+    // block counts: the last iteration, or every iteration of a profiled run
+    s.cnt = (stats || p.profile) ? ctx->d_cnt + 8 * i : nullptr;
+    s.norm_acc = ctx->d_noise + i;
+    s.err = ctx->d_small + 6;
+    s.bw = p.st_patch_w ? p.st_patch_w[i] : 0;
+    s.fw = s.bw > 0 ? p.frame_w : 0;
+    return s;
+  };
   for (int pass = 0; pass < 2; ++pass) {
     for (int i = 0; i < L; ++i) {
       const ScalePath path = choose_path(bm[i], bn[i]);
@@ -564,33 +603,19 @@ int enqueue_iteration(msllr_ctx* ctx, const Layout& lay, int M, int N, int L, co
         for (int j = 0; j < L; ++j)
           if (gated[j]) CK(cudaStreamWaitEvent(st, ctx->ev_gate[j], 0));
       const auto offs = spin_offsets(rows ? rows : M, N, bm[i], bn[i], p.spin_grid);
-      ScaleLaunch s{};
-      s.A1 = lay.Z + (size_t)i * lay.MN;
-      s.A2 = lay.R;
-      s.Zout = lay.Z + (size_t)i * lay.MN;
-      s.Wout = lay.W + (size_t)i * lay.MN;
-      s.M = M;
-      s.N = N;
-      s.ld = N;
-      s.m = bm[i];
-      s.n = bn[i];
-      s.shift = (p.cycle_spin || offs.size() > 1) ? ctx->d_shift : nullptr;
-      s.rows = rows;
-      s.tau = taus[i];
-      s.skip_bound = p.skip_bound;
-      s.warm_start = 1;
-      s.rank_out = nullptr;
-      s.nuc_acc = stats ? ctx->d_acc + i : nullptr;
-      // block counts: the last iteration, or every iteration of a profiled run
-      s.cnt = (stats || p.profile) ? ctx->d_cnt + 8 * i : nullptr;
-      s.norm_acc = ctx->d_noise + i;
-      s.err = ctx->d_small + 6;
-      s.bw = p.st_patch_w ? p.st_patch_w[i] : 0;
-      s.fw = s.bw > 0 ? p.frame_w : 0;
+      const ScaleLaunch s = scale_launch(i, offs);
       prof->scale = i;
       const bool gate = fork && wide && i > 0;
       // one block SVT, or the average over the scale's shift set
       auto run_scale = [&]() -> int {
+        if (absorbed[i]) return MSLLR_OK;  // solved inside its coarse scale's kernel
+        if (nest_of[i] >= 0) {
+          const int j = nest_of[i];
+          const ScaleLaunch sf =
+              scale_launch(j, spin_offsets(rows ? rows : M, N, bm[j], bn[j], p.spin_grid));
+          CK(launch_nested(sf, s, st, prof));
+          return MSLLR_OK;
+        }
         if (offs.size() == 1) {
           CK(launch_scale(s, lay.big[i], st, prof, gate ? ctx->ev_gate[i] : nullptr));
           return MSLLR_OK;

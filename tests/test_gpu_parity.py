@@ -584,3 +584,39 @@ def test_batched_jobs_equal_their_solo_runs_and_the_oracle(ctx):
         ctx.msllr_decompose_batch(Yb, [(1, 1), (0, 0)], torch.empty((2, 2, 64, 64), device="cuda"),
                                   [1, 2], iters=1)
     assert e.value.code == B.MSLLR_EINVAL
+
+
+@pytest.mark.parametrize("shape,scales", [
+    ((1024, 256), [(1, 1), (16, 16), (64, 64), (256, 256), (1024, 256)]),
+    ((512, 384), [(1, 1), (4, 4), (8, 8), (64, 64), (512, 384)]),
+])
+def test_nested_scales_equal_separate_kernels_bit_for_bit(ctx, shape, scales):
+    """Cross-scale tile fusion (params.nested): the fine narrow scale solved
+    inside its coarse scale's kernel (one read of R per coarse block) gives
+    the separate kernels' X and Z bit for bit, over iterations with random
+    shifts, and both match the oracle."""
+    from paper_1507_08751_gb300 import binding as B
+    M, N = shape
+    rng = np.random.default_rng(91)
+    Y = 0.3 * rng.standard_normal((M, N))
+    for m, n in scales[1:-1]:
+        for p in range(M // m):
+            for q in range(N // n):
+                if rng.random() < 0.05:
+                    Y[p * m:(p + 1) * m, q * n:(q + 1) * n] += 2.0 * np.outer(
+                        rng.standard_normal(m), rng.standard_normal(n)) / np.sqrt(m)
+    Y32 = Y.astype(np.float32)
+    lam = [O.lambda_default(M, N, m, n) for m, n in scales]
+    iters, seed = 12, 17
+    outs = []
+    for nested in (0, 1):
+        p = B.msllr_params_default()
+        p.nested = nested
+        X, Z, stats = _run_decompose(ctx, Y32, scales, lam, iters, seed, params=p)
+        outs.append((X, Z, stats))
+    np.testing.assert_array_equal(outs[0][0], outs[1][0])
+    np.testing.assert_array_equal(outs[0][1], outs[1][1])
+    assert list(outs[0][2]["blocks_zero"]) == list(outs[1][2]["blocks_zero"])
+    ref = O.admm(Y32.astype(np.float64), scales, lam, 1.0, iters,
+                 shifts=O.shift_table(seed, iters, M, N))
+    assert np.all(O.relerr(outs[1][0], ref["X"], Y32) <= TOL)
