@@ -33,7 +33,8 @@ SEED = 1507087510
 METRIC = "BlockSVT-ADMM iter/s (video 16384x256, L=5, 300 iters/job)"
 # Batching/serving-shaped jobs (dyadic scales 1, 4, 16, 64, 256 and the full
 # matrix): their full-matrix scale goes through the wide-block path.
-JOBS = {"job1024": (1024, 1024, 200), "job2048": (2048, 2048, 200), "job4096x512": (4096, 512, 200)}
+JOBS = {"job1024": (1024, 1024, 200), "job2048": (2048, 2048, 200), "job4096x512": (4096, 512, 200),
+        "precision8192": (8192, 8192, 200)}
 
 
 def parse():
@@ -407,7 +408,10 @@ def ours(a):
         Mj, Nj, it_j = JOBS[a.workload]
         if a.iters == ITERS_DEF:
             a.iters = it_j
-        Y32, scales = synth.job(replica_seed(rank), Mj, Nj, 6)
+        if a.workload == "precision8192":
+            Y32, scales = synth.precision(replica_seed(rank), Mj, Nj)
+        else:
+            Y32, scales = synth.job(replica_seed(rank), Mj, Nj, 6)
         metric = f"BlockSVT-ADMM iter/s ({a.workload}: {Mj}x{Nj}, L={len(scales)}, {a.iters} iters/job)"
         workload = f"{a.workload}-L{len(scales)}-s" + "_".join(str(m) for m, _ in scales[:-1]) + "_full"
     ITERS_OF["cur"] = a.iters

@@ -60,7 +60,7 @@ typedef enum msllr_status {
  * by one CTA each; wider ones (e.g. the full-matrix scale of a 1024 x 1024
  * matrix) by certified subspace iteration spread over many CTAs, where a
  * block's thresholded rank is at most 16. */
-#define MSLLR_MAX_BLOCK_WIDTH 4096
+#define MSLLR_MAX_BLOCK_WIDTH 8192
 
 typedef struct msllr_ctx msllr_ctx;
 

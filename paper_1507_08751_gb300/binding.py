@@ -25,7 +25,7 @@ MSLLR_ETIMEOUT = 4
 MSLLR_ENONFINITE = 5
 MSLLR_EBUSY = 6
 MAX_SCALES = 8
-MAX_BLOCK_WIDTH = 4096
+MAX_BLOCK_WIDTH = 8192
 NOISE_SCALE = (0, 0)  # block size of the noise scale (Sec. 2.1)
 KERNEL_KINDS = ("advance", "consensus", "soft1x1", "fused_small", "gram", "gram_reduce",
                 "eig_big", "rebuild", "misc", "eig_fallback", "subspace", "certificate")

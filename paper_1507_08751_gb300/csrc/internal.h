@@ -166,7 +166,7 @@ cudaError_t set_phase_buffer_warp(unsigned long long* p);
 cudaError_t configure_kernels();
 
 // Gram matrices of wide blocks on the tensor cores (k_gram_tc.cu): eligible
-// launches (m >= n, 64 < n <= 256, fewer than 2^31 elements), kernel attributes, and the launch, which
+// launches (m >= n, n > 64, fewer than 2^31 elements), kernel attributes, and the launch, which
 // writes G packed (chunks == 1) or the per-chunk partial sums in the 64 x 64
 // tile layout of the FP32 Gram path (ntiles64 tiles per chunk).
 bool gram_tc_eligible(const ScaleLaunch& s);
@@ -181,8 +181,12 @@ struct Prof;
 cudaError_t launch_nested(const ScaleLaunch& fine, const ScaleLaunch& coarse, cudaStream_t st,
                           Prof* prof);
 cudaError_t configure_gram_tc();
+// chunk_rows: rows of C per partial sum; to_part: write the partial sums
+// even for one chunk (the wide path above 256 reduces them itself)
 cudaError_t launch_gram_tc(const ScaleLaunch& s, float* G, float* part, int chunks, int nblocks,
-                           int ntiles64, cudaStream_t st);
+                           int ntiles64, int chunk_rows, int to_part, cudaStream_t st);
+// MSLLR_GRAM_FP32=1: the FP32 CUDA-core Gram kernels instead (comparisons)
+bool gram_fp32_forced();
 
 // Launchers (all asynchronous on `st`).  Return cudaGetLastError().
 cudaError_t launch_scale(const ScaleLaunch& s, const BigWorkspace& ws, cudaStream_t st,

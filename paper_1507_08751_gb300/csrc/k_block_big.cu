@@ -699,7 +699,8 @@ cudaError_t launch_big(const ScaleLaunch& s, const BigWorkspace& ws, cudaStream_
   PROF_BEFORE(KK_GRAM)
   const dim3 ggrid(d.ntiles, d.chunks, d.nblocks);
   if (gram_tc_eligible(s) && !gram_fp32_forced()) {
-    if (cudaError_t e_ = launch_gram_tc(s, ws.G, ws.part, d.chunks, d.nblocks, d.ntiles, st))
+    if (cudaError_t e_ = launch_gram_tc(s, ws.G, ws.part, d.chunks, d.nblocks, d.ntiles, kChunk,
+                                        0, st))
       return e_;
   } else if (s.fw || s.rows) {
     gram_tiles_kernel<true><<<ggrid, kGramThreads, 0, st>>>(s, ws.G, ws.part, d.chunks);

@@ -1044,7 +1044,13 @@ cudaError_t launch_huge(const ScaleLaunch& s, const BigWorkspace& ws, cudaStream
   const float thr = s.tau * s.tau;
   const int B = d.nblocks, nn = d.nn;
   PROF_BEFORE(KK_GRAM)
-  if (s.fw || s.rows)
+  if (gram_tc_eligible(s) && !gram_fp32_forced()) {
+    // tensor-core Gram (k_gram_tc.cu), partial sums in the same 64 x 64 tile
+    // layout and chunks, reduced below
+    if (cudaError_t e_ = launch_gram_tc(s, nullptr, ws.part, d.chunks, B, d.ntiles, d.chunk_rows,
+                                        1, st))
+      return e_;
+  } else if (s.fw || s.rows)
     huge_gram_kernel<true><<<dim3(d.ntiles, d.chunks, B), kHThreads, 0, st>>>(s, ws.part, d.chunk_rows,
                                                                       d.chunks, hb);
   else

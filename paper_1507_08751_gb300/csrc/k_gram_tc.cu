@@ -35,7 +35,6 @@ namespace {
 constexpr int kTT = 128;                      // output tile (MMA M = N = 128)
 constexpr int kKS = 16;                       // rows of C per pipeline stage
 constexpr int kGT = 256;                      // threads per CTA
-constexpr int kChunkRows = 256;               // rows of C per partial sum (FP32 path's chunks)
 constexpr int kT64 = 64;                      // partial-sum tile of the FP32 path
 constexpr int kTileBytes = kTT * kKS * 4;     // one operand tile, h or l: 8 KB
 constexpr int kStageBytes = 4 * kTileBytes;   // A h, A l, B h, B l
@@ -110,15 +109,19 @@ __device__ __forceinline__ size_t c_off(const BlockGeom& g, int i, int c) {
 template <bool GEN, bool ST>
 __global__ void __launch_bounds__(kGT, 3)
 gram_tc_kernel(ScaleLaunch a, float* __restrict__ G, float* __restrict__ part, int chunks,
-               int ntiles64, int* err) {
+               int ntiles64, int chunk_rows, int to_part, int* err) {
   extern __shared__ __align__(1024) unsigned char smem[];
   const int t = blockIdx.x, chunk = blockIdx.y, b = blockIdx.z;
-  const int ti = t == 0 ? 0 : 1, tj = t == 2 ? 1 : 0;  // tiles (0,0), (1,0), (1,1)
+  // tile (ti, tj), ti >= tj, of the lower triangle: t = ti (ti + 1) / 2 + tj
+  int ti = (int)((sqrtf(8.f * (float)t + 1.f) - 1.f) * 0.5f);
+  while (((ti + 1) * (ti + 2)) / 2 <= t) ++ti;
+  while ((ti * (ti + 1)) / 2 > t) --ti;
+  const int tj = t - (ti * (ti + 1)) / 2;
   const bool diag = ti == tj;
   const BlockGeom g = block_geom_t<GEN>(a, b);
   const int mm = g.mm(), nn = g.nn();
-  const int r_begin = chunk * kChunkRows;
-  const int r_end = min(mm, r_begin + kChunkRows);
+  const int r_begin = chunk * chunk_rows;
+  const int r_end = min(mm, r_begin + chunk_rows);
   const int nsteps = (r_end - r_begin + kKS - 1) / kKS;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   uint64_t* bar = reinterpret_cast<uint64_t*>(smem + kBodyBytes);
@@ -277,7 +280,7 @@ gram_tc_kernel(ScaleLaunch a, float* __restrict__ G, float* __restrict__ part, i
   }
   __syncthreads();
   if (ok) {
-    if (chunks > 1) {
+    if (chunks > 1 || to_part) {
       // partial sums: the valid 64 x 64 tiles of this 128 x 128 tile, row by row
       const int T64 = (nn + kT64 - 1) / kT64;
       for (int xr = warp; xr < 2 * kTT; xr += kGT / 32) {
@@ -315,7 +318,7 @@ gram_tc_kernel(ScaleLaunch a, float* __restrict__ G, float* __restrict__ part, i
 bool gram_tc_eligible(const ScaleLaunch& s) {
   const int nn = s.m < s.n ? s.m : s.n;
   // element offsets are 32-bit in the kernel
-  return s.m >= s.n && nn > 64 && nn <= 2 * kTT && (size_t)s.M * s.ld < ((size_t)1 << 31);
+  return s.m >= s.n && nn > 64 && (size_t)s.M * s.ld < ((size_t)1 << 31);
 }
 
 cudaError_t configure_gram_tc() {
@@ -330,19 +333,20 @@ cudaError_t configure_gram_tc() {
 }
 
 cudaError_t launch_gram_tc(const ScaleLaunch& s, float* G, float* part, int chunks, int nblocks,
-                           int ntiles64, cudaStream_t st) {
+                           int ntiles64, int chunk_rows, int to_part, cudaStream_t st) {
   const int nn = s.m < s.n ? s.m : s.n;
   if (!gram_tc_eligible(s)) return cudaErrorInvalidValue;
   const int T = (nn + kTT - 1) / kTT;
   const dim3 grid(T * (T + 1) / 2, chunks, nblocks);
   if (s.fw)
-    gram_tc_kernel<true, true><<<grid, kGT, kSmemBytes, st>>>(s, G, part, chunks, ntiles64, s.err);
+    gram_tc_kernel<true, true><<<grid, kGT, kSmemBytes, st>>>(s, G, part, chunks, ntiles64,
+                                                              chunk_rows, to_part, s.err);
   else if (s.rows)
     gram_tc_kernel<true, false><<<grid, kGT, kSmemBytes, st>>>(s, G, part, chunks, ntiles64,
-                                                               s.err);
+                                                               chunk_rows, to_part, s.err);
   else
     gram_tc_kernel<false, false><<<grid, kGT, kSmemBytes, st>>>(s, G, part, chunks, ntiles64,
-                                                                s.err);
+                                                                chunk_rows, to_part, s.err);
   return cudaGetLastError();
 }
 

@@ -152,3 +152,41 @@ def hanning_blobs(seed=BASE_SEED + 2, M=64, N=64, scales=((1, 1), (4, 4), (16, 1
             p, q = divmod(int(b), bn)
             comps[i, p * m:(p + 1) * m, q * n:(q + 1) * n] = sign[t] * amps[i] * np.outer(hm, hn)
     return comps.sum(axis=0), comps, list(scales)
+
+
+def _logspread_blocks(rng, M, N, m, n, p_active, rank=2, lo=1e-2, hi=1e2):
+    """Component of one block scale: each m x n block is active with
+    probability p_active and then holds sum_j s_j u_j v_j^T over ``rank``
+    unit vectors u_j, v_j (normalised Gaussians) with s_j log-uniform in
+    [lo, hi].  Vectorised over the active blocks."""
+    X = np.zeros((M, N), dtype=np.float32)
+    bm, bn = M // m, N // n
+    act = np.nonzero(rng.random((bm, bn)) < p_active)
+    k = act[0].size
+    if k == 0:
+        return X
+    u = rng.standard_normal((k, m, rank))
+    v = rng.standard_normal((k, n, rank))
+    u /= np.linalg.norm(u, axis=1, keepdims=True)
+    v /= np.linalg.norm(v, axis=1, keepdims=True)
+    s = 10.0 ** rng.uniform(np.log10(lo), np.log10(hi), size=(k, rank))
+    blocks = np.einsum("kmr,kr,knr->kmn", u, s, v).astype(np.float32)
+    view = X.reshape(bm, m, bn, n)
+    view[act[0], :, act[1], :] = blocks
+    return X
+
+
+def precision(seed=BASE_SEED + 5, M=8192, N=8192, p_active=0.05, p_sparse=0.02):
+    """The single large precision job: M x N with six scales 1x1, 8x8, 32x32,
+    128x128, 1024x1024 and the full matrix.  Each block of the four middle
+    scales is active with probability ``p_active`` and then rank 2 with
+    singular values log-uniform in [1e-2, 1e2], so that some sit near their
+    scale's threshold; the full matrix holds one such rank-2 term and the
+    1x1 scale ``p_sparse`` N(0,1) entries.  Returns (Y float32, scales)."""
+    rng = np.random.default_rng(seed)
+    scales = [(1, 1), (8, 8), (32, 32), (128, 128), (1024, 1024), (M, N)]
+    Y = ((rng.random((M, N)) < p_sparse) * rng.standard_normal((M, N))).astype(np.float32)
+    for (m, n) in scales[1:-1]:
+        Y += _logspread_blocks(rng, M, N, m, n, p_active)
+    Y += _logspread_blocks(rng, M, N, M, N, 1.0)
+    return Y, scales

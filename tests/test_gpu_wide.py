@@ -201,3 +201,50 @@ def test_decompose_masked_ratings_full_scale_matches_oracle(ctx):
                  shifts=O.shift_table(seed, iters, M, N), mask=mask.astype(bool))
     err = O.relerr(X, ref["X"], Y32)
     assert np.all(err <= TOL), err
+
+
+def test_full_matrix_svt_8192_closed_form(ctx):
+    """The widest full-matrix scale (8192 x 8192): for A = U diag(s) V^T with
+    orthonormal U, V the block SVT is U diag(max(s - tau, 0)) V^T exactly
+    (eq:svt); the GPU result matches it, with its rank, under a shift (the
+    full matrix ignores it)."""
+    M = N = 8192
+    rng = np.random.default_rng(81)
+    U, _ = np.linalg.qr(rng.standard_normal((M, 4)))
+    V, _ = np.linalg.qr(rng.standard_normal((N, 4)))
+    s = np.array([80.0, 40.0, 12.0, 3.0])
+    tau = 10.0
+    Ud = torch.from_numpy(U).cuda()
+    Vd = torch.from_numpy(V).cuda()
+    A = ((Ud * torch.from_numpy(s).cuda()) @ Vd.T).float().contiguous()
+    want = (Ud * torch.from_numpy(np.maximum(s - tau, 0.0)).cuda()) @ Vd.T
+    Z = torch.empty_like(A)
+    rank = torch.empty((1,), dtype=torch.int32, device="cuda")
+    ctx.msllr_blocksvt(A, Z, M, N, tau, (123, 4567), rank_out=rank)
+    torch.cuda.synchronize()
+    err = (torch.linalg.norm(Z.double() - want) / torch.linalg.norm(want)).item()
+    assert err <= TOL, f"relative error {err:.3e}"
+    assert int(rank.item()) == 3
+
+
+def test_precision_workload_8192_matches_oracle(ctx):
+    """The 8192 x 8192 job with six scales (1x1, 8x8, 32x32, 128x128,
+    1024x1024, the full matrix; rank-2 blocks with singular values spread
+    over [1e-2, 1e2]): two cycle-spun ADMM iterations from zero against the
+    FP64 oracle on the same shift table, every X_i and Z_i to 1e-4."""
+    Y32, scales = synth.precision()
+    M, N = Y32.shape
+    lam = [O.lambda_default(M, N, m, n) for m, n in scales]
+    iters, seed = 2, 29
+    X = torch.empty((len(scales), M, N), dtype=torch.float32, device="cuda")
+    Z = torch.empty_like(X)
+    ctx.msllr_decompose(dev(Y32), scales, X, lambdas=lam, iters=iters, seed=seed, Z_out=Z)
+    torch.cuda.synchronize()
+    Xh, Zh = X.cpu().numpy(), Z.cpu().numpy()
+    del X, Z
+    ref = O.admm(Y32.astype(np.float64), scales, lam, 1.0, iters,
+                 shifts=O.shift_table(seed, iters, M, N))
+    ex = O.relerr(Xh, ref["X"], Y32)
+    ez = O.relerr(Zh, ref["Z"], Y32)
+    assert np.all(ex <= TOL), ex
+    assert np.all(ez <= TOL), ez
