@@ -766,24 +766,30 @@ huge_chol_panel_kernel(float* __restrict__ H, int nn, int j, HugeBlock* __restri
     Ld[x][y] = v;
   }
   __syncthreads();
-  bool bad = false;
+  // the 64 x 64 diagonal factor, column by column (Crout form, Golub & Van
+  // Loan Sec. 4.2): thread (r, part) = (tid / 4, tid mod 4) forms a quarter
+  // of row r's inner product with row c, the four quarters are added by
+  // shuffles inside the warp; two CTA barriers per column
+  __shared__ int bad_s;
+  if (tid == 0) bad_s = 0;
+  const int r = tid >> 2, part = tid & 3;
   for (int c = 0; c < kHT; ++c) {
-    const float d = Ld[c][c];
-    if (!(d > 0.f) || !isfinite(d)) {
-      bad = true;
-      break;
+    float sdot = 0.f;
+    if (r >= c)
+      for (int k = part; k < c; k += 4) sdot = fmaf(Ld[r][k], Ld[c][k], sdot);
+    sdot += __shfl_xor_sync(0xffffffffu, sdot, 1);
+    sdot += __shfl_xor_sync(0xffffffffu, sdot, 2);
+    const float t = r >= c ? Ld[r][c] - sdot : 0.f;
+    if (r == c && part == 0) {
+      const bool ok = t > 0.f && isfinite(t);
+      if (!ok) bad_s = 1;
+      Ld[c][c] = sqrtf(ok ? t : 1.f);
     }
-    const float rc = sqrtf(d);
     __syncthreads();
-    for (int r = c + 1 + tid; r < kHT; r += kHThreads) Ld[r][c] /= rc;
-    if (tid == 0) Ld[c][c] = rc;
-    __syncthreads();
-    for (int e = tid; e < kHT * kHT; e += kHThreads) {
-      const int r = e / kHT, l = e - r * kHT;
-      if (l > c && l <= r) Ld[r][l] = fmaf(-Ld[r][c], Ld[l][c], Ld[r][l]);
-    }
+    if (r > c && part == 0) Ld[r][c] = t / Ld[c][c];
     __syncthreads();
   }
+  const bool bad = bad_s != 0;
   if (bad) {
     if (blockIdx.x == 0 && tid == 0) hb[b].chol_fail = 1;
     return;
@@ -797,12 +803,18 @@ huge_chol_panel_kernel(float* __restrict__ H, int nn, int j, HugeBlock* __restri
     Xs[x][y] = (gi < nn && gj < nn) ? Hb[(size_t)gi * nn + gj] : 0.f;
   }
   __syncthreads();
-  if (tid < kHT) {
-    const int x = tid;
+  {
+    // rows of X L^T = A: thread (x, part) = (tid / 4, tid mod 4) forms a
+    // quarter of each inner product, the row's four threads (one warp) add
+    // them by shuffles; no CTA barrier between columns
+    const int x = tid >> 2;
     for (int c = 0; c < kHT; ++c) {
-      float v = Xs[x][c];
-      for (int l = 0; l < c; ++l) v = fmaf(-Xs[x][l], Ld[c][l], v);
-      Xs[x][c] = v / Ld[c][c];
+      float sdot = 0.f;
+      for (int l = part; l < c; l += 4) sdot = fmaf(Xs[x][l], Ld[c][l], sdot);
+      sdot += __shfl_xor_sync(0xffffffffu, sdot, 1);
+      sdot += __shfl_xor_sync(0xffffffffu, sdot, 2);
+      if (part == 0) Xs[x][c] = (Xs[x][c] - sdot) / Ld[c][c];
+      __syncwarp();
     }
   }
   __syncthreads();
