@@ -467,10 +467,10 @@ def ours(a):
     roof, best = kernel_roofline(pstats, scales, M, N, pk)
     per_scale = scale_rooflines(pstats, scales, M, N, a.iters, pk)
     t_iter = t_s / (a.steps * a.iters)
-    b_survey, b_layout = (4 * L + 1) * 4 * M * N, (5 * L + 3) * 4 * M * N
+    b_state, b_layout = (4 * L + 1) * 4 * M * N, (5 * L + 3) * 4 * M * N
     iteration = {"us": round(t_iter * 1e6, 2),
-                 "bytes_state_form": b_survey, "bytes_this_layout": b_layout,
-                 "hbm_frac_state_form": round(b_survey / t_iter / 1e9 / pk["hbm_gbs"], 4),
+                 "bytes_state_form": b_state, "bytes_this_layout": b_layout,
+                 "hbm_frac_state_form": round(b_state / t_iter / 1e9 / pk["hbm_gbs"], 4),
                  "hbm_frac_this_layout": round(b_layout / t_iter / 1e9 / pk["hbm_gbs"], 4)}
     if roof is not None:
         roof["per_scale"] = per_scale
