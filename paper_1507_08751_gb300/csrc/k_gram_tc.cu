@@ -12,7 +12,8 @@
 // of l (below 2^-21 |x|): FP32-level accuracy at tensor-core rates.
 //
 // Work split: one CTA per (128 x 128 tile of the lower triangle of G, chunk
-// of rows of C, block).  Per stage of 16 rows of C the 256 threads load the
+// of rows of C, block); blocks up to 256 wide (two tile rows) and the wide
+// path's blocks above 256 alike.  Per stage of 16 rows of C the 256 threads load the
 // tile's two column ranges of A = A1 + A2 (cycle-spun gather, coalesced
 // 128-byte row segments), split them and store h and l in the canonical
 // K-major layout without swizzle; one thread issues the MMAs for the stage
@@ -21,7 +22,8 @@
 // run under the MMAs of stage s).  The epilogue reads the accumulator with
 // tcgen05.ld (warp w: TMEM lanes 32 (w mod 4) .., columns 64 (w / 4) ..) and
 // writes the packed lower triangle of G, or a partial sum per row chunk in
-// the 64 x 64 tile layout of the FP32 Gram path (same reduction kernel).
+// the 64 x 64 tile layout of the FP32 Gram kernels (reduced by the same
+// kernels: packed for blocks up to 256 wide, a full square above).
 //
 // Every wait is bounded: a wait that runs out sets the launch's error flag,
 // the CTA skips its output, frees its TMEM and returns.
