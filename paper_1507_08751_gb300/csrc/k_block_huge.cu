@@ -1083,7 +1083,7 @@ cudaError_t launch_huge(const ScaleLaunch& s, const BigWorkspace& ws, cudaStream
   // blocks whose Ritz residuals are still large
   const bool full = (s.m == launch_rows(s) && s.n == s.N);
   const bool warm = s.warm_start && (full || !s.shift);
-  const int rounds[3] = {warm ? 2 : 6, 6, 12};
+  const int rounds[3] = {warm ? 2 : 6, 4, 8};
   const dim3 gv_grid((nn + kHGvRows - 1) / kHGvRows, B);
   const int orth_chunks = (nn + kHOrthRows - 1) / kHOrthRows;
   for (int r = 0; r < 3; ++r) {
